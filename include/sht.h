@@ -1,0 +1,160 @@
+/*
+ * sht.h -- C ABI of the GB300 IDBF associated-Legendre / spherical-harmonic
+ * transform library (libsht.so).
+ *
+ * Method: Bremer, Chen & Yang, "Rapid Application of the Spherical Harmonic
+ * Transform via Interpolative Decomposition Butterfly Factorization",
+ * arXiv:2004.11346.  Section, equation and algorithm numbers below refer to it.
+ *
+ * Conventions for every entry point
+ *  - N is the transform order: degrees k = 0..2N-1, orders |m| <= 2N-1,
+ *    2N Gauss-Legendre nodes x_0 < ... < x_{2N-1} in x = cos(theta) and
+ *    M = 4N-1 equispaced phi_j = 2 pi (j + 1/2) / M (Sec. 1, the grid).
+ *  - Pbar_k^m is L2-normalised on [-1, 1] with no Condon-Shortley phase.
+ *  - Complex numbers are interleaved (re, im) doubles.
+ *  - Orders are stored in the sequence m = 0, 1, -1, 2, -2, ..., 2N-1, -(2N-1).
+ *      coefficients beta : per field 4N^2 complex; for each order the degrees
+ *                          k = |m|..2N-1 are contiguous (first coefficient of
+ *                          order m > 0 at 2N(2m-1) - m(m-1); of -m right after
+ *                          the 2N-m coefficients of +m).
+ *      ALT values g      : per field (4N-1) x 2N complex; row = order in the
+ *                          sequence above, column = node index l (ascending x).
+ *      grid values f     : per field 2N x (4N-1) complex, theta-major.
+ *    F fields are stored one after another (field stride = the per-field size).
+ *  - Data pointers are DEVICE pointers owned by the caller, unless the entry
+ *    point says otherwise.  Inputs are never modified.  Outputs must not
+ *    overlap inputs.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream: the return value reports
+ *    argument and launch errors; errors detected by the device are latched in
+ *    the plan and returned by the next call or by sht_sync().
+ *  - No entry point falls back to the CPU: without a usable CUDA device the
+ *    library returns SHT_ERR_CUDA.
+ */
+#ifndef SHT_H_
+#define SHT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sht_plan_s* sht_plan_t;
+
+typedef enum {
+  SHT_OK = 0,
+  SHT_ERR_ARG = 1,      /* invalid argument (N, eps, m, F, NULL pointer...) */
+  SHT_ERR_OOM = 2,      /* host or device allocation failed                 */
+  SHT_ERR_CUDA = 3,     /* CUDA runtime error or no device                  */
+  SHT_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up               */
+  SHT_ERR_NUMERIC = 5,  /* precomputation failed to reach the tolerance     */
+  SHT_ERR_IO = 6,       /* plan file missing, truncated or corrupt          */
+  SHT_ERR_UNSUPPORTED = 7
+} sht_status;
+
+typedef enum {
+  SHT_FP64 = 0,        /* factors and arithmetic in FP64                        */
+  SHT_FP32 = 1,        /* factors and arithmetic in FP32 (FP64 I/O)             */
+  SHT_MIXED = 2        /* tensor-core block products, FP64 turning-point blocks */
+} sht_precision;
+
+/* Plan options (Sec. 2.1, 2.3, 3.2, 3.3 and Sec. 5's parameter choices). */
+typedef struct {
+  double eps;          /* ID / rSVD truncation tolerance, absolute on the scale
+                          of the largest matrix entry (Sec. 2.1)               */
+  int n0;              /* partition stops once a turning-point block has fewer
+                          than n0 rows or columns (Sec. 3.2)                   */
+  int n_leaf;          /* IDBF leaf size: depth L = floor(log2(min dim/n_leaf)) */
+  int r_k;             /* adaptive-rank bound of the ID (Sec. 2.1)              */
+  double oversample;   /* t: the ID samples t * r_k rows (Sec. 2.1)             */
+  int rsvd_r;          /* initial rank of the randomized SVD (Sec. 5: 30)       */
+  int rsvd_q;          /* its oversampling factor q (Sec. 2.3: 2)               */
+  double trim_delta;   /* entries below trim_delta are negligible (Sec. 3.3)    */
+  int sampling;        /* 0 = mock-Chebyshev rows, 1 = random rows (Sec. 2.1)   */
+  int precision;       /* sht_precision                                          */
+  int max_fields;      /* workspace sized for this many fields per call          */
+  int flags;           /* SHT_FLAG_* bits                                        */
+  uint64_t seed;       /* seed of the randomized choices                         */
+} sht_opts;
+
+/* sht_opts.flags */
+#define SHT_FLAG_FORCE_FACTOR 1 /* keep factored blocks even when larger than dense */
+#define SHT_FLAG_HOST_ONLY 2    /* build the program on the host only: no device
+                                   upload; apply calls return SHT_ERR_UNSUPPORTED */
+
+/* Plan statistics (Sec. 5 experiments: block counts, ranks, timings). */
+typedef struct {
+  int N;
+  double eps;
+  int64_t n_units;           /* orders |m| = 0..2N-1                            */
+  int64_t n_ops;             /* dense block products in the apply program       */
+  int64_t n_blocks_idbf, n_blocks_lowrank, n_blocks_dense, n_blocks_dropped;
+  int64_t entries_idbf, entries_lowrank, entries_dense; /* stored factor entries */
+  int64_t entries_total;
+  int64_t entries_matrix;    /* entries of the unfactored parity matrices       */
+  int64_t max_rank;          /* largest ID / rSVD rank                          */
+  int64_t max_phases;
+  int64_t workspace_bytes;
+  int64_t factor_bytes;      /* bytes of the factor store in the plan precision */
+  double t_factor_s;         /* wall time of the precomputation                 */
+  double t_upload_s;         /* wall time of the host->device upload             */
+  int threads;               /* host threads used by the precomputation         */
+} sht_plan_info;
+
+/* Defaults for order N and tolerance eps (n0, n_leaf scaled with N). */
+void sht_opts_default(int N, double eps, sht_opts* out);
+
+/* Build the plan (Sec. 3.2-3.3): Gauss-Legendre rule, Legendre matrices by the
+ * three-term recurrence with an extended exponent, block partition along the
+ * turning-point curve (Eq. new5, Eq. nb), IDBF of oscillatory blocks (Sec. 2.2),
+ * randomized SVD of trimmed non-oscillatory blocks (Alg. 1), trimmed dense
+ * turning-point blocks; then upload the packed factors to the current device.
+ * N >= 1, eps in (0, 1).  opts may be NULL (defaults).  The plan owns all of
+ * its host and device memory until sht_plan_destroy. */
+sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* out);
+sht_status sht_plan_destroy(sht_plan_t plan);
+sht_status sht_plan_stats(sht_plan_t plan, sht_plan_info* out);
+
+/* The plan's Gauss-Legendre nodes and weights (2N each, ascending), copied to
+ * HOST arrays owned by the caller. */
+sht_status sht_plan_nodes(sht_plan_t plan, double* x_host, double* w_host);
+
+/* Forward ALT of F fields (Eq. sht_lt, Sec. 3.1.2 parity split and fold):
+ *   g(m, theta_l) = sum_{k=|m|}^{2N-1} beta_{k,m} Pbar_k^{|m|}(x_l)
+ * for every order.  beta: F x 4N^2 complex, g: F x (4N-1) x 2N complex. */
+sht_status alt_forward(sht_plan_t plan, const double* beta, double* g, int F, void* stream);
+
+/* Inverse ALT of F fields (Sec. 3.1.1, B = A^T W):
+ *   beta_{k,m} = sum_l w_l Pbar_k^{|m|}(x_l) g(m, theta_l). */
+sht_status alt_inverse(sht_plan_t plan, const double* g, double* beta, int F, void* stream);
+
+/* The same for one order m in [-(2N-1), 2N-1]: beta_m holds F x (2N-|m|)
+ * complex coefficients (degrees |m|..2N-1), g_m holds F x 2N complex values. */
+sht_status alt_forward_m(sht_plan_t plan, int m, const double* beta_m, double* g_m, int F, void* stream);
+sht_status alt_inverse_m(sht_plan_t plan, int m, const double* g_m, double* beta_m, int F, void* stream);
+
+/* Copy one of the plan's host-side program arrays into dst_host (caller-owned,
+ * *bytes long); with dst_host == NULL only *bytes is set to the size needed.
+ * Layouts are those of the library's internal program (units, ops, phase
+ * table, packed FP64 factors, schedule); used to inspect the factorisation. */
+typedef enum {
+  SHT_EXPORT_UNITS = 0,
+  SHT_EXPORT_OPS = 1,
+  SHT_EXPORT_PHASES = 2,
+  SHT_EXPORT_FACTORS = 3,
+  SHT_EXPORT_ORDER = 4
+} sht_export_kind;
+sht_status sht_plan_export(sht_plan_t plan, int what, void* dst_host, size_t* bytes);
+
+/* Wait for the plan's work on `stream` and return any latched device error. */
+sht_status sht_sync(sht_plan_t plan, void* stream);
+
+const char* sht_status_str(sht_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHT_H_ */

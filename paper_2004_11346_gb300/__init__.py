@@ -1,0 +1,147 @@
+"""GB300-native IDBF associated Legendre / spherical harmonic transform.
+
+Bremer, Chen & Yang, arXiv:2004.11346.  The transform runs in libsht.so
+(CUDA kernels for sm_103a behind the C ABI of include/sht.h); this package
+holds the ctypes binding (``_lib``), a torch-tensor convenience wrapper
+(``Plan``), the in-tree build (``build``) and the seeded input generators
+(``inputs``).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib
+
+__all__ = ["Plan", "OP_DTYPE", "UNIT_DTYPE", "opts"]
+
+OP_DTYPE = np.dtype([
+    ("b_off", "<i8"), ("mo", "<i4"), ("ni", "<i4"), ("ld", "<i4"), ("flags", "<i4"),
+    ("in_off", "<i4", 2), ("in_len", "<i4", 2), ("out_off", "<i4", 2), ("out_len", "<i4", 2),
+    ("phase", "<i4"), ("pad", "<i4"),
+])
+UNIT_DTYPE = np.dtype([
+    ("am", "<i4"), ("op_begin", "<i4"), ("op_end", "<i4"), ("ph_begin", "<i4"), ("nphase", "<i4"),
+    ("nrows", "<i4"), ("xe", "<i4"), ("xo", "<i4"), ("ye", "<i4"), ("yo", "<i4"), ("nce", "<i4"),
+    ("nco", "<i4"), ("pad", "<i4"), ("cost", "<f4"),
+])
+assert OP_DTYPE.itemsize == 64 and UNIT_DTYPE.itemsize == 56
+
+
+def opts(N: int, eps: float, **kw) -> _lib.sht_opts:
+    """Default plan options for (N, eps) with fields overridden by keyword."""
+    o = _lib.sht_opts_default(N, eps)
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Plan:
+    """A plan for order N at tolerance eps (see sht_plan_create in include/sht.h).
+
+    forward/inverse take CUDA float64 tensors shaped like the oracle's arrays:
+    beta (F, 4N^2, 2) and g (F, 4N-1, 2N, 2).  Work is queued on torch's
+    current CUDA stream.
+    """
+
+    def __init__(self, N: int, eps: float, **kw):
+        self.N = N
+        self.eps = eps
+        self.opts = opts(N, eps, **kw)
+        self.handle = _lib.sht_plan_create(N, eps, self.opts)
+
+    def close(self):
+        if self.handle:
+            _lib.sht_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def host_only(self) -> bool:
+        return bool(self.opts.flags & _lib.SHT_FLAG_HOST_ONLY)
+
+    def stats(self) -> dict:
+        return _lib.sht_plan_stats(self.handle)
+
+    def nodes(self):
+        x = np.empty(2 * self.N)
+        w = np.empty(2 * self.N)
+        _lib.sht_plan_nodes(self.handle, x.ctypes.data, w.ctypes.data)
+        return x, w
+
+    def program(self) -> dict:
+        """Host copies of the apply program (for inspection and tests)."""
+        ex = lambda k: _lib.sht_plan_export(self.handle, k)
+        return {
+            "units": np.frombuffer(ex(_lib.SHT_EXPORT_UNITS), dtype=UNIT_DTYPE),
+            "ops": np.frombuffer(ex(_lib.SHT_EXPORT_OPS), dtype=OP_DTYPE),
+            "phases": np.frombuffer(ex(_lib.SHT_EXPORT_PHASES), dtype=np.int32),
+            "factors": np.frombuffer(ex(_lib.SHT_EXPORT_FACTORS), dtype=np.float64),
+            "order": np.frombuffer(ex(_lib.SHT_EXPORT_ORDER), dtype=np.int32),
+        }
+
+    # ---- device entry points (torch tensors)
+    @staticmethod
+    def _stream():
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+
+    @staticmethod
+    def _dev(t, shape):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError("expected a contiguous CUDA float64 tensor")
+        if tuple(t.shape[1:]) != tuple(shape):
+            raise ValueError(f"expected shape (F, {', '.join(map(str, shape))}), got {tuple(t.shape)}")
+        return t
+
+    def forward(self, beta, out=None):
+        import torch
+        N = self.N
+        beta = self._dev(beta, (4 * N * N, 2))
+        F = beta.shape[0]
+        g = out if out is not None else torch.empty((F, 4 * N - 1, 2 * N, 2), dtype=torch.float64,
+                                                    device=beta.device)
+        self._dev(g, (4 * N - 1, 2 * N, 2))
+        _lib.alt_forward(self.handle, beta.data_ptr(), g.data_ptr(), F, self._stream())
+        return g
+
+    def inverse(self, g, out=None):
+        import torch
+        N = self.N
+        g = self._dev(g, (4 * N - 1, 2 * N, 2))
+        F = g.shape[0]
+        beta = out if out is not None else torch.empty((F, 4 * N * N, 2), dtype=torch.float64, device=g.device)
+        self._dev(beta, (4 * N * N, 2))
+        _lib.alt_inverse(self.handle, g.data_ptr(), beta.data_ptr(), F, self._stream())
+        return beta
+
+    def forward_m(self, m: int, beta_m, out=None):
+        import torch
+        N = self.N
+        beta_m = self._dev(beta_m, (2 * N - abs(m), 2))
+        F = beta_m.shape[0]
+        g = out if out is not None else torch.empty((F, 2 * N, 2), dtype=torch.float64, device=beta_m.device)
+        self._dev(g, (2 * N, 2))
+        _lib.alt_forward_m(self.handle, m, beta_m.data_ptr(), g.data_ptr(), F, self._stream())
+        return g
+
+    def inverse_m(self, m: int, g_m, out=None):
+        import torch
+        N = self.N
+        g_m = self._dev(g_m, (2 * N, 2))
+        F = g_m.shape[0]
+        b = out if out is not None else torch.empty((F, 2 * N - abs(m), 2), dtype=torch.float64,
+                                                    device=g_m.device)
+        self._dev(b, (2 * N - abs(m), 2))
+        _lib.alt_inverse_m(self.handle, m, g_m.data_ptr(), b.data_ptr(), F, self._stream())
+        return b
+
+    def sync(self):
+        _lib.sht_sync(self.handle, self._stream())

@@ -1,0 +1,175 @@
+"""ctypes binding of libsht.so (the C ABI declared in include/sht.h).
+
+Argument marshalling only: every step of the transform runs in the library.
+The functions keep the C names; pointers are plain integers (device
+addresses, e.g. ``tensor.data_ptr()``) and the stream is a ``cudaStream_t``
+as an integer (``torch.cuda.current_stream().cuda_stream``).  Loading fails
+loudly when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+SHT_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error or no device",
+          4: "device wait timed out", 5: "precomputation did not reach the tolerance",
+          6: "plan file error", 7: "unsupported"}
+SHT_FP64, SHT_FP32, SHT_MIXED = 0, 1, 2
+SHT_FLAG_FORCE_FACTOR = 1
+SHT_FLAG_HOST_ONLY = 2
+SHT_EXPORT_UNITS, SHT_EXPORT_OPS, SHT_EXPORT_PHASES, SHT_EXPORT_FACTORS, SHT_EXPORT_ORDER = range(5)
+
+
+class sht_opts(ctypes.Structure):
+    _fields_ = [
+        ("eps", ctypes.c_double),
+        ("n0", ctypes.c_int),
+        ("n_leaf", ctypes.c_int),
+        ("r_k", ctypes.c_int),
+        ("oversample", ctypes.c_double),
+        ("rsvd_r", ctypes.c_int),
+        ("rsvd_q", ctypes.c_int),
+        ("trim_delta", ctypes.c_double),
+        ("sampling", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("max_fields", ctypes.c_int),
+        ("flags", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class sht_plan_info(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int),
+        ("eps", ctypes.c_double),
+        ("n_units", ctypes.c_int64),
+        ("n_ops", ctypes.c_int64),
+        ("n_blocks_idbf", ctypes.c_int64),
+        ("n_blocks_lowrank", ctypes.c_int64),
+        ("n_blocks_dense", ctypes.c_int64),
+        ("n_blocks_dropped", ctypes.c_int64),
+        ("entries_idbf", ctypes.c_int64),
+        ("entries_lowrank", ctypes.c_int64),
+        ("entries_dense", ctypes.c_int64),
+        ("entries_total", ctypes.c_int64),
+        ("entries_matrix", ctypes.c_int64),
+        ("max_rank", ctypes.c_int64),
+        ("max_phases", ctypes.c_int64),
+        ("workspace_bytes", ctypes.c_int64),
+        ("factor_bytes", ctypes.c_int64),
+        ("t_factor_s", ctypes.c_double),
+        ("t_upload_s", ctypes.c_double),
+        ("threads", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ShtError(RuntimeError):
+    def __init__(self, what: str, status: int):
+        super().__init__(f"{what}: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+_lib = None
+EXPORTED = [
+    "sht_opts_default", "sht_plan_create", "sht_plan_destroy", "sht_plan_stats", "sht_plan_nodes",
+    "sht_plan_export", "alt_forward", "alt_inverse", "alt_forward_m", "alt_inverse_m", "sht_sync",
+    "sht_status_str",
+]
+
+
+def load(build: bool = True):
+    """Load (building first if stale) libsht.so and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise OSError(f"libsht.so not found at {path}")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    plan_p = ctypes.POINTER(ctypes.c_void_p)
+    lib.sht_opts_default.argtypes = [i, d, ctypes.POINTER(sht_opts)]
+    lib.sht_opts_default.restype = None
+    lib.sht_plan_create.argtypes = [i, d, ctypes.POINTER(sht_opts), plan_p]
+    lib.sht_plan_destroy.argtypes = [vp]
+    lib.sht_plan_stats.argtypes = [vp, ctypes.POINTER(sht_plan_info)]
+    lib.sht_plan_nodes.argtypes = [vp, vp, vp]
+    lib.sht_plan_export.argtypes = [vp, i, vp, ctypes.POINTER(ctypes.c_size_t)]
+    for name in ("alt_forward", "alt_inverse"):
+        getattr(lib, name).argtypes = [vp, vp, vp, i, vp]
+    for name in ("alt_forward_m", "alt_inverse_m"):
+        getattr(lib, name).argtypes = [vp, i, vp, vp, i, vp]
+    lib.sht_sync.argtypes = [vp, vp]
+    lib.sht_status_str.argtypes = [i]
+    lib.sht_status_str.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("sht_opts_default", "sht_status_str"):
+            getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def check(status: int, what: str):
+    if status != SHT_OK:
+        raise ShtError(what, status)
+
+
+def sht_opts_default(N: int, eps: float) -> sht_opts:
+    o = sht_opts()
+    load().sht_opts_default(N, eps, ctypes.byref(o))
+    return o
+
+
+def sht_plan_create(N: int, eps: float, opts: sht_opts | None = None) -> int:
+    h = ctypes.c_void_p()
+    check(load().sht_plan_create(N, eps, ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)),
+          "sht_plan_create")
+    return h.value
+
+
+def sht_plan_destroy(plan: int):
+    check(load().sht_plan_destroy(plan), "sht_plan_destroy")
+
+
+def sht_plan_stats(plan: int) -> dict:
+    info = sht_plan_info()
+    check(load().sht_plan_stats(plan, ctypes.byref(info)), "sht_plan_stats")
+    return info.as_dict()
+
+
+def sht_plan_nodes(plan: int, x_host: int, w_host: int):
+    check(load().sht_plan_nodes(plan, x_host, w_host), "sht_plan_nodes")
+
+
+def sht_plan_export(plan: int, what: int) -> bytes:
+    n = ctypes.c_size_t(0)
+    check(load().sht_plan_export(plan, what, None, ctypes.byref(n)), "sht_plan_export")
+    buf = ctypes.create_string_buffer(max(1, n.value))
+    check(load().sht_plan_export(plan, what, buf, ctypes.byref(n)), "sht_plan_export")
+    return buf.raw[: n.value]
+
+
+def alt_forward(plan: int, beta: int, g: int, F: int, stream: int = 0):
+    check(load().alt_forward(plan, beta, g, F, stream), "alt_forward")
+
+
+def alt_inverse(plan: int, g: int, beta: int, F: int, stream: int = 0):
+    check(load().alt_inverse(plan, g, beta, F, stream), "alt_inverse")
+
+
+def alt_forward_m(plan: int, m: int, beta_m: int, g_m: int, F: int, stream: int = 0):
+    check(load().alt_forward_m(plan, m, beta_m, g_m, F, stream), "alt_forward_m")
+
+
+def alt_inverse_m(plan: int, m: int, g_m: int, beta_m: int, F: int, stream: int = 0):
+    check(load().alt_inverse_m(plan, m, g_m, beta_m, F, stream), "alt_inverse_m")
+
+
+def sht_sync(plan: int, stream: int = 0):
+    check(load().sht_sync(plan, stream), "sht_sync")

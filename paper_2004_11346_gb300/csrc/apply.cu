@@ -1,0 +1,530 @@
+// CUDA apply of the IDBF-factored associated Legendre transform (sm_103a).
+//
+// One work item = one order |m| (both parity matrices of Sec. 3.1.2) for one
+// field.  A CTA takes items from an atomic counter in decreasing-cost order
+// (the program's schedule), and for each item:
+//   1. gathers beta_{k,+m}, beta_{k,-m} into the even/odd input rows X_e, X_o
+//      (4 real right-hand sides: Re/Im of +m and -m share Pbar^{|m|});
+//   2. runs the item's dense block products phase by phase (Sec. 3.3: IDBF
+//      levels, low-rank factors, trimmed turning-point blocks), one warp per
+//      product, each lane owning output rows;
+//   3. folds the parity outputs into g at all 2N nodes (Sec. 3.1.2):
+//      g(theta_{N+i}) = g_e + g_o, g(theta_{N-1-i}) = g_e - g_o.
+// The inverse runs the transposed products in reverse phase order after the
+// W-weighted fold (Sec. 3.1.1, B = A^T W) and scatters X back into beta.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "plan.hpp"
+
+using namespace sht;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kRT = 4;  // real right-hand sides per item: Re/Im of +m and -m
+
+struct DevPlan {
+  const Unit* units;
+  const Op* ops;
+  const int32_t* phase_tab;
+  const int32_t* order;
+  const double* fac;
+  const double* w;  // all 2N weights
+  double* ws;       // per-CTA scratch: max_rows x kRT doubles each
+  unsigned int* counter;
+  int N;
+  int nunits;
+  int max_rows;
+};
+
+__device__ __forceinline__ long coef_offset(long N, long m) {
+  long a = m < 0 ? -m : m;
+  if (a == 0) return 0;
+  long pos = 2 * N * (2 * a - 1) - a * (a - 1);
+  return m > 0 ? pos : pos + (2 * N - a);
+}
+__device__ __forceinline__ long order_slot(long m) { return m == 0 ? 0 : (m > 0 ? 2 * m - 1 : -2 * m); }
+
+__device__ __forceinline__ int seg_row(int t, const int32_t off[2], const int32_t len[2]) {
+  return t < len[0] ? off[0] + t : off[1] + (t - len[0]);
+}
+
+// Fetch the next work item (item index in schedule order) for this CTA.
+__device__ __forceinline__ int next_item(unsigned int* counter) {
+  __shared__ int s_item;
+  __syncthreads();
+  if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+  __syncthreads();
+  return s_item;
+}
+
+// Forward products of one phase range: y = B x, warp per op, lane per row.
+__device__ void run_ops_forward(const DevPlan& p, const Op* ops, int begin, int end, double* vec) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int oi = begin + warp; oi < end; oi += kWarps) {
+    const Op op = ops[oi];
+    const double* B = p.fac + op.b_off;
+    for (int i0 = 0; i0 < op.mo; i0 += 32) {
+      const int i = i0 + lane;
+      if (i >= op.mo) break;
+      double acc[kRT] = {0.0, 0.0, 0.0, 0.0};
+      for (int j = 0; j < op.ni; ++j) {
+        const int row = seg_row(j, op.in_off, op.in_len);
+        const double b = __ldg(B + (size_t)j * op.ld + i);
+        const double2* xr = reinterpret_cast<const double2*>(vec + (size_t)row * kRT);
+        const double2 x01 = __ldcg(xr), x23 = __ldcg(xr + 1);
+        acc[0] = fma(b, x01.x, acc[0]);
+        acc[1] = fma(b, x01.y, acc[1]);
+        acc[2] = fma(b, x23.x, acc[2]);
+        acc[3] = fma(b, x23.y, acc[3]);
+      }
+      const int orow = seg_row(i, op.out_off, op.out_len);
+      double* yr = vec + (size_t)orow * kRT;
+      if (op.flags & OP_FWD_ACCUM) {
+#pragma unroll
+        for (int r = 0; r < kRT; ++r) atomicAdd(yr + r, acc[r]);
+      } else {
+        __stcg(reinterpret_cast<double2*>(yr), make_double2(acc[0], acc[1]));
+        __stcg(reinterpret_cast<double2*>(yr) + 1, make_double2(acc[2], acc[3]));
+      }
+    }
+  }
+}
+
+// Transposed products: x_in = B^T y_out, warp per op, lane per output (column of B).
+__device__ void run_ops_transpose(const DevPlan& p, const Op* ops, int begin, int end, double* vec) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int oi = begin + warp; oi < end; oi += kWarps) {
+    const Op op = ops[oi];
+    const double* B = p.fac + op.b_off;
+    for (int j0 = 0; j0 < op.ni; j0 += 32) {
+      const int j = j0 + lane;
+      if (j >= op.ni) break;
+      const double* Bc = B + (size_t)j * op.ld;
+      double acc[kRT] = {0.0, 0.0, 0.0, 0.0};
+      for (int i = 0; i < op.mo; ++i) {
+        const int row = seg_row(i, op.out_off, op.out_len);
+        const double b = __ldg(Bc + i);
+        const double2* xr = reinterpret_cast<const double2*>(vec + (size_t)row * kRT);
+        const double2 x01 = __ldcg(xr), x23 = __ldcg(xr + 1);
+        acc[0] = fma(b, x01.x, acc[0]);
+        acc[1] = fma(b, x01.y, acc[1]);
+        acc[2] = fma(b, x23.x, acc[2]);
+        acc[3] = fma(b, x23.y, acc[3]);
+      }
+      const int orow = seg_row(j, op.in_off, op.in_len);
+      double* yr = vec + (size_t)orow * kRT;
+      if (op.flags & OP_BWD_ACCUM) {
+#pragma unroll
+        for (int r = 0; r < kRT; ++r) atomicAdd(yr + r, acc[r]);
+      } else {
+        __stcg(reinterpret_cast<double2*>(yr), make_double2(acc[0], acc[1]));
+        __stcg(reinterpret_cast<double2*>(yr) + 1, make_double2(acc[2], acc[3]));
+      }
+    }
+  }
+}
+
+// single != 0: one order `msingle` with compact per-order arrays (F fields of
+// 2N-|m| coefficients / 2N values); otherwise all orders, full layouts.
+__global__ void __launch_bounds__(kThreads) alt_forward_f64_kernel(DevPlan p, const double* __restrict__ beta,
+                                                                   double* __restrict__ g, int F, int single,
+                                                                   int msingle) {
+  const int N = p.N, K = 2 * N;
+  double* vec = p.ws + (size_t)blockIdx.x * p.max_rows * kRT;
+  const long ncoef = 4L * N * N, nval = (4L * N - 1) * K;
+  const int nitems = single ? F : p.nunits * F;
+  for (;;) {
+    const int item = next_item(p.counter);
+    if (item >= nitems) break;
+    const int f = single ? item : item % F;
+    const int am = single ? (msingle < 0 ? -msingle : msingle) : p.order[item / F];
+    const Unit u = p.units[am];
+    // 1. gather
+    const double* bp;
+    const double* bn;
+    if (single) {
+      bp = msingle >= 0 ? beta + 2L * f * (K - am) : nullptr;
+      bn = msingle < 0 ? beta + 2L * f * (K - am) : nullptr;
+    } else {
+      bp = beta + 2 * (f * ncoef + coef_offset(N, am));
+      bn = am > 0 ? beta + 2 * (f * ncoef + coef_offset(N, -am)) : nullptr;
+    }
+    for (int t = threadIdx.x; t < u.nce + u.nco; t += kThreads) {
+      const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;  // k - |m|
+      double2 pv = bp ? __ldg(reinterpret_cast<const double2*>(bp) + kk) : make_double2(0.0, 0.0);
+      double2 nv = bn ? __ldg(reinterpret_cast<const double2*>(bn) + kk) : make_double2(0.0, 0.0);
+      double2* xr = reinterpret_cast<double2*>(vec + (size_t)t * kRT);  // xe = 0, xo = nce
+      __stcg(xr, pv);
+      __stcg(xr + 1, nv);
+    }
+    for (int t = threadIdx.x; t < 2 * N; t += kThreads) {
+      double2* yr = reinterpret_cast<double2*>(vec + (size_t)(u.ye + t) * kRT);  // ye, yo contiguous
+      __stcg(yr, make_double2(0.0, 0.0));
+      __stcg(yr + 1, make_double2(0.0, 0.0));
+    }
+    __syncthreads();
+    // 2. phases
+    for (int ph = 0; ph < u.nphase; ++ph) {
+      run_ops_forward(p, p.ops, p.phase_tab[u.ph_begin + ph], p.phase_tab[u.ph_begin + ph + 1], vec);
+      __syncthreads();
+    }
+    // 3. parity fold into g
+    for (int i = threadIdx.x; i < N; i += kThreads) {
+      const double2* ye = reinterpret_cast<const double2*>(vec + (size_t)(u.ye + i) * kRT);
+      const double2* yo = reinterpret_cast<const double2*>(vec + (size_t)(u.yo + i) * kRT);
+      const double2 e0 = __ldcg(ye), e1 = __ldcg(ye + 1), o0 = __ldcg(yo), o1 = __ldcg(yo + 1);
+      for (int s = 0; s < 2; ++s) {
+        const long m = s == 0 ? am : -am;
+        if (s == 1 && am == 0) break;
+        double2* gp;
+        if (single) {
+          if (m != msingle) continue;
+          gp = reinterpret_cast<double2*>(g + 2L * f * K);
+        } else {
+          gp = reinterpret_cast<double2*>(g + 2 * (f * nval + order_slot(m) * K));
+        }
+        const double2 e = s == 0 ? e0 : e1, o = s == 0 ? o0 : o1;
+        gp[N + i] = make_double2(e.x + o.x, e.y + o.y);
+        gp[N - 1 - i] = make_double2(e.x - o.x, e.y - o.y);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) alt_inverse_f64_kernel(DevPlan p, const double* __restrict__ g,
+                                                                   double* __restrict__ beta, int F, int single,
+                                                                   int msingle) {
+  const int N = p.N, K = 2 * N;
+  double* vec = p.ws + (size_t)blockIdx.x * p.max_rows * kRT;
+  const long ncoef = 4L * N * N, nval = (4L * N - 1) * K;
+  const int nitems = single ? F : p.nunits * F;
+  for (;;) {
+    const int item = next_item(p.counter);
+    if (item >= nitems) break;
+    const int f = single ? item : item % F;
+    const int am = single ? (msingle < 0 ? -msingle : msingle) : p.order[item / F];
+    const Unit u = p.units[am];
+    // 1. W-weighted parity fold of g into Y_e, Y_o; zero X
+    for (int i = threadIdx.x; i < N; i += kThreads) {
+      double2 ev[2], ov[2];
+      const double wi = __ldg(p.w + N + i);
+      for (int s = 0; s < 2; ++s) {
+        const long m = s == 0 ? am : -am;
+        const double2* gp = nullptr;
+        if (single) {
+          if (m == msingle && !(s == 1 && am == 0)) gp = reinterpret_cast<const double2*>(g + 2L * f * K);
+        } else if (!(s == 1 && am == 0)) {
+          gp = reinterpret_cast<const double2*>(g + 2 * (f * nval + order_slot(m) * K));
+        }
+        double2 a = gp ? __ldg(gp + N + i) : make_double2(0.0, 0.0);
+        double2 b = gp ? __ldg(gp + N - 1 - i) : make_double2(0.0, 0.0);
+        ev[s] = make_double2(wi * (a.x + b.x), wi * (a.y + b.y));
+        ov[s] = make_double2(wi * (a.x - b.x), wi * (a.y - b.y));
+      }
+      double2* ye = reinterpret_cast<double2*>(vec + (size_t)(u.ye + i) * kRT);
+      double2* yo = reinterpret_cast<double2*>(vec + (size_t)(u.yo + i) * kRT);
+      __stcg(ye, ev[0]);
+      __stcg(ye + 1, ev[1]);
+      __stcg(yo, ov[0]);
+      __stcg(yo + 1, ov[1]);
+    }
+    for (int t = threadIdx.x; t < u.nce + u.nco; t += kThreads) {
+      double2* xr = reinterpret_cast<double2*>(vec + (size_t)t * kRT);
+      __stcg(xr, make_double2(0.0, 0.0));
+      __stcg(xr + 1, make_double2(0.0, 0.0));
+    }
+    __syncthreads();
+    // 2. transposed phases, last first
+    for (int ph = u.nphase - 1; ph >= 0; --ph) {
+      run_ops_transpose(p, p.ops, p.phase_tab[u.ph_begin + ph], p.phase_tab[u.ph_begin + ph + 1], vec);
+      __syncthreads();
+    }
+    // 3. scatter X into beta
+    double* bp;
+    double* bn;
+    if (single) {
+      bp = msingle >= 0 ? beta + 2L * f * (K - am) : nullptr;
+      bn = msingle < 0 ? beta + 2L * f * (K - am) : nullptr;
+    } else {
+      bp = beta + 2 * (f * ncoef + coef_offset(N, am));
+      bn = am > 0 ? beta + 2 * (f * ncoef + coef_offset(N, -am)) : nullptr;
+    }
+    for (int t = threadIdx.x; t < u.nce + u.nco; t += kThreads) {
+      const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
+      const double2* xr = reinterpret_cast<const double2*>(vec + (size_t)t * kRT);
+      if (bp) reinterpret_cast<double2*>(bp)[kk] = __ldcg(xr);
+      if (bn) reinterpret_cast<double2*>(bn)[kk] = __ldcg(xr + 1);
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Plan object and C ABI
+
+struct sht_plan_s {
+  HostProgram prog;
+  int device = 0;
+  int nslots = 0;
+  Unit* d_units = nullptr;
+  Op* d_ops = nullptr;
+  int32_t* d_phase = nullptr;
+  int32_t* d_order = nullptr;
+  double* d_fac = nullptr;
+  double* d_w = nullptr;
+  double* d_ws = nullptr;
+  unsigned int* d_counter = nullptr;
+  sht_status latched = SHT_OK;
+  bool host_only = false;
+};
+
+namespace {
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+  size_t bytes = std::max<size_t>(sizeof(T), v.size() * sizeof(T));
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), bytes);
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+void free_device(sht_plan_s* p) {
+  cudaFree(p->d_units);
+  cudaFree(p->d_ops);
+  cudaFree(p->d_phase);
+  cudaFree(p->d_order);
+  cudaFree(p->d_fac);
+  cudaFree(p->d_w);
+  cudaFree(p->d_ws);
+  cudaFree(p->d_counter);
+}
+
+DevPlan dev_plan(const sht_plan_s* p) {
+  DevPlan d;
+  d.units = p->d_units;
+  d.ops = p->d_ops;
+  d.phase_tab = p->d_phase;
+  d.order = p->d_order;
+  d.fac = p->d_fac;
+  d.w = p->d_w;
+  d.ws = p->d_ws;
+  d.counter = p->d_counter;
+  d.N = p->prog.N;
+  d.nunits = 2 * p->prog.N;
+  d.max_rows = p->prog.max_rows;
+  return d;
+}
+
+sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F, int single, int m,
+                  cudaStream_t st) {
+  if (p->host_only) return SHT_ERR_UNSUPPORTED;
+  // complex values are moved as 16-byte pairs
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return SHT_ERR_ARG;
+  if ((int64_t)F * 2 * p->prog.N > (int64_t)1 << 30) return SHT_ERR_ARG;
+  if (p->latched != SHT_OK) {
+    sht_status s = p->latched;
+    p->latched = SHT_OK;
+    return s;
+  }
+  if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
+  const int items = single ? F : 2 * p->prog.N * F;
+  const int grid = std::min(p->nslots, std::max(1, items));
+  DevPlan d = dev_plan(p);
+  if (fwd)
+    alt_forward_f64_kernel<<<grid, kThreads, 0, st>>>(d, in, out, F, single, m);
+  else
+    alt_inverse_f64_kernel<<<grid, kThreads, 0, st>>>(d, in, out, F, single, m);
+  return cudaGetLastError() == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sht_opts_default(int N, double eps, sht_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->eps = eps;
+  o->n0 = N >= 2048 ? 512 : std::max(16, N / 4);
+  o->n_leaf = N >= 1024 ? 64 : std::max(8, N / 16);
+  o->r_k = 150;
+  o->oversample = 2.0;
+  o->rsvd_r = 30;
+  o->rsvd_q = 2;
+  o->trim_delta = std::max(1e-3 * eps, 0x1p-52);
+  o->sampling = 0;
+  o->precision = SHT_FP64;
+  o->max_fields = 1;
+  o->flags = 0;
+  o->seed = 0x5eed2004u;
+}
+
+sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* out) {
+  if (!out || N < 1 || N > (1 << 14) || !(eps > 0.0 && eps < 1.0)) return SHT_ERR_ARG;
+  *out = nullptr;
+  sht_opts o;
+  if (opts) {
+    o = *opts;
+    o.eps = eps;
+  } else {
+    sht_opts_default(N, eps, &o);
+  }
+  if (o.n0 < 1 || o.n_leaf < 1 || o.r_k < 1 || o.rsvd_r < 1 || o.rsvd_q < 1 || !(o.oversample >= 1.0) ||
+      !(o.trim_delta >= 0.0) || o.max_fields < 1)
+    return SHT_ERR_ARG;
+  const bool host_only = (o.flags & SHT_FLAG_HOST_ONLY) != 0;
+  int ndev = 0;
+  if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)) return SHT_ERR_CUDA;
+  sht_plan_s* p = new (std::nothrow) sht_plan_s();
+  if (!p) return SHT_ERR_OOM;
+  std::string err;
+  sht_status s;
+  try {
+    s = build_program(N, o, p->prog, err);
+  } catch (const std::bad_alloc&) {
+    s = SHT_ERR_OOM;
+  }
+  if (s != SHT_OK) {
+    delete p;
+    return s;
+  }
+  if (host_only) {
+    p->host_only = true;
+    *out = p;
+    return SHT_OK;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  cudaGetDevice(&p->device);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, alt_forward_f64_kernel, kThreads, 0);
+  p->nslots = std::max(1, sms * std::max(1, per_sm));
+  const HostProgram& P = p->prog;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = upload(&p->d_units, P.units);
+  if (e == cudaSuccess) e = upload(&p->d_ops, P.ops);
+  if (e == cudaSuccess) e = upload(&p->d_phase, P.phase_tab);
+  if (e == cudaSuccess) e = upload(&p->d_order, P.order);
+  if (e == cudaSuccess) e = upload(&p->d_fac, P.factors);
+  if (e == cudaSuccess) e = upload(&p->d_w, P.w);
+  size_t ws = (size_t)p->nslots * P.max_rows * kRT * sizeof(double);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_ws), std::max<size_t>(ws, 8));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_counter), sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_device(p);
+    delete p;
+    return e == cudaErrorMemoryAllocation ? SHT_ERR_OOM : SHT_ERR_CUDA;
+  }
+  p->prog.info.workspace_bytes = (int64_t)ws;
+  p->prog.info.factor_bytes = (int64_t)(P.factors.size() * sizeof(double));
+  p->prog.info.t_upload_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = p;
+  return SHT_OK;
+}
+
+sht_status sht_plan_destroy(sht_plan_t p) {
+  if (!p) return SHT_ERR_ARG;
+  if (!p->host_only) free_device(p);
+  delete p;
+  return SHT_OK;
+}
+
+sht_status sht_plan_stats(sht_plan_t p, sht_plan_info* out) {
+  if (!p || !out) return SHT_ERR_ARG;
+  *out = p->prog.info;
+  return SHT_OK;
+}
+
+sht_status sht_plan_export(sht_plan_t p, int what, void* dst, size_t* bytes) {
+  if (!p || !bytes) return SHT_ERR_ARG;
+  const void* src = nullptr;
+  size_t n = 0;
+  const HostProgram& P = p->prog;
+  switch (what) {
+    case SHT_EXPORT_UNITS: src = P.units.data(); n = P.units.size() * sizeof(Unit); break;
+    case SHT_EXPORT_OPS: src = P.ops.data(); n = P.ops.size() * sizeof(Op); break;
+    case SHT_EXPORT_PHASES: src = P.phase_tab.data(); n = P.phase_tab.size() * sizeof(int32_t); break;
+    case SHT_EXPORT_FACTORS: src = P.factors.data(); n = P.factors.size() * sizeof(double); break;
+    case SHT_EXPORT_ORDER: src = P.order.data(); n = P.order.size() * sizeof(int32_t); break;
+    default: return SHT_ERR_ARG;
+  }
+  if (!dst) {
+    *bytes = n;
+    return SHT_OK;
+  }
+  if (*bytes < n) return SHT_ERR_ARG;
+  if (n) std::memcpy(dst, src, n);
+  *bytes = n;
+  return SHT_OK;
+}
+
+sht_status sht_plan_nodes(sht_plan_t p, double* x, double* w) {
+  if (!p || !x || !w) return SHT_ERR_ARG;
+  std::memcpy(x, p->prog.x.data(), sizeof(double) * p->prog.x.size());
+  std::memcpy(w, p->prog.w.data(), sizeof(double) * p->prog.w.size());
+  return SHT_OK;
+}
+
+sht_status alt_forward(sht_plan_t p, const double* beta, double* g, int F, void* stream) {
+  if (!p || !beta || !g || F < 0) return SHT_ERR_ARG;
+  if (F == 0) return SHT_OK;
+  return launch(p, true, beta, g, F, 0, 0, static_cast<cudaStream_t>(stream));
+}
+
+sht_status alt_inverse(sht_plan_t p, const double* g, double* beta, int F, void* stream) {
+  if (!p || !beta || !g || F < 0) return SHT_ERR_ARG;
+  if (F == 0) return SHT_OK;
+  return launch(p, false, g, beta, F, 0, 0, static_cast<cudaStream_t>(stream));
+}
+
+sht_status alt_forward_m(sht_plan_t p, int m, const double* beta_m, double* g_m, int F, void* stream) {
+  if (!p || !beta_m || !g_m || F < 0) return SHT_ERR_ARG;
+  if (m <= -2 * p->prog.N || m >= 2 * p->prog.N) return SHT_ERR_ARG;
+  if (F == 0) return SHT_OK;
+  return launch(p, true, beta_m, g_m, F, 1, m, static_cast<cudaStream_t>(stream));
+}
+
+sht_status alt_inverse_m(sht_plan_t p, int m, const double* g_m, double* beta_m, int F, void* stream) {
+  if (!p || !beta_m || !g_m || F < 0) return SHT_ERR_ARG;
+  if (m <= -2 * p->prog.N || m >= 2 * p->prog.N) return SHT_ERR_ARG;
+  if (F == 0) return SHT_OK;
+  return launch(p, false, g_m, beta_m, F, 1, m, static_cast<cudaStream_t>(stream));
+}
+
+sht_status sht_sync(sht_plan_t p, void* stream) {
+  if (!p) return SHT_ERR_ARG;
+  if (p->host_only) return SHT_ERR_UNSUPPORTED;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return SHT_ERR_CUDA;
+  sht_status s = p->latched;
+  p->latched = SHT_OK;
+  return s;
+}
+
+const char* sht_status_str(sht_status s) {
+  switch (s) {
+    case SHT_OK: return "ok";
+    case SHT_ERR_ARG: return "invalid argument";
+    case SHT_ERR_OOM: return "out of memory";
+    case SHT_ERR_CUDA: return "CUDA error or no device";
+    case SHT_ERR_TIMEOUT: return "device wait timed out";
+    case SHT_ERR_NUMERIC: return "precomputation did not reach the tolerance";
+    case SHT_ERR_IO: return "plan file error";
+    case SHT_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"
