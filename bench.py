@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the IDBF associated Legendre transform on GB300.
+
+One step = the forward ALT of a batch of F fields over every order
+|m| <= 2N-1 (gather, IDBF / low-rank / dense block products, parity fold)
+followed by the inverse ALT of its output (weighted fold, transposed
+products, scatter): every step of the apply path, on inputs resident in HBM.
+Metric: fields per second (F x ranks / seconds per step).
+
+Also reported: forward-only and inverse-only kernel times, the dominant
+kernel's roofline fraction, an end-to-end number through the public API
+with the batch copied from pinned host memory and the result read back
+every step, and the dense FP64 CPU oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   (the oracle as the reference arm)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2004_11346_gb300 import inputs  # noqa: E402
+
+METRIC = "SHT fields/s at N=1024 vs FP64 IDBF & dense ALT on 1 GB300, rel err<=1e-6"
+DEFAULT_WORKLOAD = "fp64_N1024"
+EXTRA_WORKLOADS = {
+    # smaller FP64 case used for profiling captures
+    "fp64_N512": dict(N=512, F=1, seed=0, decay=1.0, real_m0=False, eps=1e-12, precision="fp64"),
+}
+FP64_PEAK_GFLOPS = 1250.0  # GB300 nominal dense FP64 (vector) rate
+
+
+def workload(name):
+    w = dict(inputs.WORKLOADS.get(name) or EXTRA_WORKLOADS[name])
+    w["name"] = name
+    return w
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(device_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- work accounting
+def program_flops(plan, F):
+    """Algorithmic FLOPs of one forward (or inverse) launch: 2 x entries x RHS.
+
+    Each stored factor entry multiplies 4 real right-hand sides per field
+    (Re/Im of +m and -m); order m = 0 has 2.
+    """
+    prog = plan.program(parts=("units", "ops"))
+    ops, units = prog["ops"], prog["units"]
+    entries = (ops["mo"].astype(np.int64) * ops["ni"].astype(np.int64))
+    total = 0
+    for u in units:
+        e = int(entries[u["op_begin"]: u["op_end"]].sum())
+        total += e * (2 if u["am"] == 0 else 4)
+    return 2 * total * F, int(entries.sum())
+
+
+# ---------------------------------------------------------------- reference arm
+def sample_orders(N, stride):
+    return list(range(0, 2 * N, stride))
+
+
+def oracle_sample(N, beta_field, stride):
+    """Forward + inverse ALT by the oracle for every stride-th order |m| (both
+    signs); returns (seconds, fraction of the full transform's work)."""
+    import oracle
+    x, w = oracle.gl_rule(2 * N)
+    ams = sample_orders(N, stride)
+    t0 = time.perf_counter()
+    for am in ams:
+        for m in ([am, -am] if am else [0]):
+            off = oracle.coef_offset(N, m)
+            gm = oracle.alt_forward_m(N, m, beta_field[off: off + 2 * N - am], x)
+            oracle.alt_inverse_m(N, m, gm, x, w)
+    dt = time.perf_counter() - t0
+    work_s = sum((2 * N - am) * (1 if am == 0 else 2) for am in ams)
+    return dt, work_s / (4.0 * N * N)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    N = w["N"]
+    beta = inputs.workload_coefficients(w["name"], F=1)[0]
+    stride = max(1, args.ref_stride)
+    for _ in range(args.warmup):
+        oracle_sample(N, beta, stride * 4)
+    times, frac = [], 1.0
+    for _ in range(args.steps):
+        dt, frac = oracle_sample(N, beta, stride)
+        times.append(dt)
+    import oracle
+    cores = oracle.num_threads()
+    sec_per_field = float(np.mean(times)) / frac
+    value = 1.0 / sec_per_field
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(w, world),
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "fields/s", "cores": cores,
+                         "sample": f"forward+inverse ALT of every {stride}th order |m| of 1 field "
+                                   f"({frac:.3f} of the transform), scaled to one field"},
+        "e2e": {"value": value, "unit": "fields/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w, world):
+    return {"workload": w["name"], "N": w["N"], "fields_per_rank": w["F"], "global_batch": w["F"] * world,
+            "eps": w["eps"], "precision": w["precision"], "orders": 4 * w["N"] - 1,
+            "step": "forward ALT + inverse ALT", "parallelism": f"replicas{world}",
+            "l2": "inputs and factor store larger than L2"}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import paper_2004_11346_gb300 as sht
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev_index = torch.cuda.current_device()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = workload(args.workload)
+    N, F, eps = w["N"], w["F"], w["eps"]
+    t0 = time.perf_counter()
+    plan = sht.Plan(N, eps)
+    t_plan = time.perf_counter() - t0
+    st = plan.stats()
+    beta_h = inputs.coefficients(N, F, w["seed"], decay=w["decay"], real_m0=w["real_m0"], field_offset=rank * F)
+    beta = torch.from_numpy(beta_h).cuda()
+    g = torch.empty((F, 4 * N - 1, 2 * N, 2), dtype=torch.float64, device="cuda")
+    back = torch.empty_like(beta)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        plan.forward(beta, out=g)
+        plan.inverse(g, out=back)
+    torch.cuda.synchronize()
+    plan.sync()
+    rt_err = float((back - beta).norm() / beta.norm())
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev_index)
+    time.sleep(0.3)
+    e0.record(stream)
+    for i in range(K):
+        ev[i][0].record(stream)
+        plan.forward(beta, out=g)
+        ev[i][1].record(stream)
+        plan.inverse(g, out=back)
+        ev[i][2].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    plan.sync()
+    ms = e0.elapsed_time(e1) / K
+    fwd_ms = float(np.mean([ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]))
+    inv_ms = float(np.mean([ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]))
+    if world > 1:
+        t = torch.tensor([ms, fwd_ms, inv_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, fwd_ms, inv_ms = [float(v) for v in t.tolist()]
+    value = world * F / (ms * 1e-3)
+
+    # end to end through the public API: pinned host batch in, result out
+    beta_pin = torch.from_numpy(beta_h).pin_memory()
+    out_pin = torch.empty(beta_pin.shape, dtype=torch.float64).pin_memory()
+    beta_d = torch.empty_like(beta)
+    for _ in range(max(1, args.warmup)):
+        beta_d.copy_(beta_pin, non_blocking=True)
+        plan.forward(beta_d, out=g)
+        plan.inverse(g, out=back)
+        out_pin.copy_(back, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(K):
+        beta_d.copy_(beta_pin, non_blocking=True)
+        plan.forward(beta_d, out=g)
+        plan.inverse(g, out=back)
+        out_pin.copy_(back, non_blocking=True)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a0.elapsed_time(a1) / K
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    io_bytes = beta_pin.numel() * 8
+
+    flops, entries = program_flops(plan, F)
+    achieved = flops / (fwd_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(w, world),
+        "forward_ms": fwd_ms, "inverse_ms": inv_ms,
+        "forward_fields_per_s": world * F / (fwd_ms * 1e-3), "inverse_fields_per_s": world * F / (inv_ms * 1e-3),
+        "round_trip_rel_err": rt_err,
+        "roofline": {"kernel": "alt_forward_f64_kernel", "bound": "alu", "achieved": achieved,
+                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+                     "traffic": None, "flops_per_launch": flops,
+                     "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (probe measured 1.197)"},
+        "e2e": {"value": world * F / (e2e_ms * 1e-3), "unit": "fields/s", "h2d_bytes_per_step": io_bytes,
+                "d2h_bytes_per_step": io_bytes},
+        "gpu_launches": 2 * K,
+        "clocks": clk,
+        "plan": {"t_factor_s": st["t_factor_s"], "t_create_s": t_plan, "threads": st["threads"],
+                 "entries_total": st["entries_total"], "entries_matrix": st["entries_matrix"],
+                 "factor_bytes": st["factor_bytes"], "n_ops": st["n_ops"],
+                 "blocks": {"idbf": st["n_blocks_idbf"], "lowrank": st["n_blocks_lowrank"],
+                            "dense": st["n_blocks_dense"], "dropped": st["n_blocks_dropped"]},
+                 "max_rank": st["max_rank"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, frac = oracle_sample(N, beta_h[0], args.ref_stride)
+        import oracle
+        line["cpu_baseline"] = {
+            "value": frac / dt, "unit": "fields/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"forward+inverse ALT of every {args.ref_stride}th order |m| of 1 field "
+                      f"({frac:.3f} of the transform, {dt:.1f} s), scaled to one field"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--ref-stride", type=int, default=4, help="oracle samples every n-th order")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -21,6 +21,7 @@
  *                          sequence above, column = node index l (ascending x).
  *      grid values f     : per field 2N x (4N-1) complex, theta-major.
  *    F fields are stored one after another (field stride = the per-field size).
+ *    F = 0 is a no-op, and the data pointers may then be NULL.
  *  - Data pointers are DEVICE pointers owned by the caller, unless the entry
  *    point says otherwise.  Inputs are never modified.  Outputs must not
  *    overlap inputs.

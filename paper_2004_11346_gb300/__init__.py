@@ -75,16 +75,12 @@ class Plan:
         _lib.sht_plan_nodes(self.handle, x.ctypes.data, w.ctypes.data)
         return x, w
 
-    def program(self) -> dict:
+    def program(self, parts=("units", "ops", "phases", "factors", "order")) -> dict:
         """Host copies of the apply program (for inspection and tests)."""
-        ex = lambda k: _lib.sht_plan_export(self.handle, k)
-        return {
-            "units": np.frombuffer(ex(_lib.SHT_EXPORT_UNITS), dtype=UNIT_DTYPE),
-            "ops": np.frombuffer(ex(_lib.SHT_EXPORT_OPS), dtype=OP_DTYPE),
-            "phases": np.frombuffer(ex(_lib.SHT_EXPORT_PHASES), dtype=np.int32),
-            "factors": np.frombuffer(ex(_lib.SHT_EXPORT_FACTORS), dtype=np.float64),
-            "order": np.frombuffer(ex(_lib.SHT_EXPORT_ORDER), dtype=np.int32),
-        }
+        kinds = {"units": (_lib.SHT_EXPORT_UNITS, UNIT_DTYPE), "ops": (_lib.SHT_EXPORT_OPS, OP_DTYPE),
+                 "phases": (_lib.SHT_EXPORT_PHASES, np.int32), "factors": (_lib.SHT_EXPORT_FACTORS, np.float64),
+                 "order": (_lib.SHT_EXPORT_ORDER, np.int32)}
+        return {k: np.frombuffer(_lib.sht_plan_export(self.handle, kinds[k][0]), dtype=kinds[k][1]) for k in parts}
 
     # ---- device entry points (torch tensors)
     @staticmethod

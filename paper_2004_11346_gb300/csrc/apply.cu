@@ -479,28 +479,32 @@ sht_status sht_plan_nodes(sht_plan_t p, double* x, double* w) {
 }
 
 sht_status alt_forward(sht_plan_t p, const double* beta, double* g, int F, void* stream) {
-  if (!p || !beta || !g || F < 0) return SHT_ERR_ARG;
-  if (F == 0) return SHT_OK;
+  if (!p || F < 0) return SHT_ERR_ARG;
+  if (F == 0) return SHT_OK;  // nothing to do: the pointers may be NULL
+  if (!beta || !g) return SHT_ERR_ARG;
   return launch(p, true, beta, g, F, 0, 0, static_cast<cudaStream_t>(stream));
 }
 
 sht_status alt_inverse(sht_plan_t p, const double* g, double* beta, int F, void* stream) {
-  if (!p || !beta || !g || F < 0) return SHT_ERR_ARG;
+  if (!p || F < 0) return SHT_ERR_ARG;
   if (F == 0) return SHT_OK;
+  if (!beta || !g) return SHT_ERR_ARG;
   return launch(p, false, g, beta, F, 0, 0, static_cast<cudaStream_t>(stream));
 }
 
 sht_status alt_forward_m(sht_plan_t p, int m, const double* beta_m, double* g_m, int F, void* stream) {
-  if (!p || !beta_m || !g_m || F < 0) return SHT_ERR_ARG;
+  if (!p || F < 0) return SHT_ERR_ARG;
   if (m <= -2 * p->prog.N || m >= 2 * p->prog.N) return SHT_ERR_ARG;
   if (F == 0) return SHT_OK;
+  if (!beta_m || !g_m) return SHT_ERR_ARG;
   return launch(p, true, beta_m, g_m, F, 1, m, static_cast<cudaStream_t>(stream));
 }
 
 sht_status alt_inverse_m(sht_plan_t p, int m, const double* g_m, double* beta_m, int F, void* stream) {
-  if (!p || !beta_m || !g_m || F < 0) return SHT_ERR_ARG;
+  if (!p || F < 0) return SHT_ERR_ARG;
   if (m <= -2 * p->prog.N || m >= 2 * p->prog.N) return SHT_ERR_ARG;
   if (F == 0) return SHT_OK;
+  if (!beta_m || !g_m) return SHT_ERR_ARG;
   return launch(p, false, g_m, beta_m, F, 1, m, static_cast<cudaStream_t>(stream));
 }
 

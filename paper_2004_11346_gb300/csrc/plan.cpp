@@ -15,6 +15,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <numeric>
@@ -135,6 +137,7 @@ struct UnitBuild {
   int64_t n_idbf = 0, n_low = 0, n_dense = 0, n_drop = 0;
   int64_t e_idbf = 0, e_low = 0, e_dense = 0;
   int64_t max_rank = 0;
+  int64_t dbg[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // dense area by cause (diagnostics)
   int nphase = 0;
   double cost = 0.0;
   std::string err;
@@ -612,13 +615,16 @@ static void emit_block(UnitBuild& ub, const ParityMatrix& P, const sht_opts& o, 
     int L = -1;
     while ((mn >> (L + 1)) >= o.n_leaf) ++L;  // largest L with mn / 2^L >= n_leaf
     if (L >= 0 && emit_idbf(ub, b, L, force)) return;
+    ub.dbg[L >= 0 ? 0 : 1] += (int64_t)nr * nc;  // osc block kept dense (IDBF not smaller / too small)
     emit_dense(ub, b);
     return;
   }
   int ti0, ti1, tj0, tj1;
   if (!trim(b, o.trim_delta * P.scale, ti0, ti1, tj0, tj1)) { ub.n_drop += 1; return; }
   BlockCtx t{&P, i0 + ti0, ti1 - ti0, j0 + tj0, tj1 - tj0, &o, b.tol, &rng};
+  ub.dbg[cls == B_NONOSC ? 4 : 5] += (int64_t)nr * nc;  // area before trimming
   if (cls == B_NONOSC && emit_lowrank(ub, t, force)) return;
+  ub.dbg[cls == B_NONOSC ? 2 : 3] += (int64_t)t.nr * t.nc;  // trimmed block kept dense
   emit_dense(ub, t);
 }
 
@@ -768,6 +774,16 @@ sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::strin
       err = "unit layout failed validation at order " + std::to_string(am);
       return SHT_ERR_NUMERIC;
     }
+  }
+  if (std::getenv("SHT_PLAN_DEBUG")) {
+    int64_t d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int am = 0; am < K; ++am)
+      for (int t = 0; t < 8; ++t) d[t] += ub[am].dbg[t];
+    std::fprintf(stderr,
+                 "[plan] dense area: osc(idbf not smaller)=%lld osc(small)=%lld nonosc(trimmed)=%lld "
+                 "cross(trimmed)=%lld | untrimmed area nonosc=%lld cross=%lld\n",
+                 (long long)d[0], (long long)d[1], (long long)d[2], (long long)d[3], (long long)d[4],
+                 (long long)d[5]);
   }
   I.N = N;
   I.eps = opts.eps;
