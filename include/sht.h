@@ -149,6 +149,24 @@ typedef enum {
 } sht_export_kind;
 sht_status sht_plan_export(sht_plan_t plan, int what, void* dst_host, size_t* bytes);
 
+/* alt_forward_m without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory (a memory
+ * pool or arena that owns the device, real-time loops where cudaMalloc/cudaFree
+ * would synchronise the device, embedders with their own allocator).  It runs
+ * the alt_forward_m computation with its scratch (per-CTA vectors and the
+ * work counter) in a fixed 8 MiB array inside the library's device image
+ * instead of the plan's workspace, and calls no allocating routine.
+ *  - Every GPU that loads libsht.so holds that array until the process exits.
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress) with that device current; make it before any
+ *    stream capture.  The plan must belong to the current device.
+ *  - Returns SHT_ERR_ARG when one work item's vectors (the plan's largest
+ *    order: rows x 4 doubles) do not fit in the array; otherwise the result is
+ *    that of alt_forward_m, with fewer CTAs.
+ *  - All calls share the array and it keeps the last call's contents: calls
+ *    that may overlap on the GPU race on it and must be serialised. */
+sht_status alt_forward_m_noalloc(sht_plan_t plan, int m, const double* beta_m, double* g_m, int F, void* stream);
+
 /* Wait for the plan's work on `stream` and return any latched device error. */
 sht_status sht_sync(sht_plan_t plan, void* stream);
 

@@ -79,7 +79,7 @@ _lib = None
 EXPORTED = [
     "sht_opts_default", "sht_plan_create", "sht_plan_destroy", "sht_plan_stats", "sht_plan_nodes",
     "sht_plan_export", "alt_forward", "alt_inverse", "alt_forward_m", "alt_inverse_m", "sht_sync",
-    "sht_status_str",
+    "sht_status_str", "alt_forward_m_noalloc",
 ]
 
 
@@ -103,7 +103,7 @@ def load(build: bool = True):
     lib.sht_plan_export.argtypes = [vp, i, vp, ctypes.POINTER(ctypes.c_size_t)]
     for name in ("alt_forward", "alt_inverse"):
         getattr(lib, name).argtypes = [vp, vp, vp, i, vp]
-    for name in ("alt_forward_m", "alt_inverse_m"):
+    for name in ("alt_forward_m", "alt_inverse_m", "alt_forward_m_noalloc"):
         getattr(lib, name).argtypes = [vp, i, vp, vp, i, vp]
     lib.sht_sync.argtypes = [vp, vp]
     lib.sht_status_str.argtypes = [i]
@@ -169,6 +169,10 @@ def alt_forward_m(plan: int, m: int, beta_m: int, g_m: int, F: int, stream: int 
 
 def alt_inverse_m(plan: int, m: int, g_m: int, beta_m: int, F: int, stream: int = 0):
     check(load().alt_inverse_m(plan, m, g_m, beta_m, F, stream), "alt_inverse_m")
+
+
+def alt_forward_m_noalloc(plan: int, m: int, beta_m: int, g_m: int, F: int, stream: int = 0):
+    check(load().alt_forward_m_noalloc(plan, m, beta_m, g_m, F, stream), "alt_forward_m_noalloc")
 
 
 def sht_sync(plan: int, stream: int = 0):

@@ -18,6 +18,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -532,3 +533,84 @@ const char* sht_status_str(sht_status s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Forward ALT of one order without any allocation.
+//
+// Some callers cannot allocate device memory: code that runs inside a
+// memory-pool or arena that owns the whole device, real-time loops where a
+// cudaMalloc/cudaFree would synchronise the device and stall other streams,
+// and embedders whose allocator is not CUDA's.  For them this entry point runs
+// the same forward kernel as alt_forward_m, but with its per-CTA vector
+// scratch and its work counter taken from the fixed array below instead of
+// the plan's workspace.  It calls no cudaMalloc, cudaFree or allocating
+// library routine.
+//
+// The array lives in the library's device image: every GPU that loads
+// libsht.so holds kNoAllocScratchBytes of it until the process exits.  Host
+// code must not pass the array's name to a kernel (on the host it is only a
+// stand-in symbol); its device address is looked up once per device with
+// cudaGetSymbolAddress, on the first call made while that device is current.
+// Make that first call before any stream capture.  All calls share the one
+// array, so calls that may overlap on the GPU (different streams, or several
+// plans at once) race on it: serialise them.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB
+constexpr size_t kNoAllocCounterBytes = 256;              // work counter, padded
+
+static __device__ __align__(256) unsigned char noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex noalloc_mu;
+void* noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of noalloc_scratch on the current device (looked up once).
+sht_status noalloc_base(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kMaxDevices) return SHT_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(noalloc_mu);
+  if (!noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, noalloc_scratch);
+    if (e != cudaSuccess || !ptr) return SHT_ERR_CUDA;
+    noalloc_addr[dev] = ptr;
+  }
+  *out = static_cast<unsigned char*>(noalloc_addr[dev]);
+  return SHT_OK;
+}
+
+}  // namespace
+
+extern "C" sht_status alt_forward_m_noalloc(sht_plan_t p, int m, const double* beta_m, double* g_m, int F,
+                                            void* stream) {
+  if (!p || F < 0) return SHT_ERR_ARG;
+  if (m <= -2 * p->prog.N || m >= 2 * p->prog.N) return SHT_ERR_ARG;
+  if (F == 0) return SHT_OK;
+  if (!beta_m || !g_m) return SHT_ERR_ARG;
+  if (p->host_only) return SHT_ERR_UNSUPPORTED;
+  if ((reinterpret_cast<uintptr_t>(beta_m) | reinterpret_cast<uintptr_t>(g_m)) & 15u) return SHT_ERR_ARG;
+  if ((int64_t)F * 2 * p->prog.N > (int64_t)1 << 30) return SHT_ERR_ARG;
+  // one CTA's vector space must fit next to the counter
+  const size_t slot = (size_t)p->prog.max_rows * kRT * sizeof(double);
+  if (slot == 0 || slot > kNoAllocScratchBytes - kNoAllocCounterBytes) return SHT_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return SHT_ERR_ARG;
+  unsigned char* base = nullptr;
+  sht_status s = noalloc_base(dev, &base);
+  if (s != SHT_OK) return s;
+  if (p->latched != SHT_OK) {
+    s = p->latched;
+    p->latched = SHT_OK;
+    return s;
+  }
+  const int slots = (int)((kNoAllocScratchBytes - kNoAllocCounterBytes) / slot);
+  const int grid = std::max(1, std::min(std::min(slots, p->nslots), F));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DevPlan d = dev_plan(p);
+  d.counter = reinterpret_cast<unsigned int*>(base);  // must start at zero: cleared below
+  d.ws = reinterpret_cast<double*>(base + kNoAllocCounterBytes);
+  if (cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
+  alt_forward_f64_kernel<<<grid, kThreads, 0, st>>>(d, beta_m, g_m, F, 1, m);
+  return cudaGetLastError() == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
+}
