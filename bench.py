@@ -32,12 +32,13 @@ sys.path.insert(0, ROOT)
 from paper_2004_11346_gb300 import inputs  # noqa: E402
 
 METRIC = "SHT fields/s at N=1024 vs FP64 IDBF & dense ALT on 1 GB300, rel err<=1e-6"
-DEFAULT_WORKLOAD = "fp64_N1024"
+DEFAULT_WORKLOAD = "mixed_N1024_F64"
 EXTRA_WORKLOADS = {
-    # smaller FP64 case used for profiling captures
+    # smaller cases used for profiling captures
     "fp64_N512": dict(N=512, F=1, seed=0, decay=1.0, real_m0=False, eps=1e-12, precision="fp64"),
+    "mixed_N512_F16": dict(N=512, F=16, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed"),
 }
-FP64_PEAK_GFLOPS = 1250.0  # GB300 nominal dense FP64 (vector) rate
+FP64_PEAK_GFLOPS = 1250.0  # GB300 nominal FP64 (vector) rate
 
 
 def workload(name):
@@ -178,9 +179,42 @@ def config_of(w, world):
 
 
 # ---------------------------------------------------------------- our arm
+FP32_PEAK_GFLOPS = 128 * 2 * 152 * 2.07  # FP32 lanes x 2 x SMs x max SM clock (GHz)
+
+
+def plan_for(sht, w, **kw):
+    from paper_2004_11346_gb300 import _lib
+    prec = {"fp64": _lib.SHT_FP64, "mixed": _lib.SHT_MIXED, "fp32": _lib.SHT_FP32}[w["precision"]]
+    return sht.Plan(w["N"], w["eps"], precision=prec, **kw)
+
+
+def time_steps(torch, plan, beta, g, back, K, W, stream):
+    """W untimed then K timed (forward, inverse) steps; per-step and per-kernel ms."""
+    for _ in range(W):
+        plan.forward(beta, out=g)
+        plan.inverse(g, out=back)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(K):
+        ev[i][0].record(stream)
+        plan.forward(beta, out=g)
+        ev[i][1].record(stream)
+        plan.inverse(g, out=back)
+        ev[i][2].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    fwd = float(np.mean([ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]))
+    inv = float(np.mean([ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]))
+    return ms, fwd, inv
+
+
 def run_ours(args):
     import torch
     import paper_2004_11346_gb300 as sht
+    from paper_2004_11346_gb300 import _lib
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -189,9 +223,9 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     w = workload(args.workload)
-    N, F, eps = w["N"], w["F"], w["eps"]
+    N, F = w["N"], w["F"]
     t0 = time.perf_counter()
-    plan = sht.Plan(N, eps)
+    plan = plan_for(sht, w)
     t_plan = time.perf_counter() - t0
     st = plan.stats()
     beta_h = inputs.coefficients(N, F, w["seed"], decay=w["decay"], real_m0=w["real_m0"], field_offset=rank * F)
@@ -204,6 +238,13 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
+    def max_over_ranks(vals):
+        if world == 1:
+            return vals
+        t = torch.tensor(vals, device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return [float(v) for v in t.tolist()]
+
     for _ in range(args.warmup):
         plan.forward(beta, out=g)
         plan.inverse(g, out=back)
@@ -212,34 +253,18 @@ def run_ours(args):
     rt_err = float((back - beta).norm() / beta.norm())
 
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(dev_index)
     time.sleep(0.3)
-    e0.record(stream)
-    for i in range(K):
-        ev[i][0].record(stream)
-        plan.forward(beta, out=g)
-        ev[i][1].record(stream)
-        plan.inverse(g, out=back)
-        ev[i][2].record(stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, fwd_ms, inv_ms = time_steps(torch, plan, beta, g, back, K, 0, stream)
     clk = clocks.stop()
     barrier()
     plan.sync()
-    ms = e0.elapsed_time(e1) / K
-    fwd_ms = float(np.mean([ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]))
-    inv_ms = float(np.mean([ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]))
-    if world > 1:
-        t = torch.tensor([ms, fwd_ms, inv_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, fwd_ms, inv_ms = [float(v) for v in t.tolist()]
+    ms, fwd_ms, inv_ms = max_over_ranks([ms, fwd_ms, inv_ms])
     value = world * F / (ms * 1e-3)
 
-    # end to end through the public API: pinned host batch in, result out
+    # end to end through the public API: pinned host batch in, result out, every step
     beta_pin = torch.from_numpy(beta_h).pin_memory()
     out_pin = torch.empty(beta_pin.shape, dtype=torch.float64).pin_memory()
     beta_d = torch.empty_like(beta)
@@ -259,26 +284,26 @@ def run_ours(args):
         out_pin.copy_(back, non_blocking=True)
     a1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = a0.elapsed_time(a1) / K
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks([a0.elapsed_time(a1) / K])[0]
     io_bytes = beta_pin.numel() * 8
+    del beta_pin, out_pin, beta_d
 
     flops, entries = program_flops(plan, F)
     achieved = flops / (fwd_ms * 1e-3) / 1e9
+    fp64 = w["precision"] == "fp64"
+    kname = "alt_forward_f64_kernel" if fp64 else "alt_forward_f32_kernel"
+    peak = FP64_PEAK_GFLOPS if fp64 else FP32_PEAK_GFLOPS
     line = {
         "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_of(w, world),
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if fp64 else "f32", "data": "synthetic", "config": config_of(w, world),
         "forward_ms": fwd_ms, "inverse_ms": inv_ms,
         "forward_fields_per_s": world * F / (fwd_ms * 1e-3), "inverse_fields_per_s": world * F / (inv_ms * 1e-3),
         "round_trip_rel_err": rt_err,
-        "roofline": {"kernel": "alt_forward_f64_kernel", "bound": "alu", "achieved": achieved,
-                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
-                     "traffic": None, "flops_per_launch": flops,
-                     "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (probe measured 1.197)"},
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic_for(kname, w["name"]), "flops_per_launch": flops,
+                     "peak_source": ("GB300 nominal FP64 1.25 TFLOP/s (FMA-chain probe: 1.197)" if fp64 else
+                                     "128 FP32 lanes x 2 FLOP x 152 SMs x 2.07 GHz (FMA-chain probe: 73.2)")},
         "e2e": {"value": world * F / (e2e_ms * 1e-3), "unit": "fields/s", "h2d_bytes_per_step": io_bytes,
                 "d2h_bytes_per_step": io_bytes},
         "gpu_launches": 2 * K,
@@ -290,6 +315,8 @@ def run_ours(args):
                             "dense": st["n_blocks_dense"], "dropped": st["n_blocks_dropped"]},
                  "max_rank": st["max_rank"]},
     }
+    if rank == 0 and world == 1 and not args.no_compare:
+        line["compare"] = compare(torch, sht, _lib, w, plan, beta, g, args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, frac = oracle_sample(N, beta_h[0], args.ref_stride)
         import oracle
@@ -303,6 +330,49 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def compare(torch, sht, _lib, w, plan, beta, g, args, stream):
+    """The FP64 IDBF path and the dense FP64 transform on the same GPU, one
+    field each (round trip), and the headline result's error against the FP64
+    IDBF path (itself within 1e-10 of the oracle, see the tests)."""
+    N = w["N"]
+    out = {}
+    K = max(3, args.steps // 2)
+    b1 = beta[:1].contiguous()
+    g1 = torch.empty((1, 4 * N - 1, 2 * N, 2), dtype=torch.float64, device="cuda")
+    r1 = torch.empty_like(b1)
+    p64 = sht.Plan(N, 1e-12, precision=_lib.SHT_FP64)
+    ms, f, i = time_steps(torch, p64, b1, g1, r1, K, 2, stream)
+    out["fp64_idbf"] = {"fields_per_s": 1e3 / ms, "forward_ms": f, "inverse_ms": i, "eps": 1e-12,
+                        "entries": p64.stats()["entries_total"]}
+    if w["precision"] != "fp64":
+        F = beta.shape[0]
+        ref = torch.empty_like(g)
+        p64.forward(beta, out=ref)
+        plan.forward(beta, out=g)
+        torch.cuda.synchronize()
+        d = (g - ref).reshape(F, -1).norm(dim=1) / ref.reshape(F, -1).norm(dim=1)
+        out["rel_err_vs_fp64_idbf"] = {"max": float(d.max()), "median": float(d.median()),
+                                       "fields": F, "per_field": [float(v) for v in d.tolist()]}
+        del ref
+    del p64
+    pd = sht.Plan(N, 1e-12, precision=_lib.SHT_FP64, flags=_lib.SHT_FLAG_DENSE)
+    ms, f, i = time_steps(torch, pd, b1, g1, r1, K, 2, stream)
+    out["dense_fp64"] = {"fields_per_s": 1e3 / ms, "forward_ms": f, "inverse_ms": i,
+                         "entries": pd.stats()["entries_total"]}
+    del pd
+    return out
+
+
+def traffic_for(kernel, workload_name):
+    """DRAM bytes per launch from a committed ncu capture of this kernel and workload, if any."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh).get(kernel, {}).get(workload_name)
+    except (OSError, ValueError):
+        return None
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,6 +382,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--ref-stride", type=int, default=4, help="oracle samples every n-th order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 IDBF and dense comparators")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -84,6 +84,9 @@ typedef struct {
 #define SHT_FLAG_FORCE_FACTOR 1 /* keep factored blocks even when larger than dense */
 #define SHT_FLAG_HOST_ONLY 2    /* build the program on the host only: no device
                                    upload; apply calls return SHT_ERR_UNSUPPORTED */
+#define SHT_FLAG_DENSE 4        /* no partition, trimming or factorisation: every
+                                   parity matrix is applied dense (the O(N^3)
+                                   transform, kept as a baseline)                */
 
 /* Plan statistics (Sec. 5 experiments: block counts, ranks, timings). */
 typedef struct {

@@ -20,6 +20,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error or 
 SHT_FP64, SHT_FP32, SHT_MIXED = 0, 1, 2
 SHT_FLAG_FORCE_FACTOR = 1
 SHT_FLAG_HOST_ONLY = 2
+SHT_FLAG_DENSE = 4
 SHT_EXPORT_UNITS, SHT_EXPORT_OPS, SHT_EXPORT_PHASES, SHT_EXPORT_FACTORS, SHT_EXPORT_ORDER = range(5)
 
 

@@ -22,6 +22,7 @@
 #include <new>
 #include <string>
 
+#include "apply_f32.cuh"
 #include "plan.hpp"
 
 using namespace sht;
@@ -287,6 +288,10 @@ struct sht_plan_s {
   unsigned int* d_counter = nullptr;
   sht_status latched = SHT_OK;
   bool host_only = false;
+  // FP32 many-field path (precision SHT_FP32 / SHT_MIXED)
+  float* d_fac32 = nullptr;
+  float* d_ws32 = nullptr;
+  int nslots32 = 0;
 };
 
 namespace {
@@ -309,6 +314,8 @@ void free_device(sht_plan_s* p) {
   cudaFree(p->d_w);
   cudaFree(p->d_ws);
   cudaFree(p->d_counter);
+  cudaFree(p->d_fac32);
+  cudaFree(p->d_ws32);
 }
 
 DevPlan dev_plan(const sht_plan_s* p) {
@@ -339,6 +346,24 @@ sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F,
     return s;
   }
   if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
+  if (p->prog.opts.precision != SHT_FP64) {
+    F32Plan f;
+    f.units = p->d_units;
+    f.ops = p->d_ops;
+    f.phase_tab = p->d_phase;
+    f.order = p->d_order;
+    f.fac = p->d_fac32;
+    f.w = p->d_w;
+    f.ws = p->d_ws32;
+    f.counter = p->d_counter;
+    f.N = p->prog.N;
+    f.nunits = 2 * p->prog.N;
+    f.max_rows = p->prog.max_rows;
+    const int groups = (F + kF32Fields - 1) / kF32Fields;
+    const int items32 = (single ? 1 : 2 * p->prog.N) * groups;
+    const int grid32 = std::min(p->nslots32, std::max(1, items32));
+    return launch_f32(f, fwd, in, out, F, single, m, grid32, st) == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
+  }
   const int items = single ? F : 2 * p->prog.N * F;
   const int grid = std::min(p->nslots, std::max(1, items));
   DevPlan d = dev_plan(p);
@@ -423,14 +448,23 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
   size_t ws = (size_t)p->nslots * P.max_rows * kRT * sizeof(double);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_ws), std::max<size_t>(ws, 8));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_counter), sizeof(unsigned int));
+  size_t ws32 = 0;
+  if (e == cudaSuccess && o.precision != SHT_FP64) {
+    std::vector<float> f32(P.factors.begin(), P.factors.end());
+    e = upload(&p->d_fac32, f32);
+    p->nslots32 = std::max(1, sms * f32_ctas_per_sm());
+    ws32 = (size_t)p->nslots32 * P.max_rows * kF32RT * sizeof(float);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_ws32), std::max<size_t>(ws32, 8));
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_device(p);
     delete p;
     return e == cudaErrorMemoryAllocation ? SHT_ERR_OOM : SHT_ERR_CUDA;
   }
-  p->prog.info.workspace_bytes = (int64_t)ws;
-  p->prog.info.factor_bytes = (int64_t)(P.factors.size() * sizeof(double));
+  p->prog.info.workspace_bytes = (int64_t)(ws + ws32);
+  p->prog.info.factor_bytes =
+      (int64_t)(P.factors.size() * (o.precision == SHT_FP64 ? sizeof(double) : sizeof(float)));
   p->prog.info.t_upload_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = p;
   return SHT_OK;

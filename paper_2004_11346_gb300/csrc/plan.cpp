@@ -505,10 +505,18 @@ static bool emit_idbf(UnitBuild& ub, const BlockCtx& b, int L, bool force) {
   return true;
 }
 
+// Dense block: one product per chunk of at most kDenseRows rows, so that a large
+// turning-point block spreads over several warps.  Every chunk accumulates
+// into the shared output rows (forward) and input rows (transposed).
+constexpr int kDenseRows = 64;
 static void emit_dense(UnitBuild& ub, const BlockCtx& b) {
   const ParityMatrix& P = *b.P;
-  int64_t off = put_block(ub, b.nr, b.nc, [&](int i, int j) { return b.K(i, j); });
-  add_op(ub, 0, b.nr, b.nc, off, P.xbase + b.j0, b.nc, 0, 0, P.ybase + b.i0, b.nr, 0, 0, OP_FWD_ACCUM | OP_BWD_ACCUM);
+  for (int r0 = 0; r0 < b.nr; r0 += kDenseRows) {
+    const int nr = std::min(kDenseRows, b.nr - r0);
+    int64_t off = put_block(ub, nr, b.nc, [&](int i, int j) { return b.K(r0 + i, j); });
+    add_op(ub, 0, nr, b.nc, off, P.xbase + b.j0, b.nc, 0, 0, P.ybase + b.i0 + r0, nr, 0, 0,
+           OP_FWD_ACCUM | OP_BWD_ACCUM);
+  }
   ub.n_dense += 1;
   ub.e_dense += (int64_t)b.nr * b.nc;
 }
@@ -651,6 +659,11 @@ static void partition(UnitBuild& ub, const ParityMatrix& P, const sht_opts& o, R
 static void build_parity(UnitBuild& ub, const ParityMatrix& P, const sht_opts& o, Rng& rng) {
   const int N = P.A->r, nc = P.A->c;
   if (nc == 0) return;
+  if (o.flags & SHT_FLAG_DENSE) {  // the unfactored O(N^3) transform: every entry, no trimming
+    BlockCtx b{&P, 0, N, 0, nc, &o, 0.0, &rng};
+    emit_dense(ub, b);
+    return;
+  }
   // Eq. nb: b row blocks of ~N/b rows, each holding all columns (nearly square)
   long b = std::lround((double)N / (double)nc);
   b = std::max(1L, std::min((long)N, b));
