@@ -139,6 +139,23 @@ sht_status alt_inverse(sht_plan_t plan, const double* g, double* beta, int F, vo
 sht_status alt_forward_m(sht_plan_t plan, int m, const double* beta_m, double* g_m, int F, void* stream);
 sht_status alt_inverse_m(sht_plan_t plan, int m, const double* g_m, double* beta_m, int F, void* stream);
 
+/* phi direction of the SHT (Eq. sht_fft), for every node and field:
+ *   synthesis f(theta_l, phi_j) = sum_{m=-(2N-1)}^{2N-1} g(m, theta_l) e^{i m phi_j},
+ *   analysis  g(m, theta_l) = (1/M) sum_j f(theta_l, phi_j) e^{-i m phi_j},
+ * phi_j = 2 pi (j + 1/2) / M, M = 4N-1 (exact inverse of each other).  g as
+ * for alt_forward (F x (4N-1) x 2N complex), f theta-major (F x 2N x (4N-1)).
+ * Arithmetic in FP64 for FP64 plans, else FP32.  SHT_ERR_UNSUPPORTED when one
+ * length-M transform does not fit in shared memory (FP64: N <= 3584). */
+sht_status sht_phi_synthesis(sht_plan_t plan, const double* g, double* f, int F, void* stream);
+sht_status sht_phi_analysis(sht_plan_t plan, const double* f, double* g, int F, void* stream);
+
+/* Full SHT (Eq. sht_re): forward = forward ALT then phi synthesis,
+ * coefficients beta (F x 4N^2) -> grid values f (F x 2N x (4N-1));
+ * inverse = phi analysis then inverse ALT.  The ALT values pass through the
+ * plan's workspace, max_fields fields at a time. */
+sht_status sht_forward(sht_plan_t plan, const double* beta, double* f, int F, void* stream);
+sht_status sht_inverse(sht_plan_t plan, const double* f, double* beta, int F, void* stream);
+
 /* Copy one of the plan's host-side program arrays into dst_host (caller-owned,
  * *bytes long); with dst_host == NULL only *bytes is set to the size needed.
  * Layouts are those of the library's internal program (units, ops, phase

@@ -139,5 +139,50 @@ class Plan:
         _lib.alt_inverse_m(self.handle, m, g_m.data_ptr(), b.data_ptr(), F, self._stream())
         return b
 
+    def phi_synthesis(self, g, out=None):
+        """f(theta_l, phi_j) from g(m, theta_l): (F, 4N-1, 2N, 2) -> (F, 2N, 4N-1, 2)."""
+        import torch
+        N = self.N
+        g = self._dev(g, (4 * N - 1, 2 * N, 2))
+        F = g.shape[0]
+        f = out if out is not None else torch.empty((F, 2 * N, 4 * N - 1, 2), dtype=torch.float64, device=g.device)
+        self._dev(f, (2 * N, 4 * N - 1, 2))
+        _lib.sht_phi_synthesis(self.handle, g.data_ptr(), f.data_ptr(), F, self._stream())
+        return f
+
+    def phi_analysis(self, f, out=None):
+        """g(m, theta_l) from f(theta_l, phi_j): (F, 2N, 4N-1, 2) -> (F, 4N-1, 2N, 2)."""
+        import torch
+        N = self.N
+        f = self._dev(f, (2 * N, 4 * N - 1, 2))
+        F = f.shape[0]
+        g = out if out is not None else torch.empty((F, 4 * N - 1, 2 * N, 2), dtype=torch.float64, device=f.device)
+        self._dev(g, (4 * N - 1, 2 * N, 2))
+        _lib.sht_phi_analysis(self.handle, f.data_ptr(), g.data_ptr(), F, self._stream())
+        return g
+
+    def sht_forward(self, beta, out=None):
+        """Full SHT: coefficients (F, 4N^2, 2) -> grid values (F, 2N, 4N-1, 2)."""
+        import torch
+        N = self.N
+        beta = self._dev(beta, (4 * N * N, 2))
+        F = beta.shape[0]
+        f = out if out is not None else torch.empty((F, 2 * N, 4 * N - 1, 2), dtype=torch.float64,
+                                                    device=beta.device)
+        self._dev(f, (2 * N, 4 * N - 1, 2))
+        _lib.sht_forward(self.handle, beta.data_ptr(), f.data_ptr(), F, self._stream())
+        return f
+
+    def sht_inverse(self, f, out=None):
+        """Inverse SHT: grid values (F, 2N, 4N-1, 2) -> coefficients (F, 4N^2, 2)."""
+        import torch
+        N = self.N
+        f = self._dev(f, (2 * N, 4 * N - 1, 2))
+        F = f.shape[0]
+        beta = out if out is not None else torch.empty((F, 4 * N * N, 2), dtype=torch.float64, device=f.device)
+        self._dev(beta, (4 * N * N, 2))
+        _lib.sht_inverse(self.handle, f.data_ptr(), beta.data_ptr(), F, self._stream())
+        return beta
+
     def sync(self):
         _lib.sht_sync(self.handle, self._stream())

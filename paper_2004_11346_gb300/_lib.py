@@ -80,7 +80,8 @@ _lib = None
 EXPORTED = [
     "sht_opts_default", "sht_plan_create", "sht_plan_destroy", "sht_plan_stats", "sht_plan_nodes",
     "sht_plan_export", "alt_forward", "alt_inverse", "alt_forward_m", "alt_inverse_m", "sht_sync",
-    "sht_status_str", "alt_forward_m_noalloc",
+    "sht_status_str", "alt_forward_m_noalloc", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
+    "sht_inverse",
 ]
 
 
@@ -102,7 +103,8 @@ def load(build: bool = True):
     lib.sht_plan_stats.argtypes = [vp, ctypes.POINTER(sht_plan_info)]
     lib.sht_plan_nodes.argtypes = [vp, vp, vp]
     lib.sht_plan_export.argtypes = [vp, i, vp, ctypes.POINTER(ctypes.c_size_t)]
-    for name in ("alt_forward", "alt_inverse"):
+    for name in ("alt_forward", "alt_inverse", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
+                 "sht_inverse"):
         getattr(lib, name).argtypes = [vp, vp, vp, i, vp]
     for name in ("alt_forward_m", "alt_inverse_m", "alt_forward_m_noalloc"):
         getattr(lib, name).argtypes = [vp, i, vp, vp, i, vp]
@@ -174,6 +176,22 @@ def alt_inverse_m(plan: int, m: int, g_m: int, beta_m: int, F: int, stream: int 
 
 def alt_forward_m_noalloc(plan: int, m: int, beta_m: int, g_m: int, F: int, stream: int = 0):
     check(load().alt_forward_m_noalloc(plan, m, beta_m, g_m, F, stream), "alt_forward_m_noalloc")
+
+
+def sht_phi_synthesis(plan: int, g: int, f: int, F: int, stream: int = 0):
+    check(load().sht_phi_synthesis(plan, g, f, F, stream), "sht_phi_synthesis")
+
+
+def sht_phi_analysis(plan: int, f: int, g: int, F: int, stream: int = 0):
+    check(load().sht_phi_analysis(plan, f, g, F, stream), "sht_phi_analysis")
+
+
+def sht_forward(plan: int, beta: int, f: int, F: int, stream: int = 0):
+    check(load().sht_forward(plan, beta, f, F, stream), "sht_forward")
+
+
+def sht_inverse(plan: int, f: int, beta: int, F: int, stream: int = 0):
+    check(load().sht_inverse(plan, f, beta, F, stream), "sht_inverse")
 
 
 def sht_sync(plan: int, stream: int = 0):

@@ -23,6 +23,7 @@
 #include <string>
 
 #include "apply_f32.cuh"
+#include "phi_dft.cuh"
 #include "plan.hpp"
 
 using namespace sht;
@@ -292,6 +293,12 @@ struct sht_plan_s {
   float* d_fac32 = nullptr;
   float* d_ws32 = nullptr;
   int nslots32 = 0;
+  // phi-direction DFT (FP64 tables for FP64 plans, FP32 otherwise) and the
+  // ALT-value workspace of sht_forward / sht_inverse (max_fields fields)
+  PhiTables<double> phi64;
+  PhiTables<float> phi32;
+  int phi_grid = 0;
+  double* d_gws = nullptr;
 };
 
 namespace {
@@ -316,6 +323,9 @@ void free_device(sht_plan_s* p) {
   cudaFree(p->d_counter);
   cudaFree(p->d_fac32);
   cudaFree(p->d_ws32);
+  cudaFree(p->d_gws);
+  p->phi64.release();
+  p->phi32.release();
 }
 
 DevPlan dev_plan(const sht_plan_s* p) {
@@ -372,6 +382,18 @@ sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F,
   else
     alt_inverse_f64_kernel<<<grid, kThreads, 0, st>>>(d, in, out, F, single, m);
   return cudaGetLastError() == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
+}
+
+sht_status launch_phi(sht_plan_s* p, const double* in, double* out, int F, bool analysis, cudaStream_t st) {
+  if (p->host_only) return SHT_ERR_UNSUPPORTED;
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return SHT_ERR_ARG;
+  if ((int64_t)F * 2 * p->prog.N > (int64_t)1 << 30) return SHT_ERR_ARG;
+  if (p->phi_grid < 1) return SHT_ERR_UNSUPPORTED;
+  const int rows = 2 * p->prog.N * F;
+  const int grid = std::max(1, std::min(p->phi_grid, rows));
+  cudaError_t e = p->prog.opts.precision == SHT_FP64 ? p->phi64.launch(in, out, F, analysis, grid, st)
+                                                     : p->phi32.launch(in, out, F, analysis, grid, st);
+  return e == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
 }
 
 }  // namespace
@@ -456,13 +478,27 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
     ws32 = (size_t)p->nslots32 * P.max_rows * kF32RT * sizeof(float);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_ws32), std::max<size_t>(ws32, 8));
   }
+  size_t gws = 0;
+  if (e == cudaSuccess) {
+    const bool ok = o.precision == SHT_FP64 ? p->phi64.build(N) : p->phi32.build(N);
+    if (!ok) e = cudaErrorMemoryAllocation;
+    const size_t smem = o.precision == SHT_FP64 ? p->phi64.smem_bytes() : p->phi32.smem_bytes();
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    const int per_sm = smem > 0 && (size_t)optin >= smem ? std::max(1, (int)((size_t)optin / smem)) : 0;
+    p->phi_grid = sms * std::min(per_sm, 4);  // 0: transform length too long for shared memory
+  }
+  if (e == cudaSuccess) {
+    gws = (size_t)o.max_fields * (4 * (size_t)N - 1) * 2 * N * 2 * sizeof(double);
+    e = cudaMalloc(reinterpret_cast<void**>(&p->d_gws), gws);
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_device(p);
     delete p;
     return e == cudaErrorMemoryAllocation ? SHT_ERR_OOM : SHT_ERR_CUDA;
   }
-  p->prog.info.workspace_bytes = (int64_t)(ws + ws32);
+  p->prog.info.workspace_bytes = (int64_t)(ws + ws32 + gws);
   p->prog.info.factor_bytes =
       (int64_t)(P.factors.size() * (o.precision == SHT_FP64 ? sizeof(double) : sizeof(float)));
   p->prog.info.t_upload_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -541,6 +577,50 @@ sht_status alt_inverse_m(sht_plan_t p, int m, const double* g_m, double* beta_m,
   if (F == 0) return SHT_OK;
   if (!beta_m || !g_m) return SHT_ERR_ARG;
   return launch(p, false, g_m, beta_m, F, 1, m, static_cast<cudaStream_t>(stream));
+}
+
+sht_status sht_phi_synthesis(sht_plan_t p, const double* g, double* f, int F, void* stream) {
+  if (!p || F < 0) return SHT_ERR_ARG;
+  if (F == 0) return SHT_OK;
+  if (!g || !f) return SHT_ERR_ARG;
+  return launch_phi(p, g, f, F, false, static_cast<cudaStream_t>(stream));
+}
+
+sht_status sht_phi_analysis(sht_plan_t p, const double* f, double* g, int F, void* stream) {
+  if (!p || F < 0) return SHT_ERR_ARG;
+  if (F == 0) return SHT_OK;
+  if (!g || !f) return SHT_ERR_ARG;
+  return launch_phi(p, f, g, F, true, static_cast<cudaStream_t>(stream));
+}
+
+sht_status sht_forward(sht_plan_t p, const double* beta, double* f, int F, void* stream) {
+  if (!p || F < 0) return SHT_ERR_ARG;
+  if (F == 0) return SHT_OK;
+  if (!beta || !f) return SHT_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t N = p->prog.N, ncoef = 4 * N * N * 2, nval = (4 * N - 1) * 2 * N * 2;
+  for (int f0 = 0; f0 < F; f0 += p->prog.opts.max_fields) {
+    const int n = std::min(F - f0, p->prog.opts.max_fields);
+    sht_status s = launch(p, true, beta + f0 * ncoef, p->d_gws, n, 0, 0, st);
+    if (s == SHT_OK) s = launch_phi(p, p->d_gws, f + f0 * nval, n, false, st);
+    if (s != SHT_OK) return s;
+  }
+  return SHT_OK;
+}
+
+sht_status sht_inverse(sht_plan_t p, const double* f, double* beta, int F, void* stream) {
+  if (!p || F < 0) return SHT_ERR_ARG;
+  if (F == 0) return SHT_OK;
+  if (!beta || !f) return SHT_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t N = p->prog.N, ncoef = 4 * N * N * 2, nval = (4 * N - 1) * 2 * N * 2;
+  for (int f0 = 0; f0 < F; f0 += p->prog.opts.max_fields) {
+    const int n = std::min(F - f0, p->prog.opts.max_fields);
+    sht_status s = launch_phi(p, f + f0 * nval, p->d_gws, n, true, st);
+    if (s == SHT_OK) s = launch(p, false, p->d_gws, beta + f0 * ncoef, n, 0, 0, st);
+    if (s != SHT_OK) return s;
+  }
+  return SHT_OK;
 }
 
 sht_status sht_sync(sht_plan_t p, void* stream) {
