@@ -289,21 +289,16 @@ def run_ours(args):
     del beta_pin, out_pin, beta_d
 
     flops, entries = program_flops(plan, F)
-    achieved = flops / (fwd_ms * 1e-3) / 1e9
-    fp64 = w["precision"] == "fp64"
-    kname = "alt_forward_f64_kernel" if fp64 else "alt_forward_f32_kernel"
-    peak = FP64_PEAK_GFLOPS if fp64 else FP32_PEAK_GFLOPS
+    roof = roofline(plan, w, F, flops, fwd_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if fp64 else "f32", "data": "synthetic", "config": config_of(w, world),
+        "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "bf16x3 split, f32 accumulate"}[w["precision"]],
+        "data": "synthetic", "config": config_of(w, world),
         "forward_ms": fwd_ms, "inverse_ms": inv_ms,
         "forward_fields_per_s": world * F / (fwd_ms * 1e-3), "inverse_fields_per_s": world * F / (inv_ms * 1e-3),
         "round_trip_rel_err": rt_err,
-        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic_for(kname, w["name"]), "flops_per_launch": flops,
-                     "peak_source": ("GB300 nominal FP64 1.25 TFLOP/s (FMA-chain probe: 1.197)" if fp64 else
-                                     "128 FP32 lanes x 2 FLOP x 152 SMs x 2.07 GHz (FMA-chain probe: 73.2)")},
+        "roofline": roof,
         "e2e": {"value": world * F / (e2e_ms * 1e-3), "unit": "fields/s", "h2d_bytes_per_step": io_bytes,
                 "d2h_bytes_per_step": io_bytes},
         "gpu_launches": 2 * K,
@@ -361,6 +356,68 @@ def compare(torch, sht, _lib, w, plan, beta, g, args, stream):
                          "entries": pd.stats()["entries_total"]}
     del pd
     return out
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm": float(d["hbm_gbs"]), "bf16": float(d["bf16_tflops"]),
+                "bf16_sustained": float(d["bf16_tflops_sustained"]), "source": "measured"}
+    except (OSError, ValueError, KeyError):
+        return {"hbm": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
+
+
+def _r16(v):
+    return (v + 15) & ~15
+
+
+def tc_image_bytes(mo, ni):
+    """Bytes of the split-BF16 (3 pieces) operand image of one mo x ni block."""
+    if mo <= 0 or ni <= 0:
+        return 0
+    nK = (ni + 63) // 64
+    kp = 64 * (nK - 1) + _r16(ni - 64 * (nK - 1))
+    nT = (mo + 127) // 128
+    np_ = 128 * (nT - 1) + _r16(mo - 128 * (nT - 1))
+    return 2 * 3 * np_ * kp
+
+
+def roofline(plan, w, F, flops, fwd_ms):
+    """Roofline of the dominant (forward) kernel: algorithmic FLOPs and bytes per launch."""
+    N = w["N"]
+    io_bytes = F * (4 * N * N + (4 * N - 1) * 2 * N) * 16  # beta read + g written, FP64 complex
+    prec = w["precision"]
+    t = fwd_ms * 1e-3
+    if prec == "fp64":
+        kname, peak, src = "alt_forward_f64_kernel", FP64_PEAK_GFLOPS, \
+            "GB300 nominal FP64 1.25 TFLOP/s (FMA-chain probe: 1.197)"
+        return {"kernel": kname, "bound": "alu", "achieved": flops / t / 1e9, "peak": peak, "unit": "GFLOP/s",
+                "frac": flops / t / 1e9 / peak, "traffic": traffic_for(kname, w["name"]),
+                "flops_per_launch": flops, "peak_source": src}
+    if prec == "fp32":
+        kname, peak = "alt_forward_f32_kernel", FP32_PEAK_GFLOPS
+        return {"kernel": kname, "bound": "alu", "achieved": flops / t / 1e9, "peak": peak, "unit": "GFLOP/s",
+                "frac": flops / t / 1e9 / peak, "traffic": traffic_for(kname, w["name"]), "flops_per_launch": flops,
+                "peak_source": "128 FP32 lanes x 2 FLOP x 152 SMs x 2.07 GHz (FMA-chain probe: 73.2)"}
+    # tensor-core split-BF16 path: each product costs 6 BF16 MMAs
+    pk = measured_peaks()
+    ops = plan.program(parts=("ops",))["ops"]
+    img = sum(tc_image_bytes(int(mo), int(ni)) for mo, ni in zip(ops["mo"], ops["ni"]))
+    algo_bytes = img + io_bytes
+    tens_peak = pk["bf16_sustained"] / 6.0 * 1e3  # GFLOP/s of FP32-quality split products
+    t_frac = flops / t / 1e9 / tens_peak
+    h_frac = algo_bytes / t / 1e9 / pk["hbm"]
+    kname = "alt_tc_kernel"
+    base = {"kernel": kname, "traffic": traffic_for(kname, w["name"]), "flops_per_launch": flops,
+            "bytes_per_launch": algo_bytes, "factor_image_bytes": img, "io_bytes": io_bytes}
+    if t_frac >= h_frac:
+        return {**base, "bound": "tensor", "achieved": flops / t / 1e12, "peak": tens_peak / 1e3, "unit": "TFLOP/s",
+                "frac": t_frac, "peak_source": f"{pk['source']} bf16 sustained {pk['bf16_sustained']} TFLOP/s / 6 "
+                                               f"MMAs per split product; HBM frac {h_frac:.3f}"}
+    return {**base, "bound": "hbm", "achieved": algo_bytes / t / 1e9, "peak": pk["hbm"], "unit": "GB/s",
+            "frac": h_frac, "peak_source": f"{pk['source']} HBM copy {pk['hbm']} GB/s; tensor frac {t_frac:.3f}"}
 
 
 def traffic_for(kernel, workload_name):

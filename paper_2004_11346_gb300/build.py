@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libsht.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 HOST_SRC = ["plan.cpp"]
-CUDA_SRC = ["apply.cu", "apply_f32.cu", "phi_dft.cu"]
+CUDA_SRC = ["apply.cu", "apply_f32.cu", "apply_tc.cu", "phi_dft.cu"]
 
 
 def cuda_home() -> str:
@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, f + ".o")
         objs.append(o)
         jobs.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "--expt-relaxed-constexpr", *inc, "-c", os.path.join(CSRC, f), "-o", o])
+                     "--expt-relaxed-constexpr", "-Xcompiler", "-fopenmp", *inc, "-c", os.path.join(CSRC, f), "-o", o])
     procs = [subprocess.Popen(j, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for j in jobs]
     errors = []
     for j, p in zip(jobs, procs):

@@ -23,6 +23,7 @@
 #include <string>
 
 #include "apply_f32.cuh"
+#include "apply_tc.cuh"
 #include "phi_dft.cuh"
 #include "plan.hpp"
 
@@ -299,6 +300,12 @@ struct sht_plan_s {
   PhiTables<float> phi32;
   int phi_grid = 0;
   double* d_gws = nullptr;
+  // tensor-core path (precision SHT_MIXED): split-BF16 operand images
+  uint16_t* d_img = nullptr;
+  int64_t* d_imgoff = nullptr;
+  float* d_wstc = nullptr;
+  int* d_err = nullptr;
+  int nslots_tc = 0;
 };
 
 namespace {
@@ -324,6 +331,10 @@ void free_device(sht_plan_s* p) {
   cudaFree(p->d_fac32);
   cudaFree(p->d_ws32);
   cudaFree(p->d_gws);
+  cudaFree(p->d_img);
+  cudaFree(p->d_imgoff);
+  cudaFree(p->d_wstc);
+  cudaFree(p->d_err);
   p->phi64.release();
   p->phi32.release();
 }
@@ -356,7 +367,27 @@ sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F,
     return s;
   }
   if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
-  if (p->prog.opts.precision != SHT_FP64) {
+  if (p->prog.opts.precision == SHT_MIXED) {
+    TcPlan t;
+    t.units = p->d_units;
+    t.ops = p->d_ops;
+    t.phase_tab = p->d_phase;
+    t.order = p->d_order;
+    t.img = p->d_img;
+    t.img_off = p->d_imgoff;
+    t.w = p->d_w;
+    t.ws = p->d_wstc;
+    t.counter = p->d_counter;
+    t.err = p->d_err;
+    t.N = p->prog.N;
+    t.nunits = 2 * p->prog.N;
+    t.max_rows = p->prog.max_rows;
+    const int groups = (F + kTcFields - 1) / kTcFields;
+    const int items = (single ? 1 : 2 * p->prog.N) * groups;
+    const int grid_tc = std::min(p->nslots_tc, std::max(1, items));
+    return launch_tc(t, fwd, in, out, F, single, m, grid_tc, st) == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
+  }
+  if (p->prog.opts.precision == SHT_FP32) {
     F32Plan f;
     f.units = p->d_units;
     f.ops = p->d_ops;
@@ -471,7 +502,20 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_ws), std::max<size_t>(ws, 8));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_counter), sizeof(unsigned int));
   size_t ws32 = 0;
-  if (e == cudaSuccess && o.precision != SHT_FP64) {
+  if (e == cudaSuccess && o.precision == SHT_MIXED) {
+    std::vector<uint16_t> img;
+    std::vector<int64_t> off;
+    tc_build_images(P.ops, P.factors, img, off);
+    e = upload(&p->d_img, img);
+    if (e == cudaSuccess) e = upload(&p->d_imgoff, off);
+    p->nslots_tc = std::max(1, sms * tc_ctas_per_sm());
+    ws32 = (size_t)p->nslots_tc * P.max_rows * kTcR * sizeof(float);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_wstc), std::max<size_t>(ws32, 8));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+    p->prog.info.factor_bytes = (int64_t)(img.size() * sizeof(uint16_t));
+  }
+  if (e == cudaSuccess && o.precision == SHT_FP32) {
     std::vector<float> f32(P.factors.begin(), P.factors.end());
     e = upload(&p->d_fac32, f32);
     p->nslots32 = std::max(1, sms * f32_ctas_per_sm());
@@ -499,8 +543,9 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
     return e == cudaErrorMemoryAllocation ? SHT_ERR_OOM : SHT_ERR_CUDA;
   }
   p->prog.info.workspace_bytes = (int64_t)(ws + ws32 + gws);
-  p->prog.info.factor_bytes =
-      (int64_t)(P.factors.size() * (o.precision == SHT_FP64 ? sizeof(double) : sizeof(float)));
+  if (o.precision != SHT_MIXED)
+    p->prog.info.factor_bytes =
+        (int64_t)(P.factors.size() * (o.precision == SHT_FP64 ? sizeof(double) : sizeof(float)));
   p->prog.info.t_upload_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = p;
   return SHT_OK;
@@ -627,6 +672,14 @@ sht_status sht_sync(sht_plan_t p, void* stream) {
   if (!p) return SHT_ERR_ARG;
   if (p->host_only) return SHT_ERR_UNSUPPORTED;
   if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return SHT_ERR_CUDA;
+  if (p->d_err) {
+    int h = 0;
+    if (cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SHT_ERR_CUDA;
+    if (h) {
+      cudaMemset(p->d_err, 0, sizeof(int));
+      return SHT_ERR_TIMEOUT;
+    }
+  }
   sht_status s = p->latched;
   p->latched = SHT_OK;
   return s;

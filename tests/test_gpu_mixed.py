@@ -38,6 +38,8 @@ PLANS = {
     "N64_fp32": (64, dict(precision=_lib.SHT_FP32)),
     "N96_fp32_forced": (96, dict(precision=_lib.SHT_FP32, n0=16, n_leaf=8, flags=_lib.SHT_FLAG_FORCE_FACTOR)),
     "N128_mixed": (128, dict(precision=_lib.SHT_MIXED, n0=32, n_leaf=16)),
+    "N96_mixed_forced": (96, dict(precision=_lib.SHT_MIXED, n0=16, n_leaf=8, flags=_lib.SHT_FLAG_FORCE_FACTOR)),
+    "N200_mixed": (200, dict(precision=_lib.SHT_MIXED)),
 }
 
 
@@ -47,7 +49,7 @@ def plans():
 
 
 @pytest.mark.parametrize("name", list(PLANS))
-@pytest.mark.parametrize("F", [1, 8, 11])
+@pytest.mark.parametrize("F", [1, 8, 11, 40])
 def test_forward(plans, name, F):
     p = plans[name]
     N = p.N
@@ -72,8 +74,9 @@ def test_inverse(plans, name):
 
 
 @pytest.mark.parametrize("m", [0, 3, -3, 191, -191])
-def test_single_order(plans, m):
-    p = plans["N96_fp32_forced"]
+@pytest.mark.parametrize("name", ["N96_fp32_forced", "N96_mixed_forced"])
+def test_single_order(plans, m, name):
+    p = plans[name]
     N = p.N
     F = 10
     rng = np.random.default_rng(abs(m))
@@ -90,7 +93,8 @@ def test_single_order(plans, m):
     assert np.all(rel_err(bo.cpu().numpy(), ref) <= TOL_MIXED)
 
 
-@pytest.mark.parametrize("prec,tol", [(_lib.SHT_FP64, TOL_FP64), (_lib.SHT_FP32, TOL_MIXED)])
+@pytest.mark.parametrize("prec,tol", [(_lib.SHT_FP64, TOL_FP64), (_lib.SHT_FP32, TOL_MIXED),
+                                      (_lib.SHT_MIXED, TOL_MIXED)])
 def test_dense_plan(prec, tol):
     N = 48
     p = sht.Plan(N, 1e-12, precision=prec, flags=_lib.SHT_FLAG_DENSE)
