@@ -225,44 +225,54 @@ __device__ bool tc_op(const TcPlan& p, const Smem& sm, uint32_t taddr, uint32_t&
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Np >> 3) << 17) | (8u << 24);
     for (int c = 0; c < nK; ++c) {
       const int Kc = min(kTcKC, KK - kTcKC * c), Kp = (Kc + 15) & ~15;
-      // stage A = in^T: thread owns right-hand side r = tid, 8 K values per task
-      for (int k8 = 0; k8 < Kp / 8; ++k8) {
-        uint32_t h[3][4];
-#pragma unroll
-        for (int kk = 0; kk < 8; kk += 2) {
-          float v2[2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int j = kTcKC * c + 8 * k8 + kk + e;
-            v2[e] = j < KK ? __ldcg(vec + (size_t)seg_row(j, ioff, ilen) * kTcR + tid) : 0.f;
-          }
-          uint16_t q0[2], q1[2], q2[2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            float v = v2[e];
-            q0[e] = f2bf(v);
-            v -= bf2f(q0[e]);
-            q1[e] = f2bf(v);
-            v -= bf2f(q1[e]);
-            q2[e] = f2bf(v);
-          }
-          h[0][kk / 2] = (uint32_t)q0[0] | ((uint32_t)q0[1] << 16);
-          h[1][kk / 2] = (uint32_t)q1[0] | ((uint32_t)q1[1] << 16);
-          h[2][kk / 2] = (uint32_t)q2[0] | ((uint32_t)q2[1] << 16);
-        }
-        const int o = ((k8 * (kTcR / 8) + (tid >> 3)) * 64 + (tid & 7) * 8);
-#pragma unroll
-        for (int pc = 0; pc < 3; ++pc)
-          *reinterpret_cast<uint4*>(sm.A + pc * kPieceA + o) = make_uint4(h[pc][0], h[pc][1], h[pc][2], h[pc][3]);
-      }
-      // stage B: the image chunk (3 pieces) is contiguous
+      // stage B first (asynchronous 16-byte copies of the contiguous image chunk)
       {
         const uint16_t* src = img + (size_t)t * 384 * kp_tot + (size_t)Np * (192 * c);
         const int n16 = 3 * Np * Kp / 8;
-        const uint4* s4 = reinterpret_cast<const uint4*>(src);
-        uint4* d4 = reinterpret_cast<uint4*>(sm.B);
-        for (int q = tid; q < n16; q += kTcThreads) d4[q] = __ldg(s4 + q);
+        const uint32_t dB = bBase;
+        for (int q = tid; q < n16; q += kTcThreads)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dB + 16u * q), "l"(src + 8 * q)
+                       : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
       }
+      // stage A = in^T: thread owns right-hand side r = tid; all of its K values
+      // of the chunk are loaded before any is used, so the loads overlap
+      {
+        float xv[kTcKC];
+#pragma unroll
+        for (int kk = 0; kk < kTcKC; ++kk) {
+          const int j = kTcKC * c + kk;
+          xv[kk] = (kk < Kp && j < KK) ? __ldcg(vec + (size_t)seg_row(j, ioff, ilen) * kTcR + tid) : 0.f;
+        }
+#pragma unroll
+        for (int k8 = 0; k8 < kTcKC / 8; ++k8) {
+          if (k8 < Kp / 8) {
+            uint32_t h[3][4];
+#pragma unroll
+            for (int kk = 0; kk < 8; kk += 2) {
+              uint16_t q0[2], q1[2], q2[2];
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                float v = xv[8 * k8 + kk + e];
+                q0[e] = f2bf(v);
+                v -= bf2f(q0[e]);
+                q1[e] = f2bf(v);
+                v -= bf2f(q1[e]);
+                q2[e] = f2bf(v);
+              }
+              h[0][kk / 2] = (uint32_t)q0[0] | ((uint32_t)q0[1] << 16);
+              h[1][kk / 2] = (uint32_t)q1[0] | ((uint32_t)q1[1] << 16);
+              h[2][kk / 2] = (uint32_t)q2[0] | ((uint32_t)q2[1] << 16);
+            }
+            const int o = ((k8 * (kTcR / 8) + (tid >> 3)) * 64 + (tid & 7) * 8);
+#pragma unroll
+            for (int pc = 0; pc < 3; ++pc)
+              *reinterpret_cast<uint4*>(sm.A + pc * kPieceA + o) =
+                  make_uint4(h[pc][0], h[pc][1], h[pc][2], h[pc][3]);
+          }
+        }
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
@@ -374,12 +384,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
     const int nx = u.nce + u.nco;
     if (fwd) {
       // gather X: row t, column 4 fl + 2 s + c; zero Y
-      for (int idx = tid; idx < nx * kTcR; idx += kTcThreads) {
-        const int t = idx / kTcR, col = idx % kTcR;
-        const int fl = col >> 2, s = (col >> 1) & 1, cc = col & 1;
+      {
+        // column tid of every X row: field fl, sign s, Re/Im cc are fixed per thread
+        const int fl = tid >> 2, s = (tid >> 1) & 1, cc = tid & 1;
         const double* b = coef_base(in, N, am, grp * kTcFields + fl, s, F, single, msingle);
-        const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
-        __stcg(vec + (size_t)t * kTcR + col, b ? (float)__ldg(b + 2 * kk + cc) : 0.f);
+        for (int t0 = 0; t0 < nx; t0 += 8) {
+          float v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int t = t0 + e;
+            const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
+            v[e] = (b && t < nx) ? (float)__ldg(b + 2 * kk + cc) : 0.f;
+          }
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (t0 + e < nx) __stcg(vec + (size_t)(t0 + e) * kTcR + tid, v[e]);
+        }
       }
       for (int idx = tid; idx < 2 * N * kTcR; idx += kTcThreads) __stcg(vec + (size_t)u.ye * kTcR + idx, 0.f);
     } else {
@@ -452,11 +472,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
 size_t tc_smem_bytes() { return kSmemTotal; }
 
 int tc_ctas_per_sm() {
-  int n = 0;
-  cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, alt_tc_kernel, kTcThreads, kSmemTotal);
-  // each resident CTA holds kTmemCols of the 512 tensor-memory columns
-  return std::max(1, std::min(n, 512 / kTmemCols));
+  // resident CTAs per SM from the three limits: shared memory (with the
+  // driver's 1 KB per CTA), registers, and the 512 tensor-memory columns
+  int dev = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaFuncAttributes fa;
+  int regs = 255;
+  if (cudaFuncGetAttributes(&fa, alt_tc_kernel) == cudaSuccess) regs = fa.numRegs;
+  const int by_smem = (int)(smem_sm / (kSmemTotal + 1024));
+  const int by_regs = 65536 / (((regs + 7) & ~7) * kTcThreads);
+  const int by_tmem = 512 / kTmemCols;
+  return std::max(1, std::min(std::min(by_smem, by_regs), by_tmem));
 }
 
 cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, int F, int single, int m, int grid,
