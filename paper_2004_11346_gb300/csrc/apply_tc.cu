@@ -5,20 +5,27 @@
 // Every block product of the apply program, out (+)= B in, is computed
 // transposed, out^T = in^T B^T, so that the 128 right-hand sides fill the MMA
 // M dimension and the block's rows are N (tiles of <= 128, padded to 16):
-//   A operand = in^T (128 x K): staged from the FP32 vector rows, each value
-//               split into three BF16 pieces a0 + a1 + a2 (8 bits each);
+//   A operand = in^T (128 x K, MN-major): the op's input rows, kept in the
+//               scratch as three BF16 pieces a0 + a1 + a2 (8 bits each) of
+//               every value, so staging is a plain asynchronous copy;
 //   B operand = B (N x K, K-major): precomputed split-BF16 image b0 + b1 + b2;
 //   D         = 128 x N FP32 accumulator in tensor memory.
+// The CTA is warp-specialised and persistent (one per SM): a producer warp
+// streams (op, tile, 32-wide K chunk) operand stages into a 4-deep shared
+// memory ring with cp.async; an MMA warp issues the tensor-core products into
+// two double-buffered TMEM accumulator pairs; four epilogue warps drain the
+// accumulators, split the results into BF16 pieces for the next level (or add
+// them in FP32 into the shared output rows), and run the gather and the
+// parity fold.  Ops of one phase read only rows written by earlier phases: the
+// producer starts a phase after the epilogue has counted every earlier tile.
 // Per 16-wide K step six MMAs accumulate a_p b_q for p + q <= 2, which keeps
 // every product to about 2^-24 relative error (FP32 quality); a0 b0 and the
 // five smaller cross products go to two separate accumulators that the
 // epilogue adds in FP32.  Operands sit
 // in shared memory in the canonical no-swizzle K-major layout (8 x 16-byte
 // core matrices; LBO = stride between core matrices along K, SBO = along M/N).
-// One thread issues the MMAs and commits them to an mbarrier; all waits are
-// bounded and report an error status instead of hanging.  The epilogue reads
-// D with tcgen05.ld (warp w owns right-hand sides 32w..32w+31), so every
-// output row is written by 32 lanes as one coalesced 128-byte segment.
+// All waits are bounded: a wait that runs out sets an error flag, every role
+// stops, and the host reports SHT_ERR_TIMEOUT.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -110,13 +117,25 @@ void tc_build_images(const std::vector<Op>& ops, const std::vector<double>& fact
 // ---------------------------------------------------------------- device side
 namespace {
 
-constexpr int kPieceA = kTcR * kTcKC;    // elements per A piece (16 KB)
-constexpr int kPieceB = kTcNT * kTcKC;   // elements per B piece, largest
-constexpr size_t kSmemA = 3 * kPieceA * 2;
-constexpr size_t kSmemB = 3 * kPieceB * 2;
-constexpr size_t kSmemTotal = kSmemA + kSmemB + 1024 /*alignment*/ + 64;
-constexpr long kWaitLimit = 1L << 24;
-constexpr int kTmemCols = 2 * kTcNT;     // hi and lo accumulators, 128 x 128 FP32 each
+constexpr int kStages = 4;
+constexpr int kPieceA = kTcR * kTcKC * 2;      // bytes of one A piece in a stage (8 KB)
+constexpr int kStageA = 3 * kPieceA;           // 24 KB
+constexpr int kStageB = 3 * kTcNT * kTcKC * 2; // 24 KB (largest N tile)
+constexpr int kStageBytes = kStageA + kStageB;
+constexpr int kTmemCols = 512;                 // 2 accumulator pairs (hi, lo) x 128 columns
+constexpr long kWaitLimit = 1L << 22;   // try_wait polls per bounded wait
+
+struct Ctl {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t accf[2];
+  uint64_t acce[2];
+  uint32_t taddr;
+  int abort;
+  int gathered;    // items whose gather is complete
+  int done_tiles;  // tiles whose epilogue is complete (all items so far)
+};
+constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + sizeof(Ctl) + 1024;
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -131,6 +150,10 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s32(bar))
+               : "memory");
+}
 
 __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
   asm volatile(
@@ -141,11 +164,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
         "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
         "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Bounded wait for mbarrier phase `parity`; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s32(bar)) : "memory");
+}
+// Bounded wait for the phase with the given parity; on running out, flag an abort.
+__device__ __forceinline__ bool mbar_wait(Ctl* ctl, uint64_t* bar, uint32_t parity) {
   for (long it = 0; it < kWaitLimit; ++it) {
     uint32_t ok;
     asm volatile(
@@ -154,9 +183,33 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(s32(bar)), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((it & 255) == 255 && *((volatile int*)&ctl->abort)) return false;
   }
+  *((volatile int*)&ctl->abort) = 1;
   return false;
 }
+// Bounded wait until a shared counter reaches `target`.
+__device__ __forceinline__ bool counter_wait(Ctl* ctl, int* ctr, int target) {
+  for (long it = 0; it < kWaitLimit; ++it) {
+    if (*((volatile int*)ctr) >= target) {
+      __threadfence_block();
+      return true;
+    }
+    if (*((volatile int*)&ctl->abort)) return false;
+    __nanosleep(256);
+  }
+  *((volatile int*)&ctl->abort) = 1;
+  return false;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(s32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __device__ __forceinline__ long coef_offset(long N, long m) {
   long a = m < 0 ? -m : m;
@@ -168,7 +221,6 @@ __device__ __forceinline__ long order_slot(long m) { return m == 0 ? 0 : (m > 0 
 __device__ __forceinline__ int seg_row(int t, const int32_t off[2], const int32_t len[2]) {
   return t < len[0] ? off[0] + t : off[1] + (t - len[0]);
 }
-
 __device__ __forceinline__ const double* coef_base(const double* beta, int N, int am, int f, int s, int F,
                                                    int single, int msingle) {
   if (f >= F || (s == 1 && am == 0)) return nullptr;
@@ -188,155 +240,45 @@ __device__ __forceinline__ const double* value_base(const double* g, int N, int 
   return g + 2 * ((long)f * (4L * N - 1) * 2 * N + order_slot(s == 0 ? am : -am) * 2 * N);
 }
 
-__device__ __forceinline__ uint16_t f2bf(float f) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(f));
-}
+__device__ __forceinline__ uint16_t f2bf(float f) { return __bfloat16_as_ushort(__float2bfloat16_rn(f)); }
 __device__ __forceinline__ float bf2f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
-struct Smem {
-  uint16_t* A;
-  uint16_t* B;
-  uint64_t* bar;
-  uint32_t* taddr;
-  int* flag;
-};
+// value -> three BF16 pieces at column `col` of a scratch row
+__device__ __forceinline__ void put_pieces(unsigned char* row, int col, float v) {
+  unsigned short* p = reinterpret_cast<unsigned short*>(row) + col;
+  const uint16_t h0 = f2bf(v);
+  v -= bf2f(h0);
+  const uint16_t h1 = f2bf(v);
+  v -= bf2f(h1);
+  const uint16_t h2 = f2bf(v);
+  __stcg(p, (unsigned short)h0);
+  __stcg(p + kTcR, (unsigned short)h1);
+  __stcg(p + 2 * kTcR, (unsigned short)h2);
+}
+__device__ __forceinline__ float* fp32_at(unsigned char* row, int col) { return reinterpret_cast<float*>(row) + col; }
 
-// One block product, transposed onto the tensor cores.  Returns false when a
-// wait gave up (the caller stops).
-__device__ bool tc_op(const TcPlan& p, const Smem& sm, uint32_t taddr, uint32_t& phase, const Op& op, bool fwd,
-                      const uint16_t* img, float* vec) {
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int NN = fwd ? op.mo : op.ni, KK = fwd ? op.ni : op.mo;
-  const int32_t* ooff = fwd ? op.out_off : op.in_off;
-  const int32_t* olen = fwd ? op.out_len : op.in_len;
-  const bool accum = (op.flags & (fwd ? OP_FWD_ACCUM : OP_BWD_ACCUM)) != 0;
-  if (KK == 0) {  // empty product: the outputs are zero
-    if (!accum)
-      for (int i = 0; i < NN; ++i) __stcg(vec + (size_t)seg_row(i, ooff, olen) * kTcR + tid, 0.f);
-    return true;
-  }
-  const int32_t* ioff = fwd ? op.in_off : op.out_off;
-  const int32_t* ilen = fwd ? op.in_len : op.out_len;
-  const int nT = (NN + kTcNT - 1) / kTcNT, nK = (KK + kTcKC - 1) / kTcKC;
-  const int kp_tot = kTcKC * (nK - 1) + ((KK - kTcKC * (nK - 1) + 15) & ~15);
-  const uint32_t aBase = s32(sm.A), bBase = s32(sm.B);
-  for (int t = 0; t < nT; ++t) {
-    const int Nt = min(kTcNT, NN - kTcNT * t), Np = (Nt + 15) & ~15;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Np >> 3) << 17) | (8u << 24);
-    for (int c = 0; c < nK; ++c) {
-      const int Kc = min(kTcKC, KK - kTcKC * c), Kp = (Kc + 15) & ~15;
-      // stage B first (asynchronous 16-byte copies of the contiguous image chunk)
-      {
-        const uint16_t* src = img + (size_t)t * 384 * kp_tot + (size_t)Np * (192 * c);
-        const int n16 = 3 * Np * Kp / 8;
-        const uint32_t dB = bBase;
-        for (int q = tid; q < n16; q += kTcThreads)
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dB + 16u * q), "l"(src + 8 * q)
-                       : "memory");
-        asm volatile("cp.async.commit_group;" ::: "memory");
-      }
-      // stage A = in^T: thread owns right-hand side r = tid; all of its K values
-      // of the chunk are loaded before any is used, so the loads overlap
-      {
-        float xv[kTcKC];
-#pragma unroll
-        for (int kk = 0; kk < kTcKC; ++kk) {
-          const int j = kTcKC * c + kk;
-          xv[kk] = (kk < Kp && j < KK) ? __ldcg(vec + (size_t)seg_row(j, ioff, ilen) * kTcR + tid) : 0.f;
-        }
-#pragma unroll
-        for (int k8 = 0; k8 < kTcKC / 8; ++k8) {
-          if (k8 < Kp / 8) {
-            uint32_t h[3][4];
-#pragma unroll
-            for (int kk = 0; kk < 8; kk += 2) {
-              uint16_t q0[2], q1[2], q2[2];
-#pragma unroll
-              for (int e = 0; e < 2; ++e) {
-                float v = xv[8 * k8 + kk + e];
-                q0[e] = f2bf(v);
-                v -= bf2f(q0[e]);
-                q1[e] = f2bf(v);
-                v -= bf2f(q1[e]);
-                q2[e] = f2bf(v);
-              }
-              h[0][kk / 2] = (uint32_t)q0[0] | ((uint32_t)q0[1] << 16);
-              h[1][kk / 2] = (uint32_t)q1[0] | ((uint32_t)q1[1] << 16);
-              h[2][kk / 2] = (uint32_t)q2[0] | ((uint32_t)q2[1] << 16);
-            }
-            const int o = ((k8 * (kTcR / 8) + (tid >> 3)) * 64 + (tid & 7) * 8);
-#pragma unroll
-            for (int pc = 0; pc < 3; ++pc)
-              *reinterpret_cast<uint4*>(sm.A + pc * kPieceA + o) =
-                  make_uint4(h[pc][0], h[pc][1], h[pc][2], h[pc][3]);
-          }
-        }
-      }
-      asm volatile("cp.async.wait_all;" ::: "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t bPiece = (uint32_t)Np * Kp * 2;
-        const uint32_t bK = (uint32_t)(Np / 8) * 128;
-        for (int s = 0; s < Kp / 16; ++s) {
-          // a0 b0 into the "hi" accumulator, the five small cross products
-          // (p + q = 1, 2) into the "lo" accumulator: the lo sum is ~2^-8 of
-          // the hi sum, so its accumulation rounding stays negligible
-          int lo = 0;
-#pragma unroll
-          for (int pa = 0; pa < 3; ++pa)
-#pragma unroll
-            for (int pb = 0; pb < 3; ++pb) {
-              if (pa + pb > 2) continue;
-              const uint64_t ad = sdesc(aBase + pa * (kPieceA * 2) + s * 2 * 2048, 2048, 128);
-              const uint64_t bd = sdesc(bBase + pb * bPiece + s * 2 * bK, bK, 128);
-              if (pa + pb == 0) {
-                mma_bf16(taddr, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
-              } else {
-                mma_bf16(taddr + kTcNT, ad, bd, idesc, (c > 0 || s > 0 || lo > 0) ? 1u : 0u);
-                ++lo;
-              }
-            }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         s32(sm.bar))
-                     : "memory");
-      }
-      const bool ok = mbar_wait(sm.bar, phase);
-      phase ^= 1u;
-      if (!ok) *sm.flag = 1;
-      __syncthreads();
-      if (*sm.flag) return false;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: D[r][n] -> out row n, right-hand side r = 32 warp + lane
-    for (int c0 = 0; c0 < Nt; c0 += 32) {
-      uint32_t v[32], w[32];
-      tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-      tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(kTcNT + c0), w);
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int i = c0 + q;
-        if (i < Nt) {
-          float* dst = vec + (size_t)seg_row(kTcNT * t + i, ooff, olen) * kTcR + tid;
-          const float val = __uint_as_float(v[q]) + __uint_as_float(w[q]);
-          if (accum) atomicAdd(dst, val);
-          else __stcg(dst, val);
-        }
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-  }
-  return true;
+// Shape of one op in the requested direction.
+struct OpShape {
+  int NN, KK, nT, nK, kp_tot;
+};
+__device__ __forceinline__ OpShape op_shape(const Op& op, bool fwd) {
+  OpShape s;
+  s.NN = fwd ? op.mo : op.ni;
+  s.KK = fwd ? op.ni : op.mo;
+  s.nT = (s.NN + kTcNT - 1) / kTcNT;
+  s.nK = s.KK > 0 ? (s.KK + kTcKC - 1) / kTcKC : 0;
+  s.kp_tot = s.KK > 0 ? kTcKC * (s.nK - 1) + ((s.KK - kTcKC * (s.nK - 1) + 15) & ~15) : 0;
+  return s;
 }
 
-__device__ __forceinline__ int next_item(unsigned int* counter, int* s_item) {
-  __syncthreads();
-  if (threadIdx.x == 0) *s_item = (int)atomicAdd(counter, 1u);
-  __syncthreads();
-  return *s_item;
+struct Item {
+  int grp, am;
+};
+__device__ __forceinline__ Item item_of(const TcPlan& p, int it, int G, int single, int msingle) {
+  Item r;
+  r.grp = it % G;
+  r.am = single ? (msingle < 0 ? -msingle : msingle) : p.order[it / G];
+  return r;
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const double* __restrict__ in,
@@ -345,125 +287,281 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  Smem sm;
-  sm.A = reinterpret_cast<uint16_t*>(base);
-  sm.B = reinterpret_cast<uint16_t*>(base + kSmemA);
-  sm.bar = reinterpret_cast<uint64_t*>(base + kSmemA + kSmemB);
-  sm.taddr = reinterpret_cast<uint32_t*>(base + kSmemA + kSmemB + 8);
-  sm.flag = reinterpret_cast<int*>(base + kSmemA + kSmemB + 16);
-  int* s_item = reinterpret_cast<int*>(base + kSmemA + kSmemB + 24);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s32(sm.taddr)),
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&ctl->full[s], 32);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl->accf[b], 1);
+      mbar_init(&ctl->acce[b], 4);
+    }
+    ctl->abort = 0;
+    ctl->gathered = 0;
+    ctl->done_tiles = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s32(&ctl->taddr)),
                  "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s32(sm.bar)), "r"(1) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    *sm.flag = 0;
-  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t taddr = *sm.taddr;
-  uint32_t phase = 0;
+  const uint32_t taddr = ctl->taddr;
 
   const int N = p.N;
   const int G = (F + kTcFields - 1) / kTcFields;
-  float* vec = p.ws + (size_t)blockIdx.x * p.max_rows * kTcR;
   const int nitems = single ? G : p.nunits * G;
-  bool alive = true;
-  while (alive) {
-    const int item = next_item(p.counter, s_item);
-    if (item >= nitems) break;
-    const int grp = item % G;
-    const int am = single ? (msingle < 0 ? -msingle : msingle) : p.order[item / G];
-    const Unit u = p.units[am];
-    const int nx = u.nce + u.nco;
-    if (fwd) {
-      // gather X: row t, column 4 fl + 2 s + c; zero Y
-      {
-        // column tid of every X row: field fl, sign s, Re/Im cc are fixed per thread
-        const int fl = tid >> 2, s = (tid >> 1) & 1, cc = tid & 1;
-        const double* b = coef_base(in, N, am, grp * kTcFields + fl, s, F, single, msingle);
+  unsigned char* vec = p.ws + (size_t)blockIdx.x * p.max_rows * kTcRowBytes;
+  const uint32_t stage0 = s32(base);
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    long jp = 0;
+    int tiles_before = 0;
+    bool ok = true;
+    for (int it = blockIdx.x, iseq = 0; it < nitems && ok; it += gridDim.x, ++iseq) {
+      const Item itm = item_of(p, it, G, single, msingle);
+      const Unit u = p.units[itm.am];
+      ok = counter_wait(ctl, &ctl->gathered, iseq + 1);
+      for (int k = 0; k < u.nphase && ok; ++k) {
+        const int ph = fwd ? k : u.nphase - 1 - k;
+        ok = counter_wait(ctl, &ctl->done_tiles, tiles_before);
+        int tiles_here = 0;
+        for (int oi = p.phase_tab[u.ph_begin + ph]; oi < p.phase_tab[u.ph_begin + ph + 1] && ok; ++oi) {
+          const Op op = p.ops[oi];
+          const OpShape sh = op_shape(op, fwd);
+          const int32_t* ioff = fwd ? op.in_off : op.out_off;
+          const int32_t* ilen = fwd ? op.in_len : op.out_len;
+          const uint16_t* img = p.img + p.img_off[2 * oi + (fwd ? 0 : 1)];
+          for (int t = 0; t < sh.nT && ok; ++t) {
+            const int Np = (min(kTcNT, sh.NN - kTcNT * t) + 15) & ~15;
+            for (int c = 0; c < sh.nK && ok; ++c, ++jp) {
+              const int s = (int)(jp % kStages);
+              const uint32_t use = (uint32_t)(jp / kStages);
+              ok = mbar_wait(ctl, &ctl->empty[s], (use & 1u) ^ 1u);
+              if (!ok) break;
+              const int Kp = (min(kTcKC, sh.KK - kTcKC * c) + 15) & ~15;
+              const uint32_t sA = stage0 + (uint32_t)s * kStageBytes, sB = sA + kStageA;
+              // A: Kp input rows x 3 pieces x 16 chunks of 8 right-hand sides (MN-major cores)
+              for (int q = lane; q < Kp * 48; q += 32) {
+                const int kj = q / 48, rem = q % 48, pc = rem >> 4, m8 = rem & 15;
+                const int j = kTcKC * c + kj;
+                const bool valid = j < sh.KK;
+                const unsigned char* src =
+                    valid ? vec + (size_t)seg_row(j, ioff, ilen) * kTcRowBytes + pc * (kTcR * 2) + m8 * 16 : vec;
+                const uint32_t dst = sA + pc * kPieceA + ((kj >> 3) * 16 + m8) * 128 + (kj & 7) * 16;
+                cp_async16(dst, src, valid ? 16u : 0u);
+              }
+              // B: the image chunk (3 pieces, contiguous)
+              const uint16_t* src = img + (size_t)t * 384 * sh.kp_tot + (size_t)Np * (96 * c);
+              const int n16 = 3 * Np * Kp / 8;
+              for (int q = lane; q < n16; q += 32) cp_async16(sB + 16u * q, src + 8 * q, 16u);
+              cp_async_arrive(&ctl->full[s]);
+            }
+            ++tiles_here;
+          }
+        }
+        tiles_before += tiles_here;
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      long jm = 0, tm = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+        const Item itm = item_of(p, it, G, single, msingle);
+        const Unit u = p.units[itm.am];
+        for (int k = 0; k < u.nphase && ok; ++k) {
+          const int ph = fwd ? k : u.nphase - 1 - k;
+          for (int oi = p.phase_tab[u.ph_begin + ph]; oi < p.phase_tab[u.ph_begin + ph + 1] && ok; ++oi) {
+            const Op op = p.ops[oi];
+            const OpShape sh = op_shape(op, fwd);
+            for (int t = 0; t < sh.nT && ok; ++t, ++tm) {
+              const int b = (int)(tm & 1);
+              const uint32_t v = (uint32_t)(tm >> 1);
+              ok = mbar_wait(ctl, &ctl->acce[b], (v & 1u) ^ 1u);
+              if (!ok) break;
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              const int Np = (min(kTcNT, sh.NN - kTcNT * t) + 15) & ~15;
+              const uint32_t idesc =
+                  (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(Np >> 3) << 17) | (8u << 24);
+              const uint32_t dhi = taddr + (uint32_t)(b * 256), dlo = dhi + 128;
+              for (int c = 0; c < sh.nK && ok; ++c, ++jm) {
+                const int s = (int)(jm % kStages);
+                const uint32_t use = (uint32_t)(jm / kStages);
+                ok = mbar_wait(ctl, &ctl->full[s], use & 1u);
+                if (!ok) break;
+                // the stage was written by cp.async (generic proxy); the MMAs read it
+                // through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int Kp = (min(kTcKC, sh.KK - kTcKC * c) + 15) & ~15;
+                const uint32_t sA = stage0 + (uint32_t)s * kStageBytes, sB = sA + kStageA;
+                const uint32_t bPiece = (uint32_t)Np * Kp * 2, bK = (uint32_t)(Np / 8) * 128;
+                for (int ks = 0; ks < Kp / 16; ++ks) {
+                  int lo = 0;
+#pragma unroll
+                  for (int pa = 0; pa < 3; ++pa)
+#pragma unroll
+                    for (int pb = 0; pb < 3; ++pb) {
+                      if (pa + pb > 2) continue;
+                      // A MN-major: cores (k8, m8) at (k8 * 16 + m8) * 128 B: K stride 2048, M stride 128
+                      const uint64_t ad = sdesc(sA + pa * kPieceA + ks * 2 * 2048, 2048, 128);
+                      const uint64_t bd = sdesc(sB + pb * bPiece + ks * 2 * bK, bK, 128);
+                      if (pa + pb == 0) {
+                        mma_bf16(dhi, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                      } else {
+                        mma_bf16(dlo, ad, bd, idesc, (c > 0 || ks > 0 || lo > 0) ? 1u : 0u);
+                        ++lo;
+                      }
+                    }
+                }
+                mma_commit(&ctl->empty[s]);
+              }
+              if (ok) mma_commit(&ctl->accf[b]);
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue, gather, fold
+    const int e = tid - 64;       // 0..127
+    const int quad = warp & 3;    // TMEM lane quadrant of this warp
+    const int r = 32 * quad + lane;  // right-hand side read from TMEM
+    long te = 0;
+    int done = 0;
+    bool ok = true;
+    for (int it = blockIdx.x, iseq = 0; it < nitems && ok; it += gridDim.x, ++iseq) {
+      const Item itm = item_of(p, it, G, single, msingle);
+      const int am = itm.am, grp = itm.grp;
+      const Unit u = p.units[am];
+      const int nx = u.nce + u.nco;
+      if (fwd) {
+        // X rows in pieces; Y rows (FP32) zeroed
+        const int fl = e >> 2, s = (e >> 1) & 1, cc = e & 1;
+        const double* bsrc = coef_base(in, N, am, grp * kTcFields + fl, s, F, single, msingle);
         for (int t0 = 0; t0 < nx; t0 += 8) {
           float v[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int t = t0 + e;
+          for (int q = 0; q < 8; ++q) {
+            const int t = t0 + q;
             const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
-            v[e] = (b && t < nx) ? (float)__ldg(b + 2 * kk + cc) : 0.f;
+            v[q] = (bsrc && t < nx) ? (float)__ldg(bsrc + 2 * kk + cc) : 0.f;
           }
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            if (t0 + e < nx) __stcg(vec + (size_t)(t0 + e) * kTcR + tid, v[e]);
+          for (int q = 0; q < 8; ++q)
+            if (t0 + q < nx) put_pieces(vec + (size_t)(t0 + q) * kTcRowBytes, e, v[q]);
         }
-      }
-      for (int idx = tid; idx < 2 * N * kTcR; idx += kTcThreads) __stcg(vec + (size_t)u.ye * kTcR + idx, 0.f);
-    } else {
-      for (int idx = tid; idx < N * 2 * kTcFields; idx += kTcThreads) {
-        const int i = idx % N, fs = idx / N, fl = fs >> 1, s = fs & 1;
+        for (int i = 0; i < 2 * N; ++i) __stcg(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, e), 0.f);
+      } else {
+        // W-weighted parity fold of g into Y rows (pieces); X rows (FP32) zeroed
+        const int fl = e >> 2, s = (e >> 1) & 1, cc = e & 1;
         const double* gb = value_base(in, N, am, grp * kTcFields + fl, s, F, single, msingle);
-        double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
-        if (gb) {
-          a = __ldg(reinterpret_cast<const double2*>(gb) + N + i);
-          b = __ldg(reinterpret_cast<const double2*>(gb) + N - 1 - i);
+        for (int i = 0; i < N; ++i) {
+          double a = 0.0, b = 0.0;
+          if (gb) {
+            a = __ldg(gb + 2 * (N + i) + cc);
+            b = __ldg(gb + 2 * (N - 1 - i) + cc);
+          }
+          const double wi = __ldg(p.w + N + i);
+          put_pieces(vec + (size_t)(u.ye + i) * kTcRowBytes, e, (float)(wi * (a + b)));
+          put_pieces(vec + (size_t)(u.yo + i) * kTcRowBytes, e, (float)(wi * (a - b)));
         }
-        const double wi = __ldg(p.w + N + i);
-        const int col = 4 * fl + 2 * s;
-        float* ye = vec + (size_t)(u.ye + i) * kTcR + col;
-        float* yo = vec + (size_t)(u.yo + i) * kTcR + col;
-        __stcg(ye, (float)(wi * (a.x + b.x)));
-        __stcg(ye + 1, (float)(wi * (a.y + b.y)));
-        __stcg(yo, (float)(wi * (a.x - b.x)));
-        __stcg(yo + 1, (float)(wi * (a.y - b.y)));
+        for (int t = 0; t < nx; ++t) __stcg(fp32_at(vec + (size_t)t * kTcRowBytes, e), 0.f);
       }
-      for (int idx = tid; idx < nx * kTcR; idx += kTcThreads) __stcg(vec + idx, 0.f);
-    }
-    __syncthreads();
-    for (int k = 0; k < u.nphase && alive; ++k) {
-      const int ph = fwd ? k : u.nphase - 1 - k;
-      for (int oi = p.phase_tab[u.ph_begin + ph]; oi < p.phase_tab[u.ph_begin + ph + 1]; ++oi) {
-        const Op op = p.ops[oi];
-        if (!tc_op(p, sm, taddr, phase, op, fwd != 0, p.img + p.img_off[2 * oi + (fwd ? 0 : 1)], vec)) {
-          alive = false;
-          break;
+      __threadfence_block();
+      epi_bar();
+      if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
+      // tiles of every op, in the producer's order
+      for (int k = 0; k < u.nphase && ok; ++k) {
+        const int ph = fwd ? k : u.nphase - 1 - k;
+        for (int oi = p.phase_tab[u.ph_begin + ph]; oi < p.phase_tab[u.ph_begin + ph + 1] && ok; ++oi) {
+          const Op op = p.ops[oi];
+          const OpShape sh = op_shape(op, fwd);
+          const int32_t* ooff = fwd ? op.out_off : op.in_off;
+          const int32_t* olen = fwd ? op.out_len : op.in_len;
+          const bool accum = (op.flags & (fwd ? OP_FWD_ACCUM : OP_BWD_ACCUM)) != 0;
+          for (int t = 0; t < sh.nT && ok; ++t, ++te) {
+            const int b = (int)(te & 1);
+            const uint32_t v = (uint32_t)(te >> 1);
+            ok = mbar_wait(ctl, &ctl->accf[b], v & 1u);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int Nt = min(kTcNT, sh.NN - kTcNT * t);
+            if (sh.KK > 0) {
+              for (int c0 = 0; c0 < Nt; c0 += 32) {
+                uint32_t hv[32], lv[32];
+                const uint32_t lanes = (uint32_t)(32 * quad) << 16;
+                tmem_ld32(taddr + lanes + (uint32_t)(b * 256 + c0), hv);
+                tmem_ld32(taddr + lanes + (uint32_t)(b * 256 + 128 + c0), lv);
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                  const int i = c0 + q;
+                  if (i < Nt) {
+                    unsigned char* row = vec + (size_t)seg_row(kTcNT * t + i, ooff, olen) * kTcRowBytes;
+                    const float val = __uint_as_float(hv[q]) + __uint_as_float(lv[q]);
+                    if (accum) atomicAdd(fp32_at(row, r), val);
+                    else put_pieces(row, r, val);
+                  }
+                }
+              }
+            } else if (!accum) {
+              for (int i = 0; i < Nt; ++i)
+                put_pieces(vec + (size_t)seg_row(kTcNT * t + i, ooff, olen) * kTcRowBytes, r, 0.f);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->acce[b]);
+            __threadfence_block();
+            epi_bar();
+            ++done;
+            if (e == 0) *((volatile int*)&ctl->done_tiles) = done;
+          }
         }
       }
-      __syncthreads();
-    }
-    if (!alive) break;
-    if (fwd) {
-      for (int idx = tid; idx < N * 2 * kTcFields; idx += kTcThreads) {
-        const int i = idx % N, fs = idx / N, fl = fs >> 1, s = fs & 1;
-        const double* gb = value_base(out, N, am, grp * kTcFields + fl, s, F, single, msingle);
-        if (!gb) continue;
-        const int col = 4 * fl + 2 * s;
-        const float er = __ldcg(vec + (size_t)(u.ye + i) * kTcR + col);
-        const float ei = __ldcg(vec + (size_t)(u.ye + i) * kTcR + col + 1);
-        const float orr = __ldcg(vec + (size_t)(u.yo + i) * kTcR + col);
-        const float oi = __ldcg(vec + (size_t)(u.yo + i) * kTcR + col + 1);
-        double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
-        gp[N + i] = make_double2((double)er + (double)orr, (double)ei + (double)oi);
-        gp[N - 1 - i] = make_double2((double)er - (double)orr, (double)ei - (double)oi);
+      if (!ok) break;
+      // fold / scatter from the FP32 accumulation rows
+      if (fwd) {
+        for (int idx = e; idx < N * 2 * kTcFields; idx += 128) {
+          const int i = idx % N, fs = idx / N, fl = fs >> 1, s = fs & 1;
+          const double* gb = value_base(out, N, am, grp * kTcFields + fl, s, F, single, msingle);
+          if (!gb) continue;
+          const int col = 4 * fl + 2 * s;
+          const float* ye = fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, col);
+          const float* yo = fp32_at(vec + (size_t)(u.yo + i) * kTcRowBytes, col);
+          const float er = __ldcg(ye), ei = __ldcg(ye + 1), orr = __ldcg(yo), oi = __ldcg(yo + 1);
+          double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
+          gp[N + i] = make_double2((double)er + (double)orr, (double)ei + (double)oi);
+          gp[N - 1 - i] = make_double2((double)er - (double)orr, (double)ei - (double)oi);
+        }
+      } else {
+        const int fl = e >> 2, s = (e >> 1) & 1, cc = e & 1;
+        const double* bdst = coef_base(out, N, am, grp * kTcFields + fl, s, F, single, msingle);
+        if (bdst)
+          for (int t = 0; t < nx; ++t) {
+            const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
+            const_cast<double*>(bdst)[2 * kk + cc] = (double)__ldcg(fp32_at(vec + (size_t)t * kTcRowBytes, e));
+          }
       }
-    } else {
-      for (int idx = tid; idx < nx * kTcR; idx += kTcThreads) {
-        const int t = idx / kTcR, col = idx % kTcR;
-        const int fl = col >> 2, s = (col >> 1) & 1, cc = col & 1;
-        const double* b = coef_base(out, N, am, grp * kTcFields + fl, s, F, single, msingle);
-        if (!b) continue;
-        const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
-        const_cast<double*>(b)[2 * kk + cc] = (double)__ldcg(vec + (size_t)t * kTcR + col);
-      }
+      __threadfence_block();
+      epi_bar();
     }
   }
-  if (!alive && tid == 0) atomicExch(p.err, 1);
+  if (*((volatile int*)&ctl->abort) && tid == 0) atomicExch(p.err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
+  if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
 }
 
@@ -471,20 +569,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
 
 size_t tc_smem_bytes() { return kSmemTotal; }
 
-int tc_ctas_per_sm() {
-  // resident CTAs per SM from the three limits: shared memory (with the
-  // driver's 1 KB per CTA), registers, and the 512 tensor-memory columns
-  int dev = 0, smem_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  cudaFuncAttributes fa;
-  int regs = 255;
-  if (cudaFuncGetAttributes(&fa, alt_tc_kernel) == cudaSuccess) regs = fa.numRegs;
-  const int by_smem = (int)(smem_sm / (kSmemTotal + 1024));
-  const int by_regs = 65536 / (((regs + 7) & ~7) * kTcThreads);
-  const int by_tmem = 512 / kTmemCols;
-  return std::max(1, std::min(std::min(by_smem, by_regs), by_tmem));
-}
+int tc_ctas_per_sm() { return 1; }  // the kernel holds all 512 tensor-memory columns
 
 cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, int F, int single, int m, int grid,
                       cudaStream_t st) {

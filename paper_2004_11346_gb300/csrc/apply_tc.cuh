@@ -14,8 +14,9 @@ namespace sht {
 constexpr int kTcFields = 32;            // fields per work item
 constexpr int kTcR = 4 * kTcFields;      // 128 right-hand sides = MMA M
 constexpr int kTcNT = 128;               // N tile (rows of one block product)
-constexpr int kTcKC = 64;                // K chunk staged per MMA batch
-constexpr int kTcThreads = 128;          // one warpgroup
+constexpr int kTcKC = 32;                // K chunk per pipeline stage
+constexpr int kTcThreads = 192;          // producer warp, MMA warp, 4 epilogue warps
+constexpr int kTcRowBytes = 3 * kTcR * 2;  // scratch row: 3 BF16 pieces x 128 (or 128 FP32)
 
 struct TcPlan {
   const Unit* units;
@@ -25,7 +26,7 @@ struct TcPlan {
   const uint16_t* img;      // split-BF16 operand images of every op
   const int64_t* img_off;   // per op: [forward image, transposed image] element offsets
   const double* w;
-  float* ws;                // per-CTA scratch: max_rows x kTcR floats
+  unsigned char* ws;        // per-CTA scratch: max_rows rows of kTcRowBytes
   unsigned int* counter;
   int* err;                 // set to 1 when a bounded wait gives up
   int N;
