@@ -54,6 +54,22 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(vals, world, device="cpu"):
+    """Element-wise max of per-rank timings over all ranks (identity for one rank)."""
+    if world == 1:
+        return list(vals)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vals, device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def rank_fields(N, F, w, rank):
+    """The F coefficient fields rank `rank` processes: fields rank*F .. rank*F+F-1 of the seeded stream."""
+    return inputs.coefficients(N, F, w["seed"], decay=w["decay"], real_m0=w["real_m0"], field_offset=rank * F)
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -228,7 +244,7 @@ def run_ours(args):
     plan = plan_for(sht, w)
     t_plan = time.perf_counter() - t0
     st = plan.stats()
-    beta_h = inputs.coefficients(N, F, w["seed"], decay=w["decay"], real_m0=w["real_m0"], field_offset=rank * F)
+    beta_h = rank_fields(N, F, w, rank)
     beta = torch.from_numpy(beta_h).cuda()
     g = torch.empty((F, 4 * N - 1, 2 * N, 2), dtype=torch.float64, device="cuda")
     back = torch.empty_like(beta)
@@ -239,11 +255,7 @@ def run_ours(args):
             torch.distributed.barrier()
 
     def max_over_ranks(vals):
-        if world == 1:
-            return vals
-        t = torch.tensor(vals, device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return [float(v) for v in t.tolist()]
+        return reduce_max(vals, world, device="cuda")
 
     for _ in range(args.warmup):
         plan.forward(beta, out=g)

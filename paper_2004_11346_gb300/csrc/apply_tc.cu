@@ -117,7 +117,9 @@ void tc_build_images(const std::vector<Op>& ops, const std::vector<double>& fact
 // ---------------------------------------------------------------- device side
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 3;
+constexpr int kEpiWarps = 8;                  // two warpgroups drain the accumulators
+constexpr int kTrStride = 33;                 // padded 32 x 32 transpose tile (floats)
 constexpr int kPieceA = kTcR * kTcKC * 2;      // bytes of one A piece in a stage (8 KB)
 constexpr int kStageA = 3 * kPieceA;           // 24 KB
 constexpr int kStageB = 3 * kTcNT * kTcKC * 2; // 24 KB (largest N tile)
@@ -135,7 +137,8 @@ struct Ctl {
   int gathered;    // items whose gather is complete
   int done_tiles;  // tiles whose epilogue is complete (all items so far)
 };
-constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + sizeof(Ctl) + 1024;
+constexpr size_t kTrBytes = (size_t)kEpiWarps * 32 * kTrStride * 4;
+constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + kTrBytes + sizeof(Ctl) + 1024;
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -205,11 +208,20 @@ __device__ __forceinline__ bool counter_wait(Ctl* ctl, int* ctr, int target) {
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
+__device__ __forceinline__ void bulk_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(s32(bar))
+      : "memory");
+}
 __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(s32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 __device__ __forceinline__ long coef_offset(long N, long m) {
   long a = m < 0 ? -m : m;
@@ -287,16 +299,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes);
+  float* trbuf = reinterpret_cast<float*>(base + (size_t)kStages * kStageBytes);
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes + kTrBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&ctl->full[s], 32);
+      mbar_init(&ctl->full[s], 33);  // 32 cp.async arrivals + the bulk copy's expect_tx arrival
       mbar_init(&ctl->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl->accf[b], 1);
-      mbar_init(&ctl->acce[b], 4);
+      mbar_init(&ctl->acce[b], kEpiWarps);
     }
     ctl->abort = 0;
     ctl->gathered = 0;
@@ -348,20 +361,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
               if (!ok) break;
               const int Kp = (min(kTcKC, sh.KK - kTcKC * c) + 15) & ~15;
               const uint32_t sA = stage0 + (uint32_t)s * kStageBytes, sB = sA + kStageA;
-              // A: Kp input rows x 3 pieces x 16 chunks of 8 right-hand sides (MN-major cores)
-              for (int q = lane; q < Kp * 48; q += 32) {
-                const int kj = q / 48, rem = q % 48, pc = rem >> 4, m8 = rem & 15;
-                const int j = kTcKC * c + kj;
-                const bool valid = j < sh.KK;
-                const unsigned char* src =
-                    valid ? vec + (size_t)seg_row(j, ioff, ilen) * kTcRowBytes + pc * (kTcR * 2) + m8 * 16 : vec;
-                const uint32_t dst = sA + pc * kPieceA + ((kj >> 3) * 16 + m8) * 128 + (kj & 7) * 16;
-                cp_async16(dst, src, valid ? 16u : 0u);
+              // B: the image chunk (3 pieces, contiguous) in one bulk copy whose
+              // bytes the full barrier expects
+              if (lane == 0) {
+                const uint16_t* src = img + (size_t)t * 384 * sh.kp_tot + (size_t)Np * (96 * c);
+                const uint32_t bytes = (uint32_t)(3 * Np * Kp * 2);
+                bulk_expect(&ctl->full[s], bytes);
+                bulk_copy(sB, src, bytes, &ctl->full[s]);
               }
-              // B: the image chunk (3 pieces, contiguous)
-              const uint16_t* src = img + (size_t)t * 384 * sh.kp_tot + (size_t)Np * (96 * c);
-              const int n16 = 3 * Np * Kp / 8;
-              for (int q = lane; q < n16; q += 32) cp_async16(sB + 16u * q, src + 8 * q, 16u);
+              // A: Kp input rows x 3 pieces x 16 chunks of 8 right-hand sides
+              // (MN-major cores).  Lane l owns the row pointer of row l and the
+              // (piece, 8-column chunk) pairs l and l + 32 of every row.
+              {
+                const int j = kTcKC * c + lane;
+                const bool valid = lane < Kp && j < sh.KK;
+                const unsigned char* myrow = valid ? vec + (size_t)seg_row(j, ioff, ilen) * kTcRowBytes : vec;
+                const int pc0 = lane >> 4, m80 = lane & 15;           // pair lane
+                const int pc1 = (lane + 32) >> 4, m81 = (lane + 32) & 15;  // pair lane + 32 (lanes < 16)
+                const uint32_t d0 = sA + pc0 * kPieceA + m80 * 128, d1 = sA + pc1 * kPieceA + m81 * 128;
+                const uint32_t o0 = pc0 * (kTcR * 2) + m80 * 16, o1 = pc1 * (kTcR * 2) + m81 * 16;
+                for (int kj = 0; kj < Kp; ++kj) {
+                  const unsigned char* row =
+                      reinterpret_cast<const unsigned char*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(myrow), kj));
+                  const uint32_t ok_src = __shfl_sync(0xffffffffu, valid ? 16u : 0u, kj);
+                  const uint32_t kofs = (uint32_t)((kj >> 3) * 2048 + (kj & 7) * 16);
+                  cp_async16(d0 + kofs, row + o0, ok_src);
+                  if (lane < 16) cp_async16(d1 + kofs, row + o1, ok_src);
+                }
+              }
               cp_async_arrive(&ctl->full[s]);
             }
             ++tiles_here;
@@ -435,9 +462,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue, gather, fold
-    const int e = tid - 64;       // 0..127
-    const int quad = warp & 3;    // TMEM lane quadrant of this warp
-    const int r = 32 * quad + lane;  // right-hand side read from TMEM
+    const int e = tid - 64;             // 0..255
+    const int ew = warp - 2;            // epilogue warp 0..7
+    const int grp2 = ew >> 2;           // warpgroup: 32-column blocks grp2, grp2 + 2
+    const int quad = warp & 3;          // TMEM lane quadrant: right-hand sides 32 quad ..
+    const int col = e & 127, half = e >> 7;
+    float* T = trbuf + (size_t)ew * 32 * kTrStride;
     long te = 0;
     int done = 0;
     bool ok = true;
@@ -446,11 +476,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       const int am = itm.am, grp = itm.grp;
       const Unit u = p.units[am];
       const int nx = u.nce + u.nco;
+      const int fl = col >> 2, sg = (col >> 1) & 1, cc = col & 1;
       if (fwd) {
-        // X rows in pieces; Y rows (FP32) zeroed
-        const int fl = e >> 2, s = (e >> 1) & 1, cc = e & 1;
-        const double* bsrc = coef_base(in, N, am, grp * kTcFields + fl, s, F, single, msingle);
-        for (int t0 = 0; t0 < nx; t0 += 8) {
+        // X rows in pieces (column col, rows of parity `half` in batches of 8); Y rows zeroed
+        const double* bsrc = coef_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
+        for (int t0 = 8 * half; t0 < nx; t0 += 16) {
           float v[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -460,24 +490,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
           }
 #pragma unroll
           for (int q = 0; q < 8; ++q)
-            if (t0 + q < nx) put_pieces(vec + (size_t)(t0 + q) * kTcRowBytes, e, v[q]);
+            if (t0 + q < nx) put_pieces(vec + (size_t)(t0 + q) * kTcRowBytes, col, v[q]);
         }
-        for (int i = 0; i < 2 * N; ++i) __stcg(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, e), 0.f);
+        for (int i = half; i < 2 * N; i += 2) __stcg(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, col), 0.f);
       } else {
         // W-weighted parity fold of g into Y rows (pieces); X rows (FP32) zeroed
-        const int fl = e >> 2, s = (e >> 1) & 1, cc = e & 1;
-        const double* gb = value_base(in, N, am, grp * kTcFields + fl, s, F, single, msingle);
-        for (int i = 0; i < N; ++i) {
+        const double* gb = value_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
+        for (int i = half; i < N; i += 2) {
           double a = 0.0, b = 0.0;
           if (gb) {
             a = __ldg(gb + 2 * (N + i) + cc);
             b = __ldg(gb + 2 * (N - 1 - i) + cc);
           }
           const double wi = __ldg(p.w + N + i);
-          put_pieces(vec + (size_t)(u.ye + i) * kTcRowBytes, e, (float)(wi * (a + b)));
-          put_pieces(vec + (size_t)(u.yo + i) * kTcRowBytes, e, (float)(wi * (a - b)));
+          put_pieces(vec + (size_t)(u.ye + i) * kTcRowBytes, col, (float)(wi * (a + b)));
+          put_pieces(vec + (size_t)(u.yo + i) * kTcRowBytes, col, (float)(wi * (a - b)));
         }
-        for (int t = 0; t < nx; ++t) __stcg(fp32_at(vec + (size_t)t * kTcRowBytes, e), 0.f);
+        for (int t = half; t < nx; t += 2) __stcg(fp32_at(vec + (size_t)t * kTcRowBytes, col), 0.f);
       }
       __threadfence_block();
       epi_bar();
@@ -498,27 +527,64 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int Nt = min(kTcNT, sh.NN - kTcNT * t);
-            if (sh.KK > 0) {
-              for (int c0 = 0; c0 < Nt; c0 += 32) {
-                uint32_t hv[32], lv[32];
-                const uint32_t lanes = (uint32_t)(32 * quad) << 16;
-                tmem_ld32(taddr + lanes + (uint32_t)(b * 256 + c0), hv);
-                tmem_ld32(taddr + lanes + (uint32_t)(b * 256 + 128 + c0), lv);
-                tmem_wait_ld();
+            if (sh.KK > 0 || !accum) {
+              for (int c0 = 32 * grp2; c0 < Nt; c0 += 64) {
+                // this warp's 32 right-hand sides x 32 output rows c0.. of the tile
+                if (sh.KK > 0) {
+                  uint32_t hv[32], lv[32];
+                  const uint32_t lanes = (uint32_t)(32 * quad) << 16;
+                  tmem_ld32(taddr + lanes + (uint32_t)(b * 256 + c0), hv);
+                  tmem_ld32(taddr + lanes + (uint32_t)(b * 256 + 128 + c0), lv);
+                  tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                  const int i = c0 + q;
+                  for (int q = 0; q < 32; ++q) T[q * kTrStride + lane] = __uint_as_float(hv[q]) + __uint_as_float(lv[q]);
+                } else {
+#pragma unroll
+                  for (int q = 0; q < 32; ++q) T[q * kTrStride + lane] = 0.f;
+                }
+                __syncwarp();
+                // transpose: lane owns rows lane/4 + 8 kq and right-hand sides 8 (lane % 4) ..
+                const int oc = lane & 3;
+#pragma unroll
+                for (int kq = 0; kq < 4; ++kq) {
+                  const int rl = (lane >> 2) + 8 * kq, i = c0 + rl;
                   if (i < Nt) {
+                    float x[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) x[jj] = T[rl * kTrStride + 8 * oc + jj];
                     unsigned char* row = vec + (size_t)seg_row(kTcNT * t + i, ooff, olen) * kTcRowBytes;
-                    const float val = __uint_as_float(hv[q]) + __uint_as_float(lv[q]);
-                    if (accum) atomicAdd(fp32_at(row, r), val);
-                    else put_pieces(row, r, val);
+                    const int c8 = 32 * quad + 8 * oc;
+                    if (accum) {
+                      float* dst = fp32_at(row, c8);
+                      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(x[0]),
+                                   "f"(x[1]), "f"(x[2]), "f"(x[3])
+                                   : "memory");
+                      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4), "f"(x[4]),
+                                   "f"(x[5]), "f"(x[6]), "f"(x[7])
+                                   : "memory");
+                    } else {
+                      uint32_t h[3][4];
+#pragma unroll
+                      for (int jj = 0; jj < 8; jj += 2) {
+                        float a0 = x[jj], a1 = x[jj + 1];
+#pragma unroll
+                        for (int pc = 0; pc < 3; ++pc) {
+                          const __nv_bfloat162 hb = __floats2bfloat162_rn(a0, a1);
+                          const float2 hf = __bfloat1622float2(hb);
+                          a0 -= hf.x;
+                          a1 -= hf.y;
+                          h[pc][jj >> 1] = *reinterpret_cast<const uint32_t*>(&hb);
+                        }
+                      }
+#pragma unroll
+                      for (int pc = 0; pc < 3; ++pc)
+                        __stcg(reinterpret_cast<uint4*>(row + pc * (kTcR * 2) + c8 * 2),
+                               make_uint4(h[pc][0], h[pc][1], h[pc][2], h[pc][3]));
+                    }
                   }
                 }
+                __syncwarp();
               }
-            } else if (!accum) {
-              for (int i = 0; i < Nt; ++i)
-                put_pieces(vec + (size_t)seg_row(kTcNT * t + i, ooff, olen) * kTcRowBytes, r, 0.f);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -533,25 +599,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       if (!ok) break;
       // fold / scatter from the FP32 accumulation rows
       if (fwd) {
-        for (int idx = e; idx < N * 2 * kTcFields; idx += 128) {
-          const int i = idx % N, fs = idx / N, fl = fs >> 1, s = fs & 1;
-          const double* gb = value_base(out, N, am, grp * kTcFields + fl, s, F, single, msingle);
+        for (int idx = e; idx < N * 2 * kTcFields; idx += 256) {
+          const int i = idx % N, fs = idx / N, fl2 = fs >> 1, s2 = fs & 1;
+          const double* gb = value_base(out, N, am, grp * kTcFields + fl2, s2, F, single, msingle);
           if (!gb) continue;
-          const int col = 4 * fl + 2 * s;
-          const float* ye = fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, col);
-          const float* yo = fp32_at(vec + (size_t)(u.yo + i) * kTcRowBytes, col);
+          const int cl = 4 * fl2 + 2 * s2;
+          const float* ye = fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, cl);
+          const float* yo = fp32_at(vec + (size_t)(u.yo + i) * kTcRowBytes, cl);
           const float er = __ldcg(ye), ei = __ldcg(ye + 1), orr = __ldcg(yo), oi = __ldcg(yo + 1);
           double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
           gp[N + i] = make_double2((double)er + (double)orr, (double)ei + (double)oi);
           gp[N - 1 - i] = make_double2((double)er - (double)orr, (double)ei - (double)oi);
         }
       } else {
-        const int fl = e >> 2, s = (e >> 1) & 1, cc = e & 1;
-        const double* bdst = coef_base(out, N, am, grp * kTcFields + fl, s, F, single, msingle);
+        const double* bdst = coef_base(out, N, am, grp * kTcFields + fl, sg, F, single, msingle);
         if (bdst)
-          for (int t = 0; t < nx; ++t) {
+          for (int t = half; t < nx; t += 2) {
             const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
-            const_cast<double*>(bdst)[2 * kk + cc] = (double)__ldcg(fp32_at(vec + (size_t)t * kTcRowBytes, e));
+            const_cast<double*>(bdst)[2 * kk + cc] = (double)__ldcg(fp32_at(vec + (size_t)t * kTcRowBytes, col));
           }
       }
       __threadfence_block();
