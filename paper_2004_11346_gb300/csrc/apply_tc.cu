@@ -119,6 +119,9 @@ namespace {
 
 constexpr int kStages = 3;
 constexpr int kEpiWarps = 8;                  // two warpgroups drain the accumulators
+constexpr int kProdWarps = 3;                 // warps staging operands
+constexpr int kMmaWarp = kProdWarps;          // the MMA-issuing warp
+constexpr int kEpiWarp0 = kProdWarps + 1;     // first epilogue warp
 constexpr int kTrStride = 33;                 // padded 32 x 32 transpose tile (floats)
 constexpr int kPieceA = kTcR * kTcKC * 2;      // bytes of one A piece in a stage (8 KB)
 constexpr int kStageA = 3 * kPieceA;           // 24 KB
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&ctl->full[s], 33);  // 32 cp.async arrivals + the bulk copy's expect_tx arrival
+      mbar_init(&ctl->full[s], 32 * kProdWarps + 1);  // cp.async arrivals + the bulk copy's expect_tx
       mbar_init(&ctl->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -316,7 +319,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
     ctl->done_tiles = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s32(&ctl->taddr)),
                  "r"(kTmemCols)
                  : "memory");
@@ -333,8 +336,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   unsigned char* vec = p.ws + (size_t)blockIdx.x * p.max_rows * kTcRowBytes;
   const uint32_t stage0 = s32(base);
 
-  if (warp == 0) {
-    // ------------------------------------------------------------ producer
+  if (warp < kProdWarps) {
+    // ------------------------------------------------------------ producers
     long jp = 0;
     int tiles_before = 0;
     bool ok = true;
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
               const uint32_t sA = stage0 + (uint32_t)s * kStageBytes, sB = sA + kStageA;
               // B: the image chunk (3 pieces, contiguous) in one bulk copy whose
               // bytes the full barrier expects
-              if (lane == 0) {
+              if (warp == 0 && lane == 0) {
                 const uint16_t* src = img + (size_t)t * 384 * sh.kp_tot + (size_t)Np * (96 * c);
                 const uint32_t bytes = (uint32_t)(3 * Np * Kp * 2);
                 bulk_expect(&ctl->full[s], bytes);
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
                 const int pc1 = (lane + 32) >> 4, m81 = (lane + 32) & 15;  // pair lane + 32 (lanes < 16)
                 const uint32_t d0 = sA + pc0 * kPieceA + m80 * 128, d1 = sA + pc1 * kPieceA + m81 * 128;
                 const uint32_t o0 = pc0 * (kTcR * 2) + m80 * 16, o1 = pc1 * (kTcR * 2) + m81 * 16;
-                for (int kj = 0; kj < Kp; ++kj) {
+                for (int kj = warp; kj < Kp; kj += kProdWarps) {
                   const unsigned char* row =
                       reinterpret_cast<const unsigned char*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(myrow), kj));
                   const uint32_t ok_src = __shfl_sync(0xffffffffu, valid ? 16u : 0u, kj);
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
-  } else if (warp == 1) {
+  } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       long jm = 0, tm = 0;
@@ -462,8 +465,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue, gather, fold
-    const int e = tid - 64;             // 0..255
-    const int ew = warp - 2;            // epilogue warp 0..7
+    const int e = tid - 32 * kEpiWarp0;  // 0..255
+    const int ew = warp - kEpiWarp0;     // epilogue warp 0..7
     const int grp2 = ew >> 2;           // warpgroup: 32-column blocks grp2, grp2 + 2
     const int quad = warp & 3;          // TMEM lane quadrant: right-hand sides 32 quad ..
     const int col = e & 127, half = e >> 7;
@@ -480,31 +483,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       if (fwd) {
         // X rows in pieces (column col, rows of parity `half` in batches of 8); Y rows zeroed
         const double* bsrc = coef_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
-        for (int t0 = 8 * half; t0 < nx; t0 += 16) {
-          float v[8];
+        for (int t0 = 16 * half; t0 < nx; t0 += 32) {
+          float v[16];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < 16; ++q) {
             const int t = t0 + q;
             const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
             v[q] = (bsrc && t < nx) ? (float)__ldg(bsrc + 2 * kk + cc) : 0.f;
           }
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
+          for (int q = 0; q < 16; ++q)
             if (t0 + q < nx) put_pieces(vec + (size_t)(t0 + q) * kTcRowBytes, col, v[q]);
         }
         for (int i = half; i < 2 * N; i += 2) __stcg(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, col), 0.f);
       } else {
         // W-weighted parity fold of g into Y rows (pieces); X rows (FP32) zeroed
         const double* gb = value_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
-        for (int i = half; i < N; i += 2) {
-          double a = 0.0, b = 0.0;
-          if (gb) {
-            a = __ldg(gb + 2 * (N + i) + cc);
-            b = __ldg(gb + 2 * (N - 1 - i) + cc);
+        for (int i0 = 8 * half; i0 < N; i0 += 16) {
+          double a[8], b[8], wi[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int i = i0 + q;
+            const bool in_range = gb && i < N;
+            a[q] = in_range ? __ldg(gb + 2 * (N + i) + cc) : 0.0;
+            b[q] = in_range ? __ldg(gb + 2 * (N - 1 - i) + cc) : 0.0;
+            wi[q] = i < N ? __ldg(p.w + N + i) : 0.0;
           }
-          const double wi = __ldg(p.w + N + i);
-          put_pieces(vec + (size_t)(u.ye + i) * kTcRowBytes, col, (float)(wi * (a + b)));
-          put_pieces(vec + (size_t)(u.yo + i) * kTcRowBytes, col, (float)(wi * (a - b)));
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int i = i0 + q;
+            if (i < N) {
+              put_pieces(vec + (size_t)(u.ye + i) * kTcRowBytes, col, (float)(wi[q] * (a[q] + b[q])));
+              put_pieces(vec + (size_t)(u.yo + i) * kTcRowBytes, col, (float)(wi[q] * (a[q] - b[q])));
+            }
+          }
         }
         for (int t = half; t < nx; t += 2) __stcg(fp32_at(vec + (size_t)t * kTcRowBytes, col), 0.f);
       }
@@ -599,24 +611,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       if (!ok) break;
       // fold / scatter from the FP32 accumulation rows
       if (fwd) {
-        for (int idx = e; idx < N * 2 * kTcFields; idx += 256) {
-          const int i = idx % N, fs = idx / N, fl2 = fs >> 1, s2 = fs & 1;
-          const double* gb = value_base(out, N, am, grp * kTcFields + fl2, s2, F, single, msingle);
-          if (!gb) continue;
-          const int cl = 4 * fl2 + 2 * s2;
-          const float* ye = fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, cl);
-          const float* yo = fp32_at(vec + (size_t)(u.yo + i) * kTcRowBytes, cl);
-          const float er = __ldcg(ye), ei = __ldcg(ye + 1), orr = __ldcg(yo), oi = __ldcg(yo + 1);
-          double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
-          gp[N + i] = make_double2((double)er + (double)orr, (double)ei + (double)oi);
-          gp[N - 1 - i] = make_double2((double)er - (double)orr, (double)ei - (double)oi);
+        const int total = N * 2 * kTcFields;
+        for (int idx0 = e; idx0 < total; idx0 += 256 * 8) {
+          float2 ev[8], ov[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int idx = idx0 + 256 * q;
+            ev[q] = make_float2(0.f, 0.f);
+            ov[q] = make_float2(0.f, 0.f);
+            if (idx < total) {
+              const int i = idx % N, fs = idx / N, cl = 4 * (fs >> 1) + 2 * (fs & 1);
+              ev[q] = __ldcg(reinterpret_cast<const float2*>(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, cl)));
+              ov[q] = __ldcg(reinterpret_cast<const float2*>(fp32_at(vec + (size_t)(u.yo + i) * kTcRowBytes, cl)));
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int idx = idx0 + 256 * q;
+            if (idx >= total) continue;
+            const int i = idx % N, fs = idx / N;
+            const double* gb = value_base(out, N, am, grp * kTcFields + (fs >> 1), fs & 1, F, single, msingle);
+            if (!gb) continue;
+            double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
+            gp[N + i] = make_double2((double)ev[q].x + (double)ov[q].x, (double)ev[q].y + (double)ov[q].y);
+            gp[N - 1 - i] = make_double2((double)ev[q].x - (double)ov[q].x, (double)ev[q].y - (double)ov[q].y);
+          }
         }
       } else {
         const double* bdst = coef_base(out, N, am, grp * kTcFields + fl, sg, F, single, msingle);
         if (bdst)
-          for (int t = half; t < nx; t += 2) {
-            const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
-            const_cast<double*>(bdst)[2 * kk + cc] = (double)__ldcg(fp32_at(vec + (size_t)t * kTcRowBytes, col));
+          for (int t0 = 16 * half; t0 < nx; t0 += 32) {
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              v[q] = t0 + q < nx ? __ldcg(fp32_at(vec + (size_t)(t0 + q) * kTcRowBytes, col)) : 0.f;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const int t = t0 + q;
+              if (t < nx) {
+                const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
+                const_cast<double*>(bdst)[2 * kk + cc] = (double)v[q];
+              }
+            }
           }
       }
       __threadfence_block();
@@ -626,7 +662,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   if (*((volatile int*)&ctl->abort) && tid == 0) atomicExch(p.err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 1)
+  if (warp == kMmaWarp)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
 }
 
