@@ -509,7 +509,7 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
     e = upload(&p->d_img, img);
     if (e == cudaSuccess) e = upload(&p->d_imgoff, off);
     p->nslots_tc = std::max(1, sms * tc_ctas_per_sm());
-    ws32 = (size_t)p->nslots_tc * P.max_rows * kTcRowBytes;
+    ws32 = (size_t)p->nslots_tc * 2 * P.max_rows * kTcRowBytes;  // two vector spaces per CTA
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_wstc), std::max<size_t>(ws32, 8));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));

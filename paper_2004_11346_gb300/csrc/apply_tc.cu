@@ -118,10 +118,11 @@ void tc_build_images(const std::vector<Op>& ops, const std::vector<double>& fact
 namespace {
 
 constexpr int kStages = 3;
-constexpr int kEpiWarps = 8;                  // two warpgroups drain the accumulators
 constexpr int kProdWarps = 3;                 // warps staging operands
 constexpr int kMmaWarp = kProdWarps;          // the MMA-issuing warp
 constexpr int kEpiWarp0 = kProdWarps + 1;     // first epilogue warp
+constexpr int kEpiWarps = 4;                  // one warpgroup drains the accumulators
+constexpr int kIoWarp0 = kEpiWarp0 + kEpiWarps;  // 4 I/O warps: gather, parity fold / scatter
 constexpr int kTrStride = 33;                 // padded 32 x 32 transpose tile (floats)
 constexpr int kPieceA = kTcR * kTcKC * 2;      // bytes of one A piece in a stage (8 KB)
 constexpr int kStageA = 3 * kPieceA;           // 24 KB
@@ -224,7 +225,8 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(s32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void io_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
 
 __device__ __forceinline__ long coef_offset(long N, long m) {
   long a = m < 0 ? -m : m;
@@ -289,11 +291,19 @@ __device__ __forceinline__ OpShape op_shape(const Op& op, bool fwd) {
 struct Item {
   int grp, am;
 };
+__device__ __forceinline__ int row_kk(const Unit& u, int t) { return t < u.nce ? 2 * t : 2 * (t - u.nce) + 1; }
 __device__ __forceinline__ Item item_of(const TcPlan& p, int it, int G, int single, int msingle) {
   Item r;
   r.grp = it % G;
   r.am = single ? (msingle < 0 ? -msingle : msingle) : p.order[it / G];
   return r;
+}
+
+// Tiles (epilogue units) of one work item.
+__device__ int item_tiles(const TcPlan& p, const Unit& u, bool fwd) {
+  int n = 0;
+  for (int oi = u.op_begin; oi < u.op_end; ++oi) n += op_shape(p.ops[oi], fwd).nT;
+  return n;
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const double* __restrict__ in,
@@ -333,7 +343,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   const int N = p.N;
   const int G = (F + kTcFields - 1) / kTcFields;
   const int nitems = single ? G : p.nunits * G;
-  unsigned char* vec = p.ws + (size_t)blockIdx.x * p.max_rows * kTcRowBytes;
+  const size_t slot_bytes = (size_t)p.max_rows * kTcRowBytes;
+  unsigned char* slots = p.ws + (size_t)blockIdx.x * 2 * slot_bytes;  // two vector spaces, alternating by item
   const uint32_t stage0 = s32(base);
 
   if (warp < kProdWarps) {
@@ -344,6 +355,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
     for (int it = blockIdx.x, iseq = 0; it < nitems && ok; it += gridDim.x, ++iseq) {
       const Item itm = item_of(p, it, G, single, msingle);
       const Unit u = p.units[itm.am];
+      unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
       ok = counter_wait(ctl, &ctl->gathered, iseq + 1);
       for (int k = 0; k < u.nphase && ok; ++k) {
         const int ph = fwd ? k : u.nphase - 1 - k;
@@ -463,67 +475,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       }
     }
     __syncwarp();
-  } else {
-    // ------------------------------------------------------------ epilogue, gather, fold
-    const int e = tid - 32 * kEpiWarp0;  // 0..255
-    const int ew = warp - kEpiWarp0;     // epilogue warp 0..7
-    const int grp2 = ew >> 2;           // warpgroup: 32-column blocks grp2, grp2 + 2
-    const int quad = warp & 3;          // TMEM lane quadrant: right-hand sides 32 quad ..
-    const int col = e & 127, half = e >> 7;
+  } else if (warp < kIoWarp0) {
+    // accumulators -> rows: warp ew owns TMEM lane quadrant ew (right-hand sides 32 ew ..)
+    const int ew = warp - kEpiWarp0;
+    const int e = tid - 32 * kEpiWarp0;
     float* T = trbuf + (size_t)ew * 32 * kTrStride;
     long te = 0;
     int done = 0;
     bool ok = true;
     for (int it = blockIdx.x, iseq = 0; it < nitems && ok; it += gridDim.x, ++iseq) {
       const Item itm = item_of(p, it, G, single, msingle);
-      const int am = itm.am, grp = itm.grp;
-      const Unit u = p.units[am];
-      const int nx = u.nce + u.nco;
-      const int fl = col >> 2, sg = (col >> 1) & 1, cc = col & 1;
-      if (fwd) {
-        // X rows in pieces (column col, rows of parity `half` in batches of 8); Y rows zeroed
-        const double* bsrc = coef_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
-        for (int t0 = 16 * half; t0 < nx; t0 += 32) {
-          float v[16];
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int t = t0 + q;
-            const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
-            v[q] = (bsrc && t < nx) ? (float)__ldg(bsrc + 2 * kk + cc) : 0.f;
-          }
-#pragma unroll
-          for (int q = 0; q < 16; ++q)
-            if (t0 + q < nx) put_pieces(vec + (size_t)(t0 + q) * kTcRowBytes, col, v[q]);
-        }
-        for (int i = half; i < 2 * N; i += 2) __stcg(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, col), 0.f);
-      } else {
-        // W-weighted parity fold of g into Y rows (pieces); X rows (FP32) zeroed
-        const double* gb = value_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
-        for (int i0 = 8 * half; i0 < N; i0 += 16) {
-          double a[8], b[8], wi[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int i = i0 + q;
-            const bool in_range = gb && i < N;
-            a[q] = in_range ? __ldg(gb + 2 * (N + i) + cc) : 0.0;
-            b[q] = in_range ? __ldg(gb + 2 * (N - 1 - i) + cc) : 0.0;
-            wi[q] = i < N ? __ldg(p.w + N + i) : 0.0;
-          }
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int i = i0 + q;
-            if (i < N) {
-              put_pieces(vec + (size_t)(u.ye + i) * kTcRowBytes, col, (float)(wi[q] * (a[q] + b[q])));
-              put_pieces(vec + (size_t)(u.yo + i) * kTcRowBytes, col, (float)(wi[q] * (a[q] - b[q])));
-            }
-          }
-        }
-        for (int t = half; t < nx; t += 2) __stcg(fp32_at(vec + (size_t)t * kTcRowBytes, col), 0.f);
-      }
-      __threadfence_block();
-      epi_bar();
-      if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
-      // tiles of every op, in the producer's order
+      const Unit u = p.units[itm.am];
+      unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
       for (int k = 0; k < u.nphase && ok; ++k) {
         const int ph = fwd ? k : u.nphase - 1 - k;
         for (int oi = p.phase_tab[u.ph_begin + ph]; oi < p.phase_tab[u.ph_begin + ph + 1] && ok; ++oi) {
@@ -540,11 +503,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int Nt = min(kTcNT, sh.NN - kTcNT * t);
             if (sh.KK > 0 || !accum) {
-              for (int c0 = 32 * grp2; c0 < Nt; c0 += 64) {
-                // this warp's 32 right-hand sides x 32 output rows c0.. of the tile
+              for (int c0 = 0; c0 < Nt; c0 += 32) {
                 if (sh.KK > 0) {
                   uint32_t hv[32], lv[32];
-                  const uint32_t lanes = (uint32_t)(32 * quad) << 16;
+                  const uint32_t lanes = (uint32_t)(32 * ew) << 16;
                   tmem_ld32(taddr + lanes + (uint32_t)(b * 256 + c0), hv);
                   tmem_ld32(taddr + lanes + (uint32_t)(b * 256 + 128 + c0), lv);
                   tmem_wait_ld();
@@ -555,7 +517,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
                   for (int q = 0; q < 32; ++q) T[q * kTrStride + lane] = 0.f;
                 }
                 __syncwarp();
-                // transpose: lane owns rows lane/4 + 8 kq and right-hand sides 8 (lane % 4) ..
                 const int oc = lane & 3;
 #pragma unroll
                 for (int kq = 0; kq < 4; ++kq) {
@@ -565,7 +526,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) x[jj] = T[rl * kTrStride + 8 * oc + jj];
                     unsigned char* row = vec + (size_t)seg_row(kTcNT * t + i, ooff, olen) * kTcRowBytes;
-                    const int c8 = 32 * quad + 8 * oc;
+                    const int c8 = 32 * ew + 8 * oc;
                     if (accum) {
                       float* dst = fp32_at(row, c8);
                       asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(x[0]),
@@ -608,55 +569,124 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
           }
         }
       }
-      if (!ok) break;
-      // fold / scatter from the FP32 accumulation rows
-      if (fwd) {
-        const int total = N * 2 * kTcFields;
-        for (int idx0 = e; idx0 < total; idx0 += 256 * 8) {
-          float2 ev[8], ov[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int idx = idx0 + 256 * q;
-            ev[q] = make_float2(0.f, 0.f);
-            ov[q] = make_float2(0.f, 0.f);
-            if (idx < total) {
-              const int i = idx % N, fs = idx / N, cl = 4 * (fs >> 1) + 2 * (fs & 1);
-              ev[q] = __ldcg(reinterpret_cast<const float2*>(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, cl)));
-              ov[q] = __ldcg(reinterpret_cast<const float2*>(fp32_at(vec + (size_t)(u.yo + i) * kTcRowBytes, cl)));
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int idx = idx0 + 256 * q;
-            if (idx >= total) continue;
-            const int i = idx % N, fs = idx / N;
-            const double* gb = value_base(out, N, am, grp * kTcFields + (fs >> 1), fs & 1, F, single, msingle);
-            if (!gb) continue;
-            double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
-            gp[N + i] = make_double2((double)ev[q].x + (double)ov[q].x, (double)ev[q].y + (double)ov[q].y);
-            gp[N - 1 - i] = make_double2((double)ev[q].x - (double)ov[q].x, (double)ev[q].y - (double)ov[q].y);
-          }
-        }
-      } else {
-        const double* bdst = coef_base(out, N, am, grp * kTcFields + fl, sg, F, single, msingle);
-        if (bdst)
-          for (int t0 = 16 * half; t0 < nx; t0 += 32) {
+    }
+  } else if (warp >= kIoWarp0) {
+    // I/O warps: gather of item i into slot i % 2 (after the fold of item i-2 from that
+    // slot), parity fold / scatter of item i once its tiles are done
+    const int e = tid - 32 * kIoWarp0;  // 0..127 = column (right-hand side)
+    const int col = e;
+    const int fl = col >> 2, sg = (col >> 1) & 1, cc = col & 1;
+    int tiles_through = 0;
+    bool ok = true;
+    int prev_it = -1, prev_iseq = -1;
+    for (int it = blockIdx.x, iseq = 0; ok; it += gridDim.x, ++iseq) {
+      const bool have = it < nitems;
+      // 1. gather item `it` into slot iseq % 2 (its previous user, item iseq-2, is folded)
+      if (have) {
+        const Item itm = item_of(p, it, G, single, msingle);
+        const int am = itm.am, grp = itm.grp;
+        const Unit u = p.units[am];
+        unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
+        const int nx = u.nce + u.nco;
+        if (fwd) {
+          const double* bsrc = coef_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
+          for (int t0 = 0; t0 < nx; t0 += 16) {
             float v[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-              v[q] = t0 + q < nx ? __ldcg(fp32_at(vec + (size_t)(t0 + q) * kTcRowBytes, col)) : 0.f;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
               const int t = t0 + q;
-              if (t < nx) {
-                const int kk = t < u.nce ? 2 * t : 2 * (t - u.nce) + 1;
-                const_cast<double*>(bdst)[2 * kk + cc] = (double)v[q];
+              v[q] = (bsrc && t < nx) ? (float)__ldg(bsrc + 2 * row_kk(u, t) + cc) : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (t0 + q < nx) put_pieces(vec + (size_t)(t0 + q) * kTcRowBytes, col, v[q]);
+          }
+          for (int i = 0; i < 2 * N; ++i) __stcg(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, col), 0.f);
+        } else {
+          const double* gb = value_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
+          for (int i0 = 0; i0 < N; i0 += 8) {
+            double a[8], b[8], wi[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int i = i0 + q;
+              const bool in_range = gb && i < N;
+              a[q] = in_range ? __ldg(gb + 2 * (N + i) + cc) : 0.0;
+              b[q] = in_range ? __ldg(gb + 2 * (N - 1 - i) + cc) : 0.0;
+              wi[q] = i < N ? __ldg(p.w + N + i) : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int i = i0 + q;
+              if (i < N) {
+                put_pieces(vec + (size_t)(u.ye + i) * kTcRowBytes, col, (float)(wi[q] * (a[q] + b[q])));
+                put_pieces(vec + (size_t)(u.yo + i) * kTcRowBytes, col, (float)(wi[q] * (a[q] - b[q])));
               }
             }
           }
+          for (int t = 0; t < nx; ++t) __stcg(fp32_at(vec + (size_t)t * kTcRowBytes, col), 0.f);
+        }
+        __threadfence_block();
+        io_bar();
+        if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
       }
-      __threadfence_block();
-      epi_bar();
+      // 2. fold / scatter the previous item once all of its tiles are done
+      if (prev_it >= 0) {
+        const Item itm = item_of(p, prev_it, G, single, msingle);
+        const int am = itm.am, grp = itm.grp;
+        const Unit u = p.units[am];
+        unsigned char* vec = slots + (size_t)(prev_iseq & 1) * slot_bytes;
+        tiles_through += item_tiles(p, u, fwd != 0);
+        ok = counter_wait(ctl, &ctl->done_tiles, tiles_through);
+        if (!ok) break;
+        const int nx = u.nce + u.nco;
+        if (fwd) {
+          const int total = N * 2 * kTcFields;
+          for (int idx0 = e; idx0 < total; idx0 += 128 * 8) {
+            float2 ev[8], ov[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int idx = idx0 + 128 * q;
+              ev[q] = make_float2(0.f, 0.f);
+              ov[q] = make_float2(0.f, 0.f);
+              if (idx < total) {
+                const int i = idx % N, fs = idx / N, cl = 4 * (fs >> 1) + 2 * (fs & 1);
+                ev[q] = __ldcg(reinterpret_cast<const float2*>(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, cl)));
+                ov[q] = __ldcg(reinterpret_cast<const float2*>(fp32_at(vec + (size_t)(u.yo + i) * kTcRowBytes, cl)));
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int idx = idx0 + 128 * q;
+              if (idx >= total) continue;
+              const int i = idx % N, fs = idx / N;
+              const double* gb = value_base(out, N, am, grp * kTcFields + (fs >> 1), fs & 1, F, single, msingle);
+              if (!gb) continue;
+              double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
+              gp[N + i] = make_double2((double)ev[q].x + (double)ov[q].x, (double)ev[q].y + (double)ov[q].y);
+              gp[N - 1 - i] = make_double2((double)ev[q].x - (double)ov[q].x, (double)ev[q].y - (double)ov[q].y);
+            }
+          }
+        } else {
+          const double* bdst = coef_base(out, N, am, grp * kTcFields + fl, sg, F, single, msingle);
+          if (bdst)
+            for (int t0 = 0; t0 < nx; t0 += 16) {
+              float v[16];
+#pragma unroll
+              for (int q = 0; q < 16; ++q)
+                v[q] = t0 + q < nx ? __ldcg(fp32_at(vec + (size_t)(t0 + q) * kTcRowBytes, col)) : 0.f;
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                const int t = t0 + q;
+                if (t < nx) const_cast<double*>(bdst)[2 * row_kk(u, t) + cc] = (double)v[q];
+              }
+            }
+        }
+        __threadfence_block();
+        io_bar();
+      }
+      if (!have) break;
+      prev_it = it;
+      prev_iseq = iseq;
     }
   }
   if (*((volatile int*)&ctl->abort) && tid == 0) atomicExch(p.err, 1);
