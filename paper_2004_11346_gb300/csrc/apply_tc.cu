@@ -122,7 +122,7 @@ constexpr int kProdWarps = 3;                 // warps staging operands
 constexpr int kMmaWarp = kProdWarps;          // the MMA-issuing warp
 constexpr int kEpiWarp0 = kProdWarps + 1;     // first epilogue warp
 constexpr int kEpiWarps = 4;                  // one warpgroup drains the accumulators
-constexpr int kIoWarp0 = kEpiWarp0 + kEpiWarps;  // 4 I/O warps: gather, parity fold / scatter
+constexpr int kIoWarp0 = kEpiWarp0 + kEpiWarps;  // 8 I/O warps: gather, parity fold / scatter
 constexpr int kTrStride = 33;                 // padded 32 x 32 transpose tile (floats)
 constexpr int kPieceA = kTcR * kTcKC * 2;      // bytes of one A piece in a stage (8 KB)
 constexpr int kStageA = 3 * kPieceA;           // 24 KB
@@ -226,7 +226,7 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-__device__ __forceinline__ void io_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+__device__ __forceinline__ void io_bar() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
 
 __device__ __forceinline__ long coef_offset(long N, long m) {
   long a = m < 0 ? -m : m;
@@ -573,8 +573,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   } else if (warp >= kIoWarp0) {
     // I/O warps: gather of item i into slot i % 2 (after the fold of item i-2 from that
     // slot), parity fold / scatter of item i once its tiles are done
-    const int e = tid - 32 * kIoWarp0;  // 0..127 = column (right-hand side)
-    const int col = e;
+    const int e = tid - 32 * kIoWarp0;  // 0..255
+    const int col = e & 127, half = e >> 7;  // column (right-hand side); row half
     const int fl = col >> 2, sg = (col >> 1) & 1, cc = col & 1;
     int tiles_through = 0;
     bool ok = true;
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
         const int nx = u.nce + u.nco;
         if (fwd) {
           const double* bsrc = coef_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
-          for (int t0 = 0; t0 < nx; t0 += 16) {
+          for (int t0 = 16 * half; t0 < nx; t0 += 32) {
             float v[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -601,10 +601,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
             for (int q = 0; q < 16; ++q)
               if (t0 + q < nx) put_pieces(vec + (size_t)(t0 + q) * kTcRowBytes, col, v[q]);
           }
-          for (int i = 0; i < 2 * N; ++i) __stcg(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, col), 0.f);
+          for (int i = half; i < 2 * N; i += 2) __stcg(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, col), 0.f);
         } else {
           const double* gb = value_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
-          for (int i0 = 0; i0 < N; i0 += 8) {
+          for (int i0 = 8 * half; i0 < N; i0 += 16) {
             double a[8], b[8], wi[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
               }
             }
           }
-          for (int t = 0; t < nx; ++t) __stcg(fp32_at(vec + (size_t)t * kTcRowBytes, col), 0.f);
+          for (int t = half; t < nx; t += 2) __stcg(fp32_at(vec + (size_t)t * kTcRowBytes, col), 0.f);
         }
         __threadfence_block();
         io_bar();
@@ -641,11 +641,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
         const int nx = u.nce + u.nco;
         if (fwd) {
           const int total = N * 2 * kTcFields;
-          for (int idx0 = e; idx0 < total; idx0 += 128 * 8) {
+          for (int idx0 = e; idx0 < total; idx0 += 256 * 8) {
             float2 ev[8], ov[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-              const int idx = idx0 + 128 * q;
+              const int idx = idx0 + 256 * q;
               ev[q] = make_float2(0.f, 0.f);
               ov[q] = make_float2(0.f, 0.f);
               if (idx < total) {
@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-              const int idx = idx0 + 128 * q;
+              const int idx = idx0 + 256 * q;
               if (idx >= total) continue;
               const int i = idx % N, fs = idx / N;
               const double* gb = value_base(out, N, am, grp * kTcFields + (fs >> 1), fs & 1, F, single, msingle);
@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
         } else {
           const double* bdst = coef_base(out, N, am, grp * kTcFields + fl, sg, F, single, msingle);
           if (bdst)
-            for (int t0 = 0; t0 < nx; t0 += 16) {
+            for (int t0 = 16 * half; t0 < nx; t0 += 32) {
               float v[16];
 #pragma unroll
               for (int q = 0; q < 16; ++q)

@@ -15,7 +15,7 @@ constexpr int kTcFields = 32;            // fields per work item
 constexpr int kTcR = 4 * kTcFields;      // 128 right-hand sides = MMA M
 constexpr int kTcNT = 128;               // N tile (rows of one block product)
 constexpr int kTcKC = 32;                // K chunk per pipeline stage
-constexpr int kTcThreads = 384;          // 3 producer warps, MMA warp, 8 epilogue warps
+constexpr int kTcThreads = 512;          // 3 producer, 1 MMA, 4 epilogue and 8 I/O warps
 constexpr int kTcRowBytes = 3 * kTcR * 2;  // scratch row: 3 BF16 pieces x 128 (or 128 FP32)
 
 struct TcPlan {
