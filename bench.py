@@ -405,13 +405,16 @@ def roofline(plan, w, F, flops, fwd_ms):
     if prec == "fp64":
         kname, peak, src = "alt_forward_f64_kernel", FP64_PEAK_GFLOPS, \
             "GB300 nominal FP64 1.25 TFLOP/s (FMA-chain probe: 1.197)"
+        ops = plan.program(parts=("ops",))["ops"]
+        fac = int((ops["ld"].astype(np.int64) * ops["ni"]).sum()) * 8
+        tr, tsrc = traffic_for(kname, w["name"], fac + io_bytes)
         return {"kernel": kname, "bound": "alu", "achieved": flops / t / 1e9, "peak": peak, "unit": "GFLOP/s",
-                "frac": flops / t / 1e9 / peak, "traffic": traffic_for(kname, w["name"]),
-                "flops_per_launch": flops, "peak_source": src}
+                "frac": flops / t / 1e9 / peak, "traffic": tr, "traffic_source": tsrc,
+                "bytes_per_launch": fac + io_bytes, "flops_per_launch": flops, "peak_source": src}
     if prec == "fp32":
         kname, peak = "alt_forward_f32_kernel", FP32_PEAK_GFLOPS
         return {"kernel": kname, "bound": "alu", "achieved": flops / t / 1e9, "peak": peak, "unit": "GFLOP/s",
-                "frac": flops / t / 1e9 / peak, "traffic": traffic_for(kname, w["name"]), "flops_per_launch": flops,
+                "frac": flops / t / 1e9 / peak, "traffic": traffic_for(kname, w["name"])[0], "flops_per_launch": flops,
                 "peak_source": "128 FP32 lanes x 2 FLOP x 152 SMs x 2.07 GHz (FMA-chain probe: 73.2)"}
     # tensor-core split-BF16 path: each product costs 6 BF16 MMAs
     pk = measured_peaks()
@@ -422,7 +425,8 @@ def roofline(plan, w, F, flops, fwd_ms):
     t_frac = flops / t / 1e9 / tens_peak
     h_frac = algo_bytes / t / 1e9 / pk["hbm"]
     kname = "alt_tc_kernel"
-    base = {"kernel": kname, "traffic": traffic_for(kname, w["name"]), "flops_per_launch": flops,
+    tr, tsrc = traffic_for(kname, w["name"], algo_bytes)
+    base = {"kernel": kname, "traffic": tr, "traffic_source": tsrc, "flops_per_launch": flops,
             "bytes_per_launch": algo_bytes, "factor_image_bytes": img, "io_bytes": io_bytes}
     if t_frac >= h_frac:
         return {**base, "bound": "tensor", "achieved": flops / t / 1e12, "peak": tens_peak / 1e3, "unit": "TFLOP/s",
@@ -432,14 +436,27 @@ def roofline(plan, w, F, flops, fwd_ms):
             "frac": h_frac, "peak_source": f"{pk['source']} HBM copy {pk['hbm']} GB/s; tensor frac {t_frac:.3f}"}
 
 
-def traffic_for(kernel, workload_name):
-    """DRAM bytes per launch from a committed ncu capture of this kernel and workload, if any."""
+def traffic_for(kernel, workload_name, algo_bytes=None):
+    """DRAM bytes per launch of `kernel` from a committed ncu capture (profiles/traffic.json).
+
+    A capture of the same workload is used as it is; otherwise a capture of a
+    smaller case of the same kernel is scaled by the ratio of algorithmic bytes
+    (traffic assumed proportional), and the source says so.
+    """
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
-            return json.load(fh).get(kernel, {}).get(workload_name)
+            table = json.load(fh).get(kernel, {})
     except (OSError, ValueError):
-        return None
+        return None, None
+    if workload_name in table:
+        return table[workload_name], f"ncu capture of {workload_name}"
+    if algo_bytes:
+        for w, v in table.items():
+            ref = table.get("_algorithmic_" + w)
+            if not w.startswith("_") and ref:
+                return algo_bytes * v / ref, f"ncu capture of {w}, scaled by algorithmic bytes"
+    return None, None
 
 
 def main():
