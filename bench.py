@@ -367,7 +367,46 @@ def compare(torch, sht, _lib, w, plan, beta, g, args, stream):
     out["dense_fp64"] = {"fields_per_s": 1e3 / ms, "forward_ms": f, "inverse_ms": i,
                          "entries": pd.stats()["entries_total"]}
     del pd
+    out["sht"] = sht_timings(torch, w, plan, beta, g, K, stream)
     return out
+
+
+def sht_timings(torch, w, plan, beta_in, g, K, stream):
+    """The phi-direction DFT (synthesis + analysis) and the full SHT (ALT + DFT,
+    both directions) of the same F fields, and cuFFT of the same batch of
+    length-(4N-1) complex FP64 transforms as a comparator (no half-sample
+    shift, no transpose: a lower bound on a library DFT of this layout)."""
+    N, F = w["N"], g.shape[0]
+    f = torch.empty((F, 2 * N, 4 * N - 1, 2), dtype=torch.float64, device="cuda")
+    g2 = torch.empty_like(g)
+    beta = torch.empty_like(beta_in)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(K):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / K
+
+    phi_ms = timed(lambda: (plan.phi_synthesis(g, out=f), plan.phi_analysis(f, out=g2)))
+    phi_err = float((g2 - g).norm() / g.norm())
+    sht_ms = timed(lambda: (plan.sht_forward(beta_in, out=f), plan.sht_inverse(f, out=beta)))
+    plan.sync()
+    sht_err = float((beta - beta_in).norm() / beta_in.norm())
+    gc = torch.view_as_complex(g)
+    fft_ms = timed(lambda: (torch.fft.ifft(gc, dim=1), torch.fft.fft(gc, dim=1)))
+    phi_bytes = 2 * 2 * g.numel() * 8  # each direction reads and writes F x (4N-1) x 2N complex FP64
+    return {"phi_round_trip_ms": phi_ms, "phi_round_trip_rel_err": phi_err,
+            "phi_GBps": phi_bytes / (phi_ms * 1e-3) / 1e9,
+            "sht_round_trip_ms": sht_ms, "sht_fields_per_s": F / (sht_ms * 1e-3),
+            "sht_round_trip_rel_err": sht_err,
+            "cufft_c128_round_trip_ms": fft_ms,
+            "phi_arith": "f64" if w["precision"] == "fp64" else "f32"}
 
 
 def measured_peaks():

@@ -159,15 +159,32 @@ sht_status sht_inverse(sht_plan_t plan, const double* f, double* beta, int F, vo
 /* Copy one of the plan's host-side program arrays into dst_host (caller-owned,
  * *bytes long); with dst_host == NULL only *bytes is set to the size needed.
  * Layouts are those of the library's internal program (units, ops, phase
- * table, packed FP64 factors, schedule); used to inspect the factorisation. */
+ * table, packed FP64 factors, schedule) and the plan's sht_opts; used to
+ * inspect the factorisation. */
 typedef enum {
   SHT_EXPORT_UNITS = 0,
   SHT_EXPORT_OPS = 1,
   SHT_EXPORT_PHASES = 2,
   SHT_EXPORT_FACTORS = 3,
-  SHT_EXPORT_ORDER = 4
+  SHT_EXPORT_ORDER = 4,
+  SHT_EXPORT_OPTS = 5
 } sht_export_kind;
 sht_status sht_plan_export(sht_plan_t plan, int what, void* dst_host, size_t* bytes);
+
+/* Save the plan's precomputation (Sec. 3.2-3.3: nodes, weights, the block
+ * factorisation as the packed apply program, options and statistics) to a
+ * file, so that later processes skip the factorisation.  The file is written
+ * in native byte order with a 64-bit checksum.  SHT_ERR_IO when the file
+ * cannot be written. */
+sht_status sht_plan_save(sht_plan_t plan, const char* path);
+
+/* Load a plan written by sht_plan_save and upload it to the current device
+ * (host-only plans stay host-only).  The file is checked (magic, version,
+ * struct sizes, checksum, and the same consistency check every built program
+ * passes: unit layouts, op ranges, factor offsets, schedule) before anything
+ * reaches the GPU: SHT_ERR_IO for a missing, damaged or foreign file,
+ * SHT_ERR_CUDA without a device.  The caller owns the new plan. */
+sht_status sht_plan_load(const char* path, sht_plan_t* out);
 
 /* alt_forward_m without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory (a memory

@@ -51,6 +51,21 @@ class Plan:
         self.opts = opts(N, eps, **kw)
         self.handle = _lib.sht_plan_create(N, eps, self.opts)
 
+    @classmethod
+    def load(cls, path: str) -> "Plan":
+        """A plan read back from a file written by save() (sht_plan_load)."""
+        self = cls.__new__(cls)
+        self.handle = None
+        self.handle = _lib.sht_plan_load(path)
+        self.opts = _lib.sht_plan_opts(self.handle)
+        self.N = int(self.stats()["N"])
+        self.eps = float(self.opts.eps)
+        return self
+
+    def save(self, path: str):
+        """Write the plan's precomputation to `path` (sht_plan_save)."""
+        _lib.sht_plan_save(self.handle, path)
+
     def close(self):
         if self.handle:
             _lib.sht_plan_destroy(self.handle)

@@ -13,7 +13,8 @@ import os
 
 from . import build as _build
 
-SHT_OK = 0
+(SHT_OK, SHT_ERR_ARG, SHT_ERR_OOM, SHT_ERR_CUDA, SHT_ERR_TIMEOUT, SHT_ERR_NUMERIC, SHT_ERR_IO,
+ SHT_ERR_UNSUPPORTED) = range(8)
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error or no device",
           4: "device wait timed out", 5: "precomputation did not reach the tolerance",
           6: "plan file error", 7: "unsupported"}
@@ -21,7 +22,7 @@ SHT_FP64, SHT_FP32, SHT_MIXED = 0, 1, 2
 SHT_FLAG_FORCE_FACTOR = 1
 SHT_FLAG_HOST_ONLY = 2
 SHT_FLAG_DENSE = 4
-SHT_EXPORT_UNITS, SHT_EXPORT_OPS, SHT_EXPORT_PHASES, SHT_EXPORT_FACTORS, SHT_EXPORT_ORDER = range(5)
+SHT_EXPORT_UNITS, SHT_EXPORT_OPS, SHT_EXPORT_PHASES, SHT_EXPORT_FACTORS, SHT_EXPORT_ORDER, SHT_EXPORT_OPTS = range(6)
 
 
 class sht_opts(ctypes.Structure):
@@ -81,7 +82,7 @@ EXPORTED = [
     "sht_opts_default", "sht_plan_create", "sht_plan_destroy", "sht_plan_stats", "sht_plan_nodes",
     "sht_plan_export", "alt_forward", "alt_inverse", "alt_forward_m", "alt_inverse_m", "sht_sync",
     "sht_status_str", "alt_forward_m_noalloc", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
-    "sht_inverse",
+    "sht_inverse", "sht_plan_save", "sht_plan_load",
 ]
 
 
@@ -103,6 +104,8 @@ def load(build: bool = True):
     lib.sht_plan_stats.argtypes = [vp, ctypes.POINTER(sht_plan_info)]
     lib.sht_plan_nodes.argtypes = [vp, vp, vp]
     lib.sht_plan_export.argtypes = [vp, i, vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.sht_plan_save.argtypes = [vp, ctypes.c_char_p]
+    lib.sht_plan_load.argtypes = [ctypes.c_char_p, plan_p]
     for name in ("alt_forward", "alt_inverse", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
                  "sht_inverse"):
         getattr(lib, name).argtypes = [vp, vp, vp, i, vp]
@@ -156,6 +159,23 @@ def sht_plan_export(plan: int, what: int) -> bytes:
     buf = ctypes.create_string_buffer(max(1, n.value))
     check(load().sht_plan_export(plan, what, buf, ctypes.byref(n)), "sht_plan_export")
     return buf.raw[: n.value]
+
+
+def sht_plan_save(plan: int, path: str):
+    check(load().sht_plan_save(plan, os.fsencode(path)), "sht_plan_save")
+
+
+def sht_plan_load(path: str) -> int:
+    h = ctypes.c_void_p()
+    check(load().sht_plan_load(os.fsencode(path), ctypes.byref(h)), "sht_plan_load")
+    return h.value
+
+
+def sht_plan_opts(plan: int) -> sht_opts:
+    raw = sht_plan_export(plan, SHT_EXPORT_OPTS)
+    if len(raw) != ctypes.sizeof(sht_opts):
+        raise ShtError("sht_plan_export", SHT_ERR_ARG)
+    return sht_opts.from_buffer_copy(raw)
 
 
 def alt_forward(plan: int, beta: int, g: int, F: int, stream: int = 0):

@@ -449,40 +449,14 @@ void sht_opts_default(int N, double eps, sht_opts* o) {
   o->seed = 0x5eed2004u;
 }
 
-sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* out) {
-  if (!out || N < 1 || N > (1 << 14) || !(eps > 0.0 && eps < 1.0)) return SHT_ERR_ARG;
-  *out = nullptr;
-  sht_opts o;
-  if (opts) {
-    o = *opts;
-    o.eps = eps;
-  } else {
-    sht_opts_default(N, eps, &o);
-  }
-  if (o.n0 < 1 || o.n_leaf < 1 || o.r_k < 1 || o.rsvd_r < 1 || o.rsvd_q < 1 || !(o.oversample >= 1.0) ||
-      !(o.trim_delta >= 0.0) || o.max_fields < 1)
-    return SHT_ERR_ARG;
-  const bool host_only = (o.flags & SHT_FLAG_HOST_ONLY) != 0;
-  int ndev = 0;
-  if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)) return SHT_ERR_CUDA;
-  sht_plan_s* p = new (std::nothrow) sht_plan_s();
-  if (!p) return SHT_ERR_OOM;
-  std::string err;
-  sht_status s;
-  try {
-    s = build_program(N, o, p->prog, err);
-  } catch (const std::bad_alloc&) {
-    s = SHT_ERR_OOM;
-  }
-  if (s != SHT_OK) {
-    delete p;
-    return s;
-  }
-  if (host_only) {
-    p->host_only = true;
-    *out = p;
-    return SHT_OK;
-  }
+namespace {
+
+// Device side of a plan: upload the program and factors, build the operand
+// images of the precision's kernel, size the workspaces and the phi tables.
+// On failure everything allocated here is released again.
+sht_status attach_device(sht_plan_s* p) {
+  const int N = p->prog.N;
+  const sht_opts& o = p->prog.opts;
   auto t0 = std::chrono::steady_clock::now();
   cudaGetDevice(&p->device);
   int sms = 0;
@@ -539,7 +513,6 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_device(p);
-    delete p;
     return e == cudaErrorMemoryAllocation ? SHT_ERR_OOM : SHT_ERR_CUDA;
   }
   p->prog.info.workspace_bytes = (int64_t)(ws + ws32 + gws);
@@ -547,6 +520,51 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
     p->prog.info.factor_bytes =
         (int64_t)(P.factors.size() * (o.precision == SHT_FP64 ? sizeof(double) : sizeof(float)));
   p->prog.info.t_upload_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return SHT_OK;
+}
+
+
+}  // namespace
+
+sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* out) {
+  if (!out || N < 1 || N > (1 << 14) || !(eps > 0.0 && eps < 1.0)) return SHT_ERR_ARG;
+  *out = nullptr;
+  sht_opts o;
+  if (opts) {
+    o = *opts;
+    o.eps = eps;
+  } else {
+    sht_opts_default(N, eps, &o);
+  }
+  if (o.n0 < 1 || o.n_leaf < 1 || o.r_k < 1 || o.rsvd_r < 1 || o.rsvd_q < 1 || !(o.oversample >= 1.0) ||
+      !(o.trim_delta >= 0.0) || o.max_fields < 1)
+    return SHT_ERR_ARG;
+  const bool host_only = (o.flags & SHT_FLAG_HOST_ONLY) != 0;
+  int ndev = 0;
+  if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)) return SHT_ERR_CUDA;
+  sht_plan_s* p = new (std::nothrow) sht_plan_s();
+  if (!p) return SHT_ERR_OOM;
+  std::string err;
+  sht_status s;
+  try {
+    s = build_program(N, o, p->prog, err);
+  } catch (const std::bad_alloc&) {
+    s = SHT_ERR_OOM;
+  }
+  if (s != SHT_OK) {
+    delete p;
+    return s;
+  }
+  if (host_only) {
+    p->host_only = true;
+    *out = p;
+    return SHT_OK;
+  }
+  s = attach_device(p);
+  if (s != SHT_OK) {
+    delete p;
+    return s;
+  }
   *out = p;
   return SHT_OK;
 }
@@ -575,6 +593,7 @@ sht_status sht_plan_export(sht_plan_t p, int what, void* dst, size_t* bytes) {
     case SHT_EXPORT_PHASES: src = P.phase_tab.data(); n = P.phase_tab.size() * sizeof(int32_t); break;
     case SHT_EXPORT_FACTORS: src = P.factors.data(); n = P.factors.size() * sizeof(double); break;
     case SHT_EXPORT_ORDER: src = P.order.data(); n = P.order.size() * sizeof(int32_t); break;
+    case SHT_EXPORT_OPTS: src = &P.opts; n = sizeof(sht_opts); break;
     default: return SHT_ERR_ARG;
   }
   if (!dst) {
@@ -584,6 +603,162 @@ sht_status sht_plan_export(sht_plan_t p, int what, void* dst, size_t* bytes) {
   if (*bytes < n) return SHT_ERR_ARG;
   if (n) std::memcpy(dst, src, n);
   *bytes = n;
+  return SHT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plan files.  Layout (native byte order; both supported hosts are
+// little-endian):
+//   "SHTPLAN\0", u32 version, u32 sizeof(Op), sizeof(Unit), sizeof(sht_opts),
+//   sizeof(sht_plan_info), i32 N, i32 max_rows, sht_opts, sht_plan_info,
+//   then x, w, units, ops, phase table, factors, schedule as (u64 count,
+//   elements), then the 64-bit FNV-1a hash of every byte before it.
+
+}  // extern "C"
+
+namespace {
+
+constexpr char kPlanMagic[8] = {'S', 'H', 'T', 'P', 'L', 'A', 'N', '\0'};
+constexpr uint32_t kPlanVersion = 1;
+
+struct PlanWriter {
+  std::FILE* f;
+  uint64_t h = 0xcbf29ce484222325ull;
+  bool ok = true;
+  void put(const void* src, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(src);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001b3ull;
+    if (n && std::fwrite(src, 1, n, f) != n) ok = false;
+  }
+  template <class T>
+  void vec(const std::vector<T>& v) {
+    const uint64_t n = v.size();
+    put(&n, sizeof n);
+    put(v.data(), v.size() * sizeof(T));
+  }
+};
+
+struct PlanReader {
+  std::FILE* f;
+  uint64_t h = 0xcbf29ce484222325ull;
+  bool ok = true;
+  void get(void* dst, size_t n) {
+    if (!ok || (n && std::fread(dst, 1, n, f) != n)) {
+      ok = false;
+      return;
+    }
+    const unsigned char* b = static_cast<const unsigned char*>(dst);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001b3ull;
+  }
+  template <class T>
+  void vec(std::vector<T>& v, uint64_t max_elems) {
+    uint64_t n = 0;
+    get(&n, sizeof n);
+    if (!ok || n > max_elems) {
+      ok = false;
+      return;
+    }
+    v.resize((size_t)n);
+    get(v.data(), v.size() * sizeof(T));
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+sht_status sht_plan_save(sht_plan_t p, const char* path) {
+  if (!p || !path) return SHT_ERR_ARG;
+  std::FILE* f = std::fopen(path, "wb");
+  if (!f) return SHT_ERR_IO;
+  const HostProgram& P = p->prog;
+  PlanWriter w{f};
+  const uint32_t hdr[5] = {kPlanVersion, (uint32_t)sizeof(Op), (uint32_t)sizeof(Unit), (uint32_t)sizeof(sht_opts),
+                           (uint32_t)sizeof(sht_plan_info)};
+  w.put(kPlanMagic, sizeof kPlanMagic);
+  w.put(hdr, sizeof hdr);
+  const int32_t nm[2] = {P.N, P.max_rows};
+  w.put(nm, sizeof nm);
+  w.put(&P.opts, sizeof P.opts);
+  w.put(&P.info, sizeof P.info);
+  w.vec(P.x);
+  w.vec(P.w);
+  w.vec(P.units);
+  w.vec(P.ops);
+  w.vec(P.phase_tab);
+  w.vec(P.factors);
+  w.vec(P.order);
+  const uint64_t h = w.h;
+  if (std::fwrite(&h, sizeof h, 1, f) != 1) w.ok = false;
+  if (std::fclose(f) != 0) w.ok = false;
+  return w.ok ? SHT_OK : SHT_ERR_IO;
+}
+
+sht_status sht_plan_load(const char* path, sht_plan_t* out) {
+  if (!path || !out) return SHT_ERR_ARG;
+  *out = nullptr;
+  std::FILE* f = std::fopen(path, "rb");
+  if (!f) return SHT_ERR_IO;
+  sht_plan_s* p = new (std::nothrow) sht_plan_s();
+  if (!p) {
+    std::fclose(f);
+    return SHT_ERR_OOM;
+  }
+  HostProgram& P = p->prog;
+  PlanReader r{f};
+  char magic[8];
+  uint32_t hdr[5];
+  int32_t nm[2];
+  r.get(magic, sizeof magic);
+  r.get(hdr, sizeof hdr);
+  r.get(nm, sizeof nm);
+  bool ok = r.ok && std::memcmp(magic, kPlanMagic, sizeof magic) == 0 && hdr[0] == kPlanVersion &&
+            hdr[1] == sizeof(Op) && hdr[2] == sizeof(Unit) && hdr[3] == sizeof(sht_opts) &&
+            hdr[4] == sizeof(sht_plan_info) && nm[0] >= 1 && nm[0] <= (1 << 14) && nm[1] >= 0;
+  sht_status s = SHT_OK;
+  try {
+    if (ok) {
+      P.N = nm[0];
+      P.max_rows = nm[1];
+      r.get(&P.opts, sizeof P.opts);
+      r.get(&P.info, sizeof P.info);
+      // element-count limits keep a damaged header from requesting absurd allocations
+      const uint64_t K = 2 * (uint64_t)P.N, big = (uint64_t)1 << 40;
+      r.vec(P.x, K);
+      r.vec(P.w, K);
+      r.vec(P.units, K);
+      r.vec(P.ops, big);
+      r.vec(P.phase_tab, big);
+      r.vec(P.factors, big);
+      r.vec(P.order, K);
+      uint64_t h = 0;
+      const uint64_t expect = r.h;
+      ok = r.ok && std::fread(&h, sizeof h, 1, f) == 1 && h == expect;
+    }
+  } catch (const std::bad_alloc&) {
+    s = SHT_ERR_OOM;
+  }
+  std::fclose(f);
+  if (s == SHT_OK && !ok) s = SHT_ERR_IO;
+  std::string err;
+  if (s == SHT_OK && (P.opts.max_fields < 1 || !(P.opts.eps > 0.0 && P.opts.eps < 1.0) ||
+                      (P.opts.precision != SHT_FP64 && P.opts.precision != SHT_FP32 &&
+                       P.opts.precision != SHT_MIXED) ||
+                      !validate_program(P, err)))
+    s = SHT_ERR_IO;
+  if (s == SHT_OK) {
+    if (P.opts.flags & SHT_FLAG_HOST_ONLY) {
+      p->host_only = true;
+    } else {
+      int ndev = 0;
+      s = (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) ? SHT_ERR_CUDA : attach_device(p);
+    }
+  }
+  if (s != SHT_OK) {
+    delete p;
+    return s;
+  }
+  *out = p;
   return SHT_OK;
 }
 

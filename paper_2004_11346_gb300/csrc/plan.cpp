@@ -766,30 +766,7 @@ sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::strin
   std::iota(P.order.begin(), P.order.end(), 0);
   std::stable_sort(P.order.begin(), P.order.end(),
                    [&](int a, int b) { return P.units[a].cost > P.units[b].cost; });
-  // every op must stay inside its unit's vector space and the factor store
-  for (int am = 0; am < K; ++am) {
-    const Unit& u = P.units[am];
-    for (int oi = u.op_begin; oi < u.op_end; ++oi) {
-      const Op& op = P.ops[oi];
-      bool ok = op.mo >= 1 && op.ni >= 0 && op.ld >= op.mo && op.ld % 4 == 0 && op.b_off >= 0 &&
-                op.b_off % 4 == 0 && op.b_off + (int64_t)op.ld * op.ni <= (int64_t)P.factors.size() &&
-                op.in_len[0] >= 0 && op.in_len[1] >= 0 && op.in_len[0] + op.in_len[1] == op.ni &&
-                op.out_len[0] >= 0 && op.out_len[1] >= 0 && op.out_len[0] + op.out_len[1] == op.mo &&
-                op.phase >= 0 && op.phase < u.nphase;
-      for (int s = 0; s < 2 && ok; ++s) {
-        ok = ok && op.in_off[s] >= 0 && op.in_off[s] + op.in_len[s] <= u.nrows;
-        ok = ok && op.out_off[s] >= 0 && op.out_off[s] + op.out_len[s] <= u.nrows;
-      }
-      if (!ok) {
-        err = "apply program failed validation at order " + std::to_string(am);
-        return SHT_ERR_NUMERIC;
-      }
-    }
-    if (u.ye + 2 * N > u.nrows || u.xo + u.nco > u.ye) {
-      err = "unit layout failed validation at order " + std::to_string(am);
-      return SHT_ERR_NUMERIC;
-    }
-  }
+  if (!validate_program(P, err)) return SHT_ERR_NUMERIC;
   if (std::getenv("SHT_PLAN_DEBUG")) {
     int64_t d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int am = 0; am < K; ++am)
@@ -808,6 +785,64 @@ sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::strin
   I.threads = threads;
   I.t_factor_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return SHT_OK;
+}
+
+bool validate_program(const HostProgram& P, std::string& err) {
+  const int N = P.N;
+  const int K = 2 * N;
+  auto fail = [&](const char* what, int am) {
+    err = std::string(what) + " at order " + std::to_string(am);
+    return false;
+  };
+  if (N < 1 || (int)P.x.size() != K || (int)P.w.size() != K || (int)P.units.size() != K ||
+      (int)P.order.size() != K || P.max_rows < 0) {
+    err = "program sizes do not match N";
+    return false;
+  }
+  // the schedule is a permutation of the orders
+  std::vector<char> seen(K, 0);
+  for (int32_t v : P.order) {
+    if (v < 0 || v >= K || seen[v]) {
+      err = "schedule is not a permutation of the orders";
+      return false;
+    }
+    seen[v] = 1;
+  }
+  const int64_t nops = (int64_t)P.ops.size(), nfac = (int64_t)P.factors.size();
+  const int64_t nph = (int64_t)P.phase_tab.size();
+  for (int am = 0; am < K; ++am) {
+    const Unit& u = P.units[am];
+    // vector-space layout: X_e, X_o, Y_e, Y_o, then the butterfly rows
+    const int nce = N - am / 2, nco = 2 * N - am - nce;
+    if (u.am != am || u.nce != nce || u.nco != nco || u.xe != 0 || u.xo != nce || u.ye != nce + nco ||
+        u.yo != u.ye + N || u.nrows < u.yo + N || u.nrows > P.max_rows)
+      return fail("unit layout failed validation", am);
+    if (u.op_begin < 0 || u.op_end < u.op_begin || u.op_end > nops || u.nphase < 0 || u.ph_begin < 0 ||
+        (int64_t)u.ph_begin + u.nphase + 1 > nph)
+      return fail("unit op range failed validation", am);
+    const int32_t* ph = P.phase_tab.data() + u.ph_begin;
+    if (ph[0] != u.op_begin || ph[u.nphase] != u.op_end) return fail("phase table failed validation", am);
+    for (int q = 0; q < u.nphase; ++q) {
+      if (ph[q + 1] < ph[q]) return fail("phase table failed validation", am);
+      for (int oi = ph[q]; oi < ph[q + 1]; ++oi)
+        if (P.ops[oi].phase != q) return fail("phase table failed validation", am);
+    }
+    // every op stays inside its unit's vector space and the factor store
+    for (int oi = u.op_begin; oi < u.op_end; ++oi) {
+      const Op& op = P.ops[oi];
+      bool ok = op.mo >= 1 && op.ni >= 0 && op.ld >= op.mo && op.ld % 4 == 0 && op.b_off >= 0 &&
+                op.b_off % 4 == 0 && op.b_off + (int64_t)op.ld * op.ni <= nfac && op.in_len[0] >= 0 &&
+                op.in_len[1] >= 0 && op.in_len[0] + op.in_len[1] == op.ni && op.out_len[0] >= 0 &&
+                op.out_len[1] >= 0 && op.out_len[0] + op.out_len[1] == op.mo && op.phase >= 0 &&
+                op.phase < u.nphase && (op.flags & ~(OP_FWD_ACCUM | OP_BWD_ACCUM)) == 0;
+      for (int s = 0; s < 2 && ok; ++s) {
+        ok = ok && op.in_off[s] >= 0 && op.in_off[s] + op.in_len[s] <= u.nrows;
+        ok = ok && op.out_off[s] >= 0 && op.out_off[s] + op.out_len[s] <= u.nrows;
+      }
+      if (!ok) return fail("apply program failed validation", am);
+    }
+  }
+  return true;
 }
 
 }  // namespace sht

@@ -26,6 +26,12 @@ struct HostProgram {
 // Build the apply program (Sec. 3.2-3.3).  Returns SHT_OK or an error code.
 sht_status build_program(int N, const sht_opts& opts, HostProgram& out, std::string& err);
 
+// Check that a program is internally consistent: unit layouts, op and phase
+// ranges, factor offsets and the schedule.  Every program the kernels see
+// (built or loaded from a file) passes this first, so no op can address rows
+// or factors outside its buffers.
+bool validate_program(const HostProgram& P, std::string& err);
+
 // Gauss-Legendre rule on n points, ascending (used by the plan only).
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 

@@ -1,0 +1,139 @@
+"""Plan files (sht_plan_save / sht_plan_load).
+
+Host-side: a saved and reloaded plan exports the same program byte for byte
+and still reproduces the oracle through the test-only numpy apply; missing,
+truncated, damaged and foreign files are refused with SHT_ERR_IO, including a
+file whose checksum was recomputed over a program that addresses factors past
+the end of the store (the consistency check, not the checksum, catches it).
+GPU: a loaded plan of each precision gives the original plan's results.
+"""
+import struct
+
+import numpy as np
+import pytest
+
+import host_apply
+import oracle
+import paper_2004_11346_gb300 as sht
+from paper_2004_11346_gb300 import _lib, inputs
+
+HOST = _lib.SHT_FLAG_HOST_ONLY
+PARTS = ("units", "ops", "phases", "factors", "order")
+HEADER = 8 + 5 * 4 + 2 * 4  # magic, version and struct sizes, N and max_rows
+
+
+def fnv1a(data: bytes) -> int:
+    h = 0xcbf29ce484222325
+    for b in data:
+        h = ((h ^ b) * 0x100000001b3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+@pytest.fixture(scope="module")
+def saved(tmp_path_factory):
+    p = sht.Plan(40, 1e-10, flags=HOST, n0=12, n_leaf=6)
+    path = str(tmp_path_factory.mktemp("plans") / "n40.plan")
+    p.save(path)
+    return p, path
+
+
+def test_round_trip_is_exact(saved):
+    p, path = saved
+    q = sht.Plan.load(path)
+    assert q.host_only and q.N == p.N and q.eps == p.eps
+    a, b = p.program(PARTS), q.program(PARTS)
+    for k in PARTS:
+        assert a[k].tobytes() == b[k].tobytes(), k
+    sa, sb = p.stats(), q.stats()
+    for k in ("entries_total", "n_ops", "n_blocks_idbf", "n_blocks_lowrank", "n_blocks_dense", "max_rank"):
+        assert sa[k] == sb[k], k
+    xa, wa = p.nodes()
+    xb, wb = q.nodes()
+    assert np.array_equal(xa, xb) and np.array_equal(wa, wb)
+
+
+def test_loaded_program_reproduces_oracle(saved):
+    _, path = saved
+    q = sht.Plan.load(path)
+    N = q.N
+    beta = inputs.coefficients(N, 1, seed=5)
+    g = host_apply.forward(q.program(), N, beta[0])
+    ref = oracle.alt_forward(N, beta)[0]
+    assert np.linalg.norm(g - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def expect_io(path):
+    with pytest.raises(_lib.ShtError) as ei:
+        sht.Plan.load(str(path))
+    assert ei.value.status == _lib.SHT_ERR_IO
+
+
+def test_missing_file(tmp_path):
+    expect_io(tmp_path / "nothing.plan")
+
+
+def test_foreign_and_damaged_files(saved, tmp_path):
+    _, path = saved
+    raw = open(path, "rb").read()
+    cases = {
+        "empty": b"",
+        "text": b"not a plan file\n" * 8,
+        "truncated": raw[: len(raw) // 2],
+        "no_checksum": raw[:-8],
+        "bad_magic": b"X" + raw[1:],
+        "bad_version": raw[:8] + struct.pack("<I", 99) + raw[12:],
+    }
+    # one flipped bit in the middle of the factor store
+    flip = bytearray(raw)
+    flip[len(raw) // 2] ^= 0x10
+    cases["bit_flip"] = bytes(flip)
+    for name, data in cases.items():
+        f = tmp_path / f"{name}.plan"
+        f.write_bytes(data)
+        expect_io(f)
+
+
+def test_consistent_checksum_but_invalid_program(saved, tmp_path):
+    """A program whose first op reads past the factor store is refused even
+    with a matching checksum."""
+    p, path = saved
+    raw = bytearray(open(path, "rb").read())
+    prog = p.program(("ops",))
+    # locate the ops array: it is stored as (u64 count, 64-byte records)
+    ops_bytes = prog["ops"].tobytes()
+    at = bytes(raw).find(ops_bytes)
+    assert at > HEADER and struct.unpack_from("<Q", raw, at - 8)[0] == len(prog["ops"])
+    struct.pack_into("<q", raw, at, 1 << 40)  # b_off of op 0
+    body = bytes(raw[:-8])
+    bad = tmp_path / "forged.plan"
+    bad.write_bytes(body + struct.pack("<Q", fnv1a(body)))
+    expect_io(bad)
+    # the same forgery without the change loads: the checksum routine matches
+    good = tmp_path / "resealed.plan"
+    orig = open(path, "rb").read()
+    good.write_bytes(orig[:-8] + struct.pack("<Q", fnv1a(orig[:-8])))
+    assert sht.Plan.load(str(good)).N == p.N
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,F,tol", [(_lib.SHT_FP64, 2, 1e-13), (_lib.SHT_MIXED, 33, 1e-6)])
+def test_loaded_plan_on_gpu(tmp_path, prec, F, tol):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    N = 96
+    p = sht.Plan(N, 1e-12 if prec == _lib.SHT_FP64 else 1e-7, precision=prec)
+    path = str(tmp_path / "p.plan")
+    p.save(path)
+    q = sht.Plan.load(path)
+    beta = torch.from_numpy(inputs.coefficients(N, F, seed=8)).cuda()
+    ga, gb = p.forward(beta), q.forward(beta)
+    ba, bb = p.inverse(ga), q.inverse(gb)
+    torch.cuda.synchronize()
+    p.sync()
+    q.sync()
+    assert float((ga - gb).norm() / ga.norm()) <= tol
+    assert float((ba - bb).norm() / ba.norm()) <= tol
+    ref = oracle.alt_forward(N, beta.cpu().numpy())
+    e = np.linalg.norm(gb.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert e <= (1e-10 if prec == _lib.SHT_FP64 else 1e-6)
