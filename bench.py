@@ -241,7 +241,7 @@ def run_ours(args):
     w = workload(args.workload)
     N, F = w["N"], w["F"]
     t0 = time.perf_counter()
-    plan = plan_for(sht, w)
+    plan = plan_for(sht, w, max_fields=F)  # full-SHT workspace for the whole batch
     t_plan = time.perf_counter() - t0
     st = plan.stats()
     beta_h = rank_fields(N, F, w, rank)

@@ -28,7 +28,12 @@ struct C2 {
 
 namespace {
 
-constexpr int kThreads = 256;
+// threads per CTA: FP32 rows fit three CTAs per SM; an FP64 row's two buffers
+// take most of shared memory, so its single CTA carries more warps
+template <class T>
+struct PhiThreads {
+  static constexpr int value = sizeof(T) == 8 ? 512 : 256;
+};
 
 __device__ __forceinline__ long order_slot(long m) { return m == 0 ? 0 : (m > 0 ? 2 * m - 1 : -2 * m); }
 
@@ -39,6 +44,8 @@ __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
 
 // One Stockham pass of radix R: y[idxD + k Ns] = sum_r x[j + r n/R] w^{r (j%Ns + k Ns)}
 // with w = e^{s 2 pi i / (Ns R)} (s = +1 synthesis, -1 analysis via conjugation).
+// Generic form (any R): every output re-reads its R inputs; used only for
+// radices without a specialised butterfly (prime factors of M above 13).
 template <class T>
 __device__ void stockham_pass(const C2<T>* __restrict__ x, C2<T>* __restrict__ y, int n, int R, int Ns,
                               const C2<T>* __restrict__ tw, bool conj) {
@@ -62,8 +69,85 @@ __device__ void stockham_pass(const C2<T>* __restrict__ x, C2<T>* __restrict__ y
   }
 }
 
+// The same pass for a fixed small odd radix.  The phase factor splits as
+// w^{r (jn + k Ns)} = w^{r jn} * omega^{r k} (jn = j mod Ns, omega =
+// e^{s 2 pi i / R} = w^{Ns}): each thread takes whole butterflies, loads the
+// R inputs once and applies the R-1 twiddles w^{r jn} (r jn < Ns R, a table
+// entry).  The R-point DFT that remains pairs outputs k and R-k: with
+// P_r = v_r + v_{R-r}, Q_r = v_r - v_{R-r} (r = 1..h, h = (R-1)/2),
+//   y_k, y_{R-k} = v_0 + sum_r P_r cos(2 pi r k / R) +- i sum_r Q_r s sin(2 pi r k / R),
+// about a quarter of the multiplications of the direct R x R product.
+template <class T, int R>
+__device__ void stockham_pass_r(const C2<T>* __restrict__ x, C2<T>* __restrict__ y, int n, int Ns,
+                                const C2<T>* __restrict__ tw, bool conj) {
+  static_assert(R % 2 == 1, "odd radix");
+  constexpr int h = (R - 1) / 2;
+  const int nb = n / R;
+  const T sg = conj ? T(-1) : T(1);
+  T cs[h + 1], sn[h + 1];  // cos and s*sin of 2 pi t / R, t = 0..h
+#pragma unroll
+  for (int t = 0; t <= h; ++t) {
+    const C2<T> w = tw[t * Ns];
+    cs[t] = w.x;
+    sn[t] = sg * w.y;
+  }
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const int jn = j % Ns;
+    const int idxD = (j - jn) * R + jn;  // (j / Ns) * Ns R + jn
+    C2<T> v[R];
+    v[0] = x[j];
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = x[j + r * nb];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      C2<T> w = tw[r * jn];
+      w.y *= sg;
+      v[r] = cmul(v[r], w);
+    }
+    C2<T> P[h + 1], Q[h + 1];
+    T sx = v[0].x, sy = v[0].y;
+#pragma unroll
+    for (int r = 1; r <= h; ++r) {
+      P[r] = C2<T>{v[r].x + v[R - r].x, v[r].y + v[R - r].y};
+      Q[r] = C2<T>{v[r].x - v[R - r].x, v[r].y - v[R - r].y};
+      sx += P[r].x;
+      sy += P[r].y;
+    }
+    y[idxD] = C2<T>{sx, sy};
+#pragma unroll
+    for (int k = 1; k <= h; ++k) {
+      T ax = v[0].x, ay = v[0].y, bx = 0, by = 0;
+#pragma unroll
+      for (int r = 1; r <= h; ++r) {
+        const int t = (r * k) % R;  // compile-time after unrolling
+        const T c = t <= h ? cs[t] : cs[R - t];
+        const T sv = t <= h ? sn[t] : -sn[R - t];
+        ax += P[r].x * c;
+        ay += P[r].y * c;
+        bx += Q[r].x * sv;
+        by += Q[r].y * sv;
+      }
+      y[idxD + k * Ns] = C2<T>{ax - by, ay + bx};
+      y[idxD + (R - k) * Ns] = C2<T>{ax + by, ay - bx};
+    }
+  }
+}
+
 template <class T>
-__global__ void __launch_bounds__(kThreads) phi_kernel(PhiPlanDev<T> p, const double* __restrict__ in,
+__device__ __forceinline__ void run_pass(const C2<T>* x, C2<T>* y, int n, int R, int Ns, const C2<T>* tw,
+                                         bool conj) {
+  switch (R) {
+    case 3: stockham_pass_r<T, 3>(x, y, n, Ns, tw, conj); break;
+    case 5: stockham_pass_r<T, 5>(x, y, n, Ns, tw, conj); break;
+    case 7: stockham_pass_r<T, 7>(x, y, n, Ns, tw, conj); break;
+    case 11: stockham_pass_r<T, 11>(x, y, n, Ns, tw, conj); break;
+    case 13: stockham_pass_r<T, 13>(x, y, n, Ns, tw, conj); break;
+    default: stockham_pass<T>(x, y, n, R, Ns, tw, conj); break;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(PhiThreads<T>::value) phi_kernel(PhiPlanDev<T> p, const double* __restrict__ in,
                                                        double* __restrict__ out, int F, int analysis) {
   extern __shared__ unsigned char smem_raw[];
   C2<T>* buf0 = reinterpret_cast<C2<T>*>(smem_raw);
@@ -75,7 +159,8 @@ __global__ void __launch_bounds__(kThreads) phi_kernel(PhiPlanDev<T> p, const do
     const int f = row / K, l = row % K;
     // load
     if (!analysis) {
-      // c[m mod M] = g(m, l) e^{i pi m / M}
+      // c[m mod M] = g(m, l) e^{i pi m / M}; unrolled so that several strided loads are in flight
+#pragma unroll 8
       for (int mm = threadIdx.x; mm < M; mm += blockDim.x) {
         const int m = mm - (K - 1);  // -(K-1) .. K-1
         const double2 v = __ldg(reinterpret_cast<const double2*>(in) + f * nval + order_slot(m) * K + l);
@@ -84,6 +169,7 @@ __global__ void __launch_bounds__(kThreads) phi_kernel(PhiPlanDev<T> p, const do
         buf0[(m % M + M) % M] = cmul(a, s);
       }
     } else {
+#pragma unroll 8
       for (int j = threadIdx.x; j < M; j += blockDim.x) {
         const double2 v = __ldg(reinterpret_cast<const double2*>(in) + f * nval + (long)l * M + j);
         buf0[j] = C2<T>{(T)v.x, (T)v.y};
@@ -93,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) phi_kernel(PhiPlanDev<T> p, const do
     C2<T>* src = buf0;
     C2<T>* dst = buf1;
     for (int ps = 0; ps < p.npass; ++ps) {
-      stockham_pass<T>(src, dst, M, p.radix[ps], p.ns[ps], p.tw + p.tw_off[ps], analysis != 0);
+      run_pass<T>(src, dst, M, p.radix[ps], p.ns[ps], p.tw + p.tw_off[ps], analysis != 0);
       __syncthreads();
       C2<T>* t = src;
       src = dst;
@@ -205,7 +291,7 @@ cudaError_t PhiTables<T>::launch(const double* in, double* out, int F, bool anal
   const size_t smem = 2 * sizeof(C2<T>) * (size_t)M;
   cudaError_t e = cudaFuncSetAttribute(phi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  phi_kernel<T><<<grid, kThreads, smem, st>>>(d, in, out, F, analysis ? 1 : 0);
+  phi_kernel<T><<<grid, PhiThreads<T>::value, smem, st>>>(d, in, out, F, analysis ? 1 : 0);
   return cudaGetLastError();
 }
 

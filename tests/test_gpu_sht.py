@@ -34,7 +34,9 @@ def _cuda():
 
 
 @pytest.mark.parametrize("prec", [_lib.SHT_FP64, _lib.SHT_FP32])
-@pytest.mark.parametrize("N", [1, 2, 8, 16, 64])
+# M = 3, 7, 31 (prime: generic pass), 39 = 3*13, 55 = 5*11, 63 = 3*3*7, 195 = 3*5*13,
+# 255 = 3*5*17 (17: generic pass): every specialised radix that an odd M can have
+@pytest.mark.parametrize("N", [1, 2, 8, 10, 14, 16, 49, 64])
 def test_phi_synthesis_and_analysis(N, prec):
     p = sht.Plan(N, 1e-12 if prec == _lib.SHT_FP64 else 1e-7, precision=prec)
     rng = np.random.default_rng(N)
