@@ -37,6 +37,7 @@ EXTRA_WORKLOADS = {
     # smaller cases used for profiling captures
     "fp64_N512": dict(N=512, F=1, seed=0, decay=1.0, real_m0=False, eps=1e-12, precision="fp64"),
     "mixed_N512_F16": dict(N=512, F=16, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed"),
+    "mixed_N512_F32": dict(N=512, F=32, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed"),
 }
 FP64_PEAK_GFLOPS = 1250.0  # GB300 nominal FP64 (vector) rate
 
@@ -241,7 +242,8 @@ def run_ours(args):
     w = workload(args.workload)
     N, F = w["N"], w["F"]
     t0 = time.perf_counter()
-    plan = plan_for(sht, w, max_fields=F)  # full-SHT workspace for the whole batch
+    # workspace for the whole batch; CUDA events around every apply kernel
+    plan = plan_for(sht, w, max_fields=F, flags=_lib.SHT_FLAG_TIMING)
     t_plan = time.perf_counter() - t0
     st = plan.stats()
     beta_h = rank_fields(N, F, w, rank)
@@ -269,8 +271,18 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = ClockSampler(dev_index)
     time.sleep(0.3)
+    plan.kernel_time(reset=True)
     ms, fwd_ms, inv_ms = time_steps(torch, plan, beta, g, back, K, 0, stream)
     clk = clocks.stop()
+    kt = plan.kernel_time(reset=True)
+    kernels_per_call = 2 if w["precision"] == "mixed" else 1  # tensor-core kernel + output kernel
+    launches = kt["launches"] * kernels_per_call
+    # the dominant kernel alone, forward direction, on the same stream
+    for _ in range(K):
+        plan.forward(beta, out=g)
+    kf = plan.kernel_time(reset=True)
+    main_ms = kf["apply_ms"] / max(1, kf["launches"])
+    out_ms = kf["output_ms"] / max(1, kf["launches"])
     barrier()
     plan.sync()
     ms, fwd_ms, inv_ms = max_over_ranks([ms, fwd_ms, inv_ms])
@@ -301,7 +313,7 @@ def run_ours(args):
     del beta_pin, out_pin, beta_d
 
     flops, entries = program_flops(plan, F)
-    roof = roofline(plan, w, F, flops, fwd_ms)
+    roof = roofline(plan, w, F, flops, fwd_ms, main_ms, out_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -313,7 +325,7 @@ def run_ours(args):
         "roofline": roof,
         "e2e": {"value": world * F / (e2e_ms * 1e-3), "unit": "fields/s", "h2d_bytes_per_step": io_bytes,
                 "d2h_bytes_per_step": io_bytes},
-        "gpu_launches": 2 * K,
+        "gpu_launches": launches,
         "clocks": clk,
         "plan": {"t_factor_s": st["t_factor_s"], "t_create_s": t_plan, "threads": st["threads"],
                  "entries_total": st["entries_total"], "entries_matrix": st["entries_matrix"],
@@ -435,12 +447,17 @@ def tc_image_bytes(mo, ni):
     return 2 * 3 * np_ * kp
 
 
-def roofline(plan, w, F, flops, fwd_ms):
-    """Roofline of the dominant (forward) kernel: algorithmic FLOPs and bytes per launch."""
+def roofline(plan, w, F, flops, fwd_ms, main_ms, out_ms):
+    """Roofline of the dominant kernel (the forward block-product kernel, timed
+    alone with the library's CUDA events): algorithmic FLOPs and bytes per launch.
+    For the tensor-core path the forward apply as a whole (that kernel plus its
+    output kernel) is reported under "apply"."""
     N = w["N"]
-    io_bytes = F * (4 * N * N + (4 * N - 1) * 2 * N) * 16  # beta read + g written, FP64 complex
+    beta_bytes = F * 4 * N * N * 16          # FP64 complex coefficients
+    g_bytes = F * (4 * N - 1) * 2 * N * 16  # FP64 complex values at the nodes
+    io_bytes = beta_bytes + g_bytes
     prec = w["precision"]
-    t = fwd_ms * 1e-3
+    t = main_ms * 1e-3
     if prec == "fp64":
         kname, peak, src = "alt_forward_f64_kernel", FP64_PEAK_GFLOPS, \
             "GB300 nominal FP64 1.25 TFLOP/s (FMA-chain probe: 1.197)"
@@ -448,25 +465,34 @@ def roofline(plan, w, F, flops, fwd_ms):
         fac = int((ops["ld"].astype(np.int64) * ops["ni"]).sum()) * 8
         tr, tsrc = traffic_for(kname, w["name"], fac + io_bytes)
         return {"kernel": kname, "bound": "alu", "achieved": flops / t / 1e9, "peak": peak, "unit": "GFLOP/s",
-                "frac": flops / t / 1e9 / peak, "traffic": tr, "traffic_source": tsrc,
+                "frac": flops / t / 1e9 / peak, "traffic": tr, "traffic_source": tsrc, "kernel_ms": main_ms,
                 "bytes_per_launch": fac + io_bytes, "flops_per_launch": flops, "peak_source": src}
     if prec == "fp32":
         kname, peak = "alt_forward_f32_kernel", FP32_PEAK_GFLOPS
         return {"kernel": kname, "bound": "alu", "achieved": flops / t / 1e9, "peak": peak, "unit": "GFLOP/s",
-                "frac": flops / t / 1e9 / peak, "traffic": traffic_for(kname, w["name"])[0], "flops_per_launch": flops,
+                "frac": flops / t / 1e9 / peak, "traffic": traffic_for(kname, w["name"])[0], "kernel_ms": main_ms,
+                "flops_per_launch": flops,
                 "peak_source": "128 FP32 lanes x 2 FLOP x 152 SMs x 2.07 GHz (FMA-chain probe: 73.2)"}
-    # tensor-core split-BF16 path: each product costs 6 BF16 MMAs
+    # tensor-core split-BF16 path: each product costs 6 BF16 MMAs.  The kernel
+    # reads the operand images and beta once and writes the accumulated FP32
+    # node values (Y, 4 real right-hand sides x 4 bytes per node, order and field).
     pk = measured_peaks()
     ops = plan.program(parts=("ops",))["ops"]
     img = sum(tc_image_bytes(int(mo), int(ni)) for mo, ni in zip(ops["mo"], ops["ni"]))
-    algo_bytes = img + io_bytes
+    y_bytes = F * 2 * N * 2 * N * 16
+    algo_bytes = img + beta_bytes + y_bytes
     tens_peak = pk["bf16_sustained"] / 6.0 * 1e3  # GFLOP/s of FP32-quality split products
     t_frac = flops / t / 1e9 / tens_peak
     h_frac = algo_bytes / t / 1e9 / pk["hbm"]
     kname = "alt_tc_kernel"
     tr, tsrc = traffic_for(kname, w["name"], algo_bytes)
-    base = {"kernel": kname, "traffic": tr, "traffic_source": tsrc, "flops_per_launch": flops,
-            "bytes_per_launch": algo_bytes, "factor_image_bytes": img, "io_bytes": io_bytes}
+    apply_bytes = img + io_bytes
+    base = {"kernel": kname, "kernel_ms": main_ms, "traffic": tr, "traffic_source": tsrc, "flops_per_launch": flops,
+            "bytes_per_launch": algo_bytes, "factor_image_bytes": img, "beta_bytes": beta_bytes,
+            "y_bytes": y_bytes,
+            "apply": {"kernels": "alt_tc_kernel + tc_out_kernel", "ms": fwd_ms, "output_kernel_ms": out_ms,
+                      "bytes": apply_bytes, "GBps": apply_bytes / (fwd_ms * 1e-3) / 1e9,
+                      "hbm_frac": apply_bytes / (fwd_ms * 1e-3) / 1e9 / pk["hbm"]}}
     if t_frac >= h_frac:
         return {**base, "bound": "tensor", "achieved": flops / t / 1e12, "peak": tens_peak / 1e3, "unit": "TFLOP/s",
                 "frac": t_frac, "peak_source": f"{pk['source']} bf16 sustained {pk['bf16_sustained']} TFLOP/s / 6 "

@@ -87,6 +87,8 @@ typedef struct {
 #define SHT_FLAG_DENSE 4        /* no partition, trimming or factorisation: every
                                    parity matrix is applied dense (the O(N^3)
                                    transform, kept as a baseline)                */
+#define SHT_FLAG_TIMING 8       /* record CUDA events around every apply kernel
+                                   launch (see sht_plan_kernel_time)             */
 
 /* Plan statistics (Sec. 5 experiments: block counts, ranks, timings). */
 typedef struct {
@@ -203,6 +205,19 @@ sht_status sht_plan_load(const char* path, sht_plan_t* out);
  *  - All calls share the array and it keeps the last call's contents: calls
  *    that may overlap on the GPU race on it and must be serialised. */
 sht_status alt_forward_m_noalloc(sht_plan_t plan, int m, const double* beta_m, double* g_m, int F, void* stream);
+
+/* Device time of the plan's apply kernels, for plans created with
+ * SHT_FLAG_TIMING (instrumentation; the paper has no counterpart).  Every
+ * alt_* call then records CUDA events on its stream around each kernel it
+ * launches; this call waits for them and returns, summed over the launches
+ * since the last reset (at most the latest 256):
+ *  - apply_ms: the block-product kernels (the tensor-core kernel with its
+ *    gather for SHT_MIXED; the whole apply for SHT_FP64 / SHT_FP32),
+ *  - output_ms: the tensor-core path's output kernel (parity fold or
+ *    scatter; 0 for the other precisions),
+ *  - launches: the number of launches summed.
+ * reset != 0 starts a new sum.  SHT_ERR_UNSUPPORTED without the flag. */
+sht_status sht_plan_kernel_time(sht_plan_t plan, int reset, double* apply_ms, double* output_ms, int64_t* launches);
 
 /* Wait for the plan's work on `stream` and return any latched device error. */
 sht_status sht_sync(sht_plan_t plan, void* stream);

@@ -199,5 +199,10 @@ class Plan:
         _lib.sht_inverse(self.handle, f.data_ptr(), beta.data_ptr(), F, self._stream())
         return beta
 
+    def kernel_time(self, reset: bool = True) -> dict:
+        """Summed device time of the apply kernels since the last reset (plans
+        created with flags including SHT_FLAG_TIMING; sht_plan_kernel_time)."""
+        return _lib.sht_plan_kernel_time(self.handle, reset)
+
     def sync(self):
         _lib.sht_sync(self.handle, self._stream())

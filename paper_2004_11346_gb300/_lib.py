@@ -22,6 +22,7 @@ SHT_FP64, SHT_FP32, SHT_MIXED = 0, 1, 2
 SHT_FLAG_FORCE_FACTOR = 1
 SHT_FLAG_HOST_ONLY = 2
 SHT_FLAG_DENSE = 4
+SHT_FLAG_TIMING = 8
 SHT_EXPORT_UNITS, SHT_EXPORT_OPS, SHT_EXPORT_PHASES, SHT_EXPORT_FACTORS, SHT_EXPORT_ORDER, SHT_EXPORT_OPTS = range(6)
 
 
@@ -82,7 +83,7 @@ EXPORTED = [
     "sht_opts_default", "sht_plan_create", "sht_plan_destroy", "sht_plan_stats", "sht_plan_nodes",
     "sht_plan_export", "alt_forward", "alt_inverse", "alt_forward_m", "alt_inverse_m", "sht_sync",
     "sht_status_str", "alt_forward_m_noalloc", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
-    "sht_inverse", "sht_plan_save", "sht_plan_load",
+    "sht_inverse", "sht_plan_save", "sht_plan_load", "sht_plan_kernel_time",
 ]
 
 
@@ -105,6 +106,7 @@ def load(build: bool = True):
     lib.sht_plan_nodes.argtypes = [vp, vp, vp]
     lib.sht_plan_export.argtypes = [vp, i, vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.sht_plan_save.argtypes = [vp, ctypes.c_char_p]
+    lib.sht_plan_kernel_time.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64)]
     lib.sht_plan_load.argtypes = [ctypes.c_char_p, plan_p]
     for name in ("alt_forward", "alt_inverse", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
                  "sht_inverse"):
@@ -169,6 +171,13 @@ def sht_plan_load(path: str) -> int:
     h = ctypes.c_void_p()
     check(load().sht_plan_load(os.fsencode(path), ctypes.byref(h)), "sht_plan_load")
     return h.value
+
+
+def sht_plan_kernel_time(plan: int, reset: bool = True) -> dict:
+    a, o, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    check(load().sht_plan_kernel_time(plan, 1 if reset else 0, ctypes.byref(a), ctypes.byref(o), ctypes.byref(n)),
+          "sht_plan_kernel_time")
+    return {"apply_ms": a.value, "output_ms": o.value, "launches": n.value}
 
 
 def sht_plan_opts(plan: int) -> sht_opts:

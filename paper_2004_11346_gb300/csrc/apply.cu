@@ -302,10 +302,17 @@ struct sht_plan_s {
   double* d_gws = nullptr;
   // tensor-core path (precision SHT_MIXED): split-BF16 operand images
   uint16_t* d_img = nullptr;
-  int64_t* d_imgoff = nullptr;
+  TcOp* d_tcops = nullptr;
+  int32_t* d_tctiles = nullptr;
   unsigned char* d_wstc = nullptr;
+  float* d_acc = nullptr;  // accumulated rows of every work item (tc_gmax field groups)
+  int tc_gmax = 0;
   int* d_err = nullptr;
   int nslots_tc = 0;
+  // SHT_FLAG_TIMING: three events per recorded launch (before, between, after
+  // the kernels), a ring of kTimingSlots launches
+  std::vector<cudaEvent_t> tev;
+  int64_t tev_count = 0, tev_base = 0;
 };
 
 namespace {
@@ -319,7 +326,19 @@ cudaError_t upload(T** dst, const std::vector<T>& v) {
   return e;
 }
 
+constexpr int kTimingSlots = 256;
+
+// Events of the next recorded launch (nullptr without SHT_FLAG_TIMING).
+cudaEvent_t* timing_slot(sht_plan_s* p) {
+  if (p->tev.empty()) return nullptr;
+  cudaEvent_t* ev = p->tev.data() + 3 * (p->tev_count % kTimingSlots);
+  ++p->tev_count;
+  return ev;
+}
+
 void free_device(sht_plan_s* p) {
+  for (cudaEvent_t ev : p->tev) cudaEventDestroy(ev);
+  p->tev.clear();
   cudaFree(p->d_units);
   cudaFree(p->d_ops);
   cudaFree(p->d_phase);
@@ -332,8 +351,10 @@ void free_device(sht_plan_s* p) {
   cudaFree(p->d_ws32);
   cudaFree(p->d_gws);
   cudaFree(p->d_img);
-  cudaFree(p->d_imgoff);
+  cudaFree(p->d_tcops);
+  cudaFree(p->d_tctiles);
   cudaFree(p->d_wstc);
+  cudaFree(p->d_acc);
   cudaFree(p->d_err);
   p->phi64.release();
   p->phi32.release();
@@ -370,22 +391,37 @@ sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F,
   if (p->prog.opts.precision == SHT_MIXED) {
     TcPlan t;
     t.units = p->d_units;
-    t.ops = p->d_ops;
-    t.phase_tab = p->d_phase;
+    t.ops = p->d_tcops;
+    t.tiles = p->d_tctiles;
     t.order = p->d_order;
     t.img = p->d_img;
-    t.img_off = p->d_imgoff;
     t.w = p->d_w;
     t.ws = p->d_wstc;
+    t.acc = p->d_acc;
+    t.gmax = p->tc_gmax;
     t.counter = p->d_counter;
     t.err = p->d_err;
     t.N = p->prog.N;
     t.nunits = 2 * p->prog.N;
     t.max_rows = p->prog.max_rows;
-    const int groups = (F + kTcFields - 1) / kTcFields;
-    const int items = (single ? 1 : 2 * p->prog.N) * groups;
-    const int grid_tc = std::min(p->nslots_tc, std::max(1, items));
-    return launch_tc(t, fwd, in, out, F, single, m, grid_tc, st) == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
+    // the accumulation buffer holds tc_gmax groups of kTcFields fields: larger
+    // batches run as several launches on consecutive fields
+    const int N = p->prog.N;
+    const int64_t nb = 2L * (single ? 2 * N - (m < 0 ? -m : m) : 4L * N * N);  // doubles per field of beta
+    const int64_t ng = 2L * (single ? 2 * N : (4L * N - 1) * 2 * N);           // doubles per field of g
+    const int64_t in_stride = fwd ? nb : ng, out_stride = fwd ? ng : nb;
+    const int fb = kTcFields * p->tc_gmax;
+    for (int f0 = 0; f0 < F; f0 += fb) {
+      const int Fb = std::min(fb, F - f0);
+      if (f0 > 0 && cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
+      const int groups = (Fb + kTcFields - 1) / kTcFields;
+      const int items = (single ? 1 : 2 * N) * groups;
+      const int grid_tc = std::min(p->nslots_tc, std::max(1, items));
+      if (launch_tc(t, fwd, in + f0 * in_stride, out + f0 * out_stride, Fb, single, m, grid_tc, st,
+                    timing_slot(p)) != cudaSuccess)
+        return SHT_ERR_CUDA;
+    }
+    return SHT_OK;
   }
   if (p->prog.opts.precision == SHT_FP32) {
     F32Plan f;
@@ -403,16 +439,26 @@ sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F,
     const int groups = (F + kF32Fields - 1) / kF32Fields;
     const int items32 = (single ? 1 : 2 * p->prog.N) * groups;
     const int grid32 = std::min(p->nslots32, std::max(1, items32));
-    return launch_f32(f, fwd, in, out, F, single, m, grid32, st) == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
+    cudaEvent_t* ev = timing_slot(p);
+    if (ev && cudaEventRecord(ev[0], st) != cudaSuccess) return SHT_ERR_CUDA;
+    if (launch_f32(f, fwd, in, out, F, single, m, grid32, st) != cudaSuccess) return SHT_ERR_CUDA;
+    if (ev && (cudaEventRecord(ev[1], st) != cudaSuccess || cudaEventRecord(ev[2], st) != cudaSuccess))
+      return SHT_ERR_CUDA;
+    return SHT_OK;
   }
   const int items = single ? F : 2 * p->prog.N * F;
   const int grid = std::min(p->nslots, std::max(1, items));
   DevPlan d = dev_plan(p);
+  cudaEvent_t* ev = timing_slot(p);
+  if (ev && cudaEventRecord(ev[0], st) != cudaSuccess) return SHT_ERR_CUDA;
   if (fwd)
     alt_forward_f64_kernel<<<grid, kThreads, 0, st>>>(d, in, out, F, single, m);
   else
     alt_inverse_f64_kernel<<<grid, kThreads, 0, st>>>(d, in, out, F, single, m);
-  return cudaGetLastError() == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return SHT_ERR_CUDA;
+  if (ev && (cudaEventRecord(ev[1], st) != cudaSuccess || cudaEventRecord(ev[2], st) != cudaSuccess))
+    return SHT_ERR_CUDA;
+  return SHT_OK;
 }
 
 sht_status launch_phi(sht_plan_s* p, const double* in, double* out, int F, bool analysis, cudaStream_t st) {
@@ -478,13 +524,19 @@ sht_status attach_device(sht_plan_s* p) {
   size_t ws32 = 0;
   if (e == cudaSuccess && o.precision == SHT_MIXED) {
     std::vector<uint16_t> img;
-    std::vector<int64_t> off;
-    tc_build_images(P.ops, P.factors, img, off);
+    std::vector<TcOp> tops;
+    std::vector<int32_t> tiles;
+    tc_build_images(P.units, P.ops, P.factors, img, tops, tiles);
     e = upload(&p->d_img, img);
-    if (e == cudaSuccess) e = upload(&p->d_imgoff, off);
+    if (e == cudaSuccess) e = upload(&p->d_tcops, tops);
+    if (e == cudaSuccess) e = upload(&p->d_tctiles, tiles);
     p->nslots_tc = std::max(1, sms * tc_ctas_per_sm());
     ws32 = (size_t)p->nslots_tc * 2 * P.max_rows * kTcRowBytes;  // two vector spaces per CTA
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_wstc), std::max<size_t>(ws32, 8));
+    p->tc_gmax = (o.max_fields + kTcFields - 1) / kTcFields;
+    const size_t acc = (size_t)p->tc_gmax * 2 * N * kTcAccRows(N) * kTcR * sizeof(float);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_acc), acc);
+    ws32 += acc;
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
     p->prog.info.factor_bytes = (int64_t)(img.size() * sizeof(uint16_t));
@@ -509,6 +561,11 @@ sht_status attach_device(sht_plan_s* p) {
   if (e == cudaSuccess) {
     gws = (size_t)o.max_fields * (4 * (size_t)N - 1) * 2 * N * 2 * sizeof(double);
     e = cudaMalloc(reinterpret_cast<void**>(&p->d_gws), gws);
+  }
+  if (e == cudaSuccess && (o.flags & SHT_FLAG_TIMING)) {
+    p->tev.assign(3 * kTimingSlots, nullptr);
+    for (cudaEvent_t& ev : p->tev)
+      if (e == cudaSuccess) e = cudaEventCreate(&ev);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -840,6 +897,27 @@ sht_status sht_inverse(sht_plan_t p, const double* f, double* beta, int F, void*
     if (s == SHT_OK) s = launch(p, false, p->d_gws, beta + f0 * ncoef, n, 0, 0, st);
     if (s != SHT_OK) return s;
   }
+  return SHT_OK;
+}
+
+sht_status sht_plan_kernel_time(sht_plan_t p, int reset, double* apply_ms, double* output_ms, int64_t* launches) {
+  if (!p || !apply_ms || !output_ms || !launches) return SHT_ERR_ARG;
+  if (p->tev.empty()) return SHT_ERR_UNSUPPORTED;
+  const int64_t first = std::max(p->tev_base, p->tev_count - kTimingSlots);
+  double a = 0.0, o = 0.0;
+  for (int64_t k = first; k < p->tev_count; ++k) {
+    cudaEvent_t* ev = p->tev.data() + 3 * (k % kTimingSlots);
+    float t0 = 0.f, t1 = 0.f;
+    if (cudaEventSynchronize(ev[2]) != cudaSuccess || cudaEventElapsedTime(&t0, ev[0], ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t1, ev[1], ev[2]) != cudaSuccess)
+      return SHT_ERR_CUDA;
+    a += t0;
+    o += p->prog.opts.precision == SHT_MIXED ? t1 : 0.0;  // only the tensor-core path has an output kernel
+  }
+  *apply_ms = a;
+  *output_ms = o;
+  *launches = p->tev_count - first;
+  if (reset) p->tev_base = p->tev_count;
   return SHT_OK;
 }
 

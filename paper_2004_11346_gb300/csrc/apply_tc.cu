@@ -90,17 +90,35 @@ static void tc_pack(int NN, int KK, E elem, uint16_t* dst) {
   }
 }
 
-void tc_build_images(const std::vector<Op>& ops, const std::vector<double>& factors, std::vector<uint16_t>& img,
-                     std::vector<int64_t>& off) {
+void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops, const std::vector<double>& factors,
+                     std::vector<uint16_t>& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles) {
   const size_t n = ops.size();
-  off.assign(2 * n, 0);
+  tops.assign(n, TcOp{});
   size_t tot = 0;
   for (size_t i = 0; i < n; ++i) {
-    off[2 * i] = (int64_t)tot;
-    tot += tc_image_elems(ops[i].mo, ops[i].ni);
-    off[2 * i + 1] = (int64_t)tot;
-    tot += tc_image_elems(ops[i].ni, ops[i].mo);
+    const Op& op = ops[i];
+    TcOp& t = tops[i];
+    t.img[0] = (int64_t)tot;
+    tot += tc_image_elems(op.mo, op.ni);
+    t.img[1] = (int64_t)tot;
+    tot += tc_image_elems(op.ni, op.mo);
+    t.mo = op.mo;
+    t.ni = op.ni;
+    for (int s = 0; s < 2; ++s) {
+      t.in_off[s] = op.in_off[s];
+      t.in_len[s] = op.in_len[s];
+      t.out_off[s] = op.out_off[s];
+      t.out_len[s] = op.out_len[s];
+    }
+    t.flags = op.flags;
+    t.phase = op.phase;
   }
+  tiles.assign(2 * units.size(), 0);
+  for (size_t u = 0; u < units.size(); ++u)
+    for (int oi = units[u].op_begin; oi < units[u].op_end; ++oi) {
+      tiles[2 * u] += (ops[oi].mo + kTcNT - 1) / kTcNT;
+      tiles[2 * u + 1] += (ops[oi].ni + kTcNT - 1) / kTcNT;
+    }
   img.assign(std::max<size_t>(tot, 8), 0);
 #pragma omp parallel for schedule(dynamic, 64)
   for (long i = 0; i < (long)n; ++i) {
@@ -108,8 +126,8 @@ void tc_build_images(const std::vector<Op>& ops, const std::vector<double>& fact
     const double* B = factors.data() + op.b_off;
     const int ld = op.ld;
     if (op.ni > 0) {
-      tc_pack(op.mo, op.ni, [&](int r, int k) { return B[(size_t)k * ld + r]; }, img.data() + off[2 * i]);
-      tc_pack(op.ni, op.mo, [&](int r, int k) { return B[(size_t)r * ld + k]; }, img.data() + off[2 * i + 1]);
+      tc_pack(op.mo, op.ni, [&](int r, int k) { return B[(size_t)k * ld + r]; }, img.data() + tops[i].img[0]);
+      tc_pack(op.ni, op.mo, [&](int r, int k) { return B[(size_t)r * ld + k]; }, img.data() + tops[i].img[1]);
     }
   }
 }
@@ -142,7 +160,12 @@ struct Ctl {
   int done_tiles;  // tiles whose epilogue is complete (all items so far)
 };
 constexpr size_t kTrBytes = (size_t)kEpiWarps * 32 * kTrStride * 4;
-constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + kTrBytes + sizeof(Ctl) + 1024;
+// I/O transpose tiles: two 32-row x 128-column FP32 tiles (row stride padded
+// to 132 floats: 16-byte aligned rows, at most 2-way bank conflicts on the
+// column-wise accesses)
+constexpr int kIoStride = 132;
+constexpr size_t kIoBytes = (size_t)2 * 32 * kIoStride * 4;
+constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + kTrBytes + kIoBytes + sizeof(Ctl) + 1024;
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -235,9 +258,15 @@ __device__ __forceinline__ long coef_offset(long N, long m) {
   return m > 0 ? pos : pos + (2 * N - a);
 }
 __device__ __forceinline__ long order_slot(long m) { return m == 0 ? 0 : (m > 0 ? 2 * m - 1 : -2 * m); }
-__device__ __forceinline__ int seg_row(int t, const int32_t off[2], const int32_t len[2]) {
-  return t < len[0] ? off[0] + t : off[1] + (t - len[0]);
+// Two row segments held in registers: position t -> row.
+struct Segs {
+  int off0, len0, off1;
+};
+__device__ __forceinline__ Segs in_segs(const TcOp& op, bool fwd) {
+  return fwd ? Segs{op.in_off[0], op.in_len[0], op.in_off[1]} : Segs{op.out_off[0], op.out_len[0], op.out_off[1]};
 }
+__device__ __forceinline__ Segs out_segs(const TcOp& op, bool fwd) { return in_segs(op, !fwd); }
+__device__ __forceinline__ int seg_row(int t, const Segs& g) { return t < g.len0 ? g.off0 + t : g.off1 + (t - g.len0); }
 __device__ __forceinline__ const double* coef_base(const double* beta, int N, int am, int f, int s, int F,
                                                    int single, int msingle) {
   if (f >= F || (s == 1 && am == 0)) return nullptr;
@@ -257,28 +286,77 @@ __device__ __forceinline__ const double* value_base(const double* g, int N, int 
   return g + 2 * ((long)f * (4L * N - 1) * 2 * N + order_slot(s == 0 ? am : -am) * 2 * N);
 }
 
-__device__ __forceinline__ uint16_t f2bf(float f) { return __bfloat16_as_ushort(__float2bfloat16_rn(f)); }
-__device__ __forceinline__ float bf2f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
-// value -> three BF16 pieces at column `col` of a scratch row
-__device__ __forceinline__ void put_pieces(unsigned char* row, int col, float v) {
-  unsigned short* p = reinterpret_cast<unsigned short*>(row) + col;
-  const uint16_t h0 = f2bf(v);
-  v -= bf2f(h0);
-  const uint16_t h1 = f2bf(v);
-  v -= bf2f(h1);
-  const uint16_t h2 = f2bf(v);
-  __stcg(p, (unsigned short)h0);
-  __stcg(p + kTcR, (unsigned short)h1);
-  __stcg(p + 2 * kTcR, (unsigned short)h2);
+// IEEE 754 binary64 <-> binary32 conversions (round to nearest even; subnormals,
+// infinities and NaN per the standard) in integer arithmetic.  GB300's FP64
+// pipe runs at a small fraction of its integer and FP32 rates, and the I/O of
+// this path converts every input and output value once: done on the FP64
+// pipe, the conversions alone would take milliseconds per launch.  They agree
+// bit for bit with the hardware conversions (checked on 2^30 patterns).
+__device__ __forceinline__ uint64_t rne_shift(uint64_t x, int s) {
+  // x >> s rounded to nearest, ties to even (1 <= s <= 63)
+  const uint64_t q = x >> s, rem = x & ((1ull << s) - 1), half = 1ull << (s - 1);
+  return q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
 }
+__device__ __forceinline__ float f64_to_f32_bits(double d) {
+  const uint64_t b = (uint64_t)__double_as_longlong(d);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const uint64_t m = b & 0xFFFFFFFFFFFFFull;
+  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+  const int fe = e - 1023 + 127;  // binary32 biased exponent
+  if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+  if (fe >= 1) return __uint_as_float(sign | (uint32_t)(((uint64_t)fe << 23) + rne_shift(m, 29)));
+  // binary32 subnormal (or zero): value = (2^52 + m) 2^(e - 1075) = k 2^-149
+  if (e == 0 || fe < -24) return __uint_as_float(sign);
+  return __uint_as_float(sign | (uint32_t)rne_shift((1ull << 52) | m, 29 + 1 - fe));
+}
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sign = u & 0x80000000u;
+  uint32_t e = (u >> 23) & 0xFF, m = u & 0x7FFFFFu;
+  if (e == 0xFF) return __hiloint2double((int)(sign | 0x7FF00000u | (m >> 3)), (int)(m << 29));
+  if (e == 0) {
+    if (m == 0) return __hiloint2double((int)sign, 0);
+    const int sh = __clz(m) - 8;  // bring the leading one to bit 23
+    m = (m << sh) & 0x7FFFFFu;
+    e = 1 - sh + 896;
+  } else {
+    e += 896;
+  }
+  return __hiloint2double((int)(sign | (e << 20) | (m >> 3)), (int)(m << 29));
+}
+
 __device__ __forceinline__ float* fp32_at(unsigned char* row, int col) { return reinterpret_cast<float*>(row) + col; }
+
+// four consecutive values (columns col .. col+3) -> three BF16 pieces, one
+// 8-byte store per piece
+__device__ __forceinline__ void put_pieces4(unsigned char* row, int col, float4 x) {
+  float a[4] = {x.x, x.y, x.z, x.w};
+  uint32_t h[3][2];
+#pragma unroll
+  for (int jj = 0; jj < 4; jj += 2) {
+    float a0 = a[jj], a1 = a[jj + 1];
+#pragma unroll
+    for (int pc = 0; pc < 3; ++pc) {
+      const __nv_bfloat162 hb = __floats2bfloat162_rn(a0, a1);
+      const float2 hf = __bfloat1622float2(hb);
+      a0 -= hf.x;
+      a1 -= hf.y;
+      h[pc][jj >> 1] = *reinterpret_cast<const uint32_t*>(&hb);
+    }
+  }
+#pragma unroll
+  for (int pc = 0; pc < 3; ++pc)
+    __stcg(reinterpret_cast<uint2*>(row + pc * (kTcR * 2) + col * 2), make_uint2(h[pc][0], h[pc][1]));
+}
+__device__ __forceinline__ float4* row4(unsigned char* row) { return reinterpret_cast<float4*>(row); }
 
 // Shape of one op in the requested direction.
 struct OpShape {
   int NN, KK, nT, nK, kp_tot;
 };
-__device__ __forceinline__ OpShape op_shape(const Op& op, bool fwd) {
+__device__ __forceinline__ OpShape op_shape(const TcOp& op, bool fwd) {
   OpShape s;
   s.NN = fwd ? op.mo : op.ni;
   s.KK = fwd ? op.ni : op.mo;
@@ -291,7 +369,6 @@ __device__ __forceinline__ OpShape op_shape(const Op& op, bool fwd) {
 struct Item {
   int grp, am;
 };
-__device__ __forceinline__ int row_kk(const Unit& u, int t) { return t < u.nce ? 2 * t : 2 * (t - u.nce) + 1; }
 __device__ __forceinline__ Item item_of(const TcPlan& p, int it, int G, int single, int msingle) {
   Item r;
   r.grp = it % G;
@@ -299,12 +376,9 @@ __device__ __forceinline__ Item item_of(const TcPlan& p, int it, int G, int sing
   return r;
 }
 
-// Tiles (epilogue units) of one work item.
-__device__ int item_tiles(const TcPlan& p, const Unit& u, bool fwd) {
-  int n = 0;
-  for (int oi = u.op_begin; oi < u.op_end; ++oi) n += op_shape(p.ops[oi], fwd).nT;
-  return n;
-}
+// The k-th op of a unit in processing order: ascending phases forward,
+// descending phases for the transposed (inverse) apply.
+__device__ __forceinline__ int op_at(const Unit& u, int k, bool fwd) { return fwd ? u.op_begin + k : u.op_end - 1 - k; }
 
 __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const double* __restrict__ in,
                                                                double* __restrict__ out, int F, int single,
@@ -313,7 +387,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* trbuf = reinterpret_cast<float*>(base + (size_t)kStages * kStageBytes);
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes + kTrBytes);
+  float* iobuf = reinterpret_cast<float*>(base + (size_t)kStages * kStageBytes + kTrBytes);
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes + kTrBytes + kIoBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -350,67 +425,73 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   if (warp < kProdWarps) {
     // ------------------------------------------------------------ producers
     long jp = 0;
-    int tiles_before = 0;
+    int tiles_before = 0;  // tiles of all earlier phases (all items so far)
     bool ok = true;
     for (int it = blockIdx.x, iseq = 0; it < nitems && ok; it += gridDim.x, ++iseq) {
       const Item itm = item_of(p, it, G, single, msingle);
       const Unit u = p.units[itm.am];
       unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
+      const int nops = u.op_end - u.op_begin;
+      TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
       ok = counter_wait(ctl, &ctl->gathered, iseq + 1);
-      for (int k = 0; k < u.nphase && ok; ++k) {
-        const int ph = fwd ? k : u.nphase - 1 - k;
-        ok = counter_wait(ctl, &ctl->done_tiles, tiles_before);
-        int tiles_here = 0;
-        for (int oi = p.phase_tab[u.ph_begin + ph]; oi < p.phase_tab[u.ph_begin + ph + 1] && ok; ++oi) {
-          const Op op = p.ops[oi];
-          const OpShape sh = op_shape(op, fwd);
-          const int32_t* ioff = fwd ? op.in_off : op.out_off;
-          const int32_t* ilen = fwd ? op.in_len : op.out_len;
-          const uint16_t* img = p.img + p.img_off[2 * oi + (fwd ? 0 : 1)];
-          for (int t = 0; t < sh.nT && ok; ++t) {
-            const int Np = (min(kTcNT, sh.NN - kTcNT * t) + 15) & ~15;
-            for (int c = 0; c < sh.nK && ok; ++c, ++jp) {
-              const int s = (int)(jp % kStages);
-              const uint32_t use = (uint32_t)(jp / kStages);
-              ok = mbar_wait(ctl, &ctl->empty[s], (use & 1u) ^ 1u);
-              if (!ok) break;
-              const int Kp = (min(kTcKC, sh.KK - kTcKC * c) + 15) & ~15;
-              const uint32_t sA = stage0 + (uint32_t)s * kStageBytes, sB = sA + kStageA;
-              // B: the image chunk (3 pieces, contiguous) in one bulk copy whose
-              // bytes the full barrier expects
-              if (warp == 0 && lane == 0) {
-                const uint16_t* src = img + (size_t)t * 384 * sh.kp_tot + (size_t)Np * (96 * c);
-                const uint32_t bytes = (uint32_t)(3 * Np * Kp * 2);
-                bulk_expect(&ctl->full[s], bytes);
-                bulk_copy(sB, src, bytes, &ctl->full[s]);
-              }
-              // A: Kp input rows x 3 pieces x 16 chunks of 8 right-hand sides
-              // (MN-major cores).  Lane l owns the row pointer of row l and the
-              // (piece, 8-column chunk) pairs l and l + 32 of every row.
-              {
-                const int j = kTcKC * c + lane;
-                const bool valid = lane < Kp && j < sh.KK;
-                const unsigned char* myrow = valid ? vec + (size_t)seg_row(j, ioff, ilen) * kTcRowBytes : vec;
-                const int pc0 = lane >> 4, m80 = lane & 15;           // pair lane
-                const int pc1 = (lane + 32) >> 4, m81 = (lane + 32) & 15;  // pair lane + 32 (lanes < 16)
-                const uint32_t d0 = sA + pc0 * kPieceA + m80 * 128, d1 = sA + pc1 * kPieceA + m81 * 128;
-                const uint32_t o0 = pc0 * (kTcR * 2) + m80 * 16, o1 = pc1 * (kTcR * 2) + m81 * 16;
-                for (int kj = warp; kj < Kp; kj += kProdWarps) {
-                  const unsigned char* row =
-                      reinterpret_cast<const unsigned char*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(myrow), kj));
-                  const uint32_t ok_src = __shfl_sync(0xffffffffu, valid ? 16u : 0u, kj);
-                  const uint32_t kofs = (uint32_t)((kj >> 3) * 2048 + (kj & 7) * 16);
-                  cp_async16(d0 + kofs, row + o0, ok_src);
-                  if (lane < 16) cp_async16(d1 + kofs, row + o1, ok_src);
-                }
-              }
-              cp_async_arrive(&ctl->full[s]);
-            }
-            ++tiles_here;
-          }
+      int cur_phase = -1, tiles_here = 0;
+      for (int q = 0; q < nops && ok; ++q) {
+        const TcOp op = nxt;
+        if (q + 1 < nops) nxt = p.ops[op_at(u, q + 1, fwd)];
+        if (op.phase != cur_phase) {
+          // a phase reads rows that earlier phases of this item wrote: wait for
+          // their tiles (the item's first phase reads only gathered rows)
+          tiles_before += tiles_here;
+          tiles_here = 0;
+          if (cur_phase >= 0) ok = counter_wait(ctl, &ctl->done_tiles, tiles_before);
+          cur_phase = op.phase;
         }
-        tiles_before += tiles_here;
+        const OpShape sh = op_shape(op, fwd);
+        const Segs isg = in_segs(op, fwd);
+        const uint16_t* img = p.img + (fwd ? op.img[0] : op.img[1]);
+        for (int t = 0; t < sh.nT && ok; ++t) {
+          const int Np = (min(kTcNT, sh.NN - kTcNT * t) + 15) & ~15;
+          for (int c = 0; c < sh.nK && ok; ++c, ++jp) {
+            const int s = (int)(jp % kStages);
+            const uint32_t use = (uint32_t)(jp / kStages);
+            ok = mbar_wait(ctl, &ctl->empty[s], (use & 1u) ^ 1u);
+            if (!ok) break;
+            const int Kp = (min(kTcKC, sh.KK - kTcKC * c) + 15) & ~15;
+            const uint32_t sA = stage0 + (uint32_t)s * kStageBytes, sB = sA + kStageA;
+            // B: the image chunk (3 pieces, contiguous) in one bulk copy whose
+            // bytes the full barrier expects
+            if (warp == 0 && lane == 0) {
+              const uint16_t* src = img + (size_t)t * 384 * sh.kp_tot + (size_t)Np * (96 * c);
+              const uint32_t bytes = (uint32_t)(3 * Np * Kp * 2);
+              bulk_expect(&ctl->full[s], bytes);
+              bulk_copy(sB, src, bytes, &ctl->full[s]);
+            }
+            // A: Kp input rows x 3 pieces x 16 chunks of 8 right-hand sides
+            // (MN-major cores).  Lane l owns the row pointer of row l and the
+            // (piece, 8-column chunk) pairs l and l + 32 of every row.
+            {
+              const int j = kTcKC * c + lane;
+              const bool valid = lane < Kp && j < sh.KK;
+              const unsigned char* myrow = valid ? vec + (size_t)seg_row(j, isg) * kTcRowBytes : vec;
+              const int pc0 = lane >> 4, m80 = lane & 15;           // pair lane
+              const int pc1 = (lane + 32) >> 4, m81 = (lane + 32) & 15;  // pair lane + 32 (lanes < 16)
+              const uint32_t d0 = sA + pc0 * kPieceA + m80 * 128, d1 = sA + pc1 * kPieceA + m81 * 128;
+              const uint32_t o0 = pc0 * (kTcR * 2) + m80 * 16, o1 = pc1 * (kTcR * 2) + m81 * 16;
+              for (int kj = warp; kj < Kp; kj += kProdWarps) {
+                const unsigned char* row =
+                    reinterpret_cast<const unsigned char*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(myrow), kj));
+                const uint32_t ok_src = __shfl_sync(0xffffffffu, valid ? 16u : 0u, kj);
+                const uint32_t kofs = (uint32_t)((kj >> 3) * 2048 + (kj & 7) * 16);
+                cp_async16(d0 + kofs, row + o0, ok_src);
+                if (lane < 16) cp_async16(d1 + kofs, row + o1, ok_src);
+              }
+            }
+            cp_async_arrive(&ctl->full[s]);
+          }
+          ++tiles_here;
+        }
       }
+      tiles_before += tiles_here;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == kMmaWarp) {
@@ -421,10 +502,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
         const Item itm = item_of(p, it, G, single, msingle);
         const Unit u = p.units[itm.am];
-        for (int k = 0; k < u.nphase && ok; ++k) {
-          const int ph = fwd ? k : u.nphase - 1 - k;
-          for (int oi = p.phase_tab[u.ph_begin + ph]; oi < p.phase_tab[u.ph_begin + ph + 1] && ok; ++oi) {
-            const Op op = p.ops[oi];
+        const int nops = u.op_end - u.op_begin;
+        TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
+        for (int q = 0; q < nops && ok; ++q) {
+          {
+            const TcOp op = nxt;
+            if (q + 1 < nops) nxt = p.ops[op_at(u, q + 1, fwd)];
             const OpShape sh = op_shape(op, fwd);
             for (int t = 0; t < sh.nT && ok; ++t, ++tm) {
               const int b = (int)(tm & 1);
@@ -487,13 +570,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       const Item itm = item_of(p, it, G, single, msingle);
       const Unit u = p.units[itm.am];
       unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
-      for (int k = 0; k < u.nphase && ok; ++k) {
-        const int ph = fwd ? k : u.nphase - 1 - k;
-        for (int oi = p.phase_tab[u.ph_begin + ph]; oi < p.phase_tab[u.ph_begin + ph + 1] && ok; ++oi) {
-          const Op op = p.ops[oi];
+      const int nops = u.op_end - u.op_begin;
+      // accumulated rows (Y forward, X inverse) live in the item's accumulation region
+      float* acc_item = p.acc + ((size_t)itm.grp * p.nunits + itm.am) * (size_t)kTcAccRows(N) * kTcR;
+      const int acc0 = fwd ? u.ye : 0;
+      TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
+      for (int q = 0; q < nops && ok; ++q) {
+        {
+          const TcOp op = nxt;
+          if (q + 1 < nops) nxt = p.ops[op_at(u, q + 1, fwd)];
           const OpShape sh = op_shape(op, fwd);
-          const int32_t* ooff = fwd ? op.out_off : op.in_off;
-          const int32_t* olen = fwd ? op.out_len : op.in_len;
+          const Segs osg = out_segs(op, fwd);
           const bool accum = (op.flags & (fwd ? OP_FWD_ACCUM : OP_BWD_ACCUM)) != 0;
           for (int t = 0; t < sh.nT && ok; ++t, ++te) {
             const int b = (int)(te & 1);
@@ -525,10 +612,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
                     float x[8];
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) x[jj] = T[rl * kTrStride + 8 * oc + jj];
-                    unsigned char* row = vec + (size_t)seg_row(kTcNT * t + i, ooff, olen) * kTcRowBytes;
+                    const int r = seg_row(kTcNT * t + i, osg);
                     const int c8 = 32 * ew + 8 * oc;
                     if (accum) {
-                      float* dst = fp32_at(row, c8);
+                      float* dst = acc_item + (size_t)(r - acc0) * kTcR + c8;
                       asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(x[0]),
                                    "f"(x[1]), "f"(x[2]), "f"(x[3])
                                    : "memory");
@@ -536,6 +623,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
                                    "f"(x[5]), "f"(x[6]), "f"(x[7])
                                    : "memory");
                     } else {
+                      unsigned char* row = vec + (size_t)r * kTcRowBytes;
                       uint32_t h[3][4];
 #pragma unroll
                       for (int jj = 0; jj < 8; jj += 2) {
@@ -571,122 +659,87 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       }
     }
   } else if (warp >= kIoWarp0) {
-    // I/O warps: gather of item i into slot i % 2 (after the fold of item i-2 from that
-    // slot), parity fold / scatter of item i once its tiles are done
-    const int e = tid - 32 * kIoWarp0;  // 0..255
-    const int col = e & 127, half = e >> 7;  // column (right-hand side); row half
-    const int fl = col >> 2, sg = (col >> 1) & 1, cc = col & 1;
-    int tiles_through = 0;
+    // I/O warps: the gather of item i into slot i % 2, once item i - 2 (the
+    // slot's previous user) has finished all of its tiles; the outputs go to
+    // the accumulation buffer and leave through the output kernel.  Global data
+    // moves through two 32 x 128 shared tiles so that every warp access is a
+    // contiguous run: 32 degrees or nodes of one (field, sign) column pair (512
+    // bytes of FP64 complex) on the global side, whole 128-column rows on the
+    // scratch side.  Column c = 4 field + 2 sign + {re, im}.
+    const int iw = warp - kIoWarp0;  // 0..7
+    float* Te = iobuf;
+    float* To = iobuf + 32 * kIoStride;
+    const int e = tid - 32 * kIoWarp0;
+    int t_m2 = 0, t_m1 = 0;  // tiles of all items up to i-2, up to i-1
     bool ok = true;
-    int prev_it = -1, prev_iseq = -1;
-    for (int it = blockIdx.x, iseq = 0; ok; it += gridDim.x, ++iseq) {
-      const bool have = it < nitems;
-      // 1. gather item `it` into slot iseq % 2 (its previous user, item iseq-2, is folded)
-      if (have) {
-        const Item itm = item_of(p, it, G, single, msingle);
-        const int am = itm.am, grp = itm.grp;
-        const Unit u = p.units[am];
-        unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
-        const int nx = u.nce + u.nco;
-        if (fwd) {
-          const double* bsrc = coef_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
-          for (int t0 = 16 * half; t0 < nx; t0 += 32) {
-            float v[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              const int t = t0 + q;
-              v[q] = (bsrc && t < nx) ? (float)__ldg(bsrc + 2 * row_kk(u, t) + cc) : 0.f;
-            }
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-              if (t0 + q < nx) put_pieces(vec + (size_t)(t0 + q) * kTcRowBytes, col, v[q]);
+    for (int it = blockIdx.x, iseq = 0; it < nitems && ok; it += gridDim.x, ++iseq) {
+      const Item itm = item_of(p, it, G, single, msingle);
+      const int am = itm.am, grp = itm.grp;
+      const Unit u = p.units[am];
+      unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
+      const int nx = u.nce + u.nco;
+      ok = counter_wait(ctl, &ctl->done_tiles, t_m2);
+      if (!ok) break;
+      if (fwd) {
+        // X rows from beta: degree k = am + d, d even -> row d/2, d odd -> row nce + d/2
+        for (int d0 = 0; d0 < nx; d0 += 32) {
+          for (int pr = iw; pr < 2 * kTcFields; pr += 8) {
+            const int fl = pr >> 1, sgn = pr & 1, d = d0 + lane;
+            const double* bsrc = coef_base(in, N, am, grp * kTcFields + fl, sgn, F, single, msingle);
+            double2 v = make_double2(0.0, 0.0);
+            if (bsrc && d < nx) v = __ldg(reinterpret_cast<const double2*>(bsrc) + d);
+            *reinterpret_cast<float2*>(Te + lane * kIoStride + 4 * fl + 2 * sgn) =
+                make_float2(f64_to_f32_bits(v.x), f64_to_f32_bits(v.y));
           }
-          for (int i = half; i < 2 * N; i += 2) __stcg(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, col), 0.f);
-        } else {
-          const double* gb = value_base(in, N, am, grp * kTcFields + fl, sg, F, single, msingle);
-          for (int i0 = 8 * half; i0 < N; i0 += 16) {
-            double a[8], b[8], wi[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int i = i0 + q;
-              const bool in_range = gb && i < N;
-              a[q] = in_range ? __ldg(gb + 2 * (N + i) + cc) : 0.0;
-              b[q] = in_range ? __ldg(gb + 2 * (N - 1 - i) + cc) : 0.0;
-              wi[q] = i < N ? __ldg(p.w + N + i) : 0.0;
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int i = i0 + q;
-              if (i < N) {
-                put_pieces(vec + (size_t)(u.ye + i) * kTcRowBytes, col, (float)(wi[q] * (a[q] + b[q])));
-                put_pieces(vec + (size_t)(u.yo + i) * kTcRowBytes, col, (float)(wi[q] * (a[q] - b[q])));
-              }
+          io_bar();
+          for (int dl = iw; dl < 32; dl += 8) {
+            const int d = d0 + dl;
+            if (d < nx) {
+              const int t = (d & 1) ? u.nce + (d >> 1) : (d >> 1);
+              put_pieces4(vec + (size_t)t * kTcRowBytes, 4 * lane,
+                          *reinterpret_cast<const float4*>(Te + dl * kIoStride + 4 * lane));
             }
           }
-          for (int t = half; t < nx; t += 2) __stcg(fp32_at(vec + (size_t)t * kTcRowBytes, col), 0.f);
+          io_bar();
         }
-        __threadfence_block();
-        io_bar();
-        if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
-      }
-      // 2. fold / scatter the previous item once all of its tiles are done
-      if (prev_it >= 0) {
-        const Item itm = item_of(p, prev_it, G, single, msingle);
-        const int am = itm.am, grp = itm.grp;
-        const Unit u = p.units[am];
-        unsigned char* vec = slots + (size_t)(prev_iseq & 1) * slot_bytes;
-        tiles_through += item_tiles(p, u, fwd != 0);
-        ok = counter_wait(ctl, &ctl->done_tiles, tiles_through);
-        if (!ok) break;
-        const int nx = u.nce + u.nco;
-        if (fwd) {
-          const int total = N * 2 * kTcFields;
-          for (int idx0 = e; idx0 < total; idx0 += 256 * 8) {
-            float2 ev[8], ov[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int idx = idx0 + 256 * q;
-              ev[q] = make_float2(0.f, 0.f);
-              ov[q] = make_float2(0.f, 0.f);
-              if (idx < total) {
-                const int i = idx % N, fs = idx / N, cl = 4 * (fs >> 1) + 2 * (fs & 1);
-                ev[q] = __ldcg(reinterpret_cast<const float2*>(fp32_at(vec + (size_t)(u.ye + i) * kTcRowBytes, cl)));
-                ov[q] = __ldcg(reinterpret_cast<const float2*>(fp32_at(vec + (size_t)(u.yo + i) * kTcRowBytes, cl)));
-              }
+      } else {
+        // weighted parity fold of g into Y_e, Y_o (Sec. 3.1.1 with the W of B = A^T W)
+        for (int i0 = 0; i0 < N; i0 += 32) {
+          const int i = i0 + lane;
+          const float wi = i < N ? f64_to_f32_bits(__ldg(p.w + N + i)) : 0.f;
+          for (int pr = iw; pr < 2 * kTcFields; pr += 8) {
+            const int fl = pr >> 1, sgn = pr & 1;
+            const double* gb = value_base(in, N, am, grp * kTcFields + fl, sgn, F, single, msingle);
+            float2 ue = make_float2(0.f, 0.f), uo = ue;
+            if (gb && i < N) {
+              const double2 a = __ldg(reinterpret_cast<const double2*>(gb) + N + i);
+              const double2 b = __ldg(reinterpret_cast<const double2*>(gb) + N - 1 - i);
+              const float ax = f64_to_f32_bits(a.x), ay = f64_to_f32_bits(a.y);
+              const float bx = f64_to_f32_bits(b.x), by = f64_to_f32_bits(b.y);
+              ue = make_float2(wi * (ax + bx), wi * (ay + by));
+              uo = make_float2(wi * (ax - bx), wi * (ay - by));
             }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int idx = idx0 + 256 * q;
-              if (idx >= total) continue;
-              const int i = idx % N, fs = idx / N;
-              const double* gb = value_base(out, N, am, grp * kTcFields + (fs >> 1), fs & 1, F, single, msingle);
-              if (!gb) continue;
-              double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
-              gp[N + i] = make_double2((double)ev[q].x + (double)ov[q].x, (double)ev[q].y + (double)ov[q].y);
-              gp[N - 1 - i] = make_double2((double)ev[q].x - (double)ov[q].x, (double)ev[q].y - (double)ov[q].y);
+            *reinterpret_cast<float2*>(Te + lane * kIoStride + 4 * fl + 2 * sgn) = ue;
+            *reinterpret_cast<float2*>(To + lane * kIoStride + 4 * fl + 2 * sgn) = uo;
+          }
+          io_bar();
+          for (int r = iw; r < 32; r += 8) {
+            if (i0 + r < N) {
+              put_pieces4(vec + (size_t)(u.ye + i0 + r) * kTcRowBytes, 4 * lane,
+                          *reinterpret_cast<const float4*>(Te + r * kIoStride + 4 * lane));
+              put_pieces4(vec + (size_t)(u.yo + i0 + r) * kTcRowBytes, 4 * lane,
+                          *reinterpret_cast<const float4*>(To + r * kIoStride + 4 * lane));
             }
           }
-        } else {
-          const double* bdst = coef_base(out, N, am, grp * kTcFields + fl, sg, F, single, msingle);
-          if (bdst)
-            for (int t0 = 16 * half; t0 < nx; t0 += 32) {
-              float v[16];
-#pragma unroll
-              for (int q = 0; q < 16; ++q)
-                v[q] = t0 + q < nx ? __ldcg(fp32_at(vec + (size_t)(t0 + q) * kTcRowBytes, col)) : 0.f;
-#pragma unroll
-              for (int q = 0; q < 16; ++q) {
-                const int t = t0 + q;
-                if (t < nx) const_cast<double*>(bdst)[2 * row_kk(u, t) + cc] = (double)v[q];
-              }
-            }
+          io_bar();
         }
-        __threadfence_block();
-        io_bar();
       }
-      if (!have) break;
-      prev_it = it;
-      prev_iseq = iseq;
+      __threadfence_block();
+      io_bar();
+      if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
+      const int t_cur = t_m1 + p.tiles[2 * am + (fwd ? 0 : 1)];
+      t_m2 = t_m1;
+      t_m1 = t_cur;
     }
   }
   if (*((volatile int*)&ctl->abort) && tid == 0) atomicExch(p.err, 1);
@@ -696,6 +749,80 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
 }
 
+// Output side of the apply: the accumulated rows of every work item (FP32,
+// kTcR right-hand sides per row) to g (forward: the parity fold of Sec. 3.1.2,
+// g(theta_{N+i}) = y_e + y_o, g(theta_{N-1-i}) = y_e - y_o) or to beta
+// (inverse: X rows back to degrees).  A streaming kernel with many warps per
+// SM, so that this part of the I/O runs at HBM bandwidth.  One CTA step is
+// one item and 32 nodes (or degrees), transposed through shared memory so
+// that reads are whole rows and writes are 512-byte runs per (field, sign).
+constexpr int kOutThreads = 256;
+__global__ void __launch_bounds__(kOutThreads) tc_out_kernel(TcPlan p, double* __restrict__ out, int F, int single,
+                                                            int msingle, int fwd) {
+  __shared__ __align__(16) float Te[32 * kIoStride];
+  __shared__ __align__(16) float To[32 * kIoStride];
+  const int N = p.N, lane = threadIdx.x & 31, iw = threadIdx.x >> 5;
+  const int G = (F + kTcFields - 1) / kTcFields;
+  const int nitems = single ? G : p.nunits * G;
+  const int cpi = fwd ? (N + 31) / 32 : (2 * N + 31) / 32;  // chunks per item
+  const long total = (long)nitems * cpi;
+  for (long w = blockIdx.x; w < total; w += gridDim.x) {
+    const int item = (int)(w / cpi), chunk = (int)(w % cpi);
+    const int grp = item % G;
+    const int am = single ? (msingle < 0 ? -msingle : msingle) : item / G;
+    const Unit u = p.units[am];
+    const float* acc_item = p.acc + ((size_t)grp * p.nunits + am) * (size_t)kTcAccRows(N) * kTcR;
+    if (fwd) {
+      const int i0 = 32 * chunk;
+      for (int r = iw; r < 32; r += kOutThreads / 32) {
+        if (i0 + r < N) {
+          *reinterpret_cast<float4*>(Te + r * kIoStride + 4 * lane) =
+              __ldcs(reinterpret_cast<const float4*>(acc_item + (size_t)(i0 + r) * kTcR) + lane);
+          *reinterpret_cast<float4*>(To + r * kIoStride + 4 * lane) =
+              __ldcs(reinterpret_cast<const float4*>(acc_item + (size_t)(N + i0 + r) * kTcR) + lane);
+        }
+      }
+      __syncthreads();
+      const int i = i0 + lane;
+      for (int pr = iw; pr < 2 * kTcFields; pr += kOutThreads / 32) {
+        const int fl = pr >> 1, sgn = pr & 1;
+        const double* gb = value_base(out, N, am, grp * kTcFields + fl, sgn, F, single, msingle);
+        if (gb && i < N) {
+          const float2 ev = *reinterpret_cast<const float2*>(Te + lane * kIoStride + 4 * fl + 2 * sgn);
+          const float2 ov = *reinterpret_cast<const float2*>(To + lane * kIoStride + 4 * fl + 2 * sgn);
+          double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
+          __stcs(gp + N + i, make_double2(f32_to_f64_bits(ev.x + ov.x), f32_to_f64_bits(ev.y + ov.y)));
+          __stcs(gp + N - 1 - i, make_double2(f32_to_f64_bits(ev.x - ov.x), f32_to_f64_bits(ev.y - ov.y)));
+        }
+      }
+      __syncthreads();
+    } else {
+      const int nx = u.nce + u.nco, d0 = 32 * chunk;
+      if (d0 >= nx) continue;  // uniform over the CTA
+      for (int dl = iw; dl < 32; dl += kOutThreads / 32) {
+        const int d = d0 + dl;
+        if (d < nx) {
+          const int t = (d & 1) ? u.nce + (d >> 1) : (d >> 1);
+          *reinterpret_cast<float4*>(Te + dl * kIoStride + 4 * lane) =
+              __ldcs(reinterpret_cast<const float4*>(acc_item + (size_t)t * kTcR) + lane);
+        }
+      }
+      __syncthreads();
+      const int d = d0 + lane;
+      for (int pr = iw; pr < 2 * kTcFields; pr += kOutThreads / 32) {
+        const int fl = pr >> 1, sgn = pr & 1;
+        const double* bdst = coef_base(out, N, am, grp * kTcFields + fl, sgn, F, single, msingle);
+        if (bdst && d < nx) {
+          const float2 v = *reinterpret_cast<const float2*>(Te + lane * kIoStride + 4 * fl + 2 * sgn);
+          __stcs(reinterpret_cast<double2*>(const_cast<double*>(bdst)) + d,
+                 make_double2(f32_to_f64_bits(v.x), f32_to_f64_bits(v.y)));
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace
 
 size_t tc_smem_bytes() { return kSmemTotal; }
@@ -703,11 +830,36 @@ size_t tc_smem_bytes() { return kSmemTotal; }
 int tc_ctas_per_sm() { return 1; }  // the kernel holds all 512 tensor-memory columns
 
 cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, int F, int single, int m, int grid,
-                      cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
+                      cudaStream_t st, cudaEvent_t* ev) {
+  const int G = (F + kTcFields - 1) / kTcFields;
+  if (G > p.gmax) return cudaErrorInvalidValue;
+  const size_t item_bytes = (size_t)kTcAccRows(p.N) * kTcR * sizeof(float);
+  cudaError_t e;
+  if (single) {
+    const int am = m < 0 ? -m : m;
+    e = cudaMemset2DAsync(reinterpret_cast<unsigned char*>(p.acc) + (size_t)am * item_bytes,
+                          (size_t)p.nunits * item_bytes, 0, item_bytes, G, st);
+  } else {
+    e = cudaMemsetAsync(p.acc, 0, (size_t)G * p.nunits * item_bytes, st);
+  }
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(p, in, out, F, single, m, fwd ? 1 : 0);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+  const long items = (long)(single ? 1 : p.nunits) * G;
+  const long chunks = items * (fwd ? (p.N + 31) / 32 : (2 * p.N + 31) / 32);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int out_grid = (int)std::max(1L, std::min(chunks, (long)sms * 6));
+  tc_out_kernel<<<out_grid, kOutThreads, 0, st>>>(p, out, F, single, m, fwd ? 1 : 0);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
+  return e;
 }
 
 }  // namespace sht

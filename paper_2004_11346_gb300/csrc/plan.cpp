@@ -840,6 +840,22 @@ bool validate_program(const HostProgram& P, std::string& err) {
         ok = ok && op.out_off[s] >= 0 && op.out_off[s] + op.out_len[s] <= u.nrows;
       }
       if (!ok) return fail("apply program failed validation", am);
+      // shared rows are exactly the accumulated ones: an op writes Y rows (the
+      // N-node outputs of both parities) iff it accumulates forward, and reads
+      // X rows (the coefficients) iff its transpose accumulates
+      for (int s = 0; s < 2 && ok; ++s) {
+        if (op.out_len[s] > 0) {
+          const bool in_y = op.out_off[s] >= u.ye && op.out_off[s] + op.out_len[s] <= u.ye + 2 * N;
+          const bool off_y = op.out_off[s] + op.out_len[s] <= u.ye || op.out_off[s] >= u.ye + 2 * N;
+          ok = (op.flags & OP_FWD_ACCUM) ? in_y : off_y;
+        }
+        if (ok && op.in_len[s] > 0) {
+          const bool in_x = op.in_off[s] + op.in_len[s] <= nce + nco;
+          const bool off_x = op.in_off[s] >= nce + nco;
+          ok = (op.flags & OP_BWD_ACCUM) ? in_x : off_x;
+        }
+      }
+      if (!ok) return fail("accumulated rows failed validation", am);
     }
   }
   return true;

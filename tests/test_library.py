@@ -134,3 +134,10 @@ def test_program_structure():
             writes[op["out_off"][s]: op["out_off"][s] + op["out_len"][s]] += 1
     z0 = u["yo"] + N
     assert np.all(writes[z0:] == 1)
+
+
+def test_kernel_time_needs_timing_plan():
+    p = sht.Plan(16, 1e-10, flags=HOST)
+    with pytest.raises(_lib.ShtError) as ei:
+        p.kernel_time()
+    assert ei.value.status == _lib.SHT_ERR_UNSUPPORTED
