@@ -140,7 +140,8 @@ constexpr int kProdWarps = 3;                 // warps staging operands
 constexpr int kMmaWarp = kProdWarps;          // the MMA-issuing warp
 constexpr int kEpiWarp0 = kProdWarps + 1;     // first epilogue warp
 constexpr int kEpiWarps = 4;                  // one warpgroup drains the accumulators
-constexpr int kIoWarp0 = kEpiWarp0 + kEpiWarps;  // 8 I/O warps: gather, parity fold / scatter
+constexpr int kIoWarp0 = kEpiWarp0 + kEpiWarps;  // the remaining warps gather the next item's inputs
+constexpr int kIoWarps = kTcThreads / 32 - kIoWarp0;
 constexpr int kTrStride = 33;                 // padded 32 x 32 transpose tile (floats)
 constexpr int kPieceA = kTcR * kTcKC * 2;      // bytes of one A piece in a stage (8 KB)
 constexpr int kStageA = 3 * kPieceA;           // 24 KB
@@ -249,7 +250,7 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-__device__ __forceinline__ void io_bar() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+__device__ __forceinline__ void io_bar() { asm volatile("bar.sync 2, %0;" ::"n"(32 * kIoWarps) : "memory"); }
 
 __device__ __forceinline__ long coef_offset(long N, long m) {
   long a = m < 0 ? -m : m;
@@ -327,7 +328,6 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
   return __hiloint2double((int)(sign | (e << 20) | (m >> 3)), (int)(m << 29));
 }
 
-__device__ __forceinline__ float* fp32_at(unsigned char* row, int col) { return reinterpret_cast<float*>(row) + col; }
 
 // four consecutive values (columns col .. col+3) -> three BF16 pieces, one
 // 8-byte store per piece
@@ -350,7 +350,7 @@ __device__ __forceinline__ void put_pieces4(unsigned char* row, int col, float4 
   for (int pc = 0; pc < 3; ++pc)
     __stcg(reinterpret_cast<uint2*>(row + pc * (kTcR * 2) + col * 2), make_uint2(h[pc][0], h[pc][1]));
 }
-__device__ __forceinline__ float4* row4(unsigned char* row) { return reinterpret_cast<float4*>(row); }
+
 
 // Shape of one op in the requested direction.
 struct OpShape {
@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
     // contiguous run: 32 degrees or nodes of one (field, sign) column pair (512
     // bytes of FP64 complex) on the global side, whole 128-column rows on the
     // scratch side.  Column c = 4 field + 2 sign + {re, im}.
-    const int iw = warp - kIoWarp0;  // 0..7
+    const int iw = warp - kIoWarp0;  // 0 .. kIoWarps - 1
     float* Te = iobuf;
     float* To = iobuf + 32 * kIoStride;
     const int e = tid - 32 * kIoWarp0;
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       if (fwd) {
         // X rows from beta: degree k = am + d, d even -> row d/2, d odd -> row nce + d/2
         for (int d0 = 0; d0 < nx; d0 += 32) {
-          for (int pr = iw; pr < 2 * kTcFields; pr += 8) {
+          for (int pr = iw; pr < 2 * kTcFields; pr += kIoWarps) {
             const int fl = pr >> 1, sgn = pr & 1, d = d0 + lane;
             const double* bsrc = coef_base(in, N, am, grp * kTcFields + fl, sgn, F, single, msingle);
             double2 v = make_double2(0.0, 0.0);
@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
                 make_float2(f64_to_f32_bits(v.x), f64_to_f32_bits(v.y));
           }
           io_bar();
-          for (int dl = iw; dl < 32; dl += 8) {
+          for (int dl = iw; dl < 32; dl += kIoWarps) {
             const int d = d0 + dl;
             if (d < nx) {
               const int t = (d & 1) ? u.nce + (d >> 1) : (d >> 1);
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
         for (int i0 = 0; i0 < N; i0 += 32) {
           const int i = i0 + lane;
           const float wi = i < N ? f64_to_f32_bits(__ldg(p.w + N + i)) : 0.f;
-          for (int pr = iw; pr < 2 * kTcFields; pr += 8) {
+          for (int pr = iw; pr < 2 * kTcFields; pr += kIoWarps) {
             const int fl = pr >> 1, sgn = pr & 1;
             const double* gb = value_base(in, N, am, grp * kTcFields + fl, sgn, F, single, msingle);
             float2 ue = make_float2(0.f, 0.f), uo = ue;
@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
             *reinterpret_cast<float2*>(To + lane * kIoStride + 4 * fl + 2 * sgn) = uo;
           }
           io_bar();
-          for (int r = iw; r < 32; r += 8) {
+          for (int r = iw; r < 32; r += kIoWarps) {
             if (i0 + r < N) {
               put_pieces4(vec + (size_t)(u.ye + i0 + r) * kTcRowBytes, 4 * lane,
                           *reinterpret_cast<const float4*>(Te + r * kIoStride + 4 * lane));
