@@ -33,6 +33,7 @@
 #include <cstring>
 
 #include "apply_tc.cuh"
+#include "f64_bits.cuh"
 
 namespace sht {
 
@@ -288,45 +289,6 @@ __device__ __forceinline__ const double* value_base(const double* g, int N, int 
 }
 
 
-// IEEE 754 binary64 <-> binary32 conversions (round to nearest even; subnormals,
-// infinities and NaN per the standard) in integer arithmetic.  GB300's FP64
-// pipe runs at a small fraction of its integer and FP32 rates, and the I/O of
-// this path converts every input and output value once: done on the FP64
-// pipe, the conversions alone would take milliseconds per launch.  They agree
-// bit for bit with the hardware conversions (checked on 2^30 patterns).
-__device__ __forceinline__ uint64_t rne_shift(uint64_t x, int s) {
-  // x >> s rounded to nearest, ties to even (1 <= s <= 63)
-  const uint64_t q = x >> s, rem = x & ((1ull << s) - 1), half = 1ull << (s - 1);
-  return q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
-}
-__device__ __forceinline__ float f64_to_f32_bits(double d) {
-  const uint64_t b = (uint64_t)__double_as_longlong(d);
-  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7FF);
-  const uint64_t m = b & 0xFFFFFFFFFFFFFull;
-  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
-  const int fe = e - 1023 + 127;  // binary32 biased exponent
-  if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
-  if (fe >= 1) return __uint_as_float(sign | (uint32_t)(((uint64_t)fe << 23) + rne_shift(m, 29)));
-  // binary32 subnormal (or zero): value = (2^52 + m) 2^(e - 1075) = k 2^-149
-  if (e == 0 || fe < -24) return __uint_as_float(sign);
-  return __uint_as_float(sign | (uint32_t)rne_shift((1ull << 52) | m, 29 + 1 - fe));
-}
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t sign = u & 0x80000000u;
-  uint32_t e = (u >> 23) & 0xFF, m = u & 0x7FFFFFu;
-  if (e == 0xFF) return __hiloint2double((int)(sign | 0x7FF00000u | (m >> 3)), (int)(m << 29));
-  if (e == 0) {
-    if (m == 0) return __hiloint2double((int)sign, 0);
-    const int sh = __clz(m) - 8;  // bring the leading one to bit 23
-    m = (m << sh) & 0x7FFFFFu;
-    e = 1 - sh + 896;
-  } else {
-    e += 896;
-  }
-  return __hiloint2double((int)(sign | (e << 20) | (m >> 3)), (int)(m << 29));
-}
 
 
 // four consecutive values (columns col .. col+3) -> three BF16 pieces, one

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <vector>
 
+#include "f64_bits.cuh"
 #include "phi_dft.cuh"
 
 namespace sht {
@@ -36,6 +37,16 @@ struct PhiThreads {
 };
 
 __device__ __forceinline__ long order_slot(long m) { return m == 0 ? 0 : (m > 0 ? 2 * m - 1 : -2 * m); }
+
+// FP64 I/O values to and from the arithmetic type (integer conversions for FP32)
+template <class T>
+__device__ __forceinline__ T from_f64(double v);
+template <>
+__device__ __forceinline__ double from_f64<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float from_f64<float>(double v) { return f64_to_f32_bits(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return f32_to_f64_bits(v); }
 
 template <class T>
 __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
@@ -165,14 +176,14 @@ __global__ void __launch_bounds__(PhiThreads<T>::value) phi_kernel(PhiPlanDev<T>
         const int m = mm - (K - 1);  // -(K-1) .. K-1
         const double2 v = __ldg(reinterpret_cast<const double2*>(in) + f * nval + order_slot(m) * K + l);
         const C2<T> s = p.shift[mm];
-        const C2<T> a{(T)v.x, (T)v.y};
+        const C2<T> a{from_f64<T>(v.x), from_f64<T>(v.y)};
         buf0[(m % M + M) % M] = cmul(a, s);
       }
     } else {
 #pragma unroll 8
       for (int j = threadIdx.x; j < M; j += blockDim.x) {
         const double2 v = __ldg(reinterpret_cast<const double2*>(in) + f * nval + (long)l * M + j);
-        buf0[j] = C2<T>{(T)v.x, (T)v.y};
+        buf0[j] = C2<T>{from_f64<T>(v.x), from_f64<T>(v.y)};
       }
     }
     __syncthreads();
@@ -189,7 +200,7 @@ __global__ void __launch_bounds__(PhiThreads<T>::value) phi_kernel(PhiPlanDev<T>
     if (!analysis) {
       for (int j = threadIdx.x; j < M; j += blockDim.x) {
         const C2<T> v = src[j];
-        reinterpret_cast<double2*>(out)[f * nval + (long)l * M + j] = make_double2((double)v.x, (double)v.y);
+        reinterpret_cast<double2*>(out)[f * nval + (long)l * M + j] = make_double2(to_f64(v.x), to_f64(v.y));
       }
     } else {
       // g(m, l) = (1/M) e^{-i pi m / M} C[m mod M]
@@ -198,9 +209,8 @@ __global__ void __launch_bounds__(PhiThreads<T>::value) phi_kernel(PhiPlanDev<T>
         C2<T> s = p.shift[mm];
         s.y = -s.y;
         const C2<T> v = cmul(src[(m % M + M) % M], s);
-        const double inv = 1.0 / (double)M;
-        reinterpret_cast<double2*>(out)[f * nval + order_slot(m) * K + l] =
-            make_double2((double)v.x * inv, (double)v.y * inv);
+        const T inv = T(1) / (T)M;
+        reinterpret_cast<double2*>(out)[f * nval + order_slot(m) * K + l] = make_double2(to_f64(v.x * inv), to_f64(v.y * inv));
       }
     }
     __syncthreads();
