@@ -199,6 +199,8 @@ sht_status sht_plan_load(const char* path, sht_plan_t* out);
  *  - The first call on a device looks the array's device address up
  *    (cudaGetSymbolAddress) with that device current; make it before any
  *    stream capture.  The plan must belong to the current device.
+ *  - FP64 plans only (SHT_ERR_UNSUPPORTED otherwise: the other precisions do
+ *    not keep the FP64 factor store on the device).
  *  - Returns SHT_ERR_ARG when one work item's vectors (the plan's largest
  *    order: rows x 4 doubles) do not fit in the array; otherwise the result is
  *    that of alt_forward_m, with fewer CTAs.

@@ -516,9 +516,11 @@ sht_status attach_device(sht_plan_s* p) {
   if (e == cudaSuccess) e = upload(&p->d_ops, P.ops);
   if (e == cudaSuccess) e = upload(&p->d_phase, P.phase_tab);
   if (e == cudaSuccess) e = upload(&p->d_order, P.order);
-  if (e == cudaSuccess) e = upload(&p->d_fac, P.factors);
+  // the FP64 factor store is read only by the FP64 kernels; the other precisions
+  // upload their own representation below
+  if (e == cudaSuccess && o.precision == SHT_FP64) e = upload(&p->d_fac, P.factors);
   if (e == cudaSuccess) e = upload(&p->d_w, P.w);
-  size_t ws = (size_t)p->nslots * P.max_rows * kRT * sizeof(double);
+  size_t ws = o.precision == SHT_FP64 ? (size_t)p->nslots * P.max_rows * kRT * sizeof(double) : 0;
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_ws), std::max<size_t>(ws, 8));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_counter), sizeof(unsigned int));
   size_t ws32 = 0;
@@ -1008,7 +1010,7 @@ extern "C" sht_status alt_forward_m_noalloc(sht_plan_t p, int m, const double* b
   if (m <= -2 * p->prog.N || m >= 2 * p->prog.N) return SHT_ERR_ARG;
   if (F == 0) return SHT_OK;
   if (!beta_m || !g_m) return SHT_ERR_ARG;
-  if (p->host_only) return SHT_ERR_UNSUPPORTED;
+  if (p->host_only || !p->d_fac) return SHT_ERR_UNSUPPORTED;  // runs the FP64 kernels: FP64 plans only
   if ((reinterpret_cast<uintptr_t>(beta_m) | reinterpret_cast<uintptr_t>(g_m)) & 15u) return SHT_ERR_ARG;
   if ((int64_t)F * 2 * p->prog.N > (int64_t)1 << 30) return SHT_ERR_ARG;
   // one CTA's vector space must fit next to the counter

@@ -58,3 +58,13 @@ def test_noalloc_rejects_bad_arguments():
     with pytest.raises(_lib.ShtError):
         _lib.alt_forward_m_noalloc(plan.handle, 0, 0, x.data_ptr(), 1, 0)
     _lib.alt_forward_m_noalloc(plan.handle, 0, 0, 0, 0, 0)  # F = 0 is a no-op
+
+
+def test_noalloc_needs_fp64_plan():
+    """Mixed-precision plans keep no FP64 factor store on the device."""
+    N = 16
+    plan = sht.Plan(N, 1e-7, precision=_lib.SHT_MIXED)
+    x = torch.zeros((1, 2 * N, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.ShtError) as ei:
+        _lib.alt_forward_m_noalloc(plan.handle, 0, x.data_ptr(), x.data_ptr(), 1, 0)
+    assert ei.value.status == _lib.SHT_ERR_UNSUPPORTED
