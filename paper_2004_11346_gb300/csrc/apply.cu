@@ -533,8 +533,10 @@ sht_status attach_device(sht_plan_s* p) {
     if (e == cudaSuccess) e = upload(&p->d_tcops, tops);
     if (e == cudaSuccess) e = upload(&p->d_tctiles, tiles);
     p->nslots_tc = std::max(1, sms * tc_ctas_per_sm());
-    ws32 = (size_t)p->nslots_tc * 2 * P.max_rows * kTcRowBytes;  // two vector spaces per CTA
+    ws32 = (size_t)p->nslots_tc * 2 * tc_slot_bytes(P.max_rows);  // two vector spaces per CTA
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_wstc), std::max<size_t>(ws32, 8));
+    // rows that widened K chunks read but no op writes must hold finite values
+    if (e == cudaSuccess) e = cudaMemset(p->d_wstc, 0, std::max<size_t>(ws32, 8));
     p->tc_gmax = (o.max_fields + kTcFields - 1) / kTcFields;
     const size_t acc = (size_t)p->tc_gmax * 2 * N * kTcAccRows(N) * kTcR * sizeof(float);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_acc), acc);

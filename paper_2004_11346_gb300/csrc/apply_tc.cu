@@ -7,23 +7,27 @@
 // M dimension and the block's rows are N (tiles of <= 128, padded to 16):
 //   A operand = in^T (128 x K, MN-major): the op's input rows, kept in the
 //               scratch as three BF16 pieces a0 + a1 + a2 (8 bits each) of
-//               every value, so staging is a plain asynchronous copy;
-//   B operand = B (N x K, K-major): precomputed split-BF16 image b0 + b1 + b2;
+//               every value, in groups of 8 rows laid out exactly as the
+//               operand sits in shared memory, so that staging one K chunk
+//               is one or two bulk copies of whole groups;
+//   B operand = B (N x K, K-major): precomputed split-BF16 image b0 + b1 + b2,
+//               with zero columns where the K side was widened to whole groups;
 //   D         = 128 x N FP32 accumulator in tensor memory.
-// The CTA is warp-specialised and persistent (one per SM): a producer warp
-// streams (op, tile, 32-wide K chunk) operand stages into a 4-deep shared
-// memory ring with cp.async; an MMA warp issues the tensor-core products into
-// two double-buffered TMEM accumulator pairs; four epilogue warps drain the
-// accumulators, split the results into BF16 pieces for the next level (or add
-// them in FP32 into the shared output rows), and run the gather and the
-// parity fold.  Ops of one phase read only rows written by earlier phases: the
-// producer starts a phase after the epilogue has counted every earlier tile.
+// The CTA is warp-specialised and persistent (one per SM): one producer
+// thread streams (op, tile, 32-wide K chunk) operand stages into a 3-deep
+// shared memory ring with bulk copies; an MMA thread issues the tensor-core
+// products into two double-buffered TMEM accumulator pairs; four epilogue
+// warps drain the accumulators and split the results into BF16 pieces for the
+// next level (or add them in FP32 into the shared output rows); the I/O warps
+// gather the next item's inputs.  Ops of one phase read only rows written by
+// earlier phases: the producer starts a phase after the epilogue has counted
+// every earlier tile.
 // Per 16-wide K step six MMAs accumulate a_p b_q for p + q <= 2, which keeps
 // every product to about 2^-24 relative error (FP32 quality); a0 b0 and the
 // five smaller cross products go to two separate accumulators that the
-// epilogue adds in FP32.  Operands sit
-// in shared memory in the canonical no-swizzle K-major layout (8 x 16-byte
-// core matrices; LBO = stride between core matrices along K, SBO = along M/N).
+// epilogue adds in FP32.  Operands sit in shared memory in the canonical
+// no-swizzle layouts (8 x 16-byte core matrices; LBO = stride between core
+// matrices along K, SBO = along M/N).
 // All waits are bounded: a wait that runs out sets an error flag, every role
 // stops, and the host reports SHT_ERR_TIMEOUT.
 #include <cuda_bf16.h>
@@ -53,33 +57,45 @@ static inline double bf16_to_d(uint16_t h) {
   return (double)f;
 }
 
-size_t tc_image_elems(int NN, int KK) {
-  if (NN <= 0 || KK <= 0) return 0;
-  const int nK = (KK + kTcKC - 1) / kTcKC;
-  const size_t kp_tot = (size_t)kTcKC * (nK - 1) + r16(KK - kTcKC * (nK - 1));
+size_t tc_image_elems(int NN, const TcKGeom& kg) {
+  if (NN <= 0 || kg.kp_tot <= 0) return 0;
   const int nT = (NN + kTcNT - 1) / kTcNT;
   const size_t np_tot = (size_t)kTcNT * (nT - 1) + r16(NN - kTcNT * (nT - 1));
-  return 3 * np_tot * kp_tot;
+  return 3 * np_tot * (size_t)kg.kp_tot;
 }
 
 // Layout (matching the kernel): tiles t, chunks c, pieces p, then core
-// matrices (ki, mi) in K-outer order, 8 rows x 8 elements each.
+// matrices (ki, mi) in K-outer order, 8 rows x 8 elements each.  elem(n, k)
+// is the block entry for row n and K index k of the unwidened K side; K
+// positions that fall outside both segments (group widening, padding) are 0.
 template <class E>
-static void tc_pack(int NN, int KK, E elem, uint16_t* dst) {
-  const int nT = (NN + kTcNT - 1) / kTcNT, nK = (KK + kTcKC - 1) / kTcKC;
+static void tc_pack(int NN, const TcKGeom& kg, int off0, int len0, int off1, int len1, E elem, uint16_t* dst) {
+  const int nT = (NN + kTcNT - 1) / kTcNT;
+  auto korig = [&](int kp) -> int {  // widened K position -> K index, or -1
+    const int j = kp / kTcGrpRows, e = kp % kTcGrpRows;
+    if (j < kg.ng0) {
+      const int r = (kg.gs0 + j) * kTcGrpRows + e;
+      return r >= off0 && r < off0 + len0 ? r - off0 : -1;
+    }
+    if (j < kg.ngt) {
+      const int r = (kg.gs1 + j - kg.ng0) * kTcGrpRows + e;
+      return r >= off1 && r < off1 + len1 ? len0 + r - off1 : -1;
+    }
+    return -1;
+  };
   size_t o = 0;
   for (int t = 0; t < nT; ++t) {
     const int Np = r16(std::min(kTcNT, NN - kTcNT * t));
-    for (int c = 0; c < nK; ++c) {
-      const int Kp = r16(std::min(kTcKC, KK - kTcKC * c));
+    for (int c = 0; c < kg.nK; ++c) {
+      const int Kp = std::min(kTcKC, kg.kp_tot - kTcKC * c);
       // pieces of every element of the chunk
       for (int p = 0; p < 3; ++p)
         for (int ki = 0; ki < Kp / 8; ++ki)
           for (int mi = 0; mi < Np / 8; ++mi)
             for (int rr = 0; rr < 8; ++rr)
               for (int kk = 0; kk < 8; ++kk) {
-                const int n = kTcNT * t + mi * 8 + rr, k = kTcKC * c + ki * 8 + kk;
-                double v = (n < NN && k < KK) ? elem(n, k) : 0.0;
+                const int n = kTcNT * t + mi * 8 + rr, k = korig(kTcKC * c + ki * 8 + kk);
+                double v = (n < NN && k >= 0) ? elem(n, k) : 0.0;
                 uint16_t h = 0;
                 for (int q = 0; q <= p; ++q) {  // piece q of v: bf16 of the remainder
                   h = bf16_rn((float)v);
@@ -100,9 +116,9 @@ void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops,
     const Op& op = ops[i];
     TcOp& t = tops[i];
     t.img[0] = (int64_t)tot;
-    tot += tc_image_elems(op.mo, op.ni);
+    tot += tc_image_elems(op.mo, tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1]));
     t.img[1] = (int64_t)tot;
-    tot += tc_image_elems(op.ni, op.mo);
+    tot += tc_image_elems(op.ni, tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1]));
     t.mo = op.mo;
     t.ni = op.ni;
     for (int s = 0; s < 2; ++s) {
@@ -127,8 +143,12 @@ void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops,
     const double* B = factors.data() + op.b_off;
     const int ld = op.ld;
     if (op.ni > 0) {
-      tc_pack(op.mo, op.ni, [&](int r, int k) { return B[(size_t)k * ld + r]; }, img.data() + tops[i].img[0]);
-      tc_pack(op.ni, op.mo, [&](int r, int k) { return B[(size_t)r * ld + k]; }, img.data() + tops[i].img[1]);
+      const TcKGeom kf = tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1]);
+      const TcKGeom kb = tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1]);
+      tc_pack(op.mo, kf, op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1],
+              [&](int r, int k) { return B[(size_t)k * ld + r]; }, img.data() + tops[i].img[0]);
+      tc_pack(op.ni, kb, op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1],
+              [&](int r, int k) { return B[(size_t)r * ld + k]; }, img.data() + tops[i].img[1]);
     }
   }
 }
@@ -137,15 +157,14 @@ void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops,
 namespace {
 
 constexpr int kStages = 3;
-constexpr int kProdWarps = 3;                 // warps staging operands
+constexpr int kProdWarps = 3;                 // warp 0 stages operands (one thread); warps 1-2 are spare
 constexpr int kMmaWarp = kProdWarps;          // the MMA-issuing warp
 constexpr int kEpiWarp0 = kProdWarps + 1;     // first epilogue warp
 constexpr int kEpiWarps = 4;                  // one warpgroup drains the accumulators
 constexpr int kIoWarp0 = kEpiWarp0 + kEpiWarps;  // the remaining warps gather the next item's inputs
 constexpr int kIoWarps = kTcThreads / 32 - kIoWarp0;
 constexpr int kTrStride = 33;                 // padded 32 x 32 transpose tile (floats)
-constexpr int kPieceA = kTcR * kTcKC * 2;      // bytes of one A piece in a stage (8 KB)
-constexpr int kStageA = 3 * kPieceA;           // 24 KB
+constexpr int kStageA = (kTcKC / kTcGrpRows) * kTcGrpBytes;  // 4 row groups: 24 KB
 constexpr int kStageB = 3 * kTcNT * kTcKC * 2; // 24 KB (largest N tile)
 constexpr int kStageBytes = kStageA + kStageB;
 constexpr int kTmemCols = 512;                 // 2 accumulator pairs (hi, lo) x 128 columns
@@ -220,6 +239,19 @@ __device__ __forceinline__ bool mbar_wait(Ctl* ctl, uint64_t* bar, uint32_t pari
   *((volatile int*)&ctl->abort) = 1;
   return false;
 }
+// Bounded wait for a bulk copy still in flight after an abort: the CTA must
+// not exit while a copy can still write its shared memory.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  for (long it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(s32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return;
+  }
+}
 // Bounded wait until a shared counter reaches `target`.
 __device__ __forceinline__ bool counter_wait(Ctl* ctl, int* ctr, int target) {
   for (long it = 0; it < kWaitLimit; ++it) {
@@ -234,9 +266,6 @@ __device__ __forceinline__ bool counter_wait(Ctl* ctl, int* ctr, int target) {
   return false;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
 __device__ __forceinline__ void bulk_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s32(bar)), "r"(bytes) : "memory");
 }
@@ -246,12 +275,28 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
       "l"(src), "r"(bytes), "r"(s32(bar))
       : "memory");
 }
-__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(s32(bar)) : "memory");
-}
-
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 __device__ __forceinline__ void io_bar() { asm volatile("bar.sync 2, %0;" ::"n"(32 * kIoWarps) : "memory"); }
+// The named barriers with an AND over the group: every warp of the group takes
+// the same decision after a bounded wait, so none is left at a barrier alone.
+__device__ __forceinline__ bool epi_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred q, r;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred r, 1, 128, q;\n selp.u32 %0, 1, 0, r;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ bool io_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred q, r;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred r, 2, %2, q;\n selp.u32 %0, 1, 0, r;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(32 * kIoWarps)
+      : "memory");
+  return r != 0;
+}
 
 __device__ __forceinline__ long coef_offset(long N, long m) {
   long a = m < 0 ? -m : m;
@@ -291,9 +336,15 @@ __device__ __forceinline__ const double* value_base(const double* g, int N, int 
 
 
 
-// four consecutive values (columns col .. col+3) -> three BF16 pieces, one
-// 8-byte store per piece
-__device__ __forceinline__ void put_pieces4(unsigned char* row, int col, float4 x) {
+// Byte offset of (row, piece, column) in a vector space (the group layout).
+__device__ __forceinline__ size_t grp_off(int row, int pc, int col) {
+  return (size_t)(row / kTcGrpRows) * kTcGrpBytes + pc * 2048 + (col >> 3) * 128 + (row % kTcGrpRows) * 16 +
+         (col & 7) * 2;
+}
+
+// four consecutive values (columns col .. col+3, col % 4 == 0) of row `row`
+// -> three BF16 pieces, one 8-byte store per piece
+__device__ __forceinline__ void put_pieces4(unsigned char* vec, int row, int col, float4 x) {
   float a[4] = {x.x, x.y, x.z, x.w};
   uint32_t h[3][2];
 #pragma unroll
@@ -310,21 +361,23 @@ __device__ __forceinline__ void put_pieces4(unsigned char* row, int col, float4 
   }
 #pragma unroll
   for (int pc = 0; pc < 3; ++pc)
-    __stcg(reinterpret_cast<uint2*>(row + pc * (kTcR * 2) + col * 2), make_uint2(h[pc][0], h[pc][1]));
+    __stcg(reinterpret_cast<uint2*>(vec + grp_off(row, pc, col)), make_uint2(h[pc][0], h[pc][1]));
 }
 
 
 // Shape of one op in the requested direction.
 struct OpShape {
-  int NN, KK, nT, nK, kp_tot;
+  int NN, KK, nT;
+  TcKGeom kg;  // the K side widened to whole row groups (nK chunks, kp_tot columns)
 };
 __device__ __forceinline__ OpShape op_shape(const TcOp& op, bool fwd) {
   OpShape s;
   s.NN = fwd ? op.mo : op.ni;
   s.KK = fwd ? op.ni : op.mo;
   s.nT = (s.NN + kTcNT - 1) / kTcNT;
-  s.nK = s.KK > 0 ? (s.KK + kTcKC - 1) / kTcKC : 0;
-  s.kp_tot = s.KK > 0 ? kTcKC * (s.nK - 1) + ((s.KK - kTcKC * (s.nK - 1) + 15) & ~15) : 0;
+  s.kg = fwd ? tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1])
+             : tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1]);
+  if (s.KK <= 0) s.kg.nK = s.kg.ngt = s.kg.kp_tot = 0;
   return s;
 }
 
@@ -354,7 +407,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&ctl->full[s], 32 * kProdWarps + 1);  // cp.async arrivals + the bulk copy's expect_tx
+      mbar_init(&ctl->full[s], 1);  // the producer's expect_tx; the bulk copies complete the bytes
       mbar_init(&ctl->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -366,6 +419,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
     ctl->done_tiles = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // Stage memory starts at zero: the MMA of a padded last K step reads one row
+  // group that no copy fills (its operand-image columns are zero), which must
+  // hold finite values.  Afterwards stages only ever hold copied activations.
+  for (int i = tid; i < kStages * kStageBytes / 16; i += kTcThreads)
+    reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the bulk copies and MMAs
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s32(&ctl->taddr)),
                  "r"(kTmemCols)
@@ -380,22 +439,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   const int N = p.N;
   const int G = (F + kTcFields - 1) / kTcFields;
   const int nitems = single ? G : p.nunits * G;
-  const size_t slot_bytes = (size_t)p.max_rows * kTcRowBytes;
+  const size_t slot_bytes = tc_slot_bytes(p.max_rows);
   unsigned char* slots = p.ws + (size_t)blockIdx.x * 2 * slot_bytes;  // two vector spaces, alternating by item
   const uint32_t stage0 = s32(base);
 
-  if (warp < kProdWarps) {
-    // ------------------------------------------------------------ producers
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    // One thread streams the stages: per (op, N tile, K chunk) the chunk's
+    // operand-image piece block and its input row groups (at most one run of
+    // whole groups per segment), all as bulk copies whose bytes the stage's
+    // full barrier expects.
     long jp = 0;
     int tiles_before = 0;  // tiles of all earlier phases (all items so far)
     bool ok = true;
     for (int it = blockIdx.x, iseq = 0; it < nitems && ok; it += gridDim.x, ++iseq) {
       const Item itm = item_of(p, it, G, single, msingle);
       const Unit u = p.units[itm.am];
-      unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
+      const unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
       const int nops = u.op_end - u.op_begin;
       TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
-      ok = counter_wait(ctl, &ctl->gathered, iseq + 1);
+      if (lane == 0) ok = counter_wait(ctl, &ctl->gathered, iseq + 1);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
       int cur_phase = -1, tiles_here = 0;
       for (int q = 0; q < nops && ok; ++q) {
         const TcOp op = nxt;
@@ -405,57 +469,49 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
           // their tiles (the item's first phase reads only gathered rows)
           tiles_before += tiles_here;
           tiles_here = 0;
-          if (cur_phase >= 0) ok = counter_wait(ctl, &ctl->done_tiles, tiles_before);
+          if (cur_phase >= 0 && lane == 0) ok = counter_wait(ctl, &ctl->done_tiles, tiles_before);
+          ok = __shfl_sync(0xffffffffu, ok, 0);
           cur_phase = op.phase;
         }
         const OpShape sh = op_shape(op, fwd);
-        const Segs isg = in_segs(op, fwd);
+        const TcKGeom& kg = sh.kg;
         const uint16_t* img = p.img + (fwd ? op.img[0] : op.img[1]);
         for (int t = 0; t < sh.nT && ok; ++t) {
           const int Np = (min(kTcNT, sh.NN - kTcNT * t) + 15) & ~15;
-          for (int c = 0; c < sh.nK && ok; ++c, ++jp) {
-            const int s = (int)(jp % kStages);
-            const uint32_t use = (uint32_t)(jp / kStages);
-            ok = mbar_wait(ctl, &ctl->empty[s], (use & 1u) ^ 1u);
-            if (!ok) break;
-            const int Kp = (min(kTcKC, sh.KK - kTcKC * c) + 15) & ~15;
-            const uint32_t sA = stage0 + (uint32_t)s * kStageBytes, sB = sA + kStageA;
-            // B: the image chunk (3 pieces, contiguous) in one bulk copy whose
-            // bytes the full barrier expects
-            if (warp == 0 && lane == 0) {
-              const uint16_t* src = img + (size_t)t * 384 * sh.kp_tot + (size_t)Np * (96 * c);
-              const uint32_t bytes = (uint32_t)(3 * Np * Kp * 2);
-              bulk_expect(&ctl->full[s], bytes);
-              bulk_copy(sB, src, bytes, &ctl->full[s]);
-            }
-            // A: Kp input rows x 3 pieces x 16 chunks of 8 right-hand sides
-            // (MN-major cores).  Lane l owns the row pointer of row l and the
-            // (piece, 8-column chunk) pairs l and l + 32 of every row.
-            {
-              const int j = kTcKC * c + lane;
-              const bool valid = lane < Kp && j < sh.KK;
-              const unsigned char* myrow = valid ? vec + (size_t)seg_row(j, isg) * kTcRowBytes : vec;
-              const int pc0 = lane >> 4, m80 = lane & 15;           // pair lane
-              const int pc1 = (lane + 32) >> 4, m81 = (lane + 32) & 15;  // pair lane + 32 (lanes < 16)
-              const uint32_t d0 = sA + pc0 * kPieceA + m80 * 128, d1 = sA + pc1 * kPieceA + m81 * 128;
-              const uint32_t o0 = pc0 * (kTcR * 2) + m80 * 16, o1 = pc1 * (kTcR * 2) + m81 * 16;
-              for (int kj = warp; kj < Kp; kj += kProdWarps) {
-                const unsigned char* row =
-                    reinterpret_cast<const unsigned char*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(myrow), kj));
-                const uint32_t ok_src = __shfl_sync(0xffffffffu, valid ? 16u : 0u, kj);
-                const uint32_t kofs = (uint32_t)((kj >> 3) * 2048 + (kj & 7) * 16);
-                cp_async16(d0 + kofs, row + o0, ok_src);
-                if (lane < 16) cp_async16(d1 + kofs, row + o1, ok_src);
+          for (int c = 0; c < kg.nK && ok; ++c) {
+            if (lane == 0) {
+              const int s = (int)(jp % kStages);
+              const uint32_t use = (uint32_t)(jp / kStages);
+              ok = mbar_wait(ctl, &ctl->empty[s], (use & 1u) ^ 1u);
+              if (ok) {
+                const int Kp = min(kTcKC, kg.kp_tot - kTcKC * c);
+                const uint32_t sA = stage0 + (uint32_t)s * kStageBytes, sB = sA + kStageA;
+                // slots [j0, j1) of this chunk: [j0, ja) in segment 0, [ja, j1) in segment 1
+                const int j0 = 4 * c, j1 = min(4 * c + 4, kg.ngt);
+                const int ja = max(j0, min(j1, kg.ng0));
+                const uint32_t bbytes = (uint32_t)(3 * Np * Kp * 2);
+                bulk_expect(&ctl->full[s], bbytes + (uint32_t)(j1 - j0) * kTcGrpBytes);
+                bulk_copy(sB, img + (size_t)t * 384 * kg.kp_tot + (size_t)Np * (96 * c), bbytes, &ctl->full[s]);
+                if (ja > j0)
+                  bulk_copy(sA, vec + (size_t)(kg.gs0 + j0) * kTcGrpBytes, (uint32_t)(ja - j0) * kTcGrpBytes,
+                            &ctl->full[s]);
+                if (j1 > ja)
+                  bulk_copy(sA + (uint32_t)(ja - j0) * kTcGrpBytes,
+                            vec + (size_t)(kg.gs1 + ja - kg.ng0) * kTcGrpBytes, (uint32_t)(j1 - ja) * kTcGrpBytes,
+                            &ctl->full[s]);
               }
             }
-            cp_async_arrive(&ctl->full[s]);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (ok) ++jp;  // stages issued so far
           }
           ++tiles_here;
         }
       }
       tiles_before += tiles_here;
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    // after an abort, let the copies of the last issued stages land before leaving
+    if (!ok && lane == 0)
+      for (long j = max(0L, jp - kStages); j < jp; ++j) mbar_drain(&ctl->full[j % kStages], (uint32_t)(j / kStages) & 1u);
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
@@ -481,16 +537,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
               const uint32_t idesc =
                   (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(Np >> 3) << 17) | (8u << 24);
               const uint32_t dhi = taddr + (uint32_t)(b * 256), dlo = dhi + 128;
-              for (int c = 0; c < sh.nK && ok; ++c, ++jm) {
+              for (int c = 0; c < sh.kg.nK && ok; ++c, ++jm) {
                 const int s = (int)(jm % kStages);
                 const uint32_t use = (uint32_t)(jm / kStages);
                 ok = mbar_wait(ctl, &ctl->full[s], use & 1u);
                 if (!ok) break;
-                // the stage was written by cp.async (generic proxy); the MMAs read it
-                // through the async proxy
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                // the stage was filled by bulk copies (async proxy), which the
+                // MMAs read through the same proxy: the barrier orders them
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int Kp = (min(kTcKC, sh.KK - kTcKC * c) + 15) & ~15;
+                const int Kp = min(kTcKC, sh.kg.kp_tot - kTcKC * c);
                 const uint32_t sA = stage0 + (uint32_t)s * kStageBytes, sB = sA + kStageA;
                 const uint32_t bPiece = (uint32_t)Np * Kp * 2, bK = (uint32_t)(Np / 8) * 128;
                 for (int ks = 0; ks < Kp / 16; ++ks) {
@@ -500,8 +555,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
 #pragma unroll
                     for (int pb = 0; pb < 3; ++pb) {
                       if (pa + pb > 2) continue;
-                      // A MN-major: cores (k8, m8) at (k8 * 16 + m8) * 128 B: K stride 2048, M stride 128
-                      const uint64_t ad = sdesc(sA + pa * kPieceA + ks * 2 * 2048, 2048, 128);
+                      // A MN-major: core (k8, m8) of piece pa at (k8 * 3 + pa) * 2048 + m8 * 128:
+                      // K stride one row group, M stride 128
+                      const uint64_t ad = sdesc(sA + (uint32_t)(ks * 2 * kTcGrpBytes + pa * 2048), kTcGrpBytes, 128);
                       const uint64_t bd = sdesc(sB + pb * bPiece + ks * 2 * bK, bK, 128);
                       if (pa + pb == 0) {
                         mma_bf16(dhi, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
@@ -520,7 +576,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       }
     }
     __syncwarp();
-  } else if (warp < kIoWarp0) {
+  } else if (warp >= kEpiWarp0 && warp < kIoWarp0) {
     // accumulators -> rows: warp ew owns TMEM lane quadrant ew (right-hand sides 32 ew ..)
     const int ew = warp - kEpiWarp0;
     const int e = tid - 32 * kEpiWarp0;
@@ -547,7 +603,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
           for (int t = 0; t < sh.nT && ok; ++t, ++te) {
             const int b = (int)(te & 1);
             const uint32_t v = (uint32_t)(te >> 1);
-            ok = mbar_wait(ctl, &ctl->accf[b], v & 1u);
+            ok = epi_and(mbar_wait(ctl, &ctl->accf[b], v & 1u));
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int Nt = min(kTcNT, sh.NN - kTcNT * t);
@@ -585,7 +641,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
                                    "f"(x[5]), "f"(x[6]), "f"(x[7])
                                    : "memory");
                     } else {
-                      unsigned char* row = vec + (size_t)r * kTcRowBytes;
                       uint32_t h[3][4];
 #pragma unroll
                       for (int jj = 0; jj < 8; jj += 2) {
@@ -601,7 +656,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
                       }
 #pragma unroll
                       for (int pc = 0; pc < 3; ++pc)
-                        __stcg(reinterpret_cast<uint4*>(row + pc * (kTcR * 2) + c8 * 2),
+                        __stcg(reinterpret_cast<uint4*>(vec + grp_off(r, pc, c8)),
                                make_uint4(h[pc][0], h[pc][1], h[pc][2], h[pc][3]));
                     }
                   }
@@ -612,6 +667,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->acce[b]);
+            // the rows written above are read next by bulk copies (async proxy)
+            asm volatile("fence.proxy.async.global;" ::: "memory");
             __threadfence_block();
             epi_bar();
             ++done;
@@ -640,7 +697,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       const Unit u = p.units[am];
       unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
       const int nx = u.nce + u.nco;
-      ok = counter_wait(ctl, &ctl->done_tiles, t_m2);
+      ok = io_and(counter_wait(ctl, &ctl->done_tiles, t_m2));
       if (!ok) break;
       if (fwd) {
         // X rows from beta: degree k = am + d, d even -> row d/2, d odd -> row nce + d/2
@@ -658,7 +715,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
             const int d = d0 + dl;
             if (d < nx) {
               const int t = (d & 1) ? u.nce + (d >> 1) : (d >> 1);
-              put_pieces4(vec + (size_t)t * kTcRowBytes, 4 * lane,
+              put_pieces4(vec, t, 4 * lane,
                           *reinterpret_cast<const float4*>(Te + dl * kIoStride + 4 * lane));
             }
           }
@@ -687,15 +744,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
           io_bar();
           for (int r = iw; r < 32; r += kIoWarps) {
             if (i0 + r < N) {
-              put_pieces4(vec + (size_t)(u.ye + i0 + r) * kTcRowBytes, 4 * lane,
+              put_pieces4(vec, u.ye + i0 + r, 4 * lane,
                           *reinterpret_cast<const float4*>(Te + r * kIoStride + 4 * lane));
-              put_pieces4(vec + (size_t)(u.yo + i0 + r) * kTcRowBytes, 4 * lane,
+              put_pieces4(vec, u.yo + i0 + r, 4 * lane,
                           *reinterpret_cast<const float4*>(To + r * kIoStride + 4 * lane));
             }
           }
           io_bar();
         }
       }
+      asm volatile("fence.proxy.async.global;" ::: "memory");  // the rows are read by bulk copies
       __threadfence_block();
       io_bar();
       if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;

@@ -16,7 +16,41 @@ constexpr int kTcR = 4 * kTcFields;      // 128 right-hand sides = MMA M
 constexpr int kTcNT = 128;               // N tile (rows of one block product)
 constexpr int kTcKC = 32;                // K chunk per pipeline stage
 constexpr int kTcThreads = 512;          // 3 producer, 1 MMA, 4 epilogue and 8 I/O warps
-constexpr int kTcRowBytes = 3 * kTcR * 2;  // scratch row: 3 BF16 pieces x 128 (or 128 FP32)
+constexpr int kTcRowBytes = 3 * kTcR * 2;  // one scratch row: 3 BF16 pieces x 128 values
+// The scratch stores rows in groups of 8 in the tensor cores' MN-major core
+// matrix layout, so that a run of whole groups is the A operand of a K chunk
+// as it sits in shared memory and moves with one bulk copy:
+//   group g = row / 8, piece p, 8-value chunk m8 of the 128 right-hand sides,
+//   row-in-group e = row % 8:  byte (g * 3 + p) * 2048 + m8 * 128 + e * 16.
+constexpr int kTcGrpRows = 8;
+constexpr int kTcGrpBytes = kTcGrpRows * kTcRowBytes;  // 6144
+
+// Bytes of one work item's vector space (max_rows rows, whole groups, plus a
+// spare group so that a padded K chunk never reads past the slot).
+__host__ __device__ inline size_t tc_slot_bytes(int max_rows) {
+  return ((size_t)(max_rows + kTcGrpRows - 1) / kTcGrpRows + 1) * kTcGrpBytes;
+}
+
+// K side of one block product in a given direction: its input rows are the
+// two row segments (off0, len0), (off1, len1) of the vector space.  They are
+// widened to whole groups: K position 8 j + e is row 8 G(j) + e with
+// G(j) = gs0 + j for the first ng0 slots and gs1 + j - ng0 after; rows outside
+// the segments get zero columns in the operand image.  K chunks are 4 groups
+// (32), the last one rounded up to a pair of groups (the MMA K step of 16).
+struct TcKGeom {
+  int gs0, ng0, gs1, ng1, ngt, nK, kp_tot;
+};
+__host__ __device__ inline TcKGeom tc_kgeom(int off0, int len0, int off1, int len1) {
+  TcKGeom g;
+  g.gs0 = off0 / kTcGrpRows;
+  g.ng0 = len0 > 0 ? (off0 + len0 + kTcGrpRows - 1) / kTcGrpRows - g.gs0 : 0;
+  g.gs1 = off1 / kTcGrpRows;
+  g.ng1 = len1 > 0 ? (off1 + len1 + kTcGrpRows - 1) / kTcGrpRows - g.gs1 : 0;
+  g.ngt = g.ng0 + g.ng1;
+  g.nK = (g.ngt + 3) / 4;
+  g.kp_tot = g.nK > 0 ? 32 * (g.nK - 1) + 16 * ((g.ngt - 4 * (g.nK - 1) + 1) / 2) : 0;
+  return g;
+}
 
 // One op as the tensor-core kernel reads it: a single 64-byte record with the
 // offsets of its operand images, so that walking a unit's ops is one load per
@@ -37,7 +71,7 @@ struct TcPlan {
   const int32_t* order;
   const uint16_t* img;      // split-BF16 operand images of every op
   const double* w;
-  unsigned char* ws;        // per-CTA scratch: max_rows rows of kTcRowBytes
+  unsigned char* ws;        // per-CTA scratch: two vector spaces of tc_slot_bytes(max_rows)
   // Accumulated rows of every work item (forward: Y_e, Y_o; inverse: X), FP32,
   // kTcR values per row, kTcAccRows(N) rows per item; item (group g, order
   // |m|) at (g * nunits + |m|) * kTcAccRows(N) rows.  Zero before a launch.
@@ -54,8 +88,9 @@ struct TcPlan {
 // 2N - |m| <= 2N inputs of the transposed apply.
 __host__ __device__ inline int kTcAccRows(int N) { return 2 * N; }
 
-// Elements of the split-BF16 image of an NN x KK block (3 pieces, padded).
-size_t tc_image_elems(int NN, int KK);
+// Elements of the split-BF16 image of a block with NN rows and K side kg
+// (3 pieces, padded).
+size_t tc_image_elems(int NN, const TcKGeom& kg);
 
 // Build the forward (NN = mo, KK = ni) and transposed (NN = ni, KK = mo)
 // images of every op from the FP64 factor store, the kernel's op records and

@@ -143,6 +143,17 @@ struct UnitBuild {
   std::string err;
 };
 
+// Rows for one intermediate vector segment.  Segments start on a multiple of
+// 8 rows: the tensor-core apply stages its inputs in whole groups of 8 rows,
+// and the rows that pad a segment to its group end are then never written by
+// any op.
+int32_t alloc_rows(UnitBuild& ub, int n) {
+  ub.nrows = (ub.nrows + 7) & ~7;
+  const int32_t at = ub.nrows;
+  ub.nrows += n;
+  return at;
+}
+
 static inline int round4(int v) { return (v + 3) & ~3; }
 
 // Append a dense block (mo x ni, column-major accessor f(i, j)) and return its offset.
@@ -422,8 +433,7 @@ static bool emit_idbf(UnitBuild& ub, const BlockCtx& b, int L, bool force) {
     zoff[l].resize((size_t)na * nc);
     for (int a = 0; a < na; ++a)
       for (int c = 0; c < nc; ++c) {
-        zoff[l][(size_t)a * nc + c] = ub.nrows;
-        ub.nrows += (int)cskel[l][(size_t)a * nc + c].size();
+        zoff[l][(size_t)a * nc + c] = alloc_rows(ub, (int)cskel[l][(size_t)a * nc + c].size());
       }
   }
   // w offsets, row side level l', layout c-major: index c * na + a
@@ -433,8 +443,7 @@ static bool emit_idbf(UnitBuild& ub, const BlockCtx& b, int L, bool force) {
     woff[l].resize((size_t)nc * na);
     for (int c = 0; c < nc; ++c)
       for (int a = 0; a < na; ++a) {
-        woff[l][(size_t)c * na + a] = ub.nrows;
-        ub.nrows += (int)rskel[l][(size_t)c * na + a].size();
+        woff[l][(size_t)c * na + a] = alloc_rows(ub, (int)rskel[l][(size_t)c * na + a].size());
       }
   }
   // column leaves (phase 0): z_0(0, c) = V x_C
@@ -457,9 +466,12 @@ static bool emit_idbf(UnitBuild& ub, const BlockCtx& b, int L, bool force) {
         int ni = V1.c;
         int mo = V1.r + V2.r;
         int64_t off = put_block(ub, mo, ni, [&](int i, int j) { return i < V1.r ? V1(i, j) : V2(i - V1.r, j); });
-        int in0 = zoff[l - 1][(size_t)ap * ncp + 2 * c];
-        add_op(ub, l, mo, ni, off, in0, ni, 0, 0, zoff[l][(size_t)(2 * ap) * nc + c], V1.r,
-               zoff[l][(size_t)(2 * ap + 1) * nc + c], V2.r, 0);
+        // the candidates are the two children's skeleton rows, in that order
+        // (n0 + n1 == ni by construction of cand above)
+        const size_t k0 = (size_t)ap * ncp + 2 * c;
+        const int n0 = (int)cskel[l - 1][k0].size(), n1 = (int)cskel[l - 1][k0 + 1].size();
+        add_op(ub, l, mo, ni, off, zoff[l - 1][k0], n0, zoff[l - 1][k0 + 1], n1, zoff[l][(size_t)(2 * ap) * nc + c],
+               V1.r, zoff[l][(size_t)(2 * ap + 1) * nc + c], V2.r, 0);
       }
   }
   // middle (phase h+1): w_LR(c, a) = S_(a,c) z_h(a, c), S = K(p, q)
@@ -486,8 +498,12 @@ static bool emit_idbf(UnitBuild& ub, const BlockCtx& b, int L, bool force) {
         int mo = U1.r;  // |cand|, same for both
         int ni = U1.c + U2.c;
         int64_t off = put_block(ub, mo, ni, [&](int i, int j) { return j < U1.c ? U1(i, j) : U2(i, j - U1.c); });
+        // the outputs are the two children's skeleton rows, in that order
+        // (n0 + n1 == mo by construction of cand above)
+        const size_t k0 = (size_t)cp * nap + 2 * a;
+        const int n0 = (int)rskel[l - 1][k0].size(), n1 = (int)rskel[l - 1][k0 + 1].size();
         add_op(ub, phase, mo, ni, off, woff[l][(size_t)(2 * cp) * na + a], U1.c, woff[l][(size_t)(2 * cp + 1) * na + a],
-               U2.c, woff[l - 1][(size_t)cp * nap + 2 * a], mo, 0, 0, 0);
+               U2.c, woff[l - 1][k0], n0, woff[l - 1][k0 + 1], n1, 0);
       }
   }
   // row leaves (phase L+2): y_A += U_A w_0(0, a)
@@ -589,8 +605,7 @@ static bool emit_lowrank(UnitBuild& ub, const BlockCtx& b, bool force) {
       continue;
     }
     const ParityMatrix& P = *b.P;
-    int trow = ub.nrows;
-    ub.nrows += keep;
+    int trow = alloc_rows(ub, keep);
     int64_t o1 = put_block(ub, keep, n, [&](int i, int j) { return Vk(j, i); });
     add_op(ub, 0, keep, n, o1, P.xbase + b.j0, n, 0, 0, trow, keep, 0, 0, OP_BWD_ACCUM);
     int64_t o2 = put_block(ub, m, keep, [&](int i, int j) { return Uk(i, j) * s[j]; });
