@@ -156,7 +156,7 @@ void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops,
 // ---------------------------------------------------------------- device side
 namespace {
 
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 constexpr int kProdWarps = 3;                 // warp 0 stages operands (one thread); warps 1-2 are spare
 constexpr int kMmaWarp = kProdWarps;          // the MMA-issuing warp
 constexpr int kEpiWarp0 = kProdWarps + 1;     // first epilogue warp
@@ -177,16 +177,19 @@ struct Ctl {
   uint64_t acce[2];
   uint32_t taddr;
   int abort;
-  int gathered;    // items whose gather is complete
+  int gathered;    // items whose gather is complete (or found the queue empty)
   int done_tiles;  // tiles whose epilogue is complete (all items so far)
+  int ring[4];     // item index of this CTA's item iseq at ring[iseq % 4]; -1 = no more
 };
 constexpr size_t kTrBytes = (size_t)kEpiWarps * 32 * kTrStride * 4;
-// I/O transpose tiles: two 32-row x 128-column FP32 tiles (row stride padded
-// to 132 floats: 16-byte aligned rows, at most 2-way bank conflicts on the
-// column-wise accesses)
+// I/O transpose tile: 32 rows x 128 FP32 columns (row stride padded to 132
+// floats: 16-byte aligned rows, conflict-free 8-row column reads)
 constexpr int kIoStride = 132;
-constexpr size_t kIoBytes = (size_t)2 * 32 * kIoStride * 4;
+constexpr size_t kIoBytes = (size_t)32 * kIoStride * 4;
+constexpr int kPairsPerIo = 2 * kTcFields / kIoWarps;  // (field, sign) pairs per I/O warp
+static_assert(kPairsPerIo * kIoWarps == 2 * kTcFields, "I/O warps split the pairs evenly");
 constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + kTrBytes + kIoBytes + sizeof(Ctl) + 1024;
+static_assert(kSmemTotal <= 232448, "fits the 227 KB of shared memory one CTA may use");
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -264,6 +267,13 @@ __device__ __forceinline__ bool counter_wait(Ctl* ctl, int* ctr, int target) {
   }
   *((volatile int*)&ctl->abort) = 1;
   return false;
+}
+
+// This CTA's item number iseq as the I/O warps published it, once its inputs
+// are gathered; -1 when the work counter ran out.
+__device__ __forceinline__ int next_item(Ctl* ctl, int iseq, bool& ok) {
+  ok = counter_wait(ctl, &ctl->gathered, iseq + 1);
+  return ok ? *((volatile int*)&ctl->ring[iseq & 3]) : -1;
 }
 
 __device__ __forceinline__ void bulk_expect(uint64_t* bar, uint32_t bytes) {
@@ -365,6 +375,28 @@ __device__ __forceinline__ void put_pieces4(unsigned char* vec, int row, int col
 }
 
 
+// eight consecutive values (columns 8 m8 .. 8 m8 + 7) of row `row` -> three
+// BF16 pieces, one 16-byte store per piece
+__device__ __forceinline__ void put_pieces8(unsigned char* vec, int row, int m8, float4 xa, float4 xb) {
+  float a[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+  uint32_t h[3][4];
+#pragma unroll
+  for (int jj = 0; jj < 8; jj += 2) {
+    float a0 = a[jj], a1 = a[jj + 1];
+#pragma unroll
+    for (int pc = 0; pc < 3; ++pc) {
+      const __nv_bfloat162 hb = __floats2bfloat162_rn(a0, a1);
+      const float2 hf = __bfloat1622float2(hb);
+      a0 -= hf.x;
+      a1 -= hf.y;
+      h[pc][jj >> 1] = *reinterpret_cast<const uint32_t*>(&hb);
+    }
+  }
+#pragma unroll
+  for (int pc = 0; pc < 3; ++pc)
+    __stcg(reinterpret_cast<uint4*>(vec + grp_off(row, pc, 8 * m8)), make_uint4(h[pc][0], h[pc][1], h[pc][2], h[pc][3]));
+}
+
 // Shape of one op in the requested direction.
 struct OpShape {
   int NN, KK, nT;
@@ -452,14 +484,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
     long jp = 0;
     int tiles_before = 0;  // tiles of all earlier phases (all items so far)
     bool ok = true;
-    for (int it = blockIdx.x, iseq = 0; it < nitems && ok; it += gridDim.x, ++iseq) {
+    for (int iseq = 0; ok; ++iseq) {
+      // the item and its gathered inputs (the I/O warps publish both)
+      int it = -1;
+      if (lane == 0) it = next_item(ctl, iseq, ok);
+      it = __shfl_sync(0xffffffffu, it, 0);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok || it < 0) break;
       const Item itm = item_of(p, it, G, single, msingle);
       const Unit u = p.units[itm.am];
       const unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
       const int nops = u.op_end - u.op_begin;
       TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
-      if (lane == 0) ok = counter_wait(ctl, &ctl->gathered, iseq + 1);
-      ok = __shfl_sync(0xffffffffu, ok, 0);
       int cur_phase = -1, tiles_here = 0;
       for (int q = 0; q < nops && ok; ++q) {
         const TcOp op = nxt;
@@ -517,7 +553,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
     if (lane == 0) {
       long jm = 0, tm = 0;
       bool ok = true;
-      for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+      for (int iseq = 0; ok; ++iseq) {
+        const int it = next_item(ctl, iseq, ok);
+        if (!ok || it < 0) break;
         const Item itm = item_of(p, it, G, single, msingle);
         const Unit u = p.units[itm.am];
         const int nops = u.op_end - u.op_begin;
@@ -584,7 +622,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
     long te = 0;
     int done = 0;
     bool ok = true;
-    for (int it = blockIdx.x, iseq = 0; it < nitems && ok; it += gridDim.x, ++iseq) {
+    for (int iseq = 0; ok; ++iseq) {
+      const int it = next_item(ctl, iseq, ok);
+      ok = epi_and(ok);
+      if (!ok || it < 0) break;
       const Item itm = item_of(p, it, G, single, msingle);
       const Unit u = p.units[itm.am];
       unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
@@ -678,76 +719,112 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       }
     }
   } else if (warp >= kIoWarp0) {
-    // I/O warps: the gather of item i into slot i % 2, once item i - 2 (the
-    // slot's previous user) has finished all of its tiles; the outputs go to
-    // the accumulation buffer and leave through the output kernel.  Global data
-    // moves through two 32 x 128 shared tiles so that every warp access is a
-    // contiguous run: 32 degrees or nodes of one (field, sign) column pair (512
-    // bytes of FP64 complex) on the global side, whole 128-column rows on the
-    // scratch side.  Column c = 4 field + 2 sign + {re, im}.
+    // I/O warps.  They take this CTA's items from the launch's work counter
+    // (decreasing cost: orders by cost, field groups inside an order), publish
+    // each in ctl->ring for the other roles, and gather item i into slot i % 2
+    // once item i - 2 (the slot's previous user) has finished all of its tiles.
+    // The outputs go to the accumulation buffer and leave through the output
+    // kernel.  Global data moves through a 32 x 128 shared tile: every load
+    // instruction reads contiguous 512-byte runs of one (field, sign) pair, each
+    // warp keeps its 8 pairs' loads in flight together, and every store writes
+    // whole 16-byte pieces of 8 consecutive columns, 8 rows of a group at a time.
+    // Column c = 4 field + 2 sign + {re, im}.
     const int iw = warp - kIoWarp0;  // 0 .. kIoWarps - 1
-    float* Te = iobuf;
-    float* To = iobuf + 32 * kIoStride;
+    float* T = iobuf;
     const int e = tid - 32 * kIoWarp0;
     int t_m2 = 0, t_m1 = 0;  // tiles of all items up to i-2, up to i-1
     bool ok = true;
-    for (int it = blockIdx.x, iseq = 0; it < nitems && ok; it += gridDim.x, ++iseq) {
+    for (int iseq = 0; ok; ++iseq) {
+      ok = io_and(counter_wait(ctl, &ctl->done_tiles, t_m2));
+      if (!ok) break;
+      if (e == 0) {
+        const unsigned int w = atomicAdd(p.counter, 1u);
+        ctl->ring[iseq & 3] = w < (unsigned int)nitems ? (int)w : -1;
+      }
+      io_bar();
+      const int it = *((volatile int*)&ctl->ring[iseq & 3]);
+      if (it < 0) {
+        __threadfence_block();
+        if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
+        break;
+      }
       const Item itm = item_of(p, it, G, single, msingle);
       const int am = itm.am, grp = itm.grp;
       const Unit u = p.units[am];
       unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
       const int nx = u.nce + u.nco;
-      ok = io_and(counter_wait(ctl, &ctl->done_tiles, t_m2));
-      if (!ok) break;
       if (fwd) {
-        // X rows from beta: degree k = am + d, d even -> row d/2, d odd -> row nce + d/2
+        // X rows from beta: degree k = am + d; d even -> row d/2 (X_e), d odd ->
+        // row nce + d/2 (X_o).  Tile row dl = degree d0 + dl.
         for (int d0 = 0; d0 < nx; d0 += 32) {
-          for (int pr = iw; pr < 2 * kTcFields; pr += kIoWarps) {
-            const int fl = pr >> 1, sgn = pr & 1, d = d0 + lane;
-            const double* bsrc = coef_base(in, N, am, grp * kTcFields + fl, sgn, F, single, msingle);
-            double2 v = make_double2(0.0, 0.0);
-            if (bsrc && d < nx) v = __ldg(reinterpret_cast<const double2*>(bsrc) + d);
-            *reinterpret_cast<float2*>(Te + lane * kIoStride + 4 * fl + 2 * sgn) =
-                make_float2(f64_to_f32_bits(v.x), f64_to_f32_bits(v.y));
+          const int d = d0 + lane;
+          double2 v[kPairsPerIo];
+#pragma unroll
+          for (int k = 0; k < kPairsPerIo; ++k) {
+            const int pr = iw + kIoWarps * k;
+            const double* bsrc = coef_base(in, N, am, grp * kTcFields + (pr >> 1), pr & 1, F, single, msingle);
+            v[k] = (bsrc && d < nx) ? __ldg(reinterpret_cast<const double2*>(bsrc) + d) : make_double2(0.0, 0.0);
+          }
+#pragma unroll
+          for (int k = 0; k < kPairsPerIo; ++k) {
+            const int pr = iw + kIoWarps * k;
+            *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * pr) =
+                make_float2(f64_to_f32_bits(v[k].x), f64_to_f32_bits(v[k].y));
           }
           io_bar();
-          for (int dl = iw; dl < 32; dl += kIoWarps) {
-            const int d = d0 + dl;
-            if (d < nx) {
-              const int t = (d & 1) ? u.nce + (d >> 1) : (d >> 1);
-              put_pieces4(vec, t, 4 * lane,
-                          *reinterpret_cast<const float4*>(Te + dl * kIoStride + 4 * lane));
+          // warp iw: 8 rows of one parity (block iw % 4) x 8 of the 16 column
+          // chunks (half iw / 4); lane = (row, chunk)
+          const int blk = iw & 3, par = blk >> 1;
+          const int j = (blk & 1) * 8 + (lane & 7);  // row of this parity within the chunk
+          const int dd = 2 * j + par;                // its tile row
+          if (d0 + dd < nx) {
+            const int row = (par ? u.nce : 0) + (d0 >> 1) + j;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const int m8 = (iw >> 2) * 8 + q * 4 + (lane >> 3);
+              put_pieces8(vec, row, m8, *reinterpret_cast<const float4*>(T + dd * kIoStride + 8 * m8),
+                          *reinterpret_cast<const float4*>(T + dd * kIoStride + 8 * m8 + 4));
             }
           }
           io_bar();
         }
       } else {
-        // weighted parity fold of g into Y_e, Y_o (Sec. 3.1.1 with the W of B = A^T W)
-        for (int i0 = 0; i0 < N; i0 += 32) {
-          const int i = i0 + lane;
+        // weighted parity fold of g into Y_e, Y_o (Sec. 3.1.1 with the W of
+        // B = A^T W), 16 nodes i0 .. i0 + 15 at a time: lanes 0-15 read
+        // g(theta_{N+i}), lanes 16-31 g(theta_{N-1-i}) of the same node; tile
+        // rows 0-15 take u_e = w (a + b), rows 16-31 u_o = w (a - b).
+        const int hl = lane & 15, hi = lane >> 4;
+        for (int i0 = 0; i0 < N; i0 += 16) {
+          const int i = i0 + hl;
           const float wi = i < N ? f64_to_f32_bits(__ldg(p.w + N + i)) : 0.f;
-          for (int pr = iw; pr < 2 * kTcFields; pr += kIoWarps) {
-            const int fl = pr >> 1, sgn = pr & 1;
-            const double* gb = value_base(in, N, am, grp * kTcFields + fl, sgn, F, single, msingle);
-            float2 ue = make_float2(0.f, 0.f), uo = ue;
-            if (gb && i < N) {
-              const double2 a = __ldg(reinterpret_cast<const double2*>(gb) + N + i);
-              const double2 b = __ldg(reinterpret_cast<const double2*>(gb) + N - 1 - i);
-              const float ax = f64_to_f32_bits(a.x), ay = f64_to_f32_bits(a.y);
-              const float bx = f64_to_f32_bits(b.x), by = f64_to_f32_bits(b.y);
-              ue = make_float2(wi * (ax + bx), wi * (ay + by));
-              uo = make_float2(wi * (ax - bx), wi * (ay - by));
-            }
-            *reinterpret_cast<float2*>(Te + lane * kIoStride + 4 * fl + 2 * sgn) = ue;
-            *reinterpret_cast<float2*>(To + lane * kIoStride + 4 * fl + 2 * sgn) = uo;
+          double2 v[kPairsPerIo];
+#pragma unroll
+          for (int k = 0; k < kPairsPerIo; ++k) {
+            const int pr = iw + kIoWarps * k;
+            const double* gb = value_base(in, N, am, grp * kTcFields + (pr >> 1), pr & 1, F, single, msingle);
+            v[k] = (gb && i < N) ? __ldg(reinterpret_cast<const double2*>(gb) + (hi ? N - 1 - i : N + i))
+                                 : make_double2(0.0, 0.0);
+          }
+#pragma unroll
+          for (int k = 0; k < kPairsPerIo; ++k) {
+            const int pr = iw + kIoWarps * k;
+            const float x = f64_to_f32_bits(v[k].x), y = f64_to_f32_bits(v[k].y);
+            const float ox = __shfl_xor_sync(0xffffffffu, x, 16), oy = __shfl_xor_sync(0xffffffffu, y, 16);
+            // lane < 16 holds a, its partner b; lane >= 16 holds b, its partner a
+            const float2 r = hi ? make_float2(wi * (ox - x), wi * (oy - y)) : make_float2(wi * (x + ox), wi * (y + oy));
+            *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * pr) = r;
           }
           io_bar();
-          for (int r = iw; r < 32; r += kIoWarps) {
-            if (i0 + r < N) {
-              put_pieces4(vec, u.ye + i0 + r, 4 * lane,
-                          *reinterpret_cast<const float4*>(Te + r * kIoStride + 4 * lane));
-              put_pieces4(vec, u.yo + i0 + r, 4 * lane,
-                          *reinterpret_cast<const float4*>(To + r * kIoStride + 4 * lane));
+          // warp iw: tile rows 8 (iw % 4) .. + 7 x 8 of the 16 column chunks (half iw / 4)
+          const int tr = (iw & 3) * 8 + (lane & 7);
+          const int ii = i0 + (tr & 15);
+          if (ii < N) {
+            const int row = (tr < 16 ? u.ye : u.yo) + ii;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const int m8 = (iw >> 2) * 8 + q * 4 + (lane >> 3);
+              put_pieces8(vec, row, m8, *reinterpret_cast<const float4*>(T + tr * kIoStride + 8 * m8),
+                          *reinterpret_cast<const float4*>(T + tr * kIoStride + 8 * m8 + 4));
             }
           }
           io_bar();
