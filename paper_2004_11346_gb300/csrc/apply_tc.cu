@@ -575,6 +575,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
               const uint32_t idesc =
                   (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(Np >> 3) << 17) | (8u << 24);
               const uint32_t dhi = taddr + (uint32_t)(b * 256), dlo = dhi + 128;
+              // descriptors of stage 0 for this tile; a stage, a K step or a piece
+              // moves the start address, i.e. adds (byte offset / 16) to the descriptor
+              const uint32_t bK = (uint32_t)(Np / 8) * 128;
+              const uint64_t a_desc0 = sdesc(stage0, kTcGrpBytes, 128);
+              const uint64_t b_desc0 = sdesc(stage0 + kStageA, bK, 128);
               for (int c = 0; c < sh.kg.nK && ok; ++c, ++jm) {
                 const int s = (int)(jm % kStages);
                 const uint32_t use = (uint32_t)(jm / kStages);
@@ -584,26 +589,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
                 // MMAs read through the same proxy: the barrier orders them
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int Kp = min(kTcKC, sh.kg.kp_tot - kTcKC * c);
-                const uint32_t sA = stage0 + (uint32_t)s * kStageBytes, sB = sA + kStageA;
-                const uint32_t bPiece = (uint32_t)Np * Kp * 2, bK = (uint32_t)(Np / 8) * 128;
-                for (int ks = 0; ks < Kp / 16; ++ks) {
-                  int lo = 0;
+                const uint64_t stg = (uint64_t)((s * kStageBytes) >> 4);
+                const uint64_t ad0 = a_desc0 + stg, bd0 = b_desc0 + stg;
+                const uint64_t bpc = (uint64_t)((Np * Kp * 2) >> 4), bks = (uint64_t)(2 * bK >> 4);
 #pragma unroll
-                  for (int pa = 0; pa < 3; ++pa)
-#pragma unroll
-                    for (int pb = 0; pb < 3; ++pb) {
-                      if (pa + pb > 2) continue;
-                      // A MN-major: core (k8, m8) of piece pa at (k8 * 3 + pa) * 2048 + m8 * 128:
-                      // K stride one row group, M stride 128
-                      const uint64_t ad = sdesc(sA + (uint32_t)(ks * 2 * kTcGrpBytes + pa * 2048), kTcGrpBytes, 128);
-                      const uint64_t bd = sdesc(sB + pb * bPiece + ks * 2 * bK, bK, 128);
-                      if (pa + pb == 0) {
-                        mma_bf16(dhi, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                      } else {
-                        mma_bf16(dlo, ad, bd, idesc, (c > 0 || ks > 0 || lo > 0) ? 1u : 0u);
-                        ++lo;
-                      }
-                    }
+                for (int ks = 0; ks < 2; ++ks) {
+                  if (ks * 16 >= Kp) break;
+                  // A MN-major: core (k8, m8) of piece pa at (k8 * 3 + pa) * 2048 + m8 * 128
+                  // (K stride one row group, M stride 128); B K-major, pieces bpc apart
+                  const uint64_t ak = ad0 + (uint64_t)((ks * 2 * kTcGrpBytes) >> 4), bk = bd0 + ks * bks;
+                  const uint32_t first = (c > 0 || ks > 0) ? 1u : 0u;
+                  mma_bf16(dhi, ak, bk, idesc, first);                           // a0 b0
+                  mma_bf16(dlo, ak, bk + bpc, idesc, first);                     // a0 b1
+                  mma_bf16(dlo, ak + (2048 >> 4), bk, idesc, 1u);                // a1 b0
+                  mma_bf16(dlo, ak, bk + 2 * bpc, idesc, 1u);                    // a0 b2
+                  mma_bf16(dlo, ak + (2048 >> 4), bk + bpc, idesc, 1u);          // a1 b1
+                  mma_bf16(dlo, ak + (4096 >> 4), bk, idesc, 1u);                // a2 b0
                 }
                 mma_commit(&ctl->empty[s]);
               }
@@ -830,8 +831,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
           io_bar();
         }
       }
+      // the item's accumulation rows start at zero: the epilogue adds into them
+      // (forward: the 2N node rows; inverse: the nx degree rows).  Zeroing them
+      // here keeps the lines in L2 for those additions.
+      {
+        float4* acc4 = reinterpret_cast<float4*>(p.acc + ((size_t)grp * p.nunits + am) * (size_t)kTcAccRows(N) * kTcR);
+        const int n4 = (fwd ? 2 * N : nx) * (kTcR / 4);
+        for (int k = e; k < n4; k += 32 * kIoWarps) __stcg(acc4 + k, make_float4(0.f, 0.f, 0.f, 0.f));
+      }
       asm volatile("fence.proxy.async.global;" ::: "memory");  // the rows are read by bulk copies
-      __threadfence_block();
+      __threadfence();
       io_bar();
       if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
       const int t_cur = t_m1 + p.tiles[2 * am + (fwd ? 0 : 1)];
@@ -930,17 +939,8 @@ cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, 
                       cudaStream_t st, cudaEvent_t* ev) {
   const int G = (F + kTcFields - 1) / kTcFields;
   if (G > p.gmax) return cudaErrorInvalidValue;
-  const size_t item_bytes = (size_t)kTcAccRows(p.N) * kTcR * sizeof(float);
-  cudaError_t e;
-  if (single) {
-    const int am = m < 0 ? -m : m;
-    e = cudaMemset2DAsync(reinterpret_cast<unsigned char*>(p.acc) + (size_t)am * item_bytes,
-                          (size_t)p.nunits * item_bytes, 0, item_bytes, G, st);
-  } else {
-    e = cudaMemsetAsync(p.acc, 0, (size_t)G * p.nunits * item_bytes, st);
-  }
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
+  // (the kernel zeroes each item's accumulation rows itself when it gathers the item)
+  cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(p, in, out, F, single, m, fwd ? 1 : 0);

@@ -74,7 +74,8 @@ struct TcPlan {
   unsigned char* ws;        // per-CTA scratch: two vector spaces of tc_slot_bytes(max_rows)
   // Accumulated rows of every work item (forward: Y_e, Y_o; inverse: X), FP32,
   // kTcR values per row, kTcAccRows(N) rows per item; item (group g, order
-  // |m|) at (g * nunits + |m|) * kTcAccRows(N) rows.  Zero before a launch.
+  // |m|) at (g * nunits + |m|) * kTcAccRows(N) rows.  The kernel zeroes an item's
+  // rows when it gathers the item.
   float* acc;
   int gmax;                 // field groups the accumulation buffer holds
   unsigned int* counter;
@@ -98,7 +99,7 @@ size_t tc_image_elems(int NN, const TcKGeom& kg);
 void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops, const std::vector<double>& factors,
                      std::vector<uint16_t>& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles);
 
-// One apply: clear the accumulation rows, run the persistent tensor-core
+// One apply: run the persistent tensor-core
 // kernel (gather, block products), then the output kernel (parity fold to g,
 // or scatter to beta).  F <= kTcFields * p.gmax.
 // ev (optional, three events): recorded before the tensor-core kernel, between
