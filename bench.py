@@ -573,6 +573,102 @@ def traffic_for(kernel, workload_name, algo_bytes=None):
     return None, None
 
 
+UNEVEN_PREFIX = "uneven_"
+
+
+def uneven_sizes(name):
+    """'uneven_N128-1024_F256' -> ((128, 256, 512, 1024), 256): powers of two from the first to the last N."""
+    body = name[len(UNEVEN_PREFIX):]
+    ns, fs = body.split("_F")
+    lo, hi = (int(v) for v in ns.lstrip("N").split("-"))
+    sizes = []
+    n = lo
+    while n <= hi:
+        sizes.append(n)
+        n *= 2
+    return tuple(sizes), int(fs)
+
+
+def run_uneven(args):
+    """One step = forward + inverse ALT of an uneven batch (fields of several
+    orders N, one plan per N) in one tensor-core launch per direction, through
+    alt_forward_batch / alt_inverse_batch.  Compared with the same fields run
+    plan by plan (one launch per plan and direction)."""
+    import torch
+    import paper_2004_11346_gb300 as sht
+    from paper_2004_11346_gb300 import _lib
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sizes, F = uneven_sizes(args.workload)
+    eps = 1e-7
+    per_field, coeffs = inputs.uneven_batch(F, seed=1 + rank, sizes=sizes)
+    Ns = sorted(coeffs)
+    t0 = time.perf_counter()
+    plans = [sht.Plan(N, eps, precision=_lib.SHT_MIXED, max_fields=coeffs[N].shape[0]) for N in Ns]
+    t_plan = time.perf_counter() - t0
+    counts = [coeffs[N].shape[0] for N in Ns]
+    batch = sht.Batch(plans, counts)
+    betas = [torch.from_numpy(coeffs[N]).cuda() for N in Ns]
+    gs = [torch.empty((c, 4 * N - 1, 2 * N, 2), dtype=torch.float64, device="cuda") for N, c in zip(Ns, counts)]
+    backs = [torch.empty_like(b) for b in betas]
+    bptr, gptr, kptr = [b.data_ptr() for b in betas], [g.data_ptr() for g in gs], [k.data_ptr() for k in backs]
+    stream = torch.cuda.current_stream()
+
+    def step_batch():
+        _lib.alt_forward_batch(batch.handle, bptr, gptr, stream.cuda_stream)
+        _lib.alt_inverse_batch(batch.handle, gptr, kptr, stream.cuda_stream)
+
+    def step_plans():
+        for p, b, g, k in zip(plans, betas, gs, backs):
+            p.forward(b, out=g)
+            p.inverse(g, out=k)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clock = ClockSampler(torch.cuda.current_device())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clock.stop()
+        ms = e0.elapsed_time(e1) / steps
+        return reduce_max([ms], world, device="cuda")[0], clk
+
+    ms_b, clk = timed(step_batch, args.steps)
+    batch.sync()
+    err = []
+    for b, k in zip(betas, backs):
+        d = (k - b).reshape(k.shape[0], -1).norm(dim=1) / b.reshape(b.shape[0], -1).norm(dim=1)
+        err.append(float(d.max()))
+    ms_p, _ = timed(step_plans, max(1, args.steps // 2))
+    value = F * world / (ms_b * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3 split, f32 accumulate", "data": "synthetic",
+        "config": {"workload": args.workload, "sizes": list(Ns), "fields_per_size": counts, "fields_per_rank": F,
+                   "global_batch": F * world, "eps": eps, "precision": "mixed",
+                   "step": "forward ALT + inverse ALT of the whole batch, one tensor-core launch per direction",
+                   "parallelism": f"replicas{world}"},
+        "round_trip_rel_err_max_per_size": dict(zip([str(n) for n in Ns], err)),
+        "plan_by_plan": {"ms_per_step": ms_p, "fields_per_s": F * world / (ms_p * 1e-3),
+                         "launches_per_direction": 2 * len(Ns)},
+        "plan_s": t_plan, "clocks": clk, "roofline": None, "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -586,6 +682,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith(UNEVEN_PREFIX):
+        run_uneven(args)
     else:
         run_ours(args)
 

@@ -188,6 +188,39 @@ sht_status sht_plan_save(sht_plan_t plan, const char* path);
  * SHT_ERR_CUDA without a device.  The caller owns the new plan. */
 sht_status sht_plan_load(const char* path, sht_plan_t* out);
 
+/* Batches of transforms of different orders N in one launch.  Sec. 1 states
+ * the SHT for one N; a batch applies several plans (each an order N of its
+ * own, e.g. fields of different resolutions) to their own fields at once.  The
+ * work items of all plans -- (plan, order |m|, group of 32 fields) -- form one
+ * queue in decreasing order of estimated cost, which one persistent launch of
+ * the tensor-core kernel works through; each plan's output step follows.
+ *  - plans: P distinct SHT_MIXED plans (1 <= P <= 8) on the current device;
+ *    fields[q] (>= 0, <= the plan's max_fields) fields go with plans[q].
+ *  - The batch owns its work-item table, scratch and counter; it uses each
+ *    plan's accumulation rows and ALT-value workspace, so a plan must not run
+ *    other calls while a batch that contains it is in flight.
+ *  - SHT_ERR_UNSUPPORTED for host-only plans or other precisions; SHT_ERR_ARG
+ *    for bad counts, repeated plans or plans of another device. */
+typedef struct sht_batch_s* sht_batch_t;
+sht_status sht_batch_create(int P, const sht_plan_t* plans, const int* fields, sht_batch_t* out);
+sht_status sht_batch_destroy(sht_batch_t batch);
+
+/* Forward / inverse ALT of a batch (Eq. sht_lt and Sec. 3.1.1 for each plan).
+ * in and out are HOST arrays of P device pointers: plan q's fields[q] fields
+ * of beta (F x 4N^2 complex) and g (F x (4N-1) x 2N complex) in the layouts of
+ * alt_forward.  Pointers of plans with no fields may be NULL. */
+sht_status alt_forward_batch(sht_batch_t batch, const double* const* beta, double* const* g, void* stream);
+sht_status alt_inverse_batch(sht_batch_t batch, const double* const* g, double* const* beta, void* stream);
+
+/* Full SHT of a batch (Eq. sht_re for each plan): the batched ALT, then each
+ * plan's phi-direction transform (as sht_forward / sht_inverse). */
+sht_status sht_forward_batch(sht_batch_t batch, const double* const* beta, double* const* f, void* stream);
+sht_status sht_inverse_batch(sht_batch_t batch, const double* const* f, double* const* beta, void* stream);
+
+/* Wait for a batch's work on `stream`; SHT_ERR_TIMEOUT if a bounded device
+ * wait gave up. */
+sht_status sht_batch_sync(sht_batch_t batch, void* stream);
+
 /* alt_forward_m without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory (a memory
  * pool or arena that owns the device, real-time loops where cudaMalloc/cudaFree

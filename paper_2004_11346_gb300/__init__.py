@@ -12,7 +12,7 @@ import numpy as np
 
 from . import _lib
 
-__all__ = ["Plan", "OP_DTYPE", "UNIT_DTYPE", "opts"]
+__all__ = ["Plan", "Batch", "OP_DTYPE", "UNIT_DTYPE", "opts"]
 
 OP_DTYPE = np.dtype([
     ("b_off", "<i8"), ("mo", "<i4"), ("ni", "<i4"), ("ld", "<i4"), ("flags", "<i4"),
@@ -206,3 +206,66 @@ class Plan:
 
     def sync(self):
         _lib.sht_sync(self.handle, self._stream())
+
+
+class Batch:
+    """Several SHT_MIXED plans applied to their own fields in one launch
+    (sht_batch_create in include/sht.h).  fields[q] fields go with plans[q];
+    the tensors passed to the methods are per plan, shaped as for Plan."""
+
+    def __init__(self, plans, fields):
+        self.plans = list(plans)
+        self.fields = [int(f) for f in fields]
+        self.handle = _lib.sht_batch_create([p.handle for p in self.plans], self.fields)
+
+    def close(self):
+        if self.handle:
+            _lib.sht_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _args(self, xs, shape_in, shape_out):
+        import torch
+        outs = []
+        for p, F, x in zip(self.plans, self.fields, xs):
+            if F == 0:
+                outs.append(None)
+                continue
+            Plan._dev(x, shape_in(p.N))
+            if x.shape[0] != F:
+                raise ValueError(f"expected {F} fields, got {x.shape[0]}")
+            outs.append(torch.empty((F, *shape_out(p.N)), dtype=torch.float64, device=x.device))
+        ins = [x.data_ptr() if F else 0 for F, x in zip(self.fields, xs)]
+        return ins, outs, [o.data_ptr() if o is not None else 0 for o in outs]
+
+    def forward(self, betas):
+        """Forward ALT of every plan's fields: list of (F_q, 4N^2, 2) -> list of (F_q, 4N-1, 2N, 2)."""
+        ins, outs, optr = self._args(betas, lambda N: (4 * N * N, 2), lambda N: (4 * N - 1, 2 * N, 2))
+        _lib.alt_forward_batch(self.handle, ins, optr, Plan._stream())
+        return outs
+
+    def inverse(self, gs):
+        """Inverse ALT of every plan's fields: list of (F_q, 4N-1, 2N, 2) -> list of (F_q, 4N^2, 2)."""
+        ins, outs, optr = self._args(gs, lambda N: (4 * N - 1, 2 * N, 2), lambda N: (4 * N * N, 2))
+        _lib.alt_inverse_batch(self.handle, ins, optr, Plan._stream())
+        return outs
+
+    def sht_forward(self, betas):
+        """Full SHT of every plan's fields: list of (F_q, 4N^2, 2) -> list of (F_q, 2N, 4N-1, 2)."""
+        ins, outs, optr = self._args(betas, lambda N: (4 * N * N, 2), lambda N: (2 * N, 4 * N - 1, 2))
+        _lib.sht_forward_batch(self.handle, ins, optr, Plan._stream())
+        return outs
+
+    def sht_inverse(self, fs):
+        """Inverse SHT of every plan's fields: list of (F_q, 2N, 4N-1, 2) -> list of (F_q, 4N^2, 2)."""
+        ins, outs, optr = self._args(fs, lambda N: (2 * N, 4 * N - 1, 2), lambda N: (4 * N * N, 2))
+        _lib.sht_inverse_batch(self.handle, ins, optr, Plan._stream())
+        return outs
+
+    def sync(self):
+        _lib.sht_batch_sync(self.handle, Plan._stream())

@@ -83,7 +83,9 @@ EXPORTED = [
     "sht_opts_default", "sht_plan_create", "sht_plan_destroy", "sht_plan_stats", "sht_plan_nodes",
     "sht_plan_export", "alt_forward", "alt_inverse", "alt_forward_m", "alt_inverse_m", "sht_sync",
     "sht_status_str", "alt_forward_m_noalloc", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
-    "sht_inverse", "sht_plan_save", "sht_plan_load", "sht_plan_kernel_time",
+    "sht_inverse", "sht_plan_save", "sht_plan_load", "sht_plan_kernel_time", "sht_batch_create",
+    "sht_batch_destroy", "alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch",
+    "sht_batch_sync",
 ]
 
 
@@ -114,6 +116,11 @@ def load(build: bool = True):
     for name in ("alt_forward_m", "alt_inverse_m", "alt_forward_m_noalloc"):
         getattr(lib, name).argtypes = [vp, i, vp, vp, i, vp]
     lib.sht_sync.argtypes = [vp, vp]
+    lib.sht_batch_create.argtypes = [i, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int), plan_p]
+    lib.sht_batch_destroy.argtypes = [vp]
+    lib.sht_batch_sync.argtypes = [vp, vp]
+    for name in ("alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch"):
+        getattr(lib, name).argtypes = [vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), vp]
     lib.sht_status_str.argtypes = [i]
     lib.sht_status_str.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -225,3 +232,41 @@ def sht_inverse(plan: int, f: int, beta: int, F: int, stream: int = 0):
 
 def sht_sync(plan: int, stream: int = 0):
     check(load().sht_sync(plan, stream), "sht_sync")
+
+
+def sht_batch_create(plans, fields) -> int:
+    """A batch of plans with fields[q] fields for plans[q] (sht_batch_create)."""
+    P = len(plans)
+    parr = (ctypes.c_void_p * max(1, P))(*plans)
+    farr = (ctypes.c_int * max(1, P))(*fields)
+    h = ctypes.c_void_p()
+    check(load().sht_batch_create(P, parr, farr, ctypes.byref(h)), "sht_batch_create")
+    return h.value
+
+
+def sht_batch_destroy(batch: int):
+    check(load().sht_batch_destroy(batch), "sht_batch_destroy")
+
+
+def _ptrs(ptrs):
+    return (ctypes.c_void_p * max(1, len(ptrs)))(*[p or None for p in ptrs])
+
+
+def alt_forward_batch(batch: int, beta_ptrs, g_ptrs, stream: int = 0):
+    check(load().alt_forward_batch(batch, _ptrs(beta_ptrs), _ptrs(g_ptrs), stream), "alt_forward_batch")
+
+
+def alt_inverse_batch(batch: int, g_ptrs, beta_ptrs, stream: int = 0):
+    check(load().alt_inverse_batch(batch, _ptrs(g_ptrs), _ptrs(beta_ptrs), stream), "alt_inverse_batch")
+
+
+def sht_forward_batch(batch: int, beta_ptrs, f_ptrs, stream: int = 0):
+    check(load().sht_forward_batch(batch, _ptrs(beta_ptrs), _ptrs(f_ptrs), stream), "sht_forward_batch")
+
+
+def sht_inverse_batch(batch: int, f_ptrs, beta_ptrs, stream: int = 0):
+    check(load().sht_inverse_batch(batch, _ptrs(f_ptrs), _ptrs(beta_ptrs), stream), "sht_inverse_batch")
+
+
+def sht_batch_sync(batch: int, stream: int = 0):
+    check(load().sht_batch_sync(batch, stream), "sht_batch_sync")

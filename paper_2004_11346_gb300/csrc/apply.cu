@@ -376,6 +376,26 @@ DevPlan dev_plan(const sht_plan_s* p) {
   return d;
 }
 
+// The tensor-core kernel's view of a SHT_MIXED plan.
+TcPlan tc_plan_of(const sht_plan_s* p) {
+  TcPlan t;
+  t.units = p->d_units;
+  t.ops = p->d_tcops;
+  t.tiles = p->d_tctiles;
+  t.order = p->d_order;
+  t.img = p->d_img;
+  t.w = p->d_w;
+  t.ws = p->d_wstc;
+  t.acc = p->d_acc;
+  t.gmax = p->tc_gmax;
+  t.counter = p->d_counter;
+  t.err = p->d_err;
+  t.N = p->prog.N;
+  t.nunits = 2 * p->prog.N;
+  t.max_rows = p->prog.max_rows;
+  return t;
+}
+
 sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F, int single, int m,
                   cudaStream_t st) {
   if (p->host_only) return SHT_ERR_UNSUPPORTED;
@@ -389,21 +409,7 @@ sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F,
   }
   if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
   if (p->prog.opts.precision == SHT_MIXED) {
-    TcPlan t;
-    t.units = p->d_units;
-    t.ops = p->d_tcops;
-    t.tiles = p->d_tctiles;
-    t.order = p->d_order;
-    t.img = p->d_img;
-    t.w = p->d_w;
-    t.ws = p->d_wstc;
-    t.acc = p->d_acc;
-    t.gmax = p->tc_gmax;
-    t.counter = p->d_counter;
-    t.err = p->d_err;
-    t.N = p->prog.N;
-    t.nunits = 2 * p->prog.N;
-    t.max_rows = p->prog.max_rows;
+    const TcPlan t = tc_plan_of(p);
     // the accumulation buffer holds tc_gmax groups of kTcFields fields: larger
     // batches run as several launches on consecutive fields
     const int N = p->prog.N;
@@ -954,6 +960,195 @@ const char* sht_status_str(sht_status s) {
     case SHT_ERR_UNSUPPORTED: return "unsupported";
   }
   return "unknown status";
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of plans: several orders N, each with its own fields, in one launch
+// of the tensor-core kernel.  The work items of all plans, (plan, |m|, field
+// group), form one queue in decreasing order of estimated cost, so that the
+// persistent kernel balances uneven transforms across the SMs.
+
+struct sht_batch_s {
+  int device = 0;
+  int nplans = 0;
+  sht_plan_s* plans[kTcMaxPlans] = {};
+  int F[kTcMaxPlans] = {};
+  int4* d_items = nullptr;
+  int nitems = 0;
+  unsigned char* d_ws = nullptr;
+  int max_rows = 0;
+  unsigned int* d_counter = nullptr;
+  int* d_err = nullptr;
+  int grid = 0;
+};
+
+namespace {
+
+void free_batch(sht_batch_s* b) {
+  cudaFree(b->d_items);
+  cudaFree(b->d_ws);
+  cudaFree(b->d_counter);
+  cudaFree(b->d_err);
+}
+
+sht_status launch_batch(sht_batch_s* b, bool fwd, const double* const* in, double* const* out, cudaStream_t st) {
+  TcLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  for (int q = 0; q < b->nplans; ++q) {
+    sht_plan_s* p = b->plans[q];
+    if (b->F[q] > 0) {
+      if (!in[q] || !out[q]) return SHT_ERR_ARG;
+      if ((reinterpret_cast<uintptr_t>(in[q]) | reinterpret_cast<uintptr_t>(out[q])) & 15u) return SHT_ERR_ARG;
+    }
+    if (p->latched != SHT_OK) {
+      sht_status s = p->latched;
+      p->latched = SHT_OK;
+      return s;
+    }
+    L.plan[q] = tc_plan_of(p);
+    L.in[q] = in[q];
+    L.out[q] = out[q];
+    L.F[q] = b->F[q];
+  }
+  if (b->nitems == 0) return SHT_OK;
+  L.nplans = b->nplans;
+  L.items = b->d_items;
+  L.nitems = b->nitems;
+  L.ws = b->d_ws;
+  L.max_rows = b->max_rows;
+  L.counter = b->d_counter;
+  L.err = b->d_err;
+  if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
+  if (launch_tc_batch(L, fwd, std::min(b->grid, b->nitems), st) != cudaSuccess) return SHT_ERR_CUDA;
+  return SHT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sht_status sht_batch_create(int P, const sht_plan_t* plans, const int* fields, sht_batch_t* out) {
+  if (!out || !plans || !fields || P < 1 || P > kTcMaxPlans) return SHT_ERR_ARG;
+  *out = nullptr;
+  int dev = 0;
+  for (int q = 0; q < P; ++q) {
+    if (!plans[q] || fields[q] < 0) return SHT_ERR_ARG;
+    for (int r = 0; r < q; ++r)
+      if (plans[r] == plans[q]) return SHT_ERR_ARG;  // each plan's accumulation rows serve one batch slot
+    if (plans[q]->host_only || plans[q]->prog.opts.precision != SHT_MIXED) return SHT_ERR_UNSUPPORTED;
+    if (fields[q] > plans[q]->prog.opts.max_fields) return SHT_ERR_ARG;
+    if ((int64_t)fields[q] * 2 * plans[q]->prog.N > (int64_t)1 << 30) return SHT_ERR_ARG;
+  }
+  if (cudaGetDevice(&dev) != cudaSuccess) return SHT_ERR_CUDA;
+  for (int q = 0; q < P; ++q)
+    if (plans[q]->device != dev) return SHT_ERR_ARG;
+  sht_batch_s* b = new (std::nothrow) sht_batch_s();
+  if (!b) return SHT_ERR_OOM;
+  b->device = dev;
+  b->nplans = P;
+  // the queue: every (plan, |m|, field group), in decreasing estimated cost
+  // (flops per right-hand side of the order), ties by plan, order and group
+  struct Entry {
+    float cost;
+    int4 it;
+  };
+  std::vector<Entry> q;
+  for (int k = 0; k < P; ++k) {
+    const sht_plan_s* p = plans[k];
+    b->plans[k] = plans[k];
+    b->F[k] = fields[k];
+    b->max_rows = std::max(b->max_rows, p->prog.max_rows);
+    const int G = (fields[k] + kTcFields - 1) / kTcFields;
+    for (const Unit& u : p->prog.units)
+      for (int g = 0; g < G; ++g) q.push_back({u.cost, make_int4(k, u.am, g, 0)});
+  }
+  std::stable_sort(q.begin(), q.end(), [](const Entry& a, const Entry& c) { return a.cost > c.cost; });
+  std::vector<int4> items(q.size());
+  for (size_t i = 0; i < q.size(); ++i) items[i] = q[i].it;
+  b->nitems = (int)items.size();
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->grid = std::max(1, sms * tc_ctas_per_sm());
+  const size_t ws = (size_t)b->grid * 2 * tc_slot_bytes(b->max_rows);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_items), std::max<size_t>(items.size(), 1) * sizeof(int4));
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_ws), ws);
+  // rows that widened K chunks read but no op writes must hold finite values
+  if (e == cudaSuccess) e = cudaMemset(b->d_ws, 0, ws);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_counter), sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_err), sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_batch(b);
+    delete b;
+    return e == cudaErrorMemoryAllocation ? SHT_ERR_OOM : SHT_ERR_CUDA;
+  }
+  *out = b;
+  return SHT_OK;
+}
+
+sht_status sht_batch_destroy(sht_batch_t b) {
+  if (!b) return SHT_ERR_ARG;
+  cudaSetDevice(b->device);
+  free_batch(b);
+  delete b;
+  return SHT_OK;
+}
+
+sht_status alt_forward_batch(sht_batch_t b, const double* const* beta, double* const* g, void* stream) {
+  if (!b || !beta || !g) return SHT_ERR_ARG;
+  return launch_batch(b, true, beta, g, static_cast<cudaStream_t>(stream));
+}
+
+sht_status alt_inverse_batch(sht_batch_t b, const double* const* g, double* const* beta, void* stream) {
+  if (!b || !g || !beta) return SHT_ERR_ARG;
+  return launch_batch(b, false, g, beta, static_cast<cudaStream_t>(stream));
+}
+
+sht_status sht_forward_batch(sht_batch_t b, const double* const* beta, double* const* f, void* stream) {
+  if (!b || !beta || !f) return SHT_ERR_ARG;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the ALT values of every plan's fields pass through that plan's workspace
+  double* gws[kTcMaxPlans] = {};
+  for (int q = 0; q < b->nplans; ++q) gws[q] = b->plans[q]->d_gws;
+  sht_status s = launch_batch(b, true, beta, gws, st);
+  for (int q = 0; q < b->nplans && s == SHT_OK; ++q)
+    if (b->F[q] > 0) {
+      if (!f[q] || (reinterpret_cast<uintptr_t>(f[q]) & 15u)) return SHT_ERR_ARG;
+      s = launch_phi(b->plans[q], gws[q], f[q], b->F[q], false, st);
+    }
+  return s;
+}
+
+sht_status sht_inverse_batch(sht_batch_t b, const double* const* f, double* const* beta, void* stream) {
+  if (!b || !f || !beta) return SHT_ERR_ARG;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double* gws[kTcMaxPlans] = {};
+  for (int q = 0; q < b->nplans; ++q) {
+    gws[q] = b->plans[q]->d_gws;
+    if (b->F[q] > 0) {
+      if (!f[q] || (reinterpret_cast<uintptr_t>(f[q]) & 15u)) return SHT_ERR_ARG;
+      const sht_status s = launch_phi(b->plans[q], f[q], b->plans[q]->d_gws, b->F[q], true, st);
+      if (s != SHT_OK) return s;
+    }
+  }
+  return launch_batch(b, false, gws, beta, st);
+}
+
+sht_status sht_batch_sync(sht_batch_t b, void* stream) {
+  if (!b) return SHT_ERR_ARG;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return SHT_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SHT_ERR_CUDA;
+  if (h) {
+    cudaMemset(b->d_err, 0, sizeof(int));
+    return SHT_ERR_TIMEOUT;
+  }
+  return SHT_OK;
 }
 
 }  // extern "C"

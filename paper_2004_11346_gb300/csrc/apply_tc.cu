@@ -414,12 +414,21 @@ __device__ __forceinline__ OpShape op_shape(const TcOp& op, bool fwd) {
 }
 
 struct Item {
-  int grp, am;
+  int plan, grp, am;
 };
-__device__ __forceinline__ Item item_of(const TcPlan& p, int it, int G, int single, int msingle) {
+__device__ __forceinline__ Item item_of(const TcLaunch& L, int it) {
   Item r;
+  if (L.items) {
+    const int4 v = L.items[it];
+    r.plan = v.x;
+    r.am = v.y;
+    r.grp = v.z;
+    return r;
+  }
+  const int G = (L.F[0] + kTcFields - 1) / kTcFields;
+  r.plan = 0;
   r.grp = it % G;
-  r.am = single ? (msingle < 0 ? -msingle : msingle) : p.order[it / G];
+  r.am = L.single ? (L.msingle < 0 ? -L.msingle : L.msingle) : L.plan[0].order[it / G];
   return r;
 }
 
@@ -427,9 +436,7 @@ __device__ __forceinline__ Item item_of(const TcPlan& p, int it, int G, int sing
 // descending phases for the transposed (inverse) apply.
 __device__ __forceinline__ int op_at(const Unit& u, int k, bool fwd) { return fwd ? u.op_begin + k : u.op_end - 1 - k; }
 
-__global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const double* __restrict__ in,
-                                                               double* __restrict__ out, int F, int single,
-                                                               int msingle, int fwd) {
+__global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_constant__ TcLaunch L, int fwd) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -468,11 +475,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = ctl->taddr;
 
-  const int N = p.N;
-  const int G = (F + kTcFields - 1) / kTcFields;
-  const int nitems = single ? G : p.nunits * G;
-  const size_t slot_bytes = tc_slot_bytes(p.max_rows);
-  unsigned char* slots = p.ws + (size_t)blockIdx.x * 2 * slot_bytes;  // two vector spaces, alternating by item
+  const int nitems = L.nitems;
+  const size_t slot_bytes = tc_slot_bytes(L.max_rows);
+  unsigned char* slots = L.ws + (size_t)blockIdx.x * 2 * slot_bytes;  // two vector spaces, alternating by item
   const uint32_t stage0 = s32(base);
 
   if (warp == 0) {
@@ -491,7 +496,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       it = __shfl_sync(0xffffffffu, it, 0);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok || it < 0) break;
-      const Item itm = item_of(p, it, G, single, msingle);
+      const Item itm = item_of(L, it);
+      const TcPlan& p = L.plan[itm.plan];
       const Unit u = p.units[itm.am];
       const unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
       const int nops = u.op_end - u.op_begin;
@@ -556,7 +562,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       for (int iseq = 0; ok; ++iseq) {
         const int it = next_item(ctl, iseq, ok);
         if (!ok || it < 0) break;
-        const Item itm = item_of(p, it, G, single, msingle);
+        const Item itm = item_of(L, it);
+        const TcPlan& p = L.plan[itm.plan];
         const Unit u = p.units[itm.am];
         const int nops = u.op_end - u.op_begin;
         TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
@@ -627,12 +634,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       const int it = next_item(ctl, iseq, ok);
       ok = epi_and(ok);
       if (!ok || it < 0) break;
-      const Item itm = item_of(p, it, G, single, msingle);
+      const Item itm = item_of(L, it);
+      const TcPlan& p = L.plan[itm.plan];
       const Unit u = p.units[itm.am];
       unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
       const int nops = u.op_end - u.op_begin;
       // accumulated rows (Y forward, X inverse) live in the item's accumulation region
-      float* acc_item = p.acc + ((size_t)itm.grp * p.nunits + itm.am) * (size_t)kTcAccRows(N) * kTcR;
+      float* acc_item = p.acc + ((size_t)itm.grp * p.nunits + itm.am) * (size_t)kTcAccRows(p.N) * kTcR;
       const int acc0 = fwd ? u.ye : 0;
       TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
       for (int q = 0; q < nops && ok; ++q) {
@@ -739,7 +747,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       ok = io_and(counter_wait(ctl, &ctl->done_tiles, t_m2));
       if (!ok) break;
       if (e == 0) {
-        const unsigned int w = atomicAdd(p.counter, 1u);
+        const unsigned int w = atomicAdd(L.counter, 1u);
         ctl->ring[iseq & 3] = w < (unsigned int)nitems ? (int)w : -1;
       }
       io_bar();
@@ -749,8 +757,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
         if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
         break;
       }
-      const Item itm = item_of(p, it, G, single, msingle);
-      const int am = itm.am, grp = itm.grp;
+      const Item itm = item_of(L, it);
+      const TcPlan& p = L.plan[itm.plan];
+      const int am = itm.am, grp = itm.grp, N = p.N, F = L.F[itm.plan];
+      const double* in = L.in[itm.plan];
+      const int single = L.single, msingle = L.msingle;
       const Unit u = p.units[am];
       unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
       const int nx = u.nce + u.nco;
@@ -848,7 +859,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(TcPlan p, const d
       t_m1 = t_cur;
     }
   }
-  if (*((volatile int*)&ctl->abort) && tid == 0) atomicExch(p.err, 1);
+  if (*((volatile int*)&ctl->abort) && tid == 0) atomicExch(L.err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == kMmaWarp)
@@ -935,26 +946,68 @@ size_t tc_smem_bytes() { return kSmemTotal; }
 
 int tc_ctas_per_sm() { return 1; }  // the kernel holds all 512 tensor-memory columns
 
+static int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+static cudaError_t launch_out(const TcPlan& p, bool fwd, double* out, int F, int single, int m, int sms, cudaStream_t st) {
+  const int G = (F + kTcFields - 1) / kTcFields;
+  const long items = (long)(single ? 1 : p.nunits) * G;
+  const long chunks = items * (fwd ? (p.N + 31) / 32 : (2 * p.N + 31) / 32);
+  const int out_grid = (int)std::max(1L, std::min(chunks, (long)sms * 6));
+  tc_out_kernel<<<out_grid, kOutThreads, 0, st>>>(p, out, F, single, m, fwd ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, int F, int single, int m, int grid,
                       cudaStream_t st, cudaEvent_t* ev) {
   const int G = (F + kTcFields - 1) / kTcFields;
   if (G > p.gmax) return cudaErrorInvalidValue;
+  TcLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.plan[0] = p;
+  L.in[0] = in;
+  L.out[0] = out;
+  L.F[0] = F;
+  L.nplans = 1;
+  L.items = nullptr;
+  L.nitems = single ? G : p.nunits * G;
+  L.single = single;
+  L.msingle = m;
+  L.ws = p.ws;
+  L.max_rows = p.max_rows;
+  L.counter = p.counter;
+  L.err = p.err;
   // (the kernel zeroes each item's accumulation rows itself when it gathers the item)
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-  alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(p, in, out, F, single, m, fwd ? 1 : 0);
+  alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(L, fwd ? 1 : 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-  const long items = (long)(single ? 1 : p.nunits) * G;
-  const long chunks = items * (fwd ? (p.N + 31) / 32 : (2 * p.N + 31) / 32);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int out_grid = (int)std::max(1L, std::min(chunks, (long)sms * 6));
-  tc_out_kernel<<<out_grid, kOutThreads, 0, st>>>(p, out, F, single, m, fwd ? 1 : 0);
+  e = launch_out(p, fwd, out, F, single, m, sm_count(), st);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
+  return e;
+}
+
+cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t st, cudaEvent_t* ev) {
+  if (L.nplans < 1 || L.nplans > kTcMaxPlans || !L.items) return cudaErrorInvalidValue;
+  for (int q = 0; q < L.nplans; ++q)
+    if ((L.F[q] + kTcFields - 1) / kTcFields > L.plan[q].gmax) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+  alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(L, fwd ? 1 : 0);
   e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+  const int sms = sm_count();
+  for (int q = 0; q < L.nplans && e == cudaSuccess; ++q)
+    if (L.F[q] > 0) e = launch_out(L.plan[q], fwd, L.out[q], L.F[q], 0, 0, sms, st);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
   return e;
 }

@@ -89,6 +89,28 @@ struct TcPlan {
 // 2N - |m| <= 2N inputs of the transposed apply.
 __host__ __device__ inline int kTcAccRows(int N) { return 2 * N; }
 
+// One launch of the tensor-core kernel: up to kTcMaxPlans plans (orders N of
+// their own), each with its own batch of fields.  The work items are
+// (plan, order |m|, field group); they share one work counter, the per-CTA
+// scratch slots (sized for the largest plan) and the error flag.
+constexpr int kTcMaxPlans = 8;
+struct TcLaunch {
+  TcPlan plan[kTcMaxPlans];
+  const double* in[kTcMaxPlans];  // per plan: its F fields of beta (forward) or g (inverse)
+  double* out[kTcMaxPlans];       // per plan: its F fields of g (forward) or beta (inverse)
+  int F[kTcMaxPlans];
+  int nplans;
+  // Work items in processing order as (plan, |m|, field group, 0); null for
+  // one plan, whose items are then its orders in cost order x its field groups
+  const int4* items;
+  int nitems;
+  int single, msingle;            // one order msingle of plan 0 (alt_*_m)
+  unsigned char* ws;              // per-CTA scratch: two slots of tc_slot_bytes(max_rows)
+  int max_rows;
+  unsigned int* counter;          // zero before the launch
+  int* err;
+};
+
 // Elements of the split-BF16 image of a block with NN rows and K side kg
 // (3 pieces, padded).
 size_t tc_image_elems(int NN, const TcKGeom& kg);
@@ -106,6 +128,11 @@ void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops,
 // it and the output kernel, and after the output kernel.
 cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, int F, int single, int m, int grid,
                       cudaStream_t st, cudaEvent_t* ev = nullptr);
+
+// The same for a batch of plans in one launch of the tensor-core kernel (the
+// launch's items, scratch and counter set up by the caller), followed by one
+// output kernel per plan.  L.counter must be zero on the stream.
+cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t st, cudaEvent_t* ev = nullptr);
 
 size_t tc_smem_bytes();
 int tc_ctas_per_sm();

@@ -70,3 +70,23 @@ def workload_coefficients(name: str, F: int | None = None, field_offset: int = 0
     w = WORKLOADS[name]
     return coefficients(w["N"], w["F"] if F is None else F, w["seed"], decay=w["decay"],
                         real_m0=w["real_m0"], field_offset=field_offset)
+
+
+# Uneven batch: fields of mixed orders N, the sizes and then the coefficients
+# drawn from one generator (default_rng(seed)): size index per field uniform
+# over `sizes`, then for each size in increasing order its fields' Re and Im
+# i.i.d. N(0,1).
+UNEVEN_SIZES = (128, 256, 512, 1024, 2048)
+
+
+def uneven_batch(F: int = 256, seed: int = 1, sizes=UNEVEN_SIZES):
+    """(size of each field, {N: (count_N, 4N^2, 2) float64 coefficients})."""
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, len(sizes), F)
+    per_field = np.asarray(sizes, dtype=np.int64)[idx]
+    coeffs = {}
+    for N in sorted(sizes):
+        count = int((per_field == N).sum())
+        if count:
+            coeffs[N] = rng.standard_normal((count, 4 * N * N, 2))
+    return per_field, coeffs

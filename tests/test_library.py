@@ -64,6 +64,23 @@ def test_host_only_plan_refuses_device_calls():
     assert e.value.status == 7
 
 
+def test_batch_argument_errors_need_no_device():
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    assert lib.sht_batch_create(0, None, None, ctypes.byref(h)) == _lib.SHT_ERR_ARG
+    p = sht.Plan(8, 1e-7, flags=HOST, precision=_lib.SHT_MIXED)
+    with pytest.raises(_lib.ShtError) as e:  # more plans than one launch takes
+        _lib.sht_batch_create([p.handle] * 9, [1] * 9)
+    assert e.value.status == _lib.SHT_ERR_ARG
+    with pytest.raises(_lib.ShtError) as e:
+        _lib.sht_batch_create([p.handle], [-1])
+    assert e.value.status == _lib.SHT_ERR_ARG
+    with pytest.raises(_lib.ShtError) as e:  # host-only plans have no device program
+        _lib.sht_batch_create([p.handle], [1])
+    assert e.value.status == _lib.SHT_ERR_UNSUPPORTED
+    assert lib.alt_forward_batch(None, None, None, None) == _lib.SHT_ERR_ARG
+
+
 def test_plan_nodes_match_oracle():
     for N in [1, 8, 300]:
         p = sht.Plan(N, 1e-12, flags=HOST)
