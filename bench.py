@@ -42,9 +42,16 @@ EXTRA_WORKLOADS = {
 FP64_PEAK_GFLOPS = 1250.0  # GB300 nominal FP64 (vector) rate
 
 
-def workload(name):
+def workload(name, n0=None, n_leaf=None):
     w = dict(inputs.WORKLOADS.get(name) or EXTRA_WORKLOADS[name])
     w["name"] = name
+    plan = dict(w.get("plan", {}))
+    if n0:
+        plan["n0"] = n0
+    if n_leaf:
+        plan["n_leaf"] = n_leaf
+    if plan:
+        w["plan"] = plan
     return w
 
 
@@ -192,7 +199,7 @@ def config_of(w, world):
     return {"workload": w["name"], "N": w["N"], "fields_per_rank": w["F"], "global_batch": w["F"] * world,
             "eps": w["eps"], "precision": w["precision"], "orders": 4 * w["N"] - 1,
             "step": "forward ALT + inverse ALT", "parallelism": f"replicas{world}",
-            "l2": "inputs and factor store larger than L2"}
+            "l2": "inputs and factor store larger than L2", "plan": w.get("plan", "library defaults")}
 
 
 # ---------------------------------------------------------------- our arm
@@ -200,9 +207,10 @@ FP32_PEAK_GFLOPS = 128 * 2 * 152 * 2.07  # FP32 lanes x 2 x SMs x max SM clock (
 
 
 def plan_for(sht, w, **kw):
+    """The workload's plan; its partition/leaf sizes where the workload fixes them."""
     from paper_2004_11346_gb300 import _lib
     prec = {"fp64": _lib.SHT_FP64, "mixed": _lib.SHT_MIXED, "fp32": _lib.SHT_FP32}[w["precision"]]
-    return sht.Plan(w["N"], w["eps"], precision=prec, **kw)
+    return sht.Plan(w["N"], w["eps"], precision=prec, **{**w.get("plan", {}), **kw})
 
 
 def time_steps(torch, plan, beta, g, back, K, W, stream):
@@ -304,7 +312,7 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = workload(args.workload)
+    w = workload(args.workload, args.n0, args.n_leaf)
     N, F = w["N"], w["F"]
     t0 = time.perf_counter()
     # workspace for the whole batch; CUDA events around every apply kernel
@@ -679,6 +687,8 @@ def main():
     ap.add_argument("--ref-stride", type=int, default=4, help="oracle samples every n-th order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 IDBF and dense comparators")
+    ap.add_argument("--n0", type=int, default=None, help="override the workload's partition stop size n0")
+    ap.add_argument("--n-leaf", type=int, default=None, help="override the workload's IDBF leaf size")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -1,0 +1,154 @@
+"""Autotuning of the plan parameters for the tensor-core apply.
+
+The factorisation has two free size parameters: the partition stops splitting
+turning-point blocks below n0 rows or columns (Sec. 3.2), and the IDBF leaves
+hold n_leaf rows (Sec. 2.2, the depth L follows from it).  They trade stored
+factor entries against the shapes of the block products.  For the split-BF16
+tensor-core apply the time follows the pipeline stages, one per 128-row tile
+and 32-wide K chunk of every product, and the bytes those stages move. Entries
+alone are a poor guide: smaller leaves store fewer entries in more, skinnier
+products.
+
+autotune() ranks candidate (n0, n_leaf) pairs by that work model on host-only
+plans (no GPU needed), then builds the best few on the device, times a forward
+and an inverse apply of the requested batch with CUDA events, and returns the
+fastest.  The model's counts mirror how the kernel cuts the work: K sides
+widened to whole 8-row groups of the vector space, chunks of 4 groups (the
+last rounded to an even number), N tiles of 128 rows padded to 16.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib
+
+TILE_N = 128       # rows of one tensor-core tile
+GROUP_ROWS = 8     # rows of one activation group
+GROUP_BYTES = 6144  # one group: 8 rows x 3 BF16 pieces x 128 right-hand sides
+CHUNK_GROUPS = 4   # groups of one K chunk (32 rows)
+
+
+def _kside(off0, len0, off1, len1):
+    """Groups and padded K columns of one product's K side (two row segments)."""
+    ng0 = (off0 + len0 + GROUP_ROWS - 1) // GROUP_ROWS - off0 // GROUP_ROWS if len0 > 0 else 0
+    ng1 = (off1 + len1 + GROUP_ROWS - 1) // GROUP_ROWS - off1 // GROUP_ROWS if len1 > 0 else 0
+    ngt = ng0 + ng1
+    nk = (ngt + CHUNK_GROUPS - 1) // CHUNK_GROUPS
+    kp = 32 * (nk - 1) + 16 * ((ngt - CHUNK_GROUPS * (nk - 1) + 1) // 2) if nk > 0 else 0
+    return ngt, nk, kp
+
+
+def work_model(ops) -> dict:
+    """Stages, tiles, operand-image and activation bytes of one forward apply
+    of one 32-field group, from a plan's op records (Plan.program()["ops"])."""
+    mo = ops["mo"].astype(np.int64)
+    stages = tiles = img = act = 0
+    for k in range(len(ops)):
+        if ops["ni"][k] <= 0:
+            continue
+        ngt, nk, kp = _kside(*(int(v) for v in (ops["in_off"][k][0], ops["in_len"][k][0],
+                                                ops["in_off"][k][1], ops["in_len"][k][1])))
+        nn = int(mo[k])
+        nt = (nn + TILE_N - 1) // TILE_N
+        np_tot = TILE_N * (nt - 1) + ((nn - TILE_N * (nt - 1) + 15) & ~15)
+        stages += nt * nk
+        tiles += nt
+        img += 2 * 3 * np_tot * kp
+        act += nt * ngt * GROUP_BYTES
+    return {"stages": int(stages), "tiles": int(tiles), "image_bytes": int(img), "activation_bytes": int(act)}
+
+
+def model_cost(w: dict, stage_us: float = 1.2, sms: int = 152, gbps: float = 4000.0) -> float:
+    """Predicted microseconds of one forward launch per field group: the larger
+    of the stage pipeline (stage_us per stage per SM, the measured rate of the
+    kernel) and the bytes at gbps."""
+    return max(w["stages"] * stage_us / sms, (w["image_bytes"] + w["activation_bytes"]) / (gbps * 1e3))
+
+
+def candidates(N: int, eps: float):
+    """(n0, n_leaf) pairs around the defaults of sht_opts_default: n0 halved
+    and doubled, n_leaf from half to four times the default (larger leaves make
+    fewer, fuller tensor-core products)."""
+    d = _lib.sht_opts_default(N, eps)
+    out = []
+    for n0 in (d.n0 // 2, d.n0, d.n0 * 2):
+        for nl in (d.n_leaf // 2, d.n_leaf, d.n_leaf * 2, d.n_leaf * 4):
+            if n0 >= 8 and 4 <= nl <= n0 and (n0, nl) not in out:
+                out.append((n0, nl))
+    return out
+
+
+def rank(N: int, eps: float, cands=None, **plan_kw):
+    """Host-only plans for every candidate, ranked by model_cost (best first)."""
+    from . import Plan
+    rows = []
+    for n0, nl in cands or candidates(N, eps):
+        p = Plan(N, eps, flags=_lib.SHT_FLAG_HOST_ONLY, precision=_lib.SHT_MIXED, n0=n0, n_leaf=nl, **plan_kw)
+        w = work_model(p.program(("ops",))["ops"])
+        st = p.stats()
+        rows.append({"n0": n0, "n_leaf": nl, "entries": int(st["entries_total"]), **w, "model_us": model_cost(w)})
+        p.close()
+    rows.sort(key=lambda r: r["model_us"])
+    return rows
+
+
+def autotune(N: int, eps: float, fields: int, top: int = 3, steps: int = 3, cands=None, seed: int = 0):
+    """Rank the candidates by the work model, time the best `top` of them on
+    the current CUDA device (forward + inverse ALT of `fields` random fields,
+    CUDA events, after a warm-up) and return (best Plan, table of all rows).
+    The returned plan is built on the device with the winning parameters."""
+    import torch
+    from . import Plan
+    rows = rank(N, eps, cands, max_fields=fields)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    beta = torch.randn((fields, 4 * N * N, 2), dtype=torch.float64, device="cuda", generator=g)
+    gv = torch.empty((fields, 4 * N - 1, 2 * N, 2), dtype=torch.float64, device="cuda")
+    back = torch.empty_like(beta)
+    best, best_ms = None, float("inf")
+    for r in rows[:top]:
+        p = Plan(N, eps, precision=_lib.SHT_MIXED, n0=r["n0"], n_leaf=r["n_leaf"], max_fields=fields)
+        p.forward(beta, out=gv)
+        p.inverse(gv, out=back)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            p.forward(beta, out=gv)
+            p.inverse(gv, out=back)
+        e1.record()
+        torch.cuda.synchronize()
+        p.sync()
+        r["measured_ms"] = e0.elapsed_time(e1) / steps
+        if r["measured_ms"] < best_ms:
+            if best is not None:
+                best.close()
+            best, best_ms = p, r["measured_ms"]
+        else:
+            p.close()
+    return best, rows
+
+
+def main(argv=None):
+    """python -m paper_2004_11346_gb300.autotune --N 1024 --eps 1e-7 --fields 64:
+    prints one JSON line per candidate (model counts, and the measured ms of the
+    timed ones) and a last line with the winner."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--N", type=int, required=True)
+    ap.add_argument("--eps", type=float, default=1e-7)
+    ap.add_argument("--fields", type=int, default=32)
+    ap.add_argument("--top", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--cands", default=None, help="n0:n_leaf,... to rank instead of the default grid")
+    a = ap.parse_args(argv)
+    cands = [tuple(int(v) for v in c.split(":")) for c in a.cands.split(",")] if a.cands else None
+    plan, rows = autotune(a.N, a.eps, a.fields, top=a.top, steps=a.steps, cands=cands)
+    for r in rows:
+        print(json.dumps(r), flush=True)
+    print(json.dumps({"best": {"n0": int(plan.opts.n0), "n_leaf": int(plan.opts.n_leaf)}, "N": a.N, "eps": a.eps,
+                      "fields": a.fields}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -59,8 +59,10 @@ WORKLOADS = {
     "fp64_N64": dict(N=64, F=1, seed=0, decay=0.0, real_m0=True, eps=1e-12, precision="fp64"),
     # FP64 IDBF ALT at N=1024, one field, coefficients scaled by (k+1)^-1
     "fp64_N1024": dict(N=1024, F=1, seed=0, decay=1.0, real_m0=False, eps=1e-12, precision="fp64"),
-    # mixed-precision IDBF at N=1024, 64 fields, eps=1e-7
-    "mixed_N1024_F64": dict(N=1024, F=64, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed"),
+    # mixed-precision IDBF at N=1024, 64 fields, eps=1e-7; partition stop size
+    # and leaf size picked by paper_2004_11346_gb300.autotune (measured on GB300)
+    "mixed_N1024_F64": dict(N=1024, F=64, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed",
+                            plan=dict(n0=256, n_leaf=256)),
     # N=4096, 16 fields, spectrum N(0,(k+1)^-2), eps=1e-10
     "N4096_F16": dict(N=4096, F=16, seed=0, decay=1.0, real_m0=False, eps=1e-10, precision="fp64"),
 }

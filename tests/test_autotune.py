@@ -1,0 +1,55 @@
+"""The autotuner's host side: candidate parameters and the work model.
+
+The model counts what the tensor-core kernel streams per 32-field group:
+pipeline stages (128-row tiles x 32-wide K chunks of row groups), operand-image
+bytes and activation bytes.  Checked here against invariants that hold for any
+plan; the GPU test times the ranked candidates.
+"""
+import numpy as np
+
+import paper_2004_11346_gb300 as sht
+from paper_2004_11346_gb300 import _lib, autotune
+
+HOST = _lib.SHT_FLAG_HOST_ONLY
+
+
+def test_candidates_include_defaults_and_are_valid():
+    for N in (32, 256, 1024, 2048):
+        d = _lib.sht_opts_default(N, 1e-7)
+        c = autotune.candidates(N, 1e-7)
+        assert (d.n0, d.n_leaf) in c
+        assert len(set(c)) == len(c)
+        assert all(n0 >= 8 and 4 <= nl <= n0 for n0, nl in c)
+
+
+def test_work_model_invariants():
+    p = sht.Plan(48, 1e-7, flags=HOST, precision=_lib.SHT_MIXED, n0=16, n_leaf=8)
+    ops = p.program(("ops",))["ops"]
+    w = autotune.work_model(ops)
+    live = ops[ops["ni"] > 0]
+    # every product is at least one tile and one stage
+    assert w["tiles"] >= len(live) and w["stages"] >= w["tiles"]
+    # three 2-byte pieces per stored entry, before padding
+    assert w["image_bytes"] >= 6 * int((live["mo"].astype(np.int64) * live["ni"]).sum())
+    # every stage moves at least one row group of activations
+    assert w["activation_bytes"] >= autotune.GROUP_BYTES * w["tiles"]
+
+
+def test_dense_plan_counts():
+    # one dense product per (order, parity) at N=8: every product is a single
+    # tile, so the stage count is the number of K chunks of each product
+    N = 8
+    p = sht.Plan(N, 1e-7, flags=HOST | _lib.SHT_FLAG_DENSE, precision=_lib.SHT_MIXED)
+    ops = p.program(("ops",))["ops"]
+    w = autotune.work_model(ops)
+    assert np.all(ops["mo"] <= 128)
+    assert w["tiles"] == int((ops["ni"] > 0).sum())
+    assert w["stages"] >= w["tiles"]
+
+
+def test_rank_is_sorted_by_model():
+    rows = autotune.rank(64, 1e-7, [(16, 8), (32, 8), (32, 16)])
+    assert [(r["n0"], r["n_leaf"]) for r in rows] != []
+    costs = [r["model_us"] for r in rows]
+    assert costs == sorted(costs)
+    assert all(r["entries"] > 0 and r["stages"] > 0 for r in rows)
