@@ -38,7 +38,12 @@ EXTRA_WORKLOADS = {
     "fp64_N512": dict(N=512, F=1, seed=0, decay=1.0, real_m0=False, eps=1e-12, precision="fp64"),
     "mixed_N512_F16": dict(N=512, F=16, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed"),
     "mixed_N512_F32": dict(N=512, F=32, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed"),
+    # the same with the headline plan's shape scaled to N=512 (n0 = N/4, leaves 4x the default)
+    "mixed_N512_F32_tuned": dict(N=512, F=32, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed",
+                                 plan=dict(n0=128, n_leaf=128)),
 }
+# the ncu capture whose traffic a workload's roofline scales (same kernel, same plan shape, smaller case)
+TRAFFIC_REF = {"mixed_N1024_F64": "mixed_N512_F32_tuned"}
 FP64_PEAK_GFLOPS = 1250.0  # GB300 nominal FP64 (vector) rate
 
 
@@ -573,6 +578,10 @@ def traffic_for(kernel, workload_name, algo_bytes=None):
         return None, None
     if workload_name in table:
         return table[workload_name], f"ncu capture of {workload_name}"
+    ref_name = TRAFFIC_REF.get(workload_name)
+    if algo_bytes and ref_name in table and table.get("_algorithmic_" + ref_name):
+        return (algo_bytes * table[ref_name] / table["_algorithmic_" + ref_name],
+                f"ncu capture of {ref_name}, scaled by algorithmic bytes")
     if algo_bytes:
         for w, v in table.items():
             ref = table.get("_algorithmic_" + w)
