@@ -14,7 +14,7 @@
 //               with zero columns where the K side was widened to whole groups;
 //   D         = 128 x N FP32 accumulator in tensor memory.
 // The CTA is warp-specialised and persistent (one per SM): one producer
-// thread streams (op, tile, 32-wide K chunk) operand stages into a 3-deep
+// thread streams (op, tile, 32-wide K chunk) operand stages into a 4-deep
 // shared memory ring with bulk copies; an MMA thread issues the tensor-core
 // products into two double-buffered TMEM accumulator pairs; four epilogue
 // warps drain the accumulators and split the results into BF16 pieces for the

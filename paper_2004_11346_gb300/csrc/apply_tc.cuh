@@ -15,7 +15,7 @@ constexpr int kTcFields = 32;            // fields per work item
 constexpr int kTcR = 4 * kTcFields;      // 128 right-hand sides = MMA M
 constexpr int kTcNT = 128;               // N tile (rows of one block product)
 constexpr int kTcKC = 32;                // K chunk per pipeline stage
-constexpr int kTcThreads = 512;          // 3 producer, 1 MMA, 4 epilogue and 8 I/O warps
+constexpr int kTcThreads = 512;          // producer, 2 spare, MMA, 4 epilogue and 8 I/O warps
 constexpr int kTcRowBytes = 3 * kTcR * 2;  // one scratch row: 3 BF16 pieces x 128 values
 // The scratch stores rows in groups of 8 in the tensor cores' MN-major core
 // matrix layout, so that a run of whole groups is the A operand of a K chunk
