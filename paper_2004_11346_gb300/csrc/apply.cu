@@ -686,7 +686,7 @@ sht_status sht_plan_export(sht_plan_t p, int what, void* dst, size_t* bytes) {
 namespace {
 
 constexpr char kPlanMagic[8] = {'S', 'H', 'T', 'P', 'L', 'A', 'N', '\0'};
-constexpr uint32_t kPlanVersion = 1;
+constexpr uint32_t kPlanVersion = 2;  // 2: intermediate segments start on 8-row boundaries
 
 struct PlanWriter {
   std::FILE* f;

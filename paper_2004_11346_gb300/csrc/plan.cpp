@@ -855,6 +855,14 @@ bool validate_program(const HostProgram& P, std::string& err) {
         ok = ok && op.out_off[s] >= 0 && op.out_off[s] + op.out_len[s] <= u.nrows;
       }
       if (!ok) return fail("apply program failed validation", am);
+      // intermediate segments (past Y_o) start on 8-row groups: the tensor-core
+      // apply copies whole groups and relies on the rows that pad a segment to
+      // its group end being written by no op
+      for (int s = 0; s < 2 && ok; ++s) {
+        if (op.in_len[s] > 0 && op.in_off[s] >= u.yo + N) ok = op.in_off[s] % 8 == 0;
+        if (ok && op.out_len[s] > 0 && op.out_off[s] >= u.yo + N) ok = op.out_off[s] % 8 == 0;
+      }
+      if (!ok) return fail("intermediate segment not on an 8-row boundary", am);
       // shared rows are exactly the accumulated ones: an op writes Y rows (the
       // N-node outputs of both parities) iff it accumulates forward, and reads
       // X rows (the coefficients) iff its transpose accumulates

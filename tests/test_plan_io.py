@@ -115,6 +115,43 @@ def test_consistent_checksum_but_invalid_program(saved, tmp_path):
     assert sht.Plan.load(str(good)).N == p.N
 
 
+def test_intermediate_segments_must_start_on_row_groups(tmp_path):
+    """Moving one intermediate output segment off its 8-row boundary makes a
+    file with a consistent checksum fail the program check; moving it by a
+    whole group (still inside the vector space) does not."""
+    p = sht.Plan(40, 1e-10, flags=HOST | _lib.SHT_FLAG_FORCE_FACTOR, n0=12, n_leaf=6)
+    path = str(tmp_path / "factored.plan")
+    p.save(path)
+    raw = bytes(open(path, "rb").read())
+    prog = p.program(("units", "ops"))
+    units, ops = prog["units"], prog["ops"]
+    at = raw.find(ops.tobytes())
+    assert at > HEADER
+    pick = None
+    for u in units:
+        for k in range(u["op_begin"], u["op_end"]):
+            o = ops[k]
+            if o["out_len"][0] > 0 and o["out_off"][0] >= u["yo"] + p.N and \
+                    o["out_off"][0] + o["out_len"][0] + 8 <= u["nrows"]:
+                pick = k
+                break
+        if pick is not None:
+            break
+    assert pick is not None
+
+    def forged(shift, name):
+        b = bytearray(raw)
+        field = at + 64 * pick + 40  # Op.out_off[0]
+        struct.pack_into("<i", b, field, int(ops[pick]["out_off"][0]) + shift)
+        body = bytes(b[:-8])
+        out = tmp_path / name
+        out.write_bytes(body + struct.pack("<Q", fnv1a(body)))
+        return out
+
+    expect_io(forged(1, "unaligned.plan"))
+    assert sht.Plan.load(str(forged(8, "shifted.plan"))).N == p.N
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec,F,tol", [(_lib.SHT_FP64, 2, 1e-13), (_lib.SHT_MIXED, 33, 1e-6)])
 def test_loaded_plan_on_gpu(tmp_path, prec, F, tol):
