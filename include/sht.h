@@ -254,6 +254,16 @@ sht_status alt_forward_m_noalloc(sht_plan_t plan, int m, const double* beta_m, d
  * reset != 0 starts a new sum.  SHT_ERR_UNSUPPORTED without the flag. */
 sht_status sht_plan_kernel_time(sht_plan_t plan, int reset, double* apply_ms, double* output_ms, int64_t* launches);
 
+/* Self-test of the failure detection (the paper has no counterpart).  Every
+ * wait inside the tensor-core kernel is bounded (about a second); when one
+ * runs out the kernel stops all its roles, releases its tensor memory, and
+ * flags the plan, so that the next sht_sync returns SHT_ERR_TIMEOUT and the
+ * plan stays usable.  This call launches that kernel with its I/O warps
+ * publishing no work item, so that the other roles' first waits run out:
+ * after it, sht_sync must return SHT_ERR_TIMEOUT.  SHT_MIXED plans only
+ * (SHT_ERR_UNSUPPORTED otherwise).  Takes a second or more of GPU time. */
+sht_status sht_selftest_timeout(sht_plan_t plan, void* stream);
+
 /* Wait for the plan's work on `stream` and return any latched device error. */
 sht_status sht_sync(sht_plan_t plan, void* stream);
 

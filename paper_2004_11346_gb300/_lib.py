@@ -85,7 +85,7 @@ EXPORTED = [
     "sht_status_str", "alt_forward_m_noalloc", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
     "sht_inverse", "sht_plan_save", "sht_plan_load", "sht_plan_kernel_time", "sht_batch_create",
     "sht_batch_destroy", "alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch",
-    "sht_batch_sync",
+    "sht_batch_sync", "sht_selftest_timeout",
 ]
 
 
@@ -119,6 +119,7 @@ def load(build: bool = True):
     lib.sht_batch_create.argtypes = [i, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int), plan_p]
     lib.sht_batch_destroy.argtypes = [vp]
     lib.sht_batch_sync.argtypes = [vp, vp]
+    lib.sht_selftest_timeout.argtypes = [vp, vp]
     for name in ("alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch"):
         getattr(lib, name).argtypes = [vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), vp]
     lib.sht_status_str.argtypes = [i]
@@ -270,3 +271,7 @@ def sht_inverse_batch(batch: int, f_ptrs, beta_ptrs, stream: int = 0):
 
 def sht_batch_sync(batch: int, stream: int = 0):
     check(load().sht_batch_sync(batch, stream), "sht_batch_sync")
+
+
+def sht_selftest_timeout(plan: int, stream: int = 0):
+    check(load().sht_selftest_timeout(plan, stream), "sht_selftest_timeout")

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -317,10 +318,32 @@ struct sht_plan_s {
 
 namespace {
 
+// Host-side fault injection for tests: with SHT_FAIL_ALLOC=k in the
+// environment, the k-th device allocation of a plan or batch creation fails as
+// if the device were out of memory, so that the error path (everything
+// allocated so far released, SHT_ERR_OOM) can be exercised without a real
+// shortage.  The count restarts with every creation; not for concurrent use.
+int g_alloc_fail_at = 0;
+int g_alloc_seen = 0;
+
+void alloc_hook_reset() {
+  const char* v = std::getenv("SHT_FAIL_ALLOC");
+  g_alloc_fail_at = v ? std::atoi(v) : 0;
+  g_alloc_seen = 0;
+}
+
+cudaError_t plan_malloc(void** ptr, size_t bytes) {
+  if (g_alloc_fail_at > 0 && ++g_alloc_seen == g_alloc_fail_at) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(ptr, bytes);
+}
+
 template <class T>
 cudaError_t upload(T** dst, const std::vector<T>& v) {
   size_t bytes = std::max<size_t>(sizeof(T), v.size() * sizeof(T));
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), bytes);
+  cudaError_t e = plan_malloc(reinterpret_cast<void**>(dst), bytes);
   if (e != cudaSuccess) return e;
   if (!v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
   return e;
@@ -507,6 +530,7 @@ namespace {
 // images of the precision's kernel, size the workspaces and the phi tables.
 // On failure everything allocated here is released again.
 sht_status attach_device(sht_plan_s* p) {
+  alloc_hook_reset();
   const int N = p->prog.N;
   const sht_opts& o = p->prog.opts;
   auto t0 = std::chrono::steady_clock::now();
@@ -527,8 +551,8 @@ sht_status attach_device(sht_plan_s* p) {
   if (e == cudaSuccess && o.precision == SHT_FP64) e = upload(&p->d_fac, P.factors);
   if (e == cudaSuccess) e = upload(&p->d_w, P.w);
   size_t ws = o.precision == SHT_FP64 ? (size_t)p->nslots * P.max_rows * kRT * sizeof(double) : 0;
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_ws), std::max<size_t>(ws, 8));
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_counter), sizeof(unsigned int));
+  if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_ws), std::max<size_t>(ws, 8));
+  if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_counter), sizeof(unsigned int));
   size_t ws32 = 0;
   if (e == cudaSuccess && o.precision == SHT_MIXED) {
     std::vector<uint16_t> img;
@@ -540,14 +564,14 @@ sht_status attach_device(sht_plan_s* p) {
     if (e == cudaSuccess) e = upload(&p->d_tctiles, tiles);
     p->nslots_tc = std::max(1, sms * tc_ctas_per_sm());
     ws32 = (size_t)p->nslots_tc * 2 * tc_slot_bytes(P.max_rows);  // two vector spaces per CTA
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_wstc), std::max<size_t>(ws32, 8));
+    if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_wstc), std::max<size_t>(ws32, 8));
     // rows that widened K chunks read but no op writes must hold finite values
     if (e == cudaSuccess) e = cudaMemset(p->d_wstc, 0, std::max<size_t>(ws32, 8));
     p->tc_gmax = (o.max_fields + kTcFields - 1) / kTcFields;
     const size_t acc = (size_t)p->tc_gmax * 2 * N * kTcAccRows(N) * kTcR * sizeof(float);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_acc), acc);
+    if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_acc), acc);
     ws32 += acc;
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
+    if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
     p->prog.info.factor_bytes = (int64_t)(img.size() * sizeof(uint16_t));
   }
@@ -556,7 +580,7 @@ sht_status attach_device(sht_plan_s* p) {
     e = upload(&p->d_fac32, f32);
     p->nslots32 = std::max(1, sms * f32_ctas_per_sm());
     ws32 = (size_t)p->nslots32 * P.max_rows * kF32RT * sizeof(float);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_ws32), std::max<size_t>(ws32, 8));
+    if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_ws32), std::max<size_t>(ws32, 8));
   }
   size_t gws = 0;
   if (e == cudaSuccess) {
@@ -570,7 +594,7 @@ sht_status attach_device(sht_plan_s* p) {
   }
   if (e == cudaSuccess) {
     gws = (size_t)o.max_fields * (4 * (size_t)N - 1) * 2 * N * 2 * sizeof(double);
-    e = cudaMalloc(reinterpret_cast<void**>(&p->d_gws), gws);
+    e = plan_malloc(reinterpret_cast<void**>(&p->d_gws), gws);
   }
   if (e == cudaSuccess && (o.flags & SHT_FLAG_TIMING)) {
     p->tev.assign(3 * kTimingSlots, nullptr);
@@ -1046,6 +1070,7 @@ sht_status sht_batch_create(int P, const sht_plan_t* plans, const int* fields, s
     if (plans[q]->device != dev) return SHT_ERR_ARG;
   sht_batch_s* b = new (std::nothrow) sht_batch_s();
   if (!b) return SHT_ERR_OOM;
+  alloc_hook_reset();
   b->device = dev;
   b->nplans = P;
   // the queue: every (plan, |m|, field group), in decreasing estimated cost
@@ -1072,14 +1097,14 @@ sht_status sht_batch_create(int P, const sht_plan_t* plans, const int* fields, s
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->grid = std::max(1, sms * tc_ctas_per_sm());
   const size_t ws = (size_t)b->grid * 2 * tc_slot_bytes(b->max_rows);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_items), std::max<size_t>(items.size(), 1) * sizeof(int4));
+  cudaError_t e = plan_malloc(reinterpret_cast<void**>(&b->d_items), std::max<size_t>(items.size(), 1) * sizeof(int4));
   if (e == cudaSuccess && !items.empty())
     e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_ws), ws);
+  if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&b->d_ws), ws);
   // rows that widened K chunks read but no op writes must hold finite values
   if (e == cudaSuccess) e = cudaMemset(b->d_ws, 0, ws);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_counter), sizeof(unsigned int));
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_err), sizeof(int));
+  if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&b->d_counter), sizeof(unsigned int));
+  if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&b->d_err), sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -1137,6 +1162,13 @@ sht_status sht_inverse_batch(sht_batch_t b, const double* const* f, double* cons
     }
   }
   return launch_batch(b, false, gws, beta, st);
+}
+
+sht_status sht_selftest_timeout(sht_plan_t p, void* stream) {
+  if (!p) return SHT_ERR_ARG;
+  if (p->host_only || p->prog.opts.precision != SHT_MIXED) return SHT_ERR_UNSUPPORTED;
+  const TcPlan t = tc_plan_of(p);
+  return launch_tc_stall(t, 1, static_cast<cudaStream_t>(stream)) == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
 }
 
 sht_status sht_batch_sync(sht_batch_t b, void* stream) {

@@ -742,7 +742,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
     float* T = iobuf;
     const int e = tid - 32 * kIoWarp0;
     int t_m2 = 0, t_m1 = 0;  // tiles of all items up to i-2, up to i-1
-    bool ok = true;
+    bool ok = L.stall == 0;
     for (int iseq = 0; ok; ++iseq) {
       ok = io_and(counter_wait(ctl, &ctl->done_tiles, t_m2));
       if (!ok) break;
@@ -992,6 +992,24 @@ cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, 
   e = launch_out(p, fwd, out, F, single, m, sm_count(), st);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
   return e;
+}
+
+cudaError_t launch_tc_stall(const TcPlan& p, int grid, cudaStream_t st) {
+  TcLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.plan[0] = p;
+  L.F[0] = 1;
+  L.nplans = 1;
+  L.nitems = 1;
+  L.ws = p.ws;
+  L.max_rows = p.max_rows;
+  L.counter = p.counter;
+  L.err = p.err;
+  L.stall = 1;
+  cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
+  if (e != cudaSuccess) return e;
+  alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(L, 1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t st, cudaEvent_t* ev) {

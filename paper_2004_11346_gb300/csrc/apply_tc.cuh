@@ -109,6 +109,10 @@ struct TcLaunch {
   int max_rows;
   unsigned int* counter;          // zero before the launch
   int* err;
+  // Self-test of the bounded waits: the I/O warps publish no item, so every
+  // other role's wait for its first item runs out and the launch reports a
+  // timeout through err.
+  int stall;
 };
 
 // Elements of the split-BF16 image of a block with NN rows and K side kg
@@ -133,6 +137,9 @@ cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, 
 // launch's items, scratch and counter set up by the caller), followed by one
 // output kernel per plan.  L.counter must be zero on the stream.
 cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t st, cudaEvent_t* ev = nullptr);
+
+// The bounded-wait self-test on plan p (see TcLaunch::stall).
+cudaError_t launch_tc_stall(const TcPlan& p, int grid, cudaStream_t st);
 
 size_t tc_smem_bytes();
 int tc_ctas_per_sm();

@@ -81,6 +81,13 @@ def test_batch_argument_errors_need_no_device():
     assert lib.alt_forward_batch(None, None, None, None) == _lib.SHT_ERR_ARG
 
 
+def test_selftest_argument_errors_need_no_device():
+    lib = _lib.load()
+    assert lib.sht_selftest_timeout(None, None) == _lib.SHT_ERR_ARG
+    p = sht.Plan(8, 1e-7, flags=HOST, precision=_lib.SHT_MIXED)
+    assert lib.sht_selftest_timeout(p.handle, None) == _lib.SHT_ERR_UNSUPPORTED
+
+
 def test_plan_nodes_match_oracle():
     for N in [1, 8, 300]:
         p = sht.Plan(N, 1e-12, flags=HOST)
