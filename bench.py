@@ -173,6 +173,10 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    if args.workload.startswith(UNEVEN_PREFIX):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-N workloads; "
+                          "an uneven batch is the sum of its sizes' single-N transforms"}), flush=True)
+        return
     w = workload(args.workload)
     N = w["N"]
     beta = inputs.workload_coefficients(w["name"], F=1)[0]

@@ -1,0 +1,59 @@
+"""Host-side logic of bench.py and of the seeded inputs (CPU only)."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+import bench
+from paper_2004_11346_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_workload_plan_overrides():
+    w = bench.workload("mixed_N1024_F64")
+    assert w["plan"] == {"n0": 256, "n_leaf": 256}  # the autotuner's pick for the headline
+    w = bench.workload("mixed_N1024_F64", n0=512)
+    assert w["plan"] == {"n0": 512, "n_leaf": 256}
+    assert "plan" not in bench.workload("fp64_N1024")
+    assert bench.config_of(bench.workload("fp64_N1024"), 1)["plan"] == "library defaults"
+
+
+def test_headline_traffic_scales_from_its_plan_shape():
+    t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["alt_tc_kernel"]
+    ref = bench.TRAFFIC_REF["mixed_N1024_F64"]
+    v, src = bench.traffic_for("alt_tc_kernel", "mixed_N1024_F64", 1000)
+    assert ref in src and abs(v - 1000 * t[ref] / t["_algorithmic_" + ref]) < 1e-6
+    v, src = bench.traffic_for("alt_tc_kernel", "mixed_N512_F32")
+    assert v == t["mixed_N512_F32"]
+
+
+def test_uneven_workload_names():
+    assert bench.uneven_sizes("uneven_N128-1024_F256") == ((128, 256, 512, 1024), 256)
+    assert bench.uneven_sizes("uneven_N64-64_F8") == ((64,), 8)
+
+
+def test_uneven_batch_is_seeded_and_consistent():
+    sizes = (16, 32, 64)
+    per_field, coeffs = inputs.uneven_batch(40, seed=1, sizes=sizes)
+    again, coeffs2 = inputs.uneven_batch(40, seed=1, sizes=sizes)
+    assert np.array_equal(per_field, again)
+    assert set(per_field.tolist()) <= set(sizes) and len(per_field) == 40
+    assert sum(c.shape[0] for c in coeffs.values()) == 40
+    for N, c in coeffs.items():
+        assert c.shape == ((per_field == N).sum(), 4 * N * N, 2)
+        assert np.array_equal(c, coeffs2[N])
+    # the sizes are the generator's first draw: uniform integers over the size list
+    idx = np.random.default_rng(1).integers(0, len(sizes), 40)
+    assert np.array_equal(per_field, np.asarray(sizes)[idx])
+
+
+def test_reference_arm_declines_uneven_batches():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "uneven_N16-32_F4", "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                         timeout=120)
+    assert out.returncode == 0
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "unavailable" in line
