@@ -198,7 +198,9 @@ sht_status sht_plan_load(const char* path, sht_plan_t* out);
  *    fields[q] (>= 0, <= the plan's max_fields) fields go with plans[q].
  *  - The batch owns its work-item table, scratch and counter; it uses each
  *    plan's accumulation rows and ALT-value workspace, so a plan must not run
- *    other calls while a batch that contains it is in flight.
+ *    other calls while a batch that contains it is in flight, and must outlive
+ *    the batch (destroy the batch first).
+ *  - A batch with no fields at all is valid; its calls do nothing.
  *  - SHT_ERR_UNSUPPORTED for host-only plans or other precisions; SHT_ERR_ARG
  *    for bad counts, repeated plans or plans of another device. */
 typedef struct sht_batch_s* sht_batch_t;
