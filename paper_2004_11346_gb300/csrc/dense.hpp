@@ -82,24 +82,30 @@ inline int pivoted_qr(Mat& A, double tol, int kmax, std::vector<int>& perm) {
   const int m = A.r, n = A.c;
   perm.resize(n);
   for (int j = 0; j < n; ++j) perm[j] = j;
-  std::vector<double> norm2(n), v(m);
+  // squared trailing column norms, downdated after each step (the reflected
+  // row k leaves each column); a column whose downdated value has lost most of
+  // its last exact value to cancellation is recomputed exactly (the usual
+  // safeguard of column-pivoted QR, threshold sqrt(machine epsilon))
+  std::vector<double> norm2(n), exact2(n), v(m);
+  for (int j = 0; j < n; ++j) {
+    const double* aj = A.col(j);
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s += aj[i] * aj[i];
+    norm2[j] = exact2[j] = s;
+  }
+  const double kRecompute = 1.4901161193847656e-08;  // 2^-26
   int kcap = std::min(std::min(m, n), kmax);
   int k = 0;
   for (; k < kcap; ++k) {
-    // exact trailing norms (robust against downdating cancellation)
-    int p = -1;
-    double best = -1.0;
-    for (int j = k; j < n; ++j) {
-      const double* aj = A.col(j);
-      double s = 0.0;
-      for (int i = k; i < m; ++i) s += aj[i] * aj[i];
-      norm2[j] = s;
-      if (s > best) { best = s; p = j; }
-    }
-    if (std::sqrt(best) <= tol) break;
+    int p = k;
+    for (int j = k + 1; j < n; ++j)
+      if (norm2[j] > norm2[p]) p = j;
+    if (std::sqrt(norm2[p]) <= tol) break;
     if (p != k) {
       std::swap_ranges(A.col(k), A.col(k) + m, A.col(p));
       std::swap(perm[k], perm[p]);
+      std::swap(norm2[k], norm2[p]);
+      std::swap(exact2[k], exact2[p]);
     }
     double* x = A.col(k) + k;
     double beta;
@@ -109,6 +115,18 @@ inline int pivoted_qr(Mat& A, double tol, int kmax, std::vector<int>& perm) {
     apply_reflector(A, k, v.data(), tau, k + 1, n);
     x[0] = beta;
     for (int i = 1; i < m - k; ++i) x[i] = 0.0;
+    for (int j = k + 1; j < n; ++j) {
+      const double a = A(k, j);
+      const double t = norm2[j] - a * a;
+      if (t <= kRecompute * exact2[j]) {
+        const double* aj = A.col(j);
+        double s = 0.0;
+        for (int i = k + 1; i < m; ++i) s += aj[i] * aj[i];
+        norm2[j] = exact2[j] = s;
+      } else {
+        norm2[j] = t;
+      }
+    }
   }
   return k;
 }

@@ -97,33 +97,62 @@ static void legendre_parity_matrices(int N, int am, const double* xp, Mat& E, Ma
   std::vector<double> sect(am + 1);
   for (int j = 1; j <= am; ++j) sect[j] = std::sqrt((2.0 * j + 1.0) / (2.0 * j));
   const double up = std::ldexp(1.0, 256), dn = std::ldexp(1.0, -256);
-  for (int i = 0; i < N; ++i) {
-    const double x = xp[i], u = std::sqrt((1.0 - x) * (1.0 + x));
-    double v = 1.0 / std::sqrt(2.0);
-    int e = 0;  // value = v * 2^e
-    for (int j = 1; j <= am; ++j) {
-      v *= sect[j] * u;
-      if (v < dn) { v *= up; e -= 256; }
+  // Nodes in blocks of kNB: the recurrence runs for the block's nodes side by
+  // side, so that each degree's values land in kNB consecutive rows of one
+  // column (the arithmetic per node is exactly the one-node recurrence).
+  constexpr int kNB = 8;
+  for (int i0 = 0; i0 < N; i0 += kNB) {
+    const int nb = std::min(kNB, N - i0);
+    double x[kNB], p0[kNB], p1[kNB];
+    int e[kNB];  // value = p * 2^e
+    bool scaled = false;
+    for (int t = 0; t < nb; ++t) {
+      x[t] = xp[i0 + t];
+      const double u = std::sqrt((1.0 - x[t]) * (1.0 + x[t]));
+      double v = 1.0 / std::sqrt(2.0);
+      int ee = 0;
+      for (int j = 1; j <= am; ++j) {
+        v *= sect[j] * u;
+        if (v < dn) { v *= up; ee -= 256; }
+      }
+      e[t] = ee;
+      scaled = scaled || ee != 0;
+      p0[t] = v;
+      p1[t] = std::sqrt(2.0 * am + 3.0) * x[t] * v;
     }
-    auto put = [&](int k, double val) {
-      int t = k - am;
-      double y = e == 0 ? val : std::ldexp(val, e);
-      if (t & 1) O(i, t >> 1) = y; else E(i, t >> 1) = y;
+    auto put = [&](int k, const double* val) {
+      const int q = k - am;
+      double* col = (q & 1) ? &O(i0, q >> 1) : &E(i0, q >> 1);
+      if (!scaled) {
+        for (int t = 0; t < nb; ++t) col[t] = val[t];
+      } else {
+        for (int t = 0; t < nb; ++t) col[t] = e[t] == 0 ? val[t] : std::ldexp(val[t], e[t]);
+      }
     };
-    double p0 = v, p1 = std::sqrt(2.0 * am + 3.0) * x * v;
     put(am, p0);
     if (am + 1 < K) put(am + 1, p1);
     for (int k = am + 2; k < K; ++k) {
-      double p2 = a[k] * x * p1 - b[k] * p0;
-      if (e < 0 && std::fabs(p2) > up) {
-        int s = std::min(256, -e);
-        p1 = std::ldexp(p1, -s);
-        p2 = std::ldexp(p2, -s);
-        e += s;
+      double p2[kNB];
+      const double ak = a[k], bk = b[k];
+      for (int t = 0; t < nb; ++t) p2[t] = ak * x[t] * p1[t] - bk * p0[t];
+      if (scaled) {
+        bool any = false;
+        for (int t = 0; t < nb; ++t) {
+          if (e[t] < 0 && std::fabs(p2[t]) > up) {
+            const int sh = std::min(256, -e[t]);
+            p1[t] = std::ldexp(p1[t], -sh);
+            p2[t] = std::ldexp(p2[t], -sh);
+            e[t] += sh;
+          }
+          any = any || e[t] != 0;
+        }
+        scaled = any;
       }
       put(k, p2);
-      p0 = p1;
-      p1 = p2;
+      for (int t = 0; t < nb; ++t) {
+        p0[t] = p1[t];
+        p1[t] = p2[t];
+      }
     }
   }
 }
