@@ -767,27 +767,33 @@ sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::strin
 #pragma omp parallel for schedule(dynamic, 1)
   for (int am = 0; am < K; ++am) build_unit(N, am, opts, xp, ub[am], units[am]);
 
-  // concatenate into the global program
+  // concatenate into the global program: offsets first, then every unit's
+  // factors and ops copied in parallel to their places
   sht_plan_info& I = P.info;
-  int64_t fac = 0, nops = 0;
+  std::vector<int64_t> fac_at(K + 1, 0), op_at(K + 1, 0);
   for (int am = 0; am < K; ++am) {
-    fac += (int64_t)ub[am].fac.size();
-    nops += (int64_t)ub[am].ops.size();
+    fac_at[am + 1] = fac_at[am] + (int64_t)ub[am].fac.size();
+    op_at[am + 1] = op_at[am] + (int64_t)ub[am].ops.size();
   }
-  P.factors.reserve((size_t)fac);
-  P.ops.reserve((size_t)nops);
+  P.factors.resize((size_t)fac_at[K]);
+  P.ops.resize((size_t)op_at[K]);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int am = 0; am < K; ++am) {
+    UnitBuild& b = ub[am];
+    std::copy(b.fac.begin(), b.fac.end(), P.factors.begin() + fac_at[am]);
+    for (size_t q = 0; q < b.ops.size(); ++q) {
+      Op op = b.ops[q];
+      op.b_off += fac_at[am];
+      P.ops[(size_t)op_at[am] + q] = op;
+    }
+    std::vector<double>().swap(b.fac);  // the unit's copy is no longer needed
+  }
   P.units = units;
   for (int am = 0; am < K; ++am) {
     UnitBuild& b = ub[am];
     Unit& u = P.units[am];
-    int64_t base = (int64_t)P.factors.size();
-    P.factors.insert(P.factors.end(), b.fac.begin(), b.fac.end());
-    u.op_begin = (int32_t)P.ops.size();
-    for (Op op : b.ops) {
-      op.b_off += base;
-      P.ops.push_back(op);
-    }
-    u.op_end = (int32_t)P.ops.size();
+    u.op_begin = (int32_t)op_at[am];
+    u.op_end = (int32_t)op_at[am + 1];
     u.ph_begin = (int32_t)P.phase_tab.size();
     int idx = u.op_begin;
     for (int ph = 0; ph <= u.nphase; ++ph) {
