@@ -352,29 +352,6 @@ __device__ __forceinline__ size_t grp_off(int row, int pc, int col) {
          (col & 7) * 2;
 }
 
-// four consecutive values (columns col .. col+3, col % 4 == 0) of row `row`
-// -> three BF16 pieces, one 8-byte store per piece
-__device__ __forceinline__ void put_pieces4(unsigned char* vec, int row, int col, float4 x) {
-  float a[4] = {x.x, x.y, x.z, x.w};
-  uint32_t h[3][2];
-#pragma unroll
-  for (int jj = 0; jj < 4; jj += 2) {
-    float a0 = a[jj], a1 = a[jj + 1];
-#pragma unroll
-    for (int pc = 0; pc < 3; ++pc) {
-      const __nv_bfloat162 hb = __floats2bfloat162_rn(a0, a1);
-      const float2 hf = __bfloat1622float2(hb);
-      a0 -= hf.x;
-      a1 -= hf.y;
-      h[pc][jj >> 1] = *reinterpret_cast<const uint32_t*>(&hb);
-    }
-  }
-#pragma unroll
-  for (int pc = 0; pc < 3; ++pc)
-    __stcg(reinterpret_cast<uint2*>(vec + grp_off(row, pc, col)), make_uint2(h[pc][0], h[pc][1]));
-}
-
-
 // eight consecutive values (columns 8 m8 .. 8 m8 + 7) of row `row` -> three
 // BF16 pieces, one 16-byte store per piece
 __device__ __forceinline__ void put_pieces8(unsigned char* vec, int row, int m8, float4 xa, float4 xb) {
