@@ -64,7 +64,27 @@ inline double householder(double* x, int n, double& beta_out) {
 inline void apply_reflector(Mat& A, int r0, const double* v, double tau, int c0, int c1) {
   if (tau == 0.0) return;
   int n = A.r - r0;
-  for (int j = c0; j < c1; ++j) {
+  int j = c0;
+  // two columns per pass over v; each column's sums run in the same order as
+  // the one-column loop below, so the results are the same bit for bit
+  for (; j + 1 < c1; j += 2) {
+    double* a0 = A.col(j) + r0;
+    double* a1 = A.col(j + 1) + r0;
+    double d0 = a0[0], d1 = a1[0];
+    for (int i = 1; i < n; ++i) {
+      d0 += v[i] * a0[i];
+      d1 += v[i] * a1[i];
+    }
+    d0 *= tau;
+    d1 *= tau;
+    a0[0] -= d0;
+    a1[0] -= d1;
+    for (int i = 1; i < n; ++i) {
+      a0[i] -= d0 * v[i];
+      a1[i] -= d1 * v[i];
+    }
+  }
+  for (; j < c1; ++j) {
     double* aj = A.col(j) + r0;
     double d = aj[0];
     for (int i = 1; i < n; ++i) d += v[i] * aj[i];
