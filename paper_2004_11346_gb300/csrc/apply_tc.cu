@@ -68,8 +68,13 @@ size_t tc_image_elems(int NN, const TcKGeom& kg) {
 // matrices (ki, mi) in K-outer order, 8 rows x 8 elements each.  elem(n, k)
 // is the block entry for row n and K index k of the unwidened K side; K
 // positions that fall outside both segments (group widening, padding) are 0.
+// Piece p of a value v is the BF16 rounding of what pieces 0..p-1 leave of v.
+// Each (tile, chunk) is first gathered into a small buffer, walking the source
+// along its contiguous direction (k_contig: consecutive K indices adjacent),
+// and the three pieces of every value are computed in one pass.
 template <class E>
-static void tc_pack(int NN, const TcKGeom& kg, int off0, int len0, int off1, int len1, E elem, uint16_t* dst) {
+static void tc_pack(int NN, const TcKGeom& kg, int off0, int len0, int off1, int len1, E elem, bool k_contig,
+                    uint16_t* dst) {
   const int nT = (NN + kTcNT - 1) / kTcNT;
   auto korig = [&](int kp) -> int {  // widened K position -> K index, or -1
     const int j = kp / kTcGrpRows, e = kp % kTcGrpRows;
@@ -83,26 +88,41 @@ static void tc_pack(int NN, const TcKGeom& kg, int off0, int len0, int off1, int
     }
     return -1;
   };
+  std::vector<double> buf((size_t)kTcNT * kTcKC);
   size_t o = 0;
   for (int t = 0; t < nT; ++t) {
-    const int Np = r16(std::min(kTcNT, NN - kTcNT * t));
+    const int Nv = std::min(kTcNT, NN - kTcNT * t);  // valid rows of the tile
+    const int Np = r16(Nv);
     for (int c = 0; c < kg.nK; ++c) {
       const int Kp = std::min(kTcKC, kg.kp_tot - kTcKC * c);
-      // pieces of every element of the chunk
-      for (int p = 0; p < 3; ++p)
-        for (int ki = 0; ki < Kp / 8; ++ki)
-          for (int mi = 0; mi < Np / 8; ++mi)
-            for (int rr = 0; rr < 8; ++rr)
-              for (int kk = 0; kk < 8; ++kk) {
-                const int n = kTcNT * t + mi * 8 + rr, k = korig(kTcKC * c + ki * 8 + kk);
-                double v = (n < NN && k >= 0) ? elem(n, k) : 0.0;
-                uint16_t h = 0;
-                for (int q = 0; q <= p; ++q) {  // piece q of v: bf16 of the remainder
-                  h = bf16_rn((float)v);
-                  v -= bf16_to_d(h);
-                }
-                dst[o++] = h;
-              }
+      int ko[kTcKC];
+      for (int kk = 0; kk < Kp; ++kk) ko[kk] = korig(kTcKC * c + kk);
+      // buf[n * Kp + kk] = entry (tile row n, chunk column kk), zero outside
+      std::fill(buf.begin(), buf.begin() + (size_t)Np * Kp, 0.0);
+      if (k_contig) {
+        for (int n = 0; n < Nv; ++n)
+          for (int kk = 0; kk < Kp; ++kk)
+            if (ko[kk] >= 0) buf[(size_t)n * Kp + kk] = elem(kTcNT * t + n, ko[kk]);
+      } else {
+        for (int kk = 0; kk < Kp; ++kk)
+          if (ko[kk] >= 0)
+            for (int n = 0; n < Nv; ++n) buf[(size_t)n * Kp + kk] = elem(kTcNT * t + n, ko[kk]);
+      }
+      const size_t piece = (size_t)Np * Kp;
+      for (int n = 0; n < Np; ++n) {
+        const int mi = n / 8, rr = n % 8;
+        for (int kk = 0; kk < Kp; ++kk) {
+          const int ki = kk / 8;
+          const size_t at = o + ((size_t)ki * (Np / 8) + mi) * 64 + rr * 8 + kk % 8;
+          double v = buf[(size_t)n * Kp + kk];
+          for (int p = 0; p < 3; ++p) {
+            const uint16_t h = bf16_rn((float)v);
+            v -= bf16_to_d(h);
+            dst[at + p * piece] = h;
+          }
+        }
+      }
+      o += 3 * piece;
     }
   }
 }
@@ -146,9 +166,9 @@ void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops,
       const TcKGeom kf = tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1]);
       const TcKGeom kb = tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1]);
       tc_pack(op.mo, kf, op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1],
-              [&](int r, int k) { return B[(size_t)k * ld + r]; }, img.data() + tops[i].img[0]);
+              [&](int r, int k) { return B[(size_t)k * ld + r]; }, false, img.data() + tops[i].img[0]);
       tc_pack(op.ni, kb, op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1],
-              [&](int r, int k) { return B[(size_t)r * ld + k]; }, img.data() + tops[i].img[1]);
+              [&](int r, int k) { return B[(size_t)r * ld + k]; }, true, img.data() + tops[i].img[1]);
     }
   }
 }
