@@ -733,6 +733,10 @@ static void build_unit(int N, int am, const sht_opts& o, const double* xp, UnitB
   u.ye = nce + nco;
   u.yo = nce + nco + N;
   ub.nrows = nce + nco + 2 * N;
+  // the unit's factors usually take less room than its two dense matrices
+  // (rounded to 4 rows): reserving that keeps the store from being copied as
+  // it grows block by block
+  ub.fac.reserve((size_t)((N + 3) & ~3) * (size_t)(nce + nco));
   auto maxabs = [](const Mat& A) {
     double s = 0.0;
     for (double v : A.a) s = std::max(s, std::fabs(v));
