@@ -735,8 +735,9 @@ static void build_unit(int N, int am, const sht_opts& o, const double* xp, UnitB
   ub.nrows = nce + nco + 2 * N;
   // the unit's factors usually take less room than its two dense matrices
   // (rounded to 4 rows): reserving that keeps the store from being copied as
-  // it grows block by block
-  ub.fac.reserve((size_t)((N + 3) & ~3) * (size_t)(nce + nco));
+  // it grows block by block.  Capped at 2^21 doubles (16 MB, every unit up to
+  // N = 1024), since all units' stores are alive until they are concatenated.
+  ub.fac.reserve(std::min<size_t>((size_t)((N + 3) & ~3) * (size_t)(nce + nco), (size_t)1 << 21));
   auto maxabs = [](const Mat& A) {
     double s = 0.0;
     for (double v : A.a) s = std::max(s, std::fabs(v));
