@@ -173,6 +173,17 @@ typedef enum {
 } sht_export_kind;
 sht_status sht_plan_export(sht_plan_t plan, int what, void* dst_host, size_t* bytes);
 
+/* The tensor-core operand image of op `op` of the program (the index into
+ * SHT_EXPORT_OPS), for inspection; the paper has no counterpart.  The image is
+ * what the SHT_MIXED kernel streams: the op's block B (transposed != 0: B^T),
+ * split into three BF16 pieces b0 + b1 + b2 (piece p the rounding of what
+ * pieces 0..p-1 leave), in tiles of 128 rows x chunks of 32 K columns, each
+ * chunk piece by piece in 8 x 8 core matrices (K-outer).  The K side is
+ * widened to whole 8-row groups of the vector space, with zero columns where
+ * it was widened.  Copies `*count` BF16 values into dst_host (caller-owned);
+ * with dst_host == NULL only *count is set.  Works for host-only plans too. */
+sht_status sht_plan_op_image(sht_plan_t plan, int64_t op, int transposed, uint16_t* dst_host, size_t* count);
+
 /* Save the plan's precomputation (Sec. 3.2-3.3: nodes, weights, the block
  * factorisation as the packed apply program, options and statistics) to a
  * file, so that later processes skip the factorisation.  The file is written

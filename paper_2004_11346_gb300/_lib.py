@@ -85,7 +85,7 @@ EXPORTED = [
     "sht_status_str", "alt_forward_m_noalloc", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
     "sht_inverse", "sht_plan_save", "sht_plan_load", "sht_plan_kernel_time", "sht_batch_create",
     "sht_batch_destroy", "alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch",
-    "sht_batch_sync", "sht_selftest_timeout",
+    "sht_batch_sync", "sht_selftest_timeout", "sht_plan_op_image",
 ]
 
 
@@ -120,6 +120,7 @@ def load(build: bool = True):
     lib.sht_batch_destroy.argtypes = [vp]
     lib.sht_batch_sync.argtypes = [vp, vp]
     lib.sht_selftest_timeout.argtypes = [vp, vp]
+    lib.sht_plan_op_image.argtypes = [vp, ctypes.c_int64, i, vp, ctypes.POINTER(ctypes.c_size_t)]
     for name in ("alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch"):
         getattr(lib, name).argtypes = [vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), vp]
     lib.sht_status_str.argtypes = [i]
@@ -275,3 +276,14 @@ def sht_batch_sync(batch: int, stream: int = 0):
 
 def sht_selftest_timeout(plan: int, stream: int = 0):
     check(load().sht_selftest_timeout(plan, stream), "sht_selftest_timeout")
+
+
+def sht_plan_op_image(plan: int, op: int, transposed: bool):
+    """The BF16 bits (uint16 numpy array) of one op's tensor-core operand image."""
+    import numpy as np
+    n = ctypes.c_size_t(0)
+    check(load().sht_plan_op_image(plan, op, 1 if transposed else 0, None, ctypes.byref(n)), "sht_plan_op_image")
+    out = np.zeros(max(1, n.value), dtype=np.uint16)
+    check(load().sht_plan_op_image(plan, op, 1 if transposed else 0, out.ctypes.data, ctypes.byref(n)),
+          "sht_plan_op_image")
+    return out[: n.value]

@@ -697,6 +697,24 @@ sht_status sht_plan_export(sht_plan_t p, int what, void* dst, size_t* bytes) {
   return SHT_OK;
 }
 
+sht_status sht_plan_op_image(sht_plan_t p, int64_t op, int transposed, uint16_t* dst, size_t* count) {
+  if (!p || !count || op < 0 || op >= (int64_t)p->prog.ops.size()) return SHT_ERR_ARG;
+  std::vector<uint16_t> img;
+  try {
+    tc_op_image(p->prog.ops[(size_t)op], p->prog.factors, transposed != 0, img);
+  } catch (const std::bad_alloc&) {
+    return SHT_ERR_OOM;
+  }
+  if (!dst) {
+    *count = img.size();
+    return SHT_OK;
+  }
+  if (*count < img.size()) return SHT_ERR_ARG;
+  if (!img.empty()) std::memcpy(dst, img.data(), img.size() * sizeof(uint16_t));
+  *count = img.size();
+  return SHT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Plan files.  Layout (native byte order; both supported hosts are
 // little-endian):

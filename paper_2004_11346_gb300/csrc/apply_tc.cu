@@ -127,6 +127,24 @@ static void tc_pack(int NN, const TcKGeom& kg, int off0, int len0, int off1, int
   }
 }
 
+void tc_op_image(const Op& op, const std::vector<double>& factors, bool transposed, std::vector<uint16_t>& out) {
+  out.clear();
+  if (op.ni <= 0) return;
+  const double* B = factors.data() + op.b_off;
+  const int ld = op.ld;
+  if (!transposed) {
+    const TcKGeom kg = tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1]);
+    out.assign(tc_image_elems(op.mo, kg), 0);
+    tc_pack(op.mo, kg, op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1],
+            [&](int r, int k) { return B[(size_t)k * ld + r]; }, false, out.data());
+  } else {
+    const TcKGeom kg = tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1]);
+    out.assign(tc_image_elems(op.ni, kg), 0);
+    tc_pack(op.ni, kg, op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1],
+            [&](int r, int k) { return B[(size_t)r * ld + k]; }, true, out.data());
+  }
+}
+
 void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops, const std::vector<double>& factors,
                      std::vector<uint16_t>& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles) {
   const size_t n = ops.size();

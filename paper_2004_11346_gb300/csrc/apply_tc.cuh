@@ -119,6 +119,10 @@ struct TcLaunch {
 // (3 pieces, padded).
 size_t tc_image_elems(int NN, const TcKGeom& kg);
 
+// The split-BF16 image of one op in one direction (forward: B, transposed:
+// B^T), exactly as tc_build_images lays it out for the kernel.
+void tc_op_image(const Op& op, const std::vector<double>& factors, bool transposed, std::vector<uint16_t>& out);
+
 // Build the forward (NN = mo, KK = ni) and transposed (NN = ni, KK = mo)
 // images of every op from the FP64 factor store, the kernel's op records and
 // the per-unit tile counts.
