@@ -169,7 +169,9 @@ typedef enum {
   SHT_EXPORT_PHASES = 2,
   SHT_EXPORT_FACTORS = 3,
   SHT_EXPORT_ORDER = 4,
-  SHT_EXPORT_OPTS = 5
+  SHT_EXPORT_OPTS = 5,
+  SHT_EXPORT_UNIT_BLOCKS = 6  /* per order |m|: int32 counts of IDBF, low-rank, dense and dropped
+                                blocks (Sec. 5's block counts); empty for plans read from files */
 } sht_export_kind;
 sht_status sht_plan_export(sht_plan_t plan, int what, void* dst_host, size_t* bytes);
 

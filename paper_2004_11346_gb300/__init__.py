@@ -94,7 +94,8 @@ class Plan:
         """Host copies of the apply program (for inspection and tests)."""
         kinds = {"units": (_lib.SHT_EXPORT_UNITS, UNIT_DTYPE), "ops": (_lib.SHT_EXPORT_OPS, OP_DTYPE),
                  "phases": (_lib.SHT_EXPORT_PHASES, np.int32), "factors": (_lib.SHT_EXPORT_FACTORS, np.float64),
-                 "order": (_lib.SHT_EXPORT_ORDER, np.int32)}
+                 "order": (_lib.SHT_EXPORT_ORDER, np.int32),
+                 "unit_blocks": (_lib.SHT_EXPORT_UNIT_BLOCKS, np.int32)}
         return {k: np.frombuffer(_lib.sht_plan_export(self.handle, kinds[k][0]), dtype=kinds[k][1]) for k in parts}
 
     # ---- device entry points (torch tensors)

@@ -23,7 +23,8 @@ SHT_FLAG_FORCE_FACTOR = 1
 SHT_FLAG_HOST_ONLY = 2
 SHT_FLAG_DENSE = 4
 SHT_FLAG_TIMING = 8
-SHT_EXPORT_UNITS, SHT_EXPORT_OPS, SHT_EXPORT_PHASES, SHT_EXPORT_FACTORS, SHT_EXPORT_ORDER, SHT_EXPORT_OPTS = range(6)
+(SHT_EXPORT_UNITS, SHT_EXPORT_OPS, SHT_EXPORT_PHASES, SHT_EXPORT_FACTORS, SHT_EXPORT_ORDER, SHT_EXPORT_OPTS,
+ SHT_EXPORT_UNIT_BLOCKS) = range(7)
 
 
 class sht_opts(ctypes.Structure):

@@ -685,6 +685,7 @@ sht_status sht_plan_export(sht_plan_t p, int what, void* dst, size_t* bytes) {
     case SHT_EXPORT_FACTORS: src = P.factors.data(); n = P.factors.size() * sizeof(double); break;
     case SHT_EXPORT_ORDER: src = P.order.data(); n = P.order.size() * sizeof(int32_t); break;
     case SHT_EXPORT_OPTS: src = &P.opts; n = sizeof(sht_opts); break;
+    case SHT_EXPORT_UNIT_BLOCKS: src = P.unit_blocks.data(); n = P.unit_blocks.size() * sizeof(int32_t); break;
     default: return SHT_ERR_ARG;
   }
   if (!dst) {

@@ -810,6 +810,7 @@ sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::strin
     I.n_blocks_lowrank += b.n_low;
     I.n_blocks_dense += b.n_dense;
     I.n_blocks_dropped += b.n_drop;
+    P.unit_blocks.insert(P.unit_blocks.end(), {(int32_t)b.n_idbf, (int32_t)b.n_low, (int32_t)b.n_dense, (int32_t)b.n_drop});
     I.entries_idbf += b.e_idbf;
     I.entries_lowrank += b.e_low;
     I.entries_dense += b.e_dense;

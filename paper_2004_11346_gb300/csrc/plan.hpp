@@ -19,6 +19,7 @@ struct HostProgram {
   std::vector<int32_t> phase_tab;  // per unit: nphase+1 op indices (absolute)
   std::vector<double> factors;     // packed blocks (column-major, ld % 4 == 0, 32-byte aligned)
   std::vector<int32_t> order;      // units by decreasing cost (schedule)
+  std::vector<int32_t> unit_blocks;  // per unit: IDBF, low-rank, dense, dropped block counts (not in plan files)
   int32_t max_rows = 0;            // largest unit vector space (rows)
   sht_plan_info info{};
 };
