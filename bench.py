@@ -428,7 +428,7 @@ def compare(torch, sht, _lib, w, plan, beta, g, args, stream):
     p64 = sht.Plan(N, 1e-12, precision=_lib.SHT_FP64)
     ms, f, i = time_steps(torch, p64, b1, g1, r1, K, 2, stream)
     out["fp64_idbf"] = {"fields_per_s": 1e3 / ms, "forward_ms": f, "inverse_ms": i, "eps": 1e-12,
-                        "entries": p64.stats()["entries_total"]}
+                        "entries": p64.stats()["entries_total"], "t_fac_s": p64.stats()["t_factor_s"]}
     if w["precision"] != "fp64":
         F = beta.shape[0]
         ref = torch.empty_like(g)
@@ -443,8 +443,14 @@ def compare(torch, sht, _lib, w, plan, beta, g, args, stream):
     pd = sht.Plan(N, 1e-12, precision=_lib.SHT_FP64, flags=_lib.SHT_FLAG_DENSE)
     ms, f, i = time_steps(torch, pd, b1, g1, r1, K, 2, stream)
     out["dense_fp64"] = {"fields_per_s": 1e3 / ms, "forward_ms": f, "inverse_ms": i,
-                         "entries": pd.stats()["entries_total"]}
+                         "entries": pd.stats()["entries_total"], "t_mat_s": pd.stats()["t_factor_s"]}
     del pd
+    # the paper's speedup ratios (its last experiment), FP64 on both sides: the
+    # dense transform's time over the IDBF apply's, and building the dense
+    # matrices over factoring them
+    fp, dn = out["fp64_idbf"], out["dense_fp64"]
+    out["paper_ratios"] = {"t_dir_over_t_app": (dn["forward_ms"] + dn["inverse_ms"]) / (fp["forward_ms"] + fp["inverse_ms"]),
+                           "t_mat_over_t_fac": dn["t_mat_s"] / fp["t_fac_s"] if fp["t_fac_s"] > 0 else None}
     out["sht"] = sht_timings(torch, w, plan, beta, g, K, stream)
     return out
 

@@ -57,3 +57,44 @@ def test_reference_arm_declines_uneven_batches():
     assert out.returncode == 0
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and "unavailable" in line
+
+
+def test_compare_reports_the_paper_ratios(monkeypatch):
+    """compare()'s bookkeeping with stand-ins for the GPU parts: the IDBF and
+    dense plans' times and build times give the paper's two speedup ratios."""
+    class FakeTensor:
+        def __getitem__(self, k):
+            return self
+
+        def contiguous(self):
+            return self
+
+    class FakeTorch:
+        float64 = "f64"
+
+        @staticmethod
+        def empty(*a, **k):
+            return FakeTensor()
+
+        @staticmethod
+        def empty_like(x):
+            return FakeTensor()
+
+    class FakePlan:
+        def __init__(self, N, eps, precision=None, flags=0):
+            self.dense = bool(flags & 4)
+
+        def stats(self):
+            return {"entries_total": 10, "t_factor_s": 6.0 if self.dense else 2.0}
+
+    class FakeSht:
+        Plan = FakePlan
+
+    lib = type("L", (), {"SHT_FP64": 0, "SHT_FLAG_DENSE": 4})
+    times = iter([(10.0, 4.0, 6.0), (40.0, 15.0, 25.0)])  # FP64 IDBF, then dense
+    monkeypatch.setattr(bench, "time_steps", lambda *a: next(times))
+    monkeypatch.setattr(bench, "sht_timings", lambda *a: {})
+    args = type("A", (), {"steps": 4})
+    out = bench.compare(FakeTorch, FakeSht, lib, {"N": 8, "precision": "fp64"}, None, FakeTensor(), None, args, None)
+    assert out["fp64_idbf"]["t_fac_s"] == 2.0 and out["dense_fp64"]["t_mat_s"] == 6.0
+    assert out["paper_ratios"] == {"t_dir_over_t_app": 4.0, "t_mat_over_t_fac": 3.0}
