@@ -127,6 +127,37 @@ sht_status sht_plan_stats(sht_plan_t plan, sht_plan_info* out);
  * HOST arrays owned by the caller. */
 sht_status sht_plan_nodes(sht_plan_t plan, double* x_host, double* w_host);
 
+/* One order's factorisation built on its own (host only, no device needed):
+ * the per-order experiments of Sec. 5, and a way to size a plan for a large N
+ * from a sample of its orders before building it.  Every field describes
+ * exactly what sht_plan_create(N, eps, opts) builds at that order. */
+typedef struct {
+  int N;
+  int am;                    /* |m|                                             */
+  int64_t cols_even, cols_odd; /* degrees of each parity (N rows each)         */
+  int64_t n_blocks_idbf, n_blocks_lowrank, n_blocks_dense, n_blocks_dropped;
+  int64_t entries_idbf, entries_lowrank, entries_dense, entries_total;
+  int64_t entries_matrix;    /* N * (cols_even + cols_odd)                      */
+  int64_t factor_doubles;    /* the order's FP64 factor store, padding included */
+  int64_t image_elems;       /* BF16 elements of the order's tensor-core operand
+                                images, both directions (SHT_MIXED plans)       */
+  int64_t max_rank;
+  int64_t n_ops;             /* block products of the order's apply program     */
+  int64_t n_phases;
+  int64_t rows;              /* rows of the order's vector space                */
+  double flops_per_rhs;      /* the schedule's cost estimate                    */
+  double t_mat_s;            /* building the two Legendre matrices (recurrence) */
+  double t_fac_s;            /* partition, IDs / IDBF / rSVD, trimming, packing */
+} sht_order_info;
+
+/* Build the orders m[0..count) (each in [-(2N-1), 2N-1]; -m and m are one
+ * order) of the plan sht_plan_create(N, eps, opts) would build, one host
+ * thread per order, and describe each in out[0..count) (HOST array owned by
+ * the caller).  The factors are discarded.  SHT_ERR_ARG for an argument
+ * sht_plan_create would refuse, count < 0, or an order out of range;
+ * SHT_ERR_OOM when host memory runs out. */
+sht_status sht_order_stats(int N, double eps, const sht_opts* opts, int count, const int* m, sht_order_info* out);
+
 /* Forward ALT of F fields (Eq. sht_lt, Sec. 3.1.2 parity split and fold):
  *   g(m, theta_l) = sum_{k=|m|}^{2N-1} beta_{k,m} Pbar_k^{|m|}(x_l)
  * for every order.  beta: F x 4N^2 complex, g: F x (4N-1) x 2N complex. */

@@ -73,6 +73,36 @@ class sht_plan_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class sht_order_info(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int),
+        ("am", ctypes.c_int),
+        ("cols_even", ctypes.c_int64),
+        ("cols_odd", ctypes.c_int64),
+        ("n_blocks_idbf", ctypes.c_int64),
+        ("n_blocks_lowrank", ctypes.c_int64),
+        ("n_blocks_dense", ctypes.c_int64),
+        ("n_blocks_dropped", ctypes.c_int64),
+        ("entries_idbf", ctypes.c_int64),
+        ("entries_lowrank", ctypes.c_int64),
+        ("entries_dense", ctypes.c_int64),
+        ("entries_total", ctypes.c_int64),
+        ("entries_matrix", ctypes.c_int64),
+        ("factor_doubles", ctypes.c_int64),
+        ("image_elems", ctypes.c_int64),
+        ("max_rank", ctypes.c_int64),
+        ("n_ops", ctypes.c_int64),
+        ("n_phases", ctypes.c_int64),
+        ("rows", ctypes.c_int64),
+        ("flops_per_rhs", ctypes.c_double),
+        ("t_mat_s", ctypes.c_double),
+        ("t_fac_s", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ShtError(RuntimeError):
     def __init__(self, what: str, status: int):
         super().__init__(f"{what}: {STATUS.get(status, status)} (status {status})")
@@ -86,7 +116,7 @@ EXPORTED = [
     "sht_status_str", "alt_forward_m_noalloc", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
     "sht_inverse", "sht_plan_save", "sht_plan_load", "sht_plan_kernel_time", "sht_batch_create",
     "sht_batch_destroy", "alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch",
-    "sht_batch_sync", "sht_selftest_timeout", "sht_plan_op_image",
+    "sht_batch_sync", "sht_selftest_timeout", "sht_plan_op_image", "sht_order_stats",
 ]
 
 
@@ -122,6 +152,8 @@ def load(build: bool = True):
     lib.sht_batch_sync.argtypes = [vp, vp]
     lib.sht_selftest_timeout.argtypes = [vp, vp]
     lib.sht_plan_op_image.argtypes = [vp, ctypes.c_int64, i, vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.sht_order_stats.argtypes = [i, d, ctypes.POINTER(sht_opts), i, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(sht_order_info)]
     for name in ("alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch"):
         getattr(lib, name).argtypes = [vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), vp]
     lib.sht_status_str.argtypes = [i]
@@ -288,3 +320,14 @@ def sht_plan_op_image(plan: int, op: int, transposed: bool):
     check(load().sht_plan_op_image(plan, op, 1 if transposed else 0, out.ctypes.data, ctypes.byref(n)),
           "sht_plan_op_image")
     return out[: n.value]
+
+
+def sht_order_stats(N: int, eps: float, orders, opts: sht_opts | None = None) -> list:
+    """One dict per order (sht_order_info) of the plan sht_plan_create(N, eps, opts) would build."""
+    orders = [int(v) for v in orders]
+    n = len(orders)
+    marr = (ctypes.c_int * max(1, n))(*orders)
+    out = (sht_order_info * max(1, n))()
+    check(load().sht_order_stats(N, eps, ctypes.byref(opts) if opts is not None else None, n, marr, out),
+          "sht_order_stats")
+    return [out[k].as_dict() for k in range(n)]

@@ -340,8 +340,8 @@ cudaError_t plan_malloc(void** ptr, size_t bytes) {
   return cudaMalloc(ptr, bytes);
 }
 
-template <class T>
-cudaError_t upload(T** dst, const std::vector<T>& v) {
+template <class T, class A>
+cudaError_t upload(T** dst, const std::vector<T, A>& v) {
   size_t bytes = std::max<size_t>(sizeof(T), v.size() * sizeof(T));
   cudaError_t e = plan_malloc(reinterpret_cast<void**>(dst), bytes);
   if (e != cudaSuccess) return e;
@@ -555,10 +555,10 @@ sht_status attach_device(sht_plan_s* p) {
   if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_counter), sizeof(unsigned int));
   size_t ws32 = 0;
   if (e == cudaSuccess && o.precision == SHT_MIXED) {
-    std::vector<uint16_t> img;
+    TcImages img;
     std::vector<TcOp> tops;
     std::vector<int32_t> tiles;
-    tc_build_images(P.units, P.ops, P.factors, img, tops, tiles);
+    tc_build_images(P.units, P.ops, P.factors.data(), img, tops, tiles);
     e = upload(&p->d_img, img);
     if (e == cudaSuccess) e = upload(&p->d_tcops, tops);
     if (e == cudaSuccess) e = upload(&p->d_tctiles, tiles);
@@ -576,7 +576,9 @@ sht_status attach_device(sht_plan_s* p) {
     p->prog.info.factor_bytes = (int64_t)(img.size() * sizeof(uint16_t));
   }
   if (e == cudaSuccess && o.precision == SHT_FP32) {
-    std::vector<float> f32(P.factors.begin(), P.factors.end());
+    std::vector<float, UninitAlloc<float>> f32(P.factors.size());
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < (long)f32.size(); ++i) f32[(size_t)i] = (float)P.factors[(size_t)i];
     e = upload(&p->d_fac32, f32);
     p->nslots32 = std::max(1, sms * f32_ctas_per_sm());
     ws32 = (size_t)p->nslots32 * P.max_rows * kF32RT * sizeof(float);
@@ -615,21 +617,28 @@ sht_status attach_device(sht_plan_s* p) {
 }
 
 
-}  // namespace
-
-sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* out) {
-  if (!out || N < 1 || N > (1 << 14) || !(eps > 0.0 && eps < 1.0)) return SHT_ERR_ARG;
-  *out = nullptr;
-  sht_opts o;
+// The options a plan of order N is built with (the defaults when opts is
+// NULL, the tolerance always eps); false when N, eps or an option is out of
+// range.
+bool resolve_opts(int N, double eps, const sht_opts* opts, sht_opts& o) {
+  if (N < 1 || N > (1 << 14) || !(eps > 0.0 && eps < 1.0)) return false;
   if (opts) {
     o = *opts;
     o.eps = eps;
   } else {
     sht_opts_default(N, eps, &o);
   }
-  if (o.n0 < 1 || o.n_leaf < 1 || o.r_k < 1 || o.rsvd_r < 1 || o.rsvd_q < 1 || !(o.oversample >= 1.0) ||
-      !(o.trim_delta >= 0.0) || o.max_fields < 1)
-    return SHT_ERR_ARG;
+  return o.n0 >= 1 && o.n_leaf >= 1 && o.r_k >= 1 && o.rsvd_r >= 1 && o.rsvd_q >= 1 && o.oversample >= 1.0 &&
+         o.trim_delta >= 0.0 && o.max_fields >= 1;
+}
+
+}  // namespace
+
+sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* out) {
+  if (!out) return SHT_ERR_ARG;
+  *out = nullptr;
+  sht_opts o;
+  if (!resolve_opts(N, eps, opts, o)) return SHT_ERR_ARG;
   const bool host_only = (o.flags & SHT_FLAG_HOST_ONLY) != 0;
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)) return SHT_ERR_CUDA;
@@ -673,6 +682,53 @@ sht_status sht_plan_stats(sht_plan_t p, sht_plan_info* out) {
   return SHT_OK;
 }
 
+sht_status sht_order_stats(int N, double eps, const sht_opts* opts, int count, const int* m, sht_order_info* out) {
+  sht_opts o;
+  if (!resolve_opts(N, eps, opts, o) || count < 0 || (count > 0 && (!m || !out))) return SHT_ERR_ARG;
+  std::vector<int> am((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    if (m[i] <= -2 * N || m[i] >= 2 * N) return SHT_ERR_ARG;
+    am[(size_t)i] = std::abs(m[i]);
+  }
+  std::vector<OrderBuild> b;
+  try {
+    const sht_status s = build_orders(N, o, count, am.data(), b);
+    if (s != SHT_OK) return s;
+  } catch (const std::bad_alloc&) {
+    return SHT_ERR_OOM;
+  }
+  for (int i = 0; i < count; ++i) {
+    const OrderBuild& r = b[(size_t)i];
+    sht_order_info& q = out[i];
+    std::memset(&q, 0, sizeof(q));
+    q.N = N;
+    q.am = am[(size_t)i];
+    q.cols_even = r.unit.nce;
+    q.cols_odd = r.unit.nco;
+    q.n_blocks_idbf = r.n_idbf;
+    q.n_blocks_lowrank = r.n_low;
+    q.n_blocks_dense = r.n_dense;
+    q.n_blocks_dropped = r.n_drop;
+    q.entries_idbf = r.e_idbf;
+    q.entries_lowrank = r.e_low;
+    q.entries_dense = r.e_dense;
+    q.entries_total = r.e_idbf + r.e_low + r.e_dense;
+    q.entries_matrix = (int64_t)N * (r.unit.nce + r.unit.nco);
+    q.factor_doubles = r.n_factors;
+    for (const Op& op : r.ops)
+      q.image_elems += (int64_t)tc_image_elems(op.mo, tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1])) +
+                       (int64_t)tc_image_elems(op.ni, tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1]));
+    q.max_rank = r.max_rank;
+    q.n_ops = (int64_t)r.ops.size();
+    q.n_phases = r.unit.nphase;
+    q.rows = r.unit.nrows;
+    q.flops_per_rhs = r.unit.cost;
+    q.t_mat_s = r.t_mat_s;
+    q.t_fac_s = r.t_fac_s;
+  }
+  return SHT_OK;
+}
+
 sht_status sht_plan_export(sht_plan_t p, int what, void* dst, size_t* bytes) {
   if (!p || !bytes) return SHT_ERR_ARG;
   const void* src = nullptr;
@@ -702,7 +758,7 @@ sht_status sht_plan_op_image(sht_plan_t p, int64_t op, int transposed, uint16_t*
   if (!p || !count || op < 0 || op >= (int64_t)p->prog.ops.size()) return SHT_ERR_ARG;
   std::vector<uint16_t> img;
   try {
-    tc_op_image(p->prog.ops[(size_t)op], p->prog.factors, transposed != 0, img);
+    tc_op_image(p->prog.ops[(size_t)op], p->prog.factors.data(), transposed != 0, img);
   } catch (const std::bad_alloc&) {
     return SHT_ERR_OOM;
   }
@@ -740,8 +796,8 @@ struct PlanWriter {
     for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001b3ull;
     if (n && std::fwrite(src, 1, n, f) != n) ok = false;
   }
-  template <class T>
-  void vec(const std::vector<T>& v) {
+  template <class T, class A>
+  void vec(const std::vector<T, A>& v) {
     const uint64_t n = v.size();
     put(&n, sizeof n);
     put(v.data(), v.size() * sizeof(T));
@@ -760,8 +816,8 @@ struct PlanReader {
     const unsigned char* b = static_cast<const unsigned char*>(dst);
     for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001b3ull;
   }
-  template <class T>
-  void vec(std::vector<T>& v, uint64_t max_elems) {
+  template <class T, class A>
+  void vec(std::vector<T, A>& v, uint64_t max_elems) {
     uint64_t n = 0;
     get(&n, sizeof n);
     if (!ok || n > max_elems) {

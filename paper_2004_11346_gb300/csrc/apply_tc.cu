@@ -127,10 +127,10 @@ static void tc_pack(int NN, const TcKGeom& kg, int off0, int len0, int off1, int
   }
 }
 
-void tc_op_image(const Op& op, const std::vector<double>& factors, bool transposed, std::vector<uint16_t>& out) {
+void tc_op_image(const Op& op, const double* factors, bool transposed, std::vector<uint16_t>& out) {
   out.clear();
   if (op.ni <= 0) return;
-  const double* B = factors.data() + op.b_off;
+  const double* B = factors + op.b_off;
   const int ld = op.ld;
   if (!transposed) {
     const TcKGeom kg = tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1]);
@@ -145,8 +145,8 @@ void tc_op_image(const Op& op, const std::vector<double>& factors, bool transpos
   }
 }
 
-void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops, const std::vector<double>& factors,
-                     std::vector<uint16_t>& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles) {
+void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops, const double* factors,
+                     TcImages& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles) {
   const size_t n = ops.size();
   tops.assign(n, TcOp{});
   size_t tot = 0;
@@ -174,11 +174,14 @@ void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops,
       tiles[2 * u] += (ops[oi].mo + kTcNT - 1) / kTcNT;
       tiles[2 * u + 1] += (ops[oi].ni + kTcNT - 1) / kTcNT;
     }
-  img.assign(std::max<size_t>(tot, 8), 0);
+  // tc_pack writes every element of an op's two images (padding included),
+  // so only the minimum-size tail of an empty store needs zeroing here
+  img.resize(std::max<size_t>(tot, 8));
+  std::fill(img.begin() + tot, img.end(), (uint16_t)0);
 #pragma omp parallel for schedule(dynamic, 64)
   for (long i = 0; i < (long)n; ++i) {
     const Op& op = ops[i];
-    const double* B = factors.data() + op.b_off;
+    const double* B = factors + op.b_off;
     const int ld = op.ld;
     if (op.ni > 0) {
       const TcKGeom kf = tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1]);

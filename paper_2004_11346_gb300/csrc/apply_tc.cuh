@@ -121,13 +121,14 @@ size_t tc_image_elems(int NN, const TcKGeom& kg);
 
 // The split-BF16 image of one op in one direction (forward: B, transposed:
 // B^T), exactly as tc_build_images lays it out for the kernel.
-void tc_op_image(const Op& op, const std::vector<double>& factors, bool transposed, std::vector<uint16_t>& out);
+void tc_op_image(const Op& op, const double* factors, bool transposed, std::vector<uint16_t>& out);
 
 // Build the forward (NN = mo, KK = ni) and transposed (NN = ni, KK = mo)
 // images of every op from the FP64 factor store, the kernel's op records and
 // the per-unit tile counts.
-void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops, const std::vector<double>& factors,
-                     std::vector<uint16_t>& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles);
+using TcImages = std::vector<uint16_t, UninitAlloc<uint16_t>>;
+void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops, const double* factors,
+                     TcImages& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles);
 
 // One apply: run the persistent tensor-core
 // kernel (gather, block products), then the output kernel (parity fold to g,

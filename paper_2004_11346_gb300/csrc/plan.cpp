@@ -19,6 +19,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <new>
 #include <numeric>
 #include <string>
 
@@ -720,9 +721,12 @@ static void build_parity(UnitBuild& ub, const ParityMatrix& P, const sht_opts& o
   }
 }
 
-static void build_unit(int N, int am, const sht_opts& o, const double* xp, UnitBuild& ub, Unit& u) {
+static void build_unit(int N, int am, const sht_opts& o, const double* xp, UnitBuild& ub, Unit& u,
+                       double* t_mat = nullptr) {
   Mat E, O;
+  const auto t0 = std::chrono::steady_clock::now();
   legendre_parity_matrices(N, am, xp, E, O);
+  if (t_mat) *t_mat = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   const int nce = E.c, nco = O.c;
   u = Unit{};
   u.am = am;
@@ -771,6 +775,7 @@ sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::strin
   // heavy orders (small |m|) first
 #pragma omp parallel for schedule(dynamic, 1)
   for (int am = 0; am < K; ++am) build_unit(N, am, opts, xp, ub[am], units[am]);
+  const auto t_units = std::chrono::steady_clock::now();
 
   // concatenate into the global program: offsets first, then every unit's
   // factors and ops copied in parallel to their places
@@ -780,6 +785,8 @@ sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::strin
     fac_at[am + 1] = fac_at[am] + (int64_t)ub[am].fac.size();
     op_at[am + 1] = op_at[am] + (int64_t)ub[am].ops.size();
   }
+  // the store is left uninitialised here (FactorStore): the copies below
+  // write every element, and first touch its pages from all threads
   P.factors.resize((size_t)fac_at[K]);
   P.ops.resize((size_t)op_at[K]);
 #pragma omp parallel for schedule(dynamic, 4)
@@ -793,6 +800,7 @@ sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::strin
     }
     std::vector<double>().swap(b.fac);  // the unit's copy is no longer needed
   }
+  const auto t_concat = std::chrono::steady_clock::now();
   P.units = units;
   for (int am = 0; am < K; ++am) {
     UnitBuild& b = ub[am];
@@ -832,6 +840,11 @@ sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::strin
                  "cross(trimmed)=%lld | untrimmed area nonosc=%lld cross=%lld\n",
                  (long long)d[0], (long long)d[1], (long long)d[2], (long long)d[3], (long long)d[4],
                  (long long)d[5]);
+    auto sec = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+      return std::chrono::duration<double>(b - a).count();
+    };
+    std::fprintf(stderr, "[plan] units %.3f s, concatenation %.3f s, tables and checks %.3f s\n", sec(t0, t_units),
+                 sec(t_units, t_concat), sec(t_concat, std::chrono::steady_clock::now()));
   }
   I.N = N;
   I.eps = opts.eps;
@@ -841,6 +854,40 @@ sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::strin
   I.threads = threads;
   I.t_factor_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return SHT_OK;
+}
+
+sht_status build_orders(int N, const sht_opts& opts, int count, const int* am, std::vector<OrderBuild>& out) {
+  std::vector<double> x, w;
+  gauss_legendre(2 * N, x, w);
+  const double* xp = x.data() + N;
+  out.assign((size_t)count, OrderBuild{});
+  bool oom = false;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < count; ++i) {
+    OrderBuild& r = out[(size_t)i];
+    try {
+      UnitBuild ub;
+      const auto t0 = std::chrono::steady_clock::now();
+      build_unit(N, am[i], opts, xp, ub, r.unit, &r.t_mat_s);
+      r.t_fac_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() - r.t_mat_s;
+      r.unit.op_begin = 0;
+      r.unit.op_end = (int32_t)ub.ops.size();
+      r.ops = std::move(ub.ops);
+      r.n_factors = (int64_t)ub.fac.size();
+      r.n_idbf = ub.n_idbf;
+      r.n_low = ub.n_low;
+      r.n_dense = ub.n_dense;
+      r.n_drop = ub.n_drop;
+      r.e_idbf = ub.e_idbf;
+      r.e_low = ub.e_low;
+      r.e_dense = ub.e_dense;
+      r.max_rank = ub.max_rank;
+    } catch (const std::bad_alloc&) {
+#pragma omp atomic write
+      oom = true;
+    }
+  }
+  return oom ? SHT_ERR_OOM : SHT_OK;
 }
 
 bool validate_program(const HostProgram& P, std::string& err) {

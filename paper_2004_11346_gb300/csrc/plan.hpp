@@ -17,7 +17,7 @@ struct HostProgram {
   std::vector<Unit> units;         // one per |m| = 0..2N-1, indexed by |m|
   std::vector<Op> ops;             // all units' ops, grouped by unit, sorted by phase
   std::vector<int32_t> phase_tab;  // per unit: nphase+1 op indices (absolute)
-  std::vector<double> factors;     // packed blocks (column-major, ld % 4 == 0, 32-byte aligned)
+  FactorStore factors;             // packed blocks (column-major, ld % 4 == 0, 32-byte aligned)
   std::vector<int32_t> order;      // units by decreasing cost (schedule)
   std::vector<int32_t> unit_blocks;  // per unit: IDBF, low-rank, dense, dropped block counts (not in plan files)
   int32_t max_rows = 0;            // largest unit vector space (rows)
@@ -26,6 +26,26 @@ struct HostProgram {
 
 // Build the apply program (Sec. 3.2-3.3).  Returns SHT_OK or an error code.
 sht_status build_program(int N, const sht_opts& opts, HostProgram& out, std::string& err);
+
+// One order built on its own, as in the per-order experiments of Sec. 5: the
+// unit's ops (op_begin = 0) with its block statistics, and the time spent on
+// its Legendre matrices (t_mat_s) and on partitioning, factoring and packing
+// them (t_fac_s).  The factors themselves are not kept: this is for sizing
+// and timing, never for a kernel.  The unit is bit for bit the one the full
+// plan with the same N and options holds at that order.
+struct OrderBuild {
+  Unit unit{};
+  std::vector<Op> ops;
+  int64_t n_factors = 0;  // doubles in the unit's factor store
+  int64_t n_idbf = 0, n_low = 0, n_dense = 0, n_drop = 0;
+  int64_t e_idbf = 0, e_low = 0, e_dense = 0;
+  int64_t max_rank = 0;
+  double t_mat_s = 0.0, t_fac_s = 0.0;
+};
+
+// Build the orders |m| = am[0..count) (each in [0, 2N)) of an N plan, one
+// host thread per order, the orders in parallel.
+sht_status build_orders(int N, const sht_opts& opts, int count, const int* am, std::vector<OrderBuild>& out);
 
 // Check that a program is internally consistent: unit layouts, op and phase
 // ranges, factor offsets and the schedule.  Every program the kernels see

@@ -20,6 +20,10 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
+#include <new>
+#include <utility>
+#include <vector>
 
 namespace sht {
 
@@ -53,5 +57,31 @@ struct Unit {
   float cost;             // estimated flops per right-hand side
 };
 static_assert(sizeof(Unit) == 56, "Unit layout");
+
+// Allocator whose argument-less construction leaves an element uninitialised,
+// so that resizing a store of many GB does not have one thread zero it (and
+// touch every page) before the threads that fill it run.  Every element of a
+// container using it must be written before it is read.
+template <class T>
+struct UninitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = UninitAlloc<U>;
+  };
+  UninitAlloc() = default;
+  template <class U>
+  UninitAlloc(const UninitAlloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+
+// The FP64 factor store of a program: packed blocks, column-major.
+using FactorStore = std::vector<double, UninitAlloc<double>>;
 
 }  // namespace sht
