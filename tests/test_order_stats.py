@@ -143,3 +143,15 @@ def test_estimate_is_exact_with_every_order_and_close_with_a_sample():
     assert not part["exact"] and part["orders_sampled"] == 32
     for k in ("entries_total", "entries_matrix", "factor_doubles", "image_elems"):
         assert abs(part["totals"][k] / full["totals"][k] - 1) < 0.05, k
+
+
+def test_command_line(capsys):
+    import json
+    from paper_2004_11346_gb300 import orders
+    orders.main(["--N", "32", "--eps", "1e-7", "--sample", "8"])
+    d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert d["N"] == 32 and d["orders_sampled"] == 8 and 0 < d["stored_over_matrix"] <= 1.5
+    assert d["factor_bytes"]["fp64"] == 2 * d["factor_bytes"]["fp32"]
+    orders.main(["--N", "32", "--eps", "1e-7", "--at", "0,0.5,1,1.5,2"])
+    rows = [json.loads(l) for l in capsys.readouterr().out.strip().splitlines()]
+    assert [r["am"] for r in rows] == [0, 16, 32, 48, 63]
