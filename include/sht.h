@@ -141,6 +141,10 @@ typedef struct {
   int64_t factor_doubles;    /* the order's FP64 factor store, padding included */
   int64_t image_elems;       /* BF16 elements of the order's tensor-core operand
                                 images, both directions (SHT_MIXED plans)       */
+  /* the tensor-core kernel's work for one forward apply of one 32-field group:
+   * pipeline stages (128-row tiles x 32-wide K chunks), tiles, bytes of the
+   * forward operand images and of the activation row groups the stages copy */
+  int64_t tc_stages, tc_tiles, tc_image_fwd_bytes, tc_act_bytes;
   int64_t max_rank;
   int64_t n_ops;             /* block products of the order's apply program     */
   int64_t n_phases;

@@ -90,6 +90,10 @@ class sht_order_info(ctypes.Structure):
         ("entries_matrix", ctypes.c_int64),
         ("factor_doubles", ctypes.c_int64),
         ("image_elems", ctypes.c_int64),
+        ("tc_stages", ctypes.c_int64),
+        ("tc_tiles", ctypes.c_int64),
+        ("tc_image_fwd_bytes", ctypes.c_int64),
+        ("tc_act_bytes", ctypes.c_int64),
         ("max_rank", ctypes.c_int64),
         ("n_ops", ctypes.c_int64),
         ("n_phases", ctypes.c_int64),

@@ -78,28 +78,47 @@ def candidates(N: int, eps: float):
     return out
 
 
-def rank(N: int, eps: float, cands=None, **plan_kw):
-    """Host-only plans for every candidate, ranked by model_cost (best first)."""
+def sampled_work_model(N: int, eps: float, sample: int, **plan_kw):
+    """work_model and stored entries of the plan with these options, summed
+    over a stratified sample of `sample` orders built one by one on the host
+    (sht_order_stats; exact when sample >= 2N).  A full host plan at large N
+    holds its whole FP64 factor store in memory; a sample holds a few orders."""
+    from . import opts, orders
+    est = orders.estimate(N, eps, sample, opts(N, eps, precision=_lib.SHT_MIXED, **plan_kw))
+    t = est["totals"]
+    w = {"stages": t["tc_stages"], "tiles": t["tc_tiles"], "image_bytes": t["tc_image_fwd_bytes"],
+         "activation_bytes": t["tc_act_bytes"]}
+    return w, t["entries_total"]
+
+
+def rank(N: int, eps: float, cands=None, sample: int | None = None, **plan_kw):
+    """Every candidate ranked by model_cost (best first): from a host-only
+    plan of each, or, with `sample`, from that many sampled orders."""
     from . import Plan
     rows = []
     for n0, nl in cands or candidates(N, eps):
-        p = Plan(N, eps, flags=_lib.SHT_FLAG_HOST_ONLY, precision=_lib.SHT_MIXED, n0=n0, n_leaf=nl, **plan_kw)
-        w = work_model(p.program(("ops",))["ops"])
-        st = p.stats()
-        rows.append({"n0": n0, "n_leaf": nl, "entries": int(st["entries_total"]), **w, "model_us": model_cost(w)})
-        p.close()
+        if sample:
+            w, entries = sampled_work_model(N, eps, sample, n0=n0, n_leaf=nl, **plan_kw)
+        else:
+            p = Plan(N, eps, flags=_lib.SHT_FLAG_HOST_ONLY, precision=_lib.SHT_MIXED, n0=n0, n_leaf=nl, **plan_kw)
+            w = work_model(p.program(("ops",))["ops"])
+            entries = int(p.stats()["entries_total"])
+            p.close()
+        rows.append({"n0": n0, "n_leaf": nl, "entries": int(entries), **w, "model_us": model_cost(w)})
     rows.sort(key=lambda r: r["model_us"])
     return rows
 
 
-def autotune(N: int, eps: float, fields: int, top: int = 3, steps: int = 3, cands=None, seed: int = 0):
-    """Rank the candidates by the work model, time the best `top` of them on
-    the current CUDA device (forward + inverse ALT of `fields` random fields,
-    CUDA events, after a warm-up) and return (best Plan, table of all rows).
-    The returned plan is built on the device with the winning parameters."""
+def autotune(N: int, eps: float, fields: int, top: int = 3, steps: int = 3, cands=None, seed: int = 0,
+             sample: int | None = None):
+    """Rank the candidates by the work model (from sampled orders when
+    `sample` is given), time the best `top` of them on the current CUDA
+    device (forward + inverse ALT of `fields` random fields, CUDA events,
+    after a warm-up) and return (best Plan, table of all rows).  The returned
+    plan is built on the device with the winning parameters."""
     import torch
     from . import Plan
-    rows = rank(N, eps, cands, max_fields=fields)
+    rows = rank(N, eps, cands, sample=sample, max_fields=fields)
     g = torch.Generator(device="cuda").manual_seed(seed)
     beta = torch.randn((fields, 4 * N * N, 2), dtype=torch.float64, device="cuda", generator=g)
     gv = torch.empty((fields, 4 * N - 1, 2 * N, 2), dtype=torch.float64, device="cuda")
@@ -141,9 +160,16 @@ def main(argv=None):
     ap.add_argument("--top", type=int, default=3)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--cands", default=None, help="n0:n_leaf,... to rank instead of the default grid")
+    ap.add_argument("--sample", type=int, default=None,
+                    help="rank from this many sampled orders instead of full host-only plans")
+    ap.add_argument("--rank-only", action="store_true", help="print the model's ranking only (no GPU)")
     a = ap.parse_args(argv)
     cands = [tuple(int(v) for v in c.split(":")) for c in a.cands.split(",")] if a.cands else None
-    plan, rows = autotune(a.N, a.eps, a.fields, top=a.top, steps=a.steps, cands=cands)
+    if a.rank_only:
+        for r in rank(a.N, a.eps, cands, sample=a.sample, max_fields=a.fields):
+            print(json.dumps(r), flush=True)
+        return
+    plan, rows = autotune(a.N, a.eps, a.fields, top=a.top, steps=a.steps, cands=cands, sample=a.sample)
     for r in rows:
         print(json.dumps(r), flush=True)
     print(json.dumps({"best": {"n0": int(plan.opts.n0), "n_leaf": int(plan.opts.n_leaf)}, "N": a.N, "eps": a.eps,

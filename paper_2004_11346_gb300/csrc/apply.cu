@@ -715,9 +715,18 @@ sht_status sht_order_stats(int N, double eps, const sht_opts* opts, int count, c
     q.entries_total = r.e_idbf + r.e_low + r.e_dense;
     q.entries_matrix = (int64_t)N * (r.unit.nce + r.unit.nco);
     q.factor_doubles = r.n_factors;
-    for (const Op& op : r.ops)
-      q.image_elems += (int64_t)tc_image_elems(op.mo, tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1])) +
-                       (int64_t)tc_image_elems(op.ni, tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1]));
+    for (const Op& op : r.ops) {
+      const TcKGeom kf = tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1]);
+      const int64_t fwd = (int64_t)tc_image_elems(op.mo, kf);
+      q.image_elems += fwd + (int64_t)tc_image_elems(op.ni, tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1],
+                                                                       op.out_len[1]));
+      if (op.ni <= 0) continue;
+      const int64_t nt = (op.mo + kTcNT - 1) / kTcNT;
+      q.tc_stages += nt * kf.nK;
+      q.tc_tiles += nt;
+      q.tc_image_fwd_bytes += 2 * fwd;
+      q.tc_act_bytes += nt * kf.ngt * (int64_t)kTcGrpBytes;
+    }
     q.max_rank = r.max_rank;
     q.n_ops = (int64_t)r.ops.size();
     q.n_phases = r.unit.nphase;

@@ -23,7 +23,7 @@ from . import _lib
 
 SUMMED = ("n_blocks_idbf", "n_blocks_lowrank", "n_blocks_dense", "n_blocks_dropped", "entries_idbf",
           "entries_lowrank", "entries_dense", "entries_total", "entries_matrix", "factor_doubles", "image_elems",
-          "n_ops", "t_mat_s", "t_fac_s")
+          "tc_stages", "tc_tiles", "tc_image_fwd_bytes", "tc_act_bytes", "n_ops", "t_mat_s", "t_fac_s")
 
 
 def sample_orders(N: int, count: int):

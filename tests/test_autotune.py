@@ -53,3 +53,31 @@ def test_rank_is_sorted_by_model():
     costs = [r["model_us"] for r in rows]
     assert costs == sorted(costs)
     assert all(r["entries"] > 0 and r["stages"] > 0 for r in rows)
+
+
+def test_sampled_work_model_is_exact_with_every_order():
+    N, kw = 64, dict(n0=16, n_leaf=8)
+    p = sht.Plan(N, 1e-7, flags=HOST, precision=_lib.SHT_MIXED, **kw)
+    full = autotune.work_model(p.program(("ops",))["ops"])
+    w, entries = autotune.sampled_work_model(N, 1e-7, 2 * N, **kw)
+    assert w == full
+    assert entries == p.stats()["entries_total"]
+
+
+def test_sampled_work_model_is_close_with_a_sample():
+    N = 256
+    p = sht.Plan(N, 1e-7, flags=HOST, precision=_lib.SHT_MIXED)
+    full = autotune.work_model(p.program(("ops",))["ops"])
+    w, _ = autotune.sampled_work_model(N, 1e-7, 32)
+    for k in full:
+        assert abs(w[k] / full[k] - 1) < 0.05, (k, w[k], full[k])
+
+
+def test_rank_from_samples(capsys):
+    import json
+    cands = [(16, 8), (32, 8), (32, 16)]
+    rows = autotune.rank(64, 1e-7, cands, sample=128)
+    assert rows == autotune.rank(64, 1e-7, cands)  # 128 = 2N: every order
+    autotune.main(["--N", "64", "--eps", "1e-7", "--cands", "16:8,32:16", "--sample", "16", "--rank-only"])
+    out = [json.loads(l) for l in capsys.readouterr().out.strip().splitlines()]
+    assert len(out) == 2 and out[0]["model_us"] <= out[1]["model_us"]
