@@ -108,6 +108,12 @@ def test_alf_closed_forms():
     # range; the value at k = 2047 is O(1): needs the extended exponent
     (2047, 700, Fraction(15, 16)),
     (2047, 1200, Fraction(31, 32)),
+    # degrees of an N = 4096 transform: start Pbar_7000^7000(1/2) ~ 1e-437, far
+    # outside FP64, value O(1); a value near the turning point; and one whose
+    # exact size (~5e-2547) has no FP64 representation, so the oracle gives 0
+    (8191, 7000, Fraction(1, 2)),
+    (8191, 7800, Fraction(1, 3)),
+    (8191, 7900, Fraction(9, 10)),
 ])
 def test_alf_against_exact_rational(k, m, x):
     ref = pbar_exact(k, m, x)
