@@ -65,8 +65,38 @@ inline void apply_reflector(Mat& A, int r0, const double* v, double tau, int c0,
   if (tau == 0.0) return;
   int n = A.r - r0;
   int j = c0;
-  // two columns per pass over v; each column's sums run in the same order as
-  // the one-column loop below, so the results are the same bit for bit
+  // four, then two columns per pass over v: independent sums keep the adder
+  // busy, and each column's sum runs in the same order as the one-column loop
+  // below, so the results are the same bit for bit
+  for (; j + 3 < c1; j += 4) {
+    double* a0 = A.col(j) + r0;
+    double* a1 = A.col(j + 1) + r0;
+    double* a2 = A.col(j + 2) + r0;
+    double* a3 = A.col(j + 3) + r0;
+    double d0 = a0[0], d1 = a1[0], d2 = a2[0], d3 = a3[0];
+    for (int i = 1; i < n; ++i) {
+      const double vi = v[i];
+      d0 += vi * a0[i];
+      d1 += vi * a1[i];
+      d2 += vi * a2[i];
+      d3 += vi * a3[i];
+    }
+    d0 *= tau;
+    d1 *= tau;
+    d2 *= tau;
+    d3 *= tau;
+    a0[0] -= d0;
+    a1[0] -= d1;
+    a2[0] -= d2;
+    a3[0] -= d3;
+    for (int i = 1; i < n; ++i) {
+      const double vi = v[i];
+      a0[i] -= d0 * vi;
+      a1[i] -= d1 * vi;
+      a2[i] -= d2 * vi;
+      a3[i] -= d3 * vi;
+    }
+  }
   for (; j + 1 < c1; j += 2) {
     double* a0 = A.col(j) + r0;
     double* a1 = A.col(j + 1) + r0;
