@@ -815,13 +815,15 @@ struct PlanWriter {
 
 struct PlanReader {
   std::FILE* f;
+  uint64_t left;  // bytes of the file not read yet
   uint64_t h = 0xcbf29ce484222325ull;
   bool ok = true;
   void get(void* dst, size_t n) {
-    if (!ok || (n && std::fread(dst, 1, n, f) != n)) {
+    if (!ok || n > left || (n && std::fread(dst, 1, n, f) != n)) {
       ok = false;
       return;
     }
+    left -= n;
     const unsigned char* b = static_cast<const unsigned char*>(dst);
     for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001b3ull;
   }
@@ -829,7 +831,8 @@ struct PlanReader {
   void vec(std::vector<T, A>& v, uint64_t max_elems) {
     uint64_t n = 0;
     get(&n, sizeof n);
-    if (!ok || n > max_elems) {
+    // a count the rest of the file cannot hold is refused before any allocation
+    if (!ok || n > max_elems || n > left / sizeof(T)) {
       ok = false;
       return;
     }
@@ -880,7 +883,13 @@ sht_status sht_plan_load(const char* path, sht_plan_t* out) {
     return SHT_ERR_OOM;
   }
   HostProgram& P = p->prog;
-  PlanReader r{f};
+  uint64_t file_bytes = 0;
+  if (std::fseek(f, 0, SEEK_END) == 0) {
+    const long end = std::ftell(f);
+    file_bytes = end > 0 ? (uint64_t)end : 0;
+  }
+  std::rewind(f);
+  PlanReader r{f, file_bytes};
   char magic[8];
   uint32_t hdr[5];
   int32_t nm[2];
@@ -920,6 +929,11 @@ sht_status sht_plan_load(const char* path, sht_plan_t* out) {
                       (P.opts.precision != SHT_FP64 && P.opts.precision != SHT_FP32 &&
                        P.opts.precision != SHT_MIXED) ||
                       !validate_program(P, err)))
+    s = SHT_ERR_IO;
+  // the statistics' identity fields must describe this program: callers size
+  // their buffers from sht_plan_stats().N
+  if (s == SHT_OK && (P.info.N != P.N || P.info.n_units != 2 * (int64_t)P.N ||
+                      P.info.n_ops != (int64_t)P.ops.size() || !(P.info.eps == P.opts.eps)))
     s = SHT_ERR_IO;
   if (s == SHT_OK) {
     if (P.opts.flags & SHT_FLAG_HOST_ONLY) {

@@ -4,7 +4,11 @@ Host-side: a saved and reloaded plan exports the same program byte for byte
 and still reproduces the oracle through the test-only numpy apply; missing,
 truncated, damaged and foreign files are refused with SHT_ERR_IO, including a
 file whose checksum was recomputed over a program that addresses factors past
-the end of the store (the consistency check, not the checksum, catches it).
+the end of the store (the consistency check, not the checksum, catches it),
+statistics that name another N than the program, and element counts larger
+than the rest of the file (refused before allocating).  Random forgeries of
+the metadata with matching checksums are refused or load a program that
+passes an independent bounds check.
 GPU: a loaded plan of each precision gives the original plan's results.
 """
 import struct
@@ -113,6 +117,102 @@ def test_consistent_checksum_but_invalid_program(saved, tmp_path):
     orig = open(path, "rb").read()
     good.write_bytes(orig[:-8] + struct.pack("<Q", fnv1a(orig[:-8])))
     assert sht.Plan.load(str(good)).N == p.N
+
+
+def test_statistics_must_describe_the_program(saved, tmp_path):
+    """The statistics stored in the file carry N, which callers use to size
+    their buffers: a file whose statistics name another N (or op count) than
+    its program is refused even with a matching checksum."""
+    import ctypes
+    p, path = saved
+    raw = open(path, "rb").read()
+    info = HEADER + ctypes.sizeof(_lib.sht_opts)  # sht_plan_info follows the options
+    assert struct.unpack_from("<i", raw, info)[0] == p.N
+    n_ops = info + _lib.sht_plan_info.n_ops.offset
+    for field, value, fmt in ((info, p.N - 8, "<i"), (info, p.N + 8, "<i"), (n_ops, 1, "<q")):
+        b = bytearray(raw)
+        struct.pack_into(fmt, b, field, value)
+        body = bytes(b[:-8])
+        bad = tmp_path / "stats.plan"
+        bad.write_bytes(body + struct.pack("<Q", fnv1a(body)))
+        expect_io(bad)
+
+
+def test_counts_beyond_the_file_are_refused(saved, tmp_path):
+    """An element count larger than the rest of the file is refused before
+    anything is allocated (here: 2^39 ops, 32 TB)."""
+    p, path = saved
+    raw = bytearray(open(path, "rb").read())
+    at = bytes(raw).find(p.program(("ops",))["ops"].tobytes())
+    struct.pack_into("<Q", raw, at - 8, 1 << 39)
+    body = bytes(raw[:-8])
+    bad = tmp_path / "count.plan"
+    bad.write_bytes(body + struct.pack("<Q", fnv1a(body)))
+    expect_io(bad)
+
+
+def check_bounds(q):
+    """What the kernels rely on, restated independently of the library's check."""
+    P = q.program(("units", "ops", "phases", "factors", "order"))
+    N = q.N
+    u, o, ph, f = P["units"], P["ops"], P["phases"], P["factors"]
+    assert len(u) == 2 * N and sorted(P["order"]) == list(range(2 * N))
+    for a in range(2 * N):
+        U = u[a]
+        assert U["am"] == a and 0 <= U["op_begin"] <= U["op_end"] <= len(o)
+        assert U["ph_begin"] >= 0 and U["ph_begin"] + U["nphase"] + 1 <= len(ph)
+        for op in o[U["op_begin"]: U["op_end"]]:
+            assert op["ld"] >= op["mo"] >= 1 and op["b_off"] >= 0
+            assert op["b_off"] + int(op["ld"]) * int(op["ni"]) <= len(f)
+            assert op["in_len"].sum() == op["ni"] and op["out_len"].sum() == op["mo"]
+            for s in range(2):
+                assert op["in_len"][s] >= 0 and 0 <= op["in_off"][s] <= U["nrows"] - op["in_len"][s]
+                assert op["out_len"][s] >= 0 and 0 <= op["out_off"][s] <= U["nrows"] - op["out_len"][s]
+            assert 0 <= op["phase"] < U["nphase"]
+
+
+def test_forged_metadata_is_refused_or_safe(tmp_path):
+    """Random changes to the header, options, statistics, units, ops, phase
+    table and schedule of a file, resealed with a matching checksum: every
+    file either is refused or loads a program that passes check_bounds."""
+    import random
+    p = sht.Plan(12, 1e-10, flags=HOST | _lib.SHT_FLAG_FORCE_FACTOR, n0=6, n_leaf=3)
+    path = tmp_path / "small.plan"
+    p.save(str(path))
+    raw = open(path, "rb").read()
+    body0 = raw[:-8]
+    prog = p.program(("units", "ops", "phases", "order"))
+    regions = [(0, HEADER + 200)]
+    for k in ("units", "ops", "phases", "order"):
+        b = prog[k].tobytes()
+        at = body0.find(b)
+        assert at > 0
+        regions.append((at - 8, at + len(b)))
+    rng = random.Random(2004)
+    vals = [0, 1, -1, 2, 7, 8, 9, 63, 64, 65, 1 << 15, 1 << 30, -(1 << 31), (1 << 31) - 1]
+    outcomes = {}
+    for t in range(150):
+        b = bytearray(body0)
+        for _ in range(rng.randint(1, 2)):
+            lo, hi = rng.choice(regions)
+            off = rng.randrange(lo, hi - 4) & ~3
+            if rng.random() < 0.5:
+                struct.pack_into("<i", b, off, rng.choice(vals))
+            else:
+                struct.pack_into("<i", b, off, struct.unpack_from("<i", b, off)[0] + rng.choice([-9, -8, -1, 1, 8, 9]))
+        body = bytes(b)
+        f = tmp_path / "forged.plan"
+        f.write_bytes(body + struct.pack("<Q", fnv1a(body)))
+        try:
+            q = sht.Plan.load(str(f))
+        except _lib.ShtError as e:
+            assert e.status in (_lib.SHT_ERR_IO, _lib.SHT_ERR_OOM, _lib.SHT_ERR_CUDA), e.status
+            outcomes[e.status] = outcomes.get(e.status, 0) + 1
+            continue
+        check_bounds(q)
+        outcomes["loaded"] = outcomes.get("loaded", 0) + 1
+        q.close()
+    assert outcomes.get(_lib.SHT_ERR_IO, 0) > 50 and outcomes.get("loaded", 0) > 5
 
 
 def test_intermediate_segments_must_start_on_row_groups(tmp_path):
