@@ -8,7 +8,8 @@ and inverse ALT to the scale of its tolerance: the IDs, the randomized SVD
 so the transform of N(0,1) coefficients stays at the scale of eps: bounded
 here by 10 eps (over 250 random option sets the largest relative error seen
 was 0.8 eps), far below what a dropped block or a misplaced product would
-cause.  Plans with the same options and seed are identical.
+cause.  Plans with the same options and seed are identical, and single
+orders built on their own (sht_order_stats) match the plan's units.
 """
 import numpy as np
 import pytest
@@ -61,3 +62,13 @@ def test_random_plans_reproduce_the_oracle(case):
     q = sht.Plan(N, eps, **kw).program()
     for part in ("units", "ops", "factors"):
         assert prog[part].tobytes() == q[part].tobytes()
+    # an order built on its own is the plan's unit at that order
+    units = prog["units"]
+    blocks = p.program(("unit_blocks",))["unit_blocks"].reshape(-1, 4)
+    ms = sorted({0, N, 2 * N - 1, N // 2})
+    for r in _lib.sht_order_stats(N, eps, ms, sht.opts(N, eps, **kw)):
+        u = units[r["am"]]
+        assert (r["n_ops"], r["rows"], r["n_phases"]) == (u["op_end"] - u["op_begin"], u["nrows"], u["nphase"])
+        assert r["flops_per_rhs"] == float(u["cost"])
+        assert (r["n_blocks_idbf"], r["n_blocks_lowrank"], r["n_blocks_dense"], r["n_blocks_dropped"]) == \
+            tuple(int(v) for v in blocks[r["am"]])
