@@ -231,9 +231,11 @@ sht_status sht_plan_save(sht_plan_t plan, const char* path);
 /* Load a plan written by sht_plan_save and upload it to the current device
  * (host-only plans stay host-only).  The file is checked (magic, version,
  * struct sizes, checksum, and the same consistency check every built program
- * passes: unit layouts, op ranges, factor offsets, schedule) before anything
- * reaches the GPU: SHT_ERR_IO for a missing, damaged or foreign file,
- * SHT_ERR_CUDA without a device.  The caller owns the new plan. */
+ * passes: unit layouts, op ranges, factor offsets, schedule; statistics that
+ * describe that program) before anything reaches the GPU, and no array is
+ * allocated larger than the rest of the file could hold: SHT_ERR_IO for a
+ * missing, damaged or foreign file, SHT_ERR_CUDA without a device.  The
+ * caller owns the new plan. */
 sht_status sht_plan_load(const char* path, sht_plan_t* out);
 
 /* Batches of transforms of different orders N in one launch.  Sec. 1 states
