@@ -703,7 +703,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--ref-stride", type=int, default=4, help="oracle samples every n-th order")
+    ap.add_argument("--ref-stride", type=int, default=8, help="oracle samples every n-th order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 IDBF and dense comparators")
     ap.add_argument("--n0", type=int, default=None, help="override the workload's partition stop size n0")
