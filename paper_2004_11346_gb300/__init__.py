@@ -96,7 +96,7 @@ class Plan:
                  "phases": (_lib.SHT_EXPORT_PHASES, np.int32), "factors": (_lib.SHT_EXPORT_FACTORS, np.float64),
                  "order": (_lib.SHT_EXPORT_ORDER, np.int32),
                  "unit_blocks": (_lib.SHT_EXPORT_UNIT_BLOCKS, np.int32)}
-        return {k: np.frombuffer(_lib.sht_plan_export(self.handle, kinds[k][0]), dtype=kinds[k][1]) for k in parts}
+        return {k: _lib.sht_plan_export(self.handle, kinds[k][0]).view(kinds[k][1]) for k in parts}
 
     # ---- device entry points (torch tensors)
     @staticmethod

@@ -201,12 +201,14 @@ def sht_plan_nodes(plan: int, x_host: int, w_host: int):
     check(load().sht_plan_nodes(plan, x_host, w_host), "sht_plan_nodes")
 
 
-def sht_plan_export(plan: int, what: int) -> bytes:
+def sht_plan_export(plan: int, what: int):
+    """The exported array's bytes, copied once into a new numpy uint8 array."""
+    import numpy as np
     n = ctypes.c_size_t(0)
     check(load().sht_plan_export(plan, what, None, ctypes.byref(n)), "sht_plan_export")
-    buf = ctypes.create_string_buffer(max(1, n.value))
-    check(load().sht_plan_export(plan, what, buf, ctypes.byref(n)), "sht_plan_export")
-    return buf.raw[: n.value]
+    buf = np.empty(max(1, n.value), dtype=np.uint8)
+    check(load().sht_plan_export(plan, what, buf.ctypes.data, ctypes.byref(n)), "sht_plan_export")
+    return buf[: n.value]
 
 
 def sht_plan_save(plan: int, path: str):
