@@ -2,9 +2,10 @@
 
 Bremer, Chen & Yang, arXiv:2004.11346.  The transform runs in libsht.so
 (CUDA kernels for sm_103a behind the C ABI of include/sht.h); this package
-holds the ctypes binding (``_lib``), a torch-tensor convenience wrapper
-(``Plan``), the in-tree build (``build``) and the seeded input generators
-(``inputs``).
+holds the ctypes binding (``_lib``), torch-tensor convenience wrappers
+(``Plan``, ``Batch``), the in-tree build (``build``), the seeded input
+generators (``inputs``), the plan-parameter autotuner (``autotune``) and the
+per-order statistics and plan sizing (``orders``).
 """
 from __future__ import annotations
 
