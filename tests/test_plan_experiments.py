@@ -1,15 +1,24 @@
-"""The paper's plan experiment on block counts (Sec. 5, first experiment), CPU.
+"""The paper's plan experiments of Sec. 5 that need no timing, CPU.
 
-After the blocks that hold no non-negligible entry are dropped, the number of
-remaining blocks of one order grows nearly linearly with N, for m = N/2, N and
-3N/2 (the paper's figure of block counts; its data is not printed).  Here with
-the partition's stop size fixed (n0 = 32) as in the paper (n0 = 512 over its
-larger N), so that deeper partitions come from N alone.
+Block counts: after the blocks that hold no non-negligible entry are dropped,
+the number of remaining blocks of one order grows nearly linearly with N, for
+m = N/2, N and 3N/2 (the paper's figure of block counts; its data is not
+printed).  Here with the partition's stop size fixed (n0 = 32) as in the paper
+(n0 = 512 over its larger N), so that deeper partitions come from N alone.
+
+Error against the order: the paper's relative errors of the forward and
+inverse ALT of one order, over 256 sampled rows (nodes, resp. degrees) of the
+even or odd matrix (its eps^fwd and eps^inv), are not affected by m: every
+order stays within the tolerance, and none is less accurate than m = 0.
+order_errors computes them for the matrices a plan represents, against the
+oracle's.
 """
 import numpy as np
 
+import oracle
 import paper_2004_11346_gb300 as sht
 from paper_2004_11346_gb300 import _lib
+from test_factorization import represented
 
 HOST = _lib.SHT_FLAG_HOST_ONLY
 
@@ -41,3 +50,44 @@ def test_loaded_plans_have_no_block_counts(tmp_path):
     p.save(path)
     q = sht.Plan.load(path)
     assert q.program(("unit_blocks",))["unit_blocks"].size == 0
+
+
+def order_errors(p, prog, am, rng):
+    """[(eps_fwd, eps_inv)] of the even and odd matrix of order |m| = am:
+    random N(0,1) right-hand sides (Re, Im), 256 sampled rows (or all)."""
+    N = p.N
+    x, w = p.nodes()
+    xp, wp = x[N:], w[N:]
+    T = oracle.alf_table(am, 2 * N - 1, xp)
+    ae, ao, _, _ = represented(prog, prog["units"][am])
+    out = []
+    for pm, ref in ((ae, T[:, 0::2]), (ao, T[:, 1::2])):
+        if ref.size == 0:
+            continue
+        xv = rng.standard_normal((ref.shape[1], 2))
+        s1 = rng.choice(N, min(256, N), replace=False)
+        gb, gd = (pm @ xv)[s1], (ref @ xv)[s1]
+        gv = rng.standard_normal((N, 2)) * wp[:, None]
+        s2 = rng.choice(ref.shape[1], min(256, ref.shape[1]), replace=False)
+        ab, ad = (pm.T @ gv)[s2], (ref.T @ gv)[s2]
+        out.append((float(np.sqrt(((gb - gd) ** 2).sum() / (gd ** 2).sum())),
+                    float(np.sqrt(((ab - ad) ** 2).sum() / (ad ** 2).sum()))))
+    return out
+
+
+def test_error_does_not_depend_on_the_order():
+    # factored blocks kept even where they are larger than dense, so that
+    # every order has IDBF blocks at this small N
+    N, eps = 128, 1e-10
+    p = sht.Plan(N, eps, flags=HOST | _lib.SHT_FLAG_FORCE_FACTOR)
+    prog = p.program()
+    rng = np.random.default_rng(0)
+    ams = [min(2 * N - 1, int(f * N)) for f in (0, 0.5, 1.0, 1.5)]
+    errs = {am: order_errors(p, prog, am, rng) for am in ams}
+    flat = [e for v in errs.values() for pair in v for e in pair]
+    assert max(flat) <= 2 * eps, errs
+    # no order is less accurate than m = 0, whose matrices are single
+    # butterflies of the greatest depth (larger orders hold smaller, shallower
+    # ones next to trimmed turning-point blocks)
+    worst = [max(e for pair in errs[am] for e in pair) for am in ams]
+    assert max(worst[1:]) <= 1.5 * worst[0], errs
