@@ -152,21 +152,31 @@ def sample_orders(N, stride):
     return list(range(0, 2 * N, stride))
 
 
-def oracle_sample(N, beta_field, stride):
+def oracle_sample(N, beta_field, stride, g_check=None):
     """Forward + inverse ALT by the oracle for every stride-th order |m| (both
-    signs); returns (seconds, fraction of the full transform's work)."""
+    signs); returns (seconds, fraction of the full transform's work), plus,
+    when g_check (one field's ALT values, (4N-1, 2N, 2)) is given, the
+    per-order relative errors of g_check against the oracle's forward values
+    (compared after the timed loop)."""
     import oracle
     x, w = oracle.gl_rule(2 * N)
     ams = sample_orders(N, stride)
+    keep = {}
     t0 = time.perf_counter()
     for am in ams:
         for m in ([am, -am] if am else [0]):
             off = oracle.coef_offset(N, m)
             gm = oracle.alt_forward_m(N, m, beta_field[off: off + 2 * N - am], x)
             oracle.alt_inverse_m(N, m, gm, x, w)
+            if g_check is not None:
+                keep[m] = gm
     dt = time.perf_counter() - t0
     work_s = sum((2 * N - am) * (1 if am == 0 else 2) for am in ams)
-    return dt, work_s / (4.0 * N * N)
+    if g_check is None:
+        return dt, work_s / (4.0 * N * N)
+    errs = [float(np.linalg.norm(g_check[oracle.order_slot(m)] - ref) / np.linalg.norm(ref))
+            for m, ref in keep.items()]
+    return dt, work_s / (4.0 * N * N), errs
 
 
 def run_reference(args):
@@ -243,6 +253,37 @@ def time_steps(torch, plan, beta, g, back, K, W, stream):
     fwd = float(np.mean([ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]))
     inv = float(np.mean([ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]))
     return ms, fwd, inv
+
+
+def time_graph(torch, plan, beta, g, back, K, W, stream):
+    """The step (forward then inverse ALT) captured once in a CUDA graph, then
+    W untimed and K timed replays, each bracketed by CUDA events on the
+    replaying stream.  Returns (median ms, mean ms over the K-step region)."""
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):  # warm the capture stream's state once, outside the capture
+        plan.forward(beta, out=g)
+        plan.inverse(g, out=back)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.forward(beta, out=g)
+        plan.inverse(g, out=back)
+    torch.cuda.synchronize()
+    for _ in range(W):
+        graph.replay()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    rs = torch.cuda.current_stream()
+    ev[0].record(rs)
+    for i in range(K):
+        graph.replay()
+        ev[i + 1].record(rs)
+    torch.cuda.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
+    del graph
+    return float(np.median(per)), ev[0].elapsed_time(ev[K]) / K
 
 
 def run_e2e(torch, plan, beta_h, g, K, W, barrier, chunk=32):
@@ -349,17 +390,22 @@ def run_ours(args):
     rt_err = float((back - beta).norm() / beta.norm())
 
     K = args.steps
+    kernels_per_call = 2 if w["precision"] == "mixed" else 1  # tensor-core kernel + output kernel
+    # headline: K replays of the step captured in a CUDA graph, the library's
+    # event instrumentation paused; value from the median replay
+    plan.set_timing(False)
     barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(dev_index)
     time.sleep(0.3)
-    plan.kernel_time(reset=True)
-    ms, fwd_ms, inv_ms = time_steps(torch, plan, beta, g, back, K, 0, stream)
+    ms, ms_mean = time_graph(torch, plan, beta, g, back, K, max(3, args.warmup), stream)
     clk = clocks.stop()
-    kt = plan.kernel_time(reset=True)
-    kernels_per_call = 2 if w["precision"] == "mixed" else 1  # tensor-core kernel + output kernel
-    launches = kt["launches"] * kernels_per_call
-    # the dominant kernel alone, forward direction, on the same stream
+    launches = K * 2 * kernels_per_call  # forward + inverse per step
+    plan.set_timing(True)
+    # separate pass: forward / inverse split and the dominant kernel alone
+    # (library CUDA events around each kernel, on the launching stream)
+    _, fwd_ms, inv_ms = time_steps(torch, plan, beta, g, back, K, 1, stream)
+    plan.kernel_time(reset=True)
     for _ in range(K):
         plan.forward(beta, out=g)
     kf = plan.kernel_time(reset=True)
@@ -367,7 +413,7 @@ def run_ours(args):
     out_ms = kf["output_ms"] / max(1, kf["launches"])
     barrier()
     plan.sync()
-    ms, fwd_ms, inv_ms = max_over_ranks([ms, fwd_ms, inv_ms])
+    ms, ms_mean, fwd_ms, inv_ms = max_over_ranks([ms, ms_mean, fwd_ms, inv_ms])
     value = world * F / (ms * 1e-3)
 
     # end to end through the public API: every step copies the batch in from
@@ -382,7 +428,9 @@ def run_ours(args):
     roof = roofline(plan, w, F, flops, fwd_ms, main_ms, out_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms, "ms_per_step_mean": ms_mean,
+        "timing": f"median of {K} CUDA-graph replays of the step (event-timed each), instrumentation off",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "bf16x3 split, f32 accumulate"}[w["precision"]],
         "data": "synthetic", "config": config_of(w, world),
         "forward_ms": fwd_ms, "inverse_ms": inv_ms,
@@ -403,12 +451,23 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_compare:
         line["compare"] = compare(torch, sht, _lib, w, plan, beta, g, args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, frac = oracle_sample(N, beta_h[0], args.ref_stride)
+        # the oracle's forward outputs of the timed sample double as a parity
+        # check of this run's forward ALT of field 0 at those orders
+        plan.forward(beta, out=g)
+        torch.cuda.synchronize()
+        g0 = g[0].cpu().numpy()
+        dt, frac, errs = oracle_sample(N, beta_h[0], args.ref_stride, g_check=g0)
         import oracle
         line["cpu_baseline"] = {
             "value": frac / dt, "unit": "fields/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"forward+inverse ALT of every {args.ref_stride}th order |m| of 1 field "
                       f"({frac:.3f} of the transform, {dt:.1f} s), scaled to one field"}
+        line["rel_err_vs_oracle"] = {
+            "forward_max_per_order": float(max(errs)), "forward_median_per_order": float(np.median(errs)),
+            "orders": len(errs), "field": 0,
+            "what": "per-order relative l2 error of this run's forward ALT against the oracle's outputs of the "
+                    "timed cpu_baseline sample (every sampled order, both signs); the tests check every "
+                    "field forward and inverse"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -429,6 +488,7 @@ def compare(torch, sht, _lib, w, plan, beta, g, args, stream):
     ms, f, i = time_steps(torch, p64, b1, g1, r1, K, 2, stream)
     out["fp64_idbf"] = {"fields_per_s": 1e3 / ms, "forward_ms": f, "inverse_ms": i, "eps": 1e-12,
                         "entries": p64.stats()["entries_total"], "t_fac_s": p64.stats()["t_factor_s"]}
+    ref = None
     if w["precision"] != "fp64":
         F = beta.shape[0]
         ref = torch.empty_like(g)
@@ -438,7 +498,25 @@ def compare(torch, sht, _lib, w, plan, beta, g, args, stream):
         d = (g - ref).reshape(F, -1).norm(dim=1) / ref.reshape(F, -1).norm(dim=1)
         out["rel_err_vs_fp64_idbf"] = {"max": float(d.max()), "median": float(d.median()),
                                        "fields": F, "per_field": [float(v) for v in d.tolist()]}
-        del ref
+        # like against like: the unfactored O(N^3) transform on the same
+        # tensor-core kernels and precision, same fields, same step
+        F = beta.shape[0]
+        pdm = sht.Plan(N, w["eps"], precision=_lib.SHT_MIXED, flags=_lib.SHT_FLAG_DENSE, max_fields=F)
+        back2 = torch.empty_like(beta)
+        med, mean = time_graph(torch, pdm, beta, g, back2, K, 2, stream)
+        pdm.forward(beta, out=g)
+        torch.cuda.synchronize()
+        pdm.sync()
+        d = (g - ref).reshape(F, -1).norm(dim=1) / ref.reshape(F, -1).norm(dim=1)
+        st = pdm.stats()
+        out["dense_mixed"] = {"fields_per_s": F / (med * 1e-3), "ms_per_step": med, "ms_per_step_mean": mean,
+                              "entries": st["entries_total"], "image_bytes": st["factor_bytes"],
+                              "rel_err_vs_fp64_idbf_max": float(d.max()),
+                              "what": "SHT_FLAG_DENSE plan, same tensor-core kernels, same 64 fields, "
+                                      "forward + inverse, median of CUDA-graph replays"}
+        del pdm, back2, ref
+        torch.cuda.empty_cache()
+    out["sht"] = sht_timings(torch, w, plan, beta, g, K, stream, p64=p64)
     del p64
     pd = sht.Plan(N, 1e-12, precision=_lib.SHT_FP64, flags=_lib.SHT_FLAG_DENSE)
     ms, f, i = time_steps(torch, pd, b1, g1, r1, K, 2, stream)
@@ -451,15 +529,16 @@ def compare(torch, sht, _lib, w, plan, beta, g, args, stream):
     fp, dn = out["fp64_idbf"], out["dense_fp64"]
     out["paper_ratios"] = {"t_dir_over_t_app": (dn["forward_ms"] + dn["inverse_ms"]) / (fp["forward_ms"] + fp["inverse_ms"]),
                            "t_mat_over_t_fac": dn["t_mat_s"] / fp["t_fac_s"] if fp["t_fac_s"] > 0 else None}
-    out["sht"] = sht_timings(torch, w, plan, beta, g, K, stream)
     return out
 
 
-def sht_timings(torch, w, plan, beta_in, g, K, stream):
+def sht_timings(torch, w, plan, beta_in, g, K, stream, p64=None):
     """The phi-direction DFT (synthesis + analysis) and the full SHT (ALT + DFT,
     both directions) of the same F fields, and cuFFT of the same batch of
-    length-(4N-1) complex FP64 transforms as a comparator (no half-sample
-    shift, no transpose: a lower bound on a library DFT of this layout)."""
+    length-(4N-1) transforms as comparators, precision against precision: the
+    plan's FP32 DFT against complex64 cuFFT, the FP64 plan's DFT against
+    complex128 cuFFT (cuFFT without the half-sample shift and the transpose:
+    a lower bound on a library DFT of this layout)."""
     N, F = w["N"], g.shape[0]
     f = torch.empty((F, 2 * N, 4 * N - 1, 2), dtype=torch.float64, device="cuda")
     g2 = torch.empty_like(g)
@@ -483,14 +562,25 @@ def sht_timings(torch, w, plan, beta_in, g, K, stream):
     plan.sync()
     sht_err = float((beta - beta_in).norm() / beta_in.norm())
     gc = torch.view_as_complex(g)
-    fft_ms = timed(lambda: (torch.fft.ifft(gc, dim=1), torch.fft.fft(gc, dim=1)))
+    fft128_ms = timed(lambda: (torch.fft.ifft(gc, dim=1), torch.fft.fft(gc, dim=1)))
+    g64 = gc.to(torch.complex64)
+    fft64_ms = timed(lambda: (torch.fft.ifft(g64, dim=1), torch.fft.fft(g64, dim=1)))
+    del g64
     phi_bytes = 2 * 2 * g.numel() * 8  # each direction reads and writes F x (4N-1) x 2N complex FP64
-    return {"phi_round_trip_ms": phi_ms, "phi_round_trip_rel_err": phi_err,
-            "phi_GBps": phi_bytes / (phi_ms * 1e-3) / 1e9,
-            "sht_round_trip_ms": sht_ms, "sht_fields_per_s": F / (sht_ms * 1e-3),
-            "sht_round_trip_rel_err": sht_err,
-            "cufft_c128_round_trip_ms": fft_ms,
-            "phi_arith": "f64" if w["precision"] == "fp64" else "f32"}
+    out = {"phi_round_trip_ms": phi_ms, "phi_round_trip_rel_err": phi_err,
+           "phi_GBps": phi_bytes / (phi_ms * 1e-3) / 1e9,
+           "phi_hbm_frac": phi_bytes / (phi_ms * 1e-3) / 1e9 / measured_peaks()["hbm"],
+           "sht_round_trip_ms": sht_ms, "sht_fields_per_s": F / (sht_ms * 1e-3),
+           "sht_round_trip_rel_err": sht_err,
+           "phi_arith": "f64" if w["precision"] == "fp64" else "f32",
+           "cufft_c64_round_trip_ms": fft64_ms, "cufft_c128_round_trip_ms": fft128_ms}
+    if p64 is not None and w["precision"] != "fp64":
+        # the FP64 plan's own phi transform on the same batch, against complex128 cuFFT
+        phi64_ms = timed(lambda: (p64.phi_synthesis(g, out=f), p64.phi_analysis(f, out=g2)))
+        p64.sync()
+        out["phi_fp64_round_trip_ms"] = phi64_ms
+        out["phi_fp64_round_trip_rel_err"] = float((g2 - g).norm() / g.norm())
+    return out
 
 
 def measured_peaks():
@@ -550,7 +640,10 @@ def roofline(plan, w, F, flops, fwd_ms, main_ms, out_ms):
     # node values (Y, 4 real right-hand sides x 4 bytes per node, order and field).
     pk = measured_peaks()
     ops = plan.program(parts=("ops",))["ops"]
-    img = sum(tc_image_bytes(int(mo), int(ni)) for mo, ni in zip(ops["mo"], ops["ni"]))
+    # algorithmic factor bytes: 6 bytes (three BF16 pieces) per stored entry,
+    # with no tile padding or group widening; the padded image is reported too
+    img = 6 * int((ops["mo"].astype(np.int64) * ops["ni"].astype(np.int64)).sum())
+    img_padded = sum(tc_image_bytes(int(mo), int(ni)) for mo, ni in zip(ops["mo"], ops["ni"]))
     y_bytes = F * 2 * N * 2 * N * 16
     algo_bytes = img + beta_bytes + y_bytes
     tens_peak = pk["bf16_sustained"] / 6.0 * 1e3  # GFLOP/s of FP32-quality split products
@@ -560,7 +653,8 @@ def roofline(plan, w, F, flops, fwd_ms, main_ms, out_ms):
     tr, tsrc = traffic_for(kname, w["name"], algo_bytes)
     apply_bytes = img + io_bytes
     base = {"kernel": kname, "kernel_ms": main_ms, "traffic": tr, "traffic_source": tsrc, "flops_per_launch": flops,
-            "bytes_per_launch": algo_bytes, "factor_image_bytes": img, "beta_bytes": beta_bytes,
+            "bytes_per_launch": algo_bytes, "factor_image_bytes": img, "factor_image_bytes_padded": img_padded,
+            "beta_bytes": beta_bytes,
             "y_bytes": y_bytes,
             "apply": {"kernels": "alt_tc_kernel + tc_out_kernel", "ms": fwd_ms, "output_kernel_ms": out_ms,
                       "bytes": apply_bytes, "GBps": apply_bytes / (fwd_ms * 1e-3) / 1e9,

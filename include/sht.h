@@ -58,7 +58,12 @@ typedef enum {
 typedef enum {
   SHT_FP64 = 0,        /* factors and arithmetic in FP64                        */
   SHT_FP32 = 1,        /* factors and arithmetic in FP32 (FP64 I/O)             */
-  SHT_MIXED = 2        /* tensor-core block products, FP64 turning-point blocks */
+  SHT_MIXED = 2        /* every block product (IDBF levels, low-rank factors and
+                          the dense turning-point blocks) on the tensor cores as
+                          split-BF16 (3 pieces) with FP32 accumulation; FP64
+                          only in the precomputation and the FP64 I/O.  Measured
+                          relative error against the FP64 definition: about
+                          2e-7 per field at eps = 1e-7, N = 1024               */
 } sht_precision;
 
 /* Plan options (Sec. 2.1, 2.3, 3.2, 3.3 and Sec. 5's parameter choices). */
@@ -281,9 +286,13 @@ sht_status sht_batch_sync(sht_batch_t batch, void* stream);
  * work counter) in a fixed 8 MiB array inside the library's device image
  * instead of the plan's workspace, and calls no allocating routine.
  *  - Every GPU that loads libsht.so holds that array until the process exits.
- *  - The first call on a device looks the array's device address up
- *    (cudaGetSymbolAddress) with that device current; make it before any
- *    stream capture.  The plan must belong to the current device.
+ *  - sht_plan_create / sht_plan_load look the array's device address up
+ *    (cudaGetSymbolAddress, with the plan's device current) and keep it in
+ *    the plan, so this call does no set-up of its own.  The plan must belong
+ *    to the current device, in the context it was created in (a plan does not
+ *    survive cudaDeviceReset).
+ *  - Plans created with SHT_FLAG_TIMING count its launches in
+ *    sht_plan_kernel_time like those of the other apply calls.
  *  - FP64 plans only (SHT_ERR_UNSUPPORTED otherwise: the other precisions do
  *    not keep the FP64 factor store on the device).
  *  - Returns SHT_ERR_ARG when one work item's vectors (the plan's largest
@@ -305,6 +314,14 @@ sht_status alt_forward_m_noalloc(sht_plan_t plan, int m, const double* beta_m, d
  *  - launches: the number of launches summed.
  * reset != 0 starts a new sum.  SHT_ERR_UNSUPPORTED without the flag. */
 sht_status sht_plan_kernel_time(sht_plan_t plan, int reset, double* apply_ms, double* output_ms, int64_t* launches);
+
+/* Pause (enable = 0) or resume (enable != 0) the event recording of a plan
+ * created with SHT_FLAG_TIMING (instrumentation; the paper has no
+ * counterpart), e.g. so that a timed loop runs without the extra events and a
+ * separate pass collects the per-kernel split.  Launches made while paused
+ * are not counted by sht_plan_kernel_time.  SHT_ERR_UNSUPPORTED without the
+ * flag. */
+sht_status sht_plan_set_timing(sht_plan_t plan, int enable);
 
 /* Self-test of the failure detection (the paper has no counterpart).  Every
  * wait inside the tensor-core kernel is bounded (about a second); when one

@@ -155,6 +155,33 @@ def alt_inverse_m(N: int, m: int, g_m: np.ndarray, x=None, w=None) -> np.ndarray
     return out
 
 
+def alt_forward_m_fields(N: int, m: int, beta_m: np.ndarray, x_nodes) -> np.ndarray:
+    """g(m, .) of F fields of order m at arbitrary nodes (Eq. sht_lt).
+
+    beta_m: (F, 2N-|m|, 2).  The sum over degrees is one matrix product of the
+    table T[i, k-|m|] = Pbar_k^{|m|}(x_i) (``alf_table``) with the coefficients:
+    the same definition as ``alt_forward_m``, for many fields at once.
+    """
+    beta_m = np.asarray(beta_m, dtype=np.float64)
+    assert beta_m.ndim == 3 and beta_m.shape[1] == 2 * N - abs(m)
+    T = alf_table(abs(m), 2 * N - 1, x_nodes)
+    return np.einsum("ik,fkc->fic", T, beta_m)
+
+
+def alt_inverse_m_fields(N: int, m: int, g_m: np.ndarray, x=None, w=None) -> np.ndarray:
+    """beta_{k,m}, k = |m|..2N-1, of F fields from g(m, theta_l) (Sec. 3.1.1).
+
+    g_m: (F, 2N, 2).  beta_k = sum_l w_l Pbar_k^{|m|}(x_l) g_l as one matrix
+    product of the transposed table with the weighted values.
+    """
+    if x is None or w is None:
+        x, w = gl_rule(2 * N)
+    g_m = np.asarray(g_m, dtype=np.float64)
+    assert g_m.ndim == 3 and g_m.shape[1] == 2 * N
+    T = alf_table(abs(m), 2 * N - 1, x)
+    return np.einsum("ik,fic->fkc", T, np.asarray(w)[None, :, None] * g_m)
+
+
 def phi_synthesis(N: int, g: np.ndarray) -> np.ndarray:
     """f(theta_l, phi_j) = sum_m g(m, theta_l) e^{i m phi_j}: (F,4N-1,2N,2) -> (F,2N,4N-1,2)."""
     g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1, 4 * N - 1, 2 * N, 2)

@@ -206,6 +206,10 @@ class Plan:
         created with flags including SHT_FLAG_TIMING; sht_plan_kernel_time)."""
         return _lib.sht_plan_kernel_time(self.handle, reset)
 
+    def set_timing(self, enable: bool):
+        """Pause or resume the kernel-time events of a SHT_FLAG_TIMING plan."""
+        _lib.sht_plan_set_timing(self.handle, enable)
+
     def sync(self):
         _lib.sht_sync(self.handle, self._stream())
 

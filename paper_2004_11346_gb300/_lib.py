@@ -120,7 +120,7 @@ EXPORTED = [
     "sht_status_str", "alt_forward_m_noalloc", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
     "sht_inverse", "sht_plan_save", "sht_plan_load", "sht_plan_kernel_time", "sht_batch_create",
     "sht_batch_destroy", "alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch",
-    "sht_batch_sync", "sht_selftest_timeout", "sht_plan_op_image", "sht_order_stats",
+    "sht_batch_sync", "sht_selftest_timeout", "sht_plan_op_image", "sht_order_stats", "sht_plan_set_timing",
 ]
 
 
@@ -145,6 +145,7 @@ def load(build: bool = True):
     lib.sht_plan_save.argtypes = [vp, ctypes.c_char_p]
     lib.sht_plan_kernel_time.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64)]
     lib.sht_plan_load.argtypes = [ctypes.c_char_p, plan_p]
+    lib.sht_plan_set_timing.argtypes = [vp, i]
     for name in ("alt_forward", "alt_inverse", "sht_phi_synthesis", "sht_phi_analysis", "sht_forward",
                  "sht_inverse"):
         getattr(lib, name).argtypes = [vp, vp, vp, i, vp]
@@ -226,6 +227,10 @@ def sht_plan_kernel_time(plan: int, reset: bool = True) -> dict:
     check(load().sht_plan_kernel_time(plan, 1 if reset else 0, ctypes.byref(a), ctypes.byref(o), ctypes.byref(n)),
           "sht_plan_kernel_time")
     return {"apply_ms": a.value, "output_ms": o.value, "launches": n.value}
+
+
+def sht_plan_set_timing(plan: int, enable: bool):
+    check(load().sht_plan_set_timing(plan, 1 if enable else 0), "sht_plan_set_timing")
 
 
 def sht_plan_opts(plan: int) -> sht_opts:

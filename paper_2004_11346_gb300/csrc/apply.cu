@@ -19,7 +19,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <string>
 
@@ -275,6 +274,36 @@ __global__ void __launch_bounds__(kThreads) alt_inverse_f64_kernel(DevPlan p, co
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Scratch of the forward single-order ALT without any allocation
+// (alt_forward_m_noalloc, at the end of this file).
+//
+// Some callers cannot allocate device memory: code that runs inside a
+// memory-pool or arena that owns the whole device, real-time loops where a
+// cudaMalloc/cudaFree would synchronise the device and stall other streams,
+// and embedders whose allocator is not CUDA's.  For them that entry point runs
+// the same forward kernel as alt_forward_m, but with its per-CTA vector
+// scratch and its work counter taken from the fixed array below instead of
+// the plan's workspace.  It calls no cudaMalloc, cudaFree or allocating
+// library routine.
+//
+// The array lives in the library's device image: every GPU that loads
+// libsht.so holds kNoAllocScratchBytes of it until the process exits.  Host
+// code must not pass the array's name to a kernel (on the host it is only a
+// stand-in symbol); its device address is looked up with cudaGetSymbolAddress
+// when a plan is created, with the plan's device current, and kept in the
+// plan, so the entry point itself does no set-up.  All calls share the one
+// array, so calls that may overlap on the GPU (different streams, or several
+// plans at once) race on it: serialise them.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB
+constexpr size_t kNoAllocCounterBytes = 256;              // work counter, padded
+
+static __device__ __align__(256) unsigned char noalloc_scratch[kNoAllocScratchBytes];
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // Plan object and C ABI
 
 struct sht_plan_s {
@@ -310,10 +339,14 @@ struct sht_plan_s {
   int tc_gmax = 0;
   int* d_err = nullptr;
   int nslots_tc = 0;
+  // device address of noalloc_scratch in this plan's context (looked up at
+  // creation; used only by alt_forward_m_noalloc)
+  unsigned char* d_noalloc = nullptr;
   // SHT_FLAG_TIMING: three events per recorded launch (before, between, after
   // the kernels), a ring of kTimingSlots launches
   std::vector<cudaEvent_t> tev;
   int64_t tev_count = 0, tev_base = 0;
+  bool timing_on = true;  // sht_plan_set_timing
 };
 
 namespace {
@@ -353,7 +386,7 @@ constexpr int kTimingSlots = 256;
 
 // Events of the next recorded launch (nullptr without SHT_FLAG_TIMING).
 cudaEvent_t* timing_slot(sht_plan_s* p) {
-  if (p->tev.empty()) return nullptr;
+  if (p->tev.empty() || !p->timing_on) return nullptr;
   cudaEvent_t* ev = p->tev.data() + 3 * (p->tev_count % kTimingSlots);
   ++p->tev_count;
   return ev;
@@ -553,6 +586,12 @@ sht_status attach_device(sht_plan_s* p) {
   size_t ws = o.precision == SHT_FP64 ? (size_t)p->nslots * P.max_rows * kRT * sizeof(double) : 0;
   if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_ws), std::max<size_t>(ws, 8));
   if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_counter), sizeof(unsigned int));
+  if (e == cudaSuccess && o.precision == SHT_FP64) {
+    void* na = nullptr;
+    e = cudaGetSymbolAddress(&na, noalloc_scratch);
+    if (e == cudaSuccess && !na) e = cudaErrorInvalidSymbol;
+    p->d_noalloc = static_cast<unsigned char*>(na);
+  }
   size_t ws32 = 0;
   if (e == cudaSuccess && o.precision == SHT_MIXED) {
     TcImages img;
@@ -1053,6 +1092,13 @@ sht_status sht_plan_kernel_time(sht_plan_t p, int reset, double* apply_ms, doubl
   return SHT_OK;
 }
 
+sht_status sht_plan_set_timing(sht_plan_t p, int enable) {
+  if (!p) return SHT_ERR_ARG;
+  if (p->tev.empty()) return SHT_ERR_UNSUPPORTED;
+  p->timing_on = enable != 0;
+  return SHT_OK;
+}
+
 sht_status sht_sync(sht_plan_t p, void* stream) {
   if (!p) return SHT_ERR_ARG;
   if (p->host_only) return SHT_ERR_UNSUPPORTED;
@@ -1283,54 +1329,6 @@ sht_status sht_batch_sync(sht_batch_t b, void* stream) {
 
 }  // extern "C"
 
-// ---------------------------------------------------------------------------
-// Forward ALT of one order without any allocation.
-//
-// Some callers cannot allocate device memory: code that runs inside a
-// memory-pool or arena that owns the whole device, real-time loops where a
-// cudaMalloc/cudaFree would synchronise the device and stall other streams,
-// and embedders whose allocator is not CUDA's.  For them this entry point runs
-// the same forward kernel as alt_forward_m, but with its per-CTA vector
-// scratch and its work counter taken from the fixed array below instead of
-// the plan's workspace.  It calls no cudaMalloc, cudaFree or allocating
-// library routine.
-//
-// The array lives in the library's device image: every GPU that loads
-// libsht.so holds kNoAllocScratchBytes of it until the process exits.  Host
-// code must not pass the array's name to a kernel (on the host it is only a
-// stand-in symbol); its device address is looked up once per device with
-// cudaGetSymbolAddress, on the first call made while that device is current.
-// Make that first call before any stream capture.  All calls share the one
-// array, so calls that may overlap on the GPU (different streams, or several
-// plans at once) race on it: serialise them.
-
-namespace {
-
-constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB
-constexpr size_t kNoAllocCounterBytes = 256;              // work counter, padded
-
-static __device__ __align__(256) unsigned char noalloc_scratch[kNoAllocScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex noalloc_mu;
-void* noalloc_addr[kMaxDevices] = {nullptr};
-
-// Device address of noalloc_scratch on the current device (looked up once).
-sht_status noalloc_base(int dev, unsigned char** out) {
-  if (dev < 0 || dev >= kMaxDevices) return SHT_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(noalloc_mu);
-  if (!noalloc_addr[dev]) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, noalloc_scratch);
-    if (e != cudaSuccess || !ptr) return SHT_ERR_CUDA;
-    noalloc_addr[dev] = ptr;
-  }
-  *out = static_cast<unsigned char*>(noalloc_addr[dev]);
-  return SHT_OK;
-}
-
-}  // namespace
-
 extern "C" sht_status alt_forward_m_noalloc(sht_plan_t p, int m, const double* beta_m, double* g_m, int F,
                                             void* stream) {
   if (!p || F < 0) return SHT_ERR_ARG;
@@ -1345,11 +1343,10 @@ extern "C" sht_status alt_forward_m_noalloc(sht_plan_t p, int m, const double* b
   if (slot == 0 || slot > kNoAllocScratchBytes - kNoAllocCounterBytes) return SHT_ERR_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return SHT_ERR_ARG;
-  unsigned char* base = nullptr;
-  sht_status s = noalloc_base(dev, &base);
-  if (s != SHT_OK) return s;
+  unsigned char* base = p->d_noalloc;  // looked up when the plan was created
+  if (!base) return SHT_ERR_CUDA;
   if (p->latched != SHT_OK) {
-    s = p->latched;
+    const sht_status s = p->latched;
     p->latched = SHT_OK;
     return s;
   }
@@ -1360,6 +1357,11 @@ extern "C" sht_status alt_forward_m_noalloc(sht_plan_t p, int m, const double* b
   d.counter = reinterpret_cast<unsigned int*>(base);  // must start at zero: cleared below
   d.ws = reinterpret_cast<double*>(base + kNoAllocCounterBytes);
   if (cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
+  cudaEvent_t* ev = timing_slot(p);  // SHT_FLAG_TIMING plans: counted like every other apply launch
+  if (ev && cudaEventRecord(ev[0], st) != cudaSuccess) return SHT_ERR_CUDA;
   alt_forward_f64_kernel<<<grid, kThreads, 0, st>>>(d, beta_m, g_m, F, 1, m);
-  return cudaGetLastError() == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return SHT_ERR_CUDA;
+  if (ev && (cudaEventRecord(ev[1], st) != cudaSuccess || cudaEventRecord(ev[2], st) != cudaSuccess))
+    return SHT_ERR_CUDA;
+  return SHT_OK;
 }

@@ -93,7 +93,7 @@ def test_compare_reports_the_paper_ratios(monkeypatch):
     lib = type("L", (), {"SHT_FP64": 0, "SHT_FLAG_DENSE": 4})
     times = iter([(10.0, 4.0, 6.0), (40.0, 15.0, 25.0)])  # FP64 IDBF, then dense
     monkeypatch.setattr(bench, "time_steps", lambda *a: next(times))
-    monkeypatch.setattr(bench, "sht_timings", lambda *a: {})
+    monkeypatch.setattr(bench, "sht_timings", lambda *a, **k: {})
     args = type("A", (), {"steps": 4})
     out = bench.compare(FakeTorch, FakeSht, lib, {"N": 8, "precision": "fp64"}, None, FakeTensor(), None, args, None)
     assert out["fp64_idbf"]["t_fac_s"] == 2.0 and out["dense_fp64"]["t_mat_s"] == 6.0

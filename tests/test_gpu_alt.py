@@ -11,6 +11,7 @@ import pytest
 import oracle
 import paper_2004_11346_gb300 as sht
 from paper_2004_11346_gb300 import _lib, inputs
+from parity import max_order_err, order_err_coefficients, order_err_values
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -56,8 +57,12 @@ def test_forward_all_orders(plans, name):
     torch.cuda.synchronize()
     p.sync()
     ref = oracle.alt_forward(N, beta)
-    err = rel_err(g.cpu().numpy(), ref)
+    got = g.cpu().numpy()
+    err = rel_err(got, ref)
     assert np.all(err <= TOL_FP64), err
+    # every (field, order) on its own, not only the field's norm
+    eo = order_err_values(got, ref)
+    assert max_order_err(eo) <= TOL_FP64, np.unravel_index(np.nanargmax(eo), eo.shape)
 
 
 @pytest.mark.parametrize("name", list(PLANS))
@@ -70,8 +75,11 @@ def test_inverse_all_orders(plans, name):
     beta = p.inverse(dev(g))
     torch.cuda.synchronize()
     ref = oracle.alt_inverse(N, g)
-    err = rel_err(beta.cpu().numpy(), ref)
+    got = beta.cpu().numpy()
+    err = rel_err(got, ref)
     assert np.all(err <= TOL_FP64), err
+    eo = order_err_coefficients(got, ref, N)
+    assert max_order_err(eo) <= TOL_FP64, np.unravel_index(np.nanargmax(eo), eo.shape)
 
 
 def test_round_trip(plans):

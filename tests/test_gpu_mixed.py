@@ -10,6 +10,7 @@ import pytest
 import oracle
 import paper_2004_11346_gb300 as sht
 from paper_2004_11346_gb300 import _lib, inputs
+from parity import max_order_err, order_err_coefficients, order_err_values
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -57,8 +58,12 @@ def test_forward(plans, name, F):
     g = p.forward(dev(beta))
     torch.cuda.synchronize()
     p.sync()
-    err = rel_err(g.cpu().numpy(), oracle.alt_forward(N, beta))
+    got, ref = g.cpu().numpy(), oracle.alt_forward(N, beta)
+    err = rel_err(got, ref)
     assert np.all(err <= TOL_MIXED), err
+    # every (field, order) on its own, not only the field's norm
+    eo = order_err_values(got, ref)
+    assert max_order_err(eo) <= TOL_MIXED, np.unravel_index(np.nanargmax(eo), eo.shape)
 
 
 @pytest.mark.parametrize("name", list(PLANS))
@@ -69,8 +74,11 @@ def test_inverse(plans, name):
     g = np.random.default_rng(3).standard_normal((F, 4 * N - 1, 2 * N, 2))
     b = p.inverse(dev(g))
     torch.cuda.synchronize()
-    err = rel_err(b.cpu().numpy(), oracle.alt_inverse(N, g))
+    got, ref = b.cpu().numpy(), oracle.alt_inverse(N, g)
+    err = rel_err(got, ref)
     assert np.all(err <= TOL_MIXED), err
+    eo = order_err_coefficients(got, ref, N)
+    assert max_order_err(eo) <= TOL_MIXED, np.unravel_index(np.nanargmax(eo), eo.shape)
 
 
 @pytest.mark.parametrize("m", [0, 3, -3, 191, -191])

@@ -38,3 +38,21 @@ def test_kernel_time(prec, eps, F, tol):
     assert np.all(e <= tol)
     e2 = np.linalg.norm((back.cpu().numpy() - oracle.alt_inverse(N, g.cpu().numpy())).reshape(F, -1), axis=1)
     assert np.all(e2 <= tol * np.linalg.norm(back.cpu().numpy().reshape(F, -1), axis=1))
+
+
+def test_timing_can_be_paused():
+    N, F = 32, 3
+    p = sht.Plan(N, 1e-7, precision=_lib.SHT_MIXED, max_fields=F, flags=_lib.SHT_FLAG_TIMING)
+    b = torch.from_numpy(inputs.coefficients(N, F, seed=3)).cuda()
+    p.kernel_time()
+    p.set_timing(False)
+    g = p.forward(b)
+    assert p.kernel_time()["launches"] == 0
+    p.set_timing(True)
+    g2 = p.forward(b)
+    assert p.kernel_time()["launches"] == 1
+    torch.cuda.synchronize()
+    assert torch.equal(g, g2) or float((g - g2).norm() / g.norm()) < 1e-6
+    q = sht.Plan(N, 1e-7, precision=_lib.SHT_MIXED)
+    with pytest.raises(_lib.ShtError):
+        q.set_timing(False)

@@ -219,6 +219,22 @@ def test_alt_single_order_matches_batched():
         np.testing.assert_allclose(bm, beta[0, off: off + 2 * N - abs(m)], atol=1e-13)
 
 
+def test_alt_m_fields_match_single_field_calls():
+    # the many-field helpers are the same sums as the per-field definitions
+    N = 24
+    x, w = oracle.gl_rule(2 * N)
+    rng = np.random.default_rng(12)
+    for m in [0, 5, -5, 2 * N - 1, -(2 * N - 1)]:
+        bm = rng.standard_normal((3, 2 * N - abs(m), 2))
+        got = oracle.alt_forward_m_fields(N, m, bm, x)
+        ref = np.stack([oracle.alt_forward_m(N, m, bm[f], x) for f in range(3)])
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+        gm = rng.standard_normal((3, 2 * N, 2))
+        got = oracle.alt_inverse_m_fields(N, m, gm, x, w)
+        ref = np.stack([oracle.alt_inverse_m(N, m, gm[f], x, w) for f in range(3)])
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
 def test_parity_symmetry():
     # Sec. 3.1.2: terms with k-|m| even are even in x, odd ones odd in x
     N = 16

@@ -68,3 +68,15 @@ def test_noalloc_needs_fp64_plan():
     with pytest.raises(_lib.ShtError) as ei:
         _lib.alt_forward_m_noalloc(plan.handle, 0, x.data_ptr(), x.data_ptr(), 1, 0)
     assert ei.value.status == _lib.SHT_ERR_UNSUPPORTED
+
+
+def test_noalloc_launches_are_timed():
+    """With SHT_FLAG_TIMING the entry point's launches are counted like the others."""
+    N = 32
+    plan = sht.Plan(N, 1e-12, flags=_lib.SHT_FLAG_TIMING)
+    x = torch.from_numpy(np.random.default_rng(1).standard_normal((2, 2 * N - 3, 2))).cuda()
+    y = torch.empty((2, 2 * N, 2), dtype=torch.float64, device="cuda")
+    plan.kernel_time()
+    _lib.alt_forward_m_noalloc(plan.handle, 3, x.data_ptr(), y.data_ptr(), 2, 0)
+    t = plan.kernel_time()
+    assert t["launches"] == 1 and t["apply_ms"] > 0
