@@ -12,9 +12,11 @@ products.
 autotune() ranks candidate (n0, n_leaf) pairs by that work model on host-only
 plans (no GPU needed), then builds the best few on the device, times a forward
 and an inverse apply of the requested batch with CUDA events, and returns the
-fastest.  The model's counts mirror how the kernel cuts the work: K sides
-widened to whole 8-row groups of the vector space, chunks of 4 groups (the
-last rounded to an even number), N tiles of 128 rows padded to 16.
+fastest.  The model's counts mirror how the kernel cuts the work: segments
+moved to the kernel's scratch rows (X_o, Y_e and Y_o start on whole groups),
+K sides widened to whole 8-row groups, chunks of 4 groups (the last rounded
+to an even number), the outputs of products that write intermediate rows
+widened to whole groups too, N tiles of 128 rows padded to 16.
 """
 from __future__ import annotations
 
@@ -26,35 +28,79 @@ TILE_N = 128       # rows of one tensor-core tile
 GROUP_ROWS = 8     # rows of one activation group
 GROUP_BYTES = 6144  # one group: 8 rows x 3 BF16 pieces x 128 right-hand sides
 CHUNK_GROUPS = 4   # groups of one K chunk (32 rows)
+FWD_ACCUM = 1      # op flag: forward outputs accumulate (Y rows)
 
 
-def _kside(off0, len0, off1, len1):
-    """Groups and padded K columns of one product's K side (two row segments)."""
+def _r8(v):
+    return (v + 7) & ~7
+
+
+def scratch_rows(nce, nco, N):
+    """(xo, ye, yo, shift) of the tensor-core scratch layout of one order:
+    X_o, Y_e and Y_o start on whole groups, intermediates move by `shift`."""
+    xo = _r8(nce)
+    ye = _r8(xo + nco)
+    yo = ye + _r8(N)
+    return xo, ye, yo, _r8(yo + N) - _r8(nce + nco + 2 * N)
+
+
+def _seg_row(off, nce, nco, N, rows):
+    xo, ye, yo, shift = rows
+    if off < nce:
+        return off
+    if off < nce + nco:
+        return off - nce + xo
+    if off < nce + nco + N:
+        return off - nce - nco + ye
+    if off < nce + nco + 2 * N:
+        return off - nce - nco - N + yo
+    return off + shift
+
+
+def _groups(off0, len0, off1, len1):
+    """Groups of one side of a product (two row segments) widened to whole groups."""
     ng0 = (off0 + len0 + GROUP_ROWS - 1) // GROUP_ROWS - off0 // GROUP_ROWS if len0 > 0 else 0
     ng1 = (off1 + len1 + GROUP_ROWS - 1) // GROUP_ROWS - off1 // GROUP_ROWS if len1 > 0 else 0
-    ngt = ng0 + ng1
+    return ng0 + ng1
+
+
+def _kside(ngt):
+    """K chunks and padded K columns of a side of ngt groups."""
     nk = (ngt + CHUNK_GROUPS - 1) // CHUNK_GROUPS
     kp = 32 * (nk - 1) + 16 * ((ngt - CHUNK_GROUPS * (nk - 1) + 1) // 2) if nk > 0 else 0
-    return ngt, nk, kp
+    return nk, kp
 
 
-def work_model(ops) -> dict:
+def work_model(ops, units, N) -> dict:
     """Stages, tiles, operand-image and activation bytes of one forward apply
-    of one 32-field group, from a plan's op records (Plan.program()["ops"])."""
-    mo = ops["mo"].astype(np.int64)
+    of one 32-field group, from a plan's op and unit records (Plan.program()):
+    segments moved to the scratch rows, K sides widened to whole groups, the
+    outputs of non-accumulating products widened likewise, tiles of TILE_N."""
     stages = tiles = img = act = 0
-    for k in range(len(ops)):
-        if ops["ni"][k] <= 0:
-            continue
-        ngt, nk, kp = _kside(*(int(v) for v in (ops["in_off"][k][0], ops["in_len"][k][0],
-                                                ops["in_off"][k][1], ops["in_len"][k][1])))
-        nn = int(mo[k])
-        nt = (nn + TILE_N - 1) // TILE_N
-        np_tot = TILE_N * (nt - 1) + ((nn - TILE_N * (nt - 1) + 15) & ~15)
-        stages += nt * nk
-        tiles += nt
-        img += 2 * 3 * np_tot * kp
-        act += nt * ngt * GROUP_BYTES
+    for u in units:
+        nce, nco = int(u["nce"]), int(u["nco"])
+        rows = scratch_rows(nce, nco, N)
+        for k in range(int(u["op_begin"]), int(u["op_end"])):
+            op = ops[k]
+            if op["ni"] <= 0:
+                continue
+
+            def segs(offs, lens):
+                return [_seg_row(int(o), nce, nco, N, rows) if int(l) > 0 else 0 for o, l in zip(offs, lens)]
+            io, il = segs(op["in_off"], op["in_len"]), [int(v) for v in op["in_len"]]
+            ngt = _groups(io[0], il[0], io[1], il[1])
+            nk, kp = _kside(ngt)
+            if int(op["flags"]) & FWD_ACCUM:
+                nn = int(op["mo"])
+            else:
+                oo, ol = segs(op["out_off"], op["out_len"]), [int(v) for v in op["out_len"]]
+                nn = GROUP_ROWS * _groups(oo[0], ol[0], oo[1], ol[1])
+            nt = (nn + TILE_N - 1) // TILE_N
+            np_tot = TILE_N * (nt - 1) + ((nn - TILE_N * (nt - 1) + 15) & ~15)
+            stages += nt * nk
+            tiles += nt
+            img += 2 * 3 * np_tot * kp
+            act += nt * ngt * GROUP_BYTES
     return {"stages": int(stages), "tiles": int(tiles), "image_bytes": int(img), "activation_bytes": int(act)}
 
 
@@ -101,7 +147,8 @@ def rank(N: int, eps: float, cands=None, sample: int | None = None, **plan_kw):
             w, entries = sampled_work_model(N, eps, sample, n0=n0, n_leaf=nl, **plan_kw)
         else:
             p = Plan(N, eps, flags=_lib.SHT_FLAG_HOST_ONLY, precision=_lib.SHT_MIXED, n0=n0, n_leaf=nl, **plan_kw)
-            w = work_model(p.program(("ops",))["ops"])
+            prog = p.program(("ops", "units"))
+            w = work_model(prog["ops"], prog["units"], N)
             entries = int(p.stats()["entries_total"])
             p.close()
         rows.append({"n0": n0, "n_leaf": nl, "entries": int(entries), **w, "model_us": model_cost(w)})

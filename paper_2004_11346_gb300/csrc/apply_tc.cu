@@ -5,29 +5,34 @@
 // Every block product of the apply program, out (+)= B in, is computed
 // transposed, out^T = in^T B^T, so that the 128 right-hand sides fill the MMA
 // M dimension and the block's rows are N (tiles of <= 128, padded to 16):
-//   A operand = in^T (128 x K, MN-major): the op's input rows, kept in the
+//   A operand = in^T (128 x K, K-major): the op's input rows, kept in the
 //               scratch as three BF16 pieces a0 + a1 + a2 (8 bits each) of
 //               every value, in groups of 8 rows laid out exactly as the
 //               operand sits in shared memory, so that staging one K chunk
 //               is one or two bulk copies of whole groups;
 //   B operand = B (N x K, K-major): precomputed split-BF16 image b0 + b1 + b2,
-//               with zero columns where the K side was widened to whole groups;
-//   D         = 128 x N FP32 accumulator in tensor memory.
+//               with zero columns where the K side was widened to whole groups
+//               (and zero rows where an intermediate output side was);
+//   D         = 128 x N FP32 accumulators in tensor memory.
 // The CTA is warp-specialised and persistent (one per SM): one producer
 // thread streams (op, tile, 32-wide K chunk) operand stages into a 4-deep
 // shared memory ring with bulk copies; an MMA thread issues the tensor-core
-// products into two double-buffered TMEM accumulator pairs; four epilogue
-// warps drain the accumulators and split the results into BF16 pieces for the
-// next level (or add them in FP32 into the shared output rows); the I/O warps
-// gather the next item's inputs.  Ops of one phase read only rows written by
-// earlier phases: the producer starts a phase after the epilogue has counted
-// every earlier tile.
+// products into two alternating TMEM accumulator pairs; four epilogue warps drain
+// them, each thread one right-hand side, and either split the results into
+// BF16 pieces for the next level (eight rows per 16-byte store) or add them
+// in FP32 into the item's accumulation rows; eight I/O warps gather the next
+// item's inputs and write the previous item's outputs (the parity fold of
+// Sec. 3.1.2 forward, the scatter to the coefficients transposed).  Ops of
+// one phase read only rows written by earlier phases: the producer starts a
+// phase after the epilogue has counted every earlier tile.
 // Per 16-wide K step six MMAs accumulate a_p b_q for p + q <= 2, which keeps
 // every product to about 2^-24 relative error (FP32 quality); a0 b0 and the
 // five smaller cross products go to two separate accumulators that the
-// epilogue adds in FP32.  Operands sit in shared memory in the canonical
-// no-swizzle layouts (8 x 16-byte core matrices; LBO = stride between core
-// matrices along K, SBO = along M/N).
+// epilogue adds in FP32 (the tensor cores' FP32 accumulation is not rounded to
+// nearest: summing the small terms into the large accumulator measured 8x the
+// error at N = 1024).  Operands sit in
+// shared memory in the canonical no-swizzle K-major layout (8 x 16-byte core
+// matrices; LBO = stride between core matrices along K, SBO = along M/N).
 // All waits are bounded: a wait that runs out sets an error flag, every role
 // stops, and the host reports SHT_ERR_TIMEOUT.
 #include <cuda_bf16.h>
@@ -57,56 +62,76 @@ static inline double bf16_to_d(uint16_t h) {
   return (double)f;
 }
 
-size_t tc_image_elems(int NN, const TcKGeom& kg) {
-  if (NN <= 0 || kg.kp_tot <= 0) return 0;
-  const int nT = (NN + kTcNT - 1) / kTcNT;
-  const size_t np_tot = (size_t)kTcNT * (nT - 1) + r16(NN - kTcNT * (nT - 1));
-  return 3 * np_tot * (size_t)kg.kp_tot;
+TcOp tc_op_of(const Op& op, const Unit& u, int N) {
+  const TcRows tr = tc_rows(u.nce, u.nco, N);
+  TcOp t{};
+  t.mo = op.mo;
+  t.ni = op.ni;
+  for (int s = 0; s < 2; ++s) {
+    t.in_len[s] = op.in_len[s];
+    t.out_len[s] = op.out_len[s];
+    t.in_off[s] = op.in_len[s] > 0 ? tc_seg_row(op.in_off[s], u.nce, u.nco, N, tr) : 0;
+    t.out_off[s] = op.out_len[s] > 0 ? tc_seg_row(op.out_off[s], u.nce, u.nco, N, tr) : 0;
+  }
+  t.flags = op.flags;
+  t.phase = op.phase;
+  return t;
 }
 
-// Layout (matching the kernel): tiles t, chunks c, pieces p, then core
-// matrices (ki, mi) in K-outer order, 8 rows x 8 elements each.  elem(n, k)
-// is the block entry for row n and K index k of the unwidened K side; K
-// positions that fall outside both segments (group widening, padding) are 0.
-// Piece p of a value v is the BF16 rounding of what pieces 0..p-1 leave of v.
-// Each (tile, chunk) is first gathered into a small buffer, walking the source
-// along its contiguous direction (k_contig: consecutive K indices adjacent),
-// and the three pieces of every value are computed in one pass.
+// Widened position -> index into the unwidened side (0 .. len0 + len1 - 1),
+// or -1 where the position only pads.
+static inline int widened_index(const TcKGeom& g, int off0, int len0, int off1, int len1, int pos) {
+  const int j = pos / kTcGrpRows, e = pos % kTcGrpRows;
+  if (j < g.ng0) {
+    const int r = (g.gs0 + j) * kTcGrpRows + e;
+    return r >= off0 && r < off0 + len0 ? r - off0 : -1;
+  }
+  if (j < g.ngt) {
+    const int r = (g.gs1 + j - g.ng0) * kTcGrpRows + e;
+    return r >= off1 && r < off1 + len1 ? len0 + r - off1 : -1;
+  }
+  return -1;
+}
+
+// Layout (matching the kernel): tiles t of kTcNT positions, chunks c, pieces
+// p, then core matrices (ki, mi) in K-outer order, 8 positions x 8 elements
+// each.  elem(n, k) is the block entry for output index n and input index k
+// of the unwidened sides; positions that stand for no row (widening, padding)
+// are 0.  Piece p of a value v is the BF16 rounding of what pieces 0..p-1
+// leave of v.  Each (tile, chunk) is first gathered into a small buffer,
+// walking the source along its contiguous direction (k_contig: consecutive K
+// indices adjacent), and the three pieces of every value are computed in one
+// pass.
 template <class E>
-static void tc_pack(int NN, const TcKGeom& kg, int off0, int len0, int off1, int len1, E elem, bool k_contig,
+static void tc_pack(const TcDir& d, const int* no, const int* nl, const int* ko, const int* kl, E elem, bool k_contig,
                     uint16_t* dst) {
-  const int nT = (NN + kTcNT - 1) / kTcNT;
-  auto korig = [&](int kp) -> int {  // widened K position -> K index, or -1
-    const int j = kp / kTcGrpRows, e = kp % kTcGrpRows;
-    if (j < kg.ng0) {
-      const int r = (kg.gs0 + j) * kTcGrpRows + e;
-      return r >= off0 && r < off0 + len0 ? r - off0 : -1;
-    }
-    if (j < kg.ngt) {
-      const int r = (kg.gs1 + j - kg.ng0) * kTcGrpRows + e;
-      return r >= off1 && r < off1 + len1 ? len0 + r - off1 : -1;
-    }
-    return -1;
-  };
+  const TcKGeom& kg = d.kg;
   std::vector<double> buf((size_t)kTcNT * kTcKC);
+  std::vector<int> nidx(kTcNT);
   size_t o = 0;
-  for (int t = 0; t < nT; ++t) {
-    const int Nv = std::min(kTcNT, NN - kTcNT * t);  // valid rows of the tile
+  for (int t = 0; t < d.nT; ++t) {
+    const int Nv = std::min(kTcNT, d.NN - kTcNT * t);  // positions of the tile
     const int Np = r16(Nv);
+    for (int n = 0; n < Np; ++n) {
+      const int pos = kTcNT * t + n;
+      nidx[n] = n >= Nv ? -1 : d.accum ? pos : widened_index(d.ng, no[0], nl[0], no[1], nl[1], pos);
+    }
     for (int c = 0; c < kg.nK; ++c) {
       const int Kp = std::min(kTcKC, kg.kp_tot - kTcKC * c);
-      int ko[kTcKC];
-      for (int kk = 0; kk < Kp; ++kk) ko[kk] = korig(kTcKC * c + kk);
-      // buf[n * Kp + kk] = entry (tile row n, chunk column kk), zero outside
+      int kx[kTcKC];
+      for (int kk = 0; kk < Kp; ++kk) kx[kk] = widened_index(kg, ko[0], kl[0], ko[1], kl[1], kTcKC * c + kk);
+      // buf[n * Kp + kk] = entry (tile position n, chunk column kk), zero outside
       std::fill(buf.begin(), buf.begin() + (size_t)Np * Kp, 0.0);
       if (k_contig) {
-        for (int n = 0; n < Nv; ++n)
-          for (int kk = 0; kk < Kp; ++kk)
-            if (ko[kk] >= 0) buf[(size_t)n * Kp + kk] = elem(kTcNT * t + n, ko[kk]);
+        for (int n = 0; n < Np; ++n)
+          if (nidx[n] >= 0)
+            for (int kk = 0; kk < Kp; ++kk)
+              if (kx[kk] >= 0) buf[(size_t)n * Kp + kk] = elem(nidx[n], kx[kk]);
       } else {
         for (int kk = 0; kk < Kp; ++kk)
-          if (ko[kk] >= 0)
-            for (int n = 0; n < Nv; ++n) buf[(size_t)n * Kp + kk] = elem(kTcNT * t + n, ko[kk]);
+          if (kx[kk] >= 0)
+            for (int n = 0; n < Np; ++n)
+              if (nidx[n] >= 0) buf[(size_t)n * Kp + kk] = elem(nidx[n], kx[kk]);
       }
       const size_t piece = (size_t)Np * Kp;
       for (int n = 0; n < Np; ++n) {
@@ -127,70 +152,54 @@ static void tc_pack(int NN, const TcKGeom& kg, int off0, int len0, int off1, int
   }
 }
 
-void tc_op_image(const Op& op, const double* factors, bool transposed, std::vector<uint16_t>& out) {
-  out.clear();
-  if (op.ni <= 0) return;
+static void pack_dir(const Op& op, const TcOp& top, const double* factors, bool transposed, uint16_t* dst) {
   const double* B = factors + op.b_off;
   const int ld = op.ld;
-  if (!transposed) {
-    const TcKGeom kg = tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1]);
-    out.assign(tc_image_elems(op.mo, kg), 0);
-    tc_pack(op.mo, kg, op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1],
-            [&](int r, int k) { return B[(size_t)k * ld + r]; }, false, out.data());
-  } else {
-    const TcKGeom kg = tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1]);
-    out.assign(tc_image_elems(op.ni, kg), 0);
-    tc_pack(op.ni, kg, op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1],
-            [&](int r, int k) { return B[(size_t)r * ld + k]; }, true, out.data());
-  }
+  const TcDir d = tc_dir(top, !transposed);
+  if (tc_image_elems(d) == 0) return;
+  if (!transposed)
+    tc_pack(d, top.out_off, top.out_len, top.in_off, top.in_len, [&](int r, int k) { return B[(size_t)k * ld + r]; },
+            false, dst);
+  else
+    tc_pack(d, top.in_off, top.in_len, top.out_off, top.out_len, [&](int r, int k) { return B[(size_t)r * ld + k]; },
+            true, dst);
 }
 
-void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops, const double* factors,
-                     TcImages& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles) {
+void tc_op_image(const Op& op, const TcOp& top, const double* factors, bool transposed, std::vector<uint16_t>& out) {
+  out.assign(tc_image_elems(tc_dir(top, !transposed)), 0);
+  pack_dir(op, top, factors, transposed, out.data());
+}
+
+void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op>& ops, const double* factors,
+                     TcImages& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles, int& max_rows) {
   const size_t n = ops.size();
   tops.assign(n, TcOp{});
-  size_t tot = 0;
-  for (size_t i = 0; i < n; ++i) {
-    const Op& op = ops[i];
-    TcOp& t = tops[i];
-    t.img[0] = (int64_t)tot;
-    tot += tc_image_elems(op.mo, tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1]));
-    t.img[1] = (int64_t)tot;
-    tot += tc_image_elems(op.ni, tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1]));
-    t.mo = op.mo;
-    t.ni = op.ni;
-    for (int s = 0; s < 2; ++s) {
-      t.in_off[s] = op.in_off[s];
-      t.in_len[s] = op.in_len[s];
-      t.out_off[s] = op.out_off[s];
-      t.out_len[s] = op.out_len[s];
-    }
-    t.flags = op.flags;
-    t.phase = op.phase;
-  }
   tiles.assign(2 * units.size(), 0);
-  for (size_t u = 0; u < units.size(); ++u)
-    for (int oi = units[u].op_begin; oi < units[u].op_end; ++oi) {
-      tiles[2 * u] += (ops[oi].mo + kTcNT - 1) / kTcNT;
-      tiles[2 * u + 1] += (ops[oi].ni + kTcNT - 1) / kTcNT;
+  max_rows = 0;
+  size_t tot = 0;
+  for (size_t u = 0; u < units.size(); ++u) {
+    const Unit& un = units[u];
+    max_rows = std::max(max_rows, tc_nrows(un.nrows, un.nce, un.nco, N));
+    for (int oi = un.op_begin; oi < un.op_end; ++oi) {
+      TcOp& t = tops[(size_t)oi];
+      t = tc_op_of(ops[(size_t)oi], un, N);
+      const TcDir df = tc_dir(t, true), db = tc_dir(t, false);
+      t.img[0] = (int64_t)tot;
+      tot += tc_image_elems(df);
+      t.img[1] = (int64_t)tot;
+      tot += tc_image_elems(db);
+      tiles[2 * u] += df.nT;
+      tiles[2 * u + 1] += db.nT;
     }
-  // tc_pack writes every element of an op's two images (padding included),
+  }
+  // pack_dir writes every element of an op's two images (padding included),
   // so only the minimum-size tail of an empty store needs zeroing here
   img.resize(std::max<size_t>(tot, 8));
   std::fill(img.begin() + tot, img.end(), (uint16_t)0);
 #pragma omp parallel for schedule(dynamic, 64)
   for (long i = 0; i < (long)n; ++i) {
-    const Op& op = ops[i];
-    const double* B = factors + op.b_off;
-    const int ld = op.ld;
-    if (op.ni > 0) {
-      const TcKGeom kf = tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1]);
-      const TcKGeom kb = tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1]);
-      tc_pack(op.mo, kf, op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1],
-              [&](int r, int k) { return B[(size_t)k * ld + r]; }, false, img.data() + tops[i].img[0]);
-      tc_pack(op.ni, kb, op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1],
-              [&](int r, int k) { return B[(size_t)r * ld + k]; }, true, img.data() + tops[i].img[1]);
-    }
+    pack_dir(ops[(size_t)i], tops[(size_t)i], factors, false, img.data() + tops[(size_t)i].img[0]);
+    pack_dir(ops[(size_t)i], tops[(size_t)i], factors, true, img.data() + tops[(size_t)i].img[1]);
   }
 }
 
@@ -198,18 +207,22 @@ void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops,
 namespace {
 
 constexpr int kStages = 4;
-constexpr int kProdWarps = 3;                 // warp 0 stages operands (one thread); warps 1-2 are spare
-constexpr int kMmaWarp = kProdWarps;          // the MMA-issuing warp
-constexpr int kEpiWarp0 = kProdWarps + 1;     // first epilogue warp
-constexpr int kEpiWarps = 4;                  // one warpgroup drains the accumulators
-constexpr int kIoWarp0 = kEpiWarp0 + kEpiWarps;  // the remaining warps gather the next item's inputs
+constexpr int kProdWarp = 0;                  // one thread stages operands
+constexpr int kMmaWarp = 1;                   // one thread issues the MMAs; the warp owns TMEM
+constexpr int kEpiWarp0 = 4;                  // warps 4-7: TMEM lane quadrants 0-3
+constexpr int kEpiWarps = 4;
+constexpr int kIoWarp0 = 8;                   // warps 8-15 gather inputs and write outputs
 constexpr int kIoWarps = kTcThreads / 32 - kIoWarp0;
-constexpr int kTrStride = 33;                 // padded 32 x 32 transpose tile (floats)
+constexpr int kIoThreads = 32 * kIoWarps;
+constexpr int kPairs = 2 * kTcFields;         // (field, sign) pairs of an item: right-hand sides 2 pr, 2 pr + 1
+constexpr int kIoPhases = kIoThreads / kPairs;
+static_assert(kIoPhases * kPairs == kIoThreads, "I/O threads split the pairs evenly");
 constexpr int kStageA = (kTcKC / kTcGrpRows) * kTcGrpBytes;  // 4 row groups: 24 KB
-constexpr int kStageB = 3 * kTcNT * kTcKC * 2; // 24 KB (largest N tile)
+constexpr int kStageB = 3 * kTcNT * kTcKC * 2;               // 24 KB (largest N tile)
 constexpr int kStageBytes = kStageA + kStageB;
-constexpr int kTmemCols = 512;                 // 2 accumulator pairs (hi, lo) x 128 columns
-constexpr long kWaitLimit = 1L << 22;   // try_wait polls per bounded wait
+constexpr int kAccCols = 2 * kTcNT;             // an accumulator pair (hi, lo) of N columns each
+constexpr int kTmemCols = 2 * kAccCols;         // two pairs, alternating by tile
+constexpr long kWaitLimit = 1L << 22;           // try_wait polls per bounded wait
 
 struct Ctl {
   uint64_t full[kStages];
@@ -222,14 +235,7 @@ struct Ctl {
   int done_tiles;  // tiles whose epilogue is complete (all items so far)
   int ring[4];     // item index of this CTA's item iseq at ring[iseq % 4]; -1 = no more
 };
-constexpr size_t kTrBytes = (size_t)kEpiWarps * 32 * kTrStride * 4;
-// I/O transpose tile: 32 rows x 128 FP32 columns (row stride padded to 132
-// floats: 16-byte aligned rows, conflict-free 8-row column reads)
-constexpr int kIoStride = 132;
-constexpr size_t kIoBytes = (size_t)32 * kIoStride * 4;
-constexpr int kPairsPerIo = 2 * kTcFields / kIoWarps;  // (field, sign) pairs per I/O warp
-static_assert(kPairsPerIo * kIoWarps == 2 * kTcFields, "I/O warps split the pairs evenly");
-constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + kTrBytes + kIoBytes + sizeof(Ctl) + 1024;
+constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + sizeof(Ctl) + 1024;
 static_assert(kSmemTotal <= 232448, "fits the 227 KB of shared memory one CTA may use");
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -327,7 +333,7 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-__device__ __forceinline__ void io_bar() { asm volatile("bar.sync 2, %0;" ::"n"(32 * kIoWarps) : "memory"); }
+__device__ __forceinline__ void io_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kIoThreads) : "memory"); }
 // The named barriers with an AND over the group: every warp of the group takes
 // the same decision after a bounded wait, so none is left at a barrier alone.
 __device__ __forceinline__ bool epi_and(bool v) {
@@ -344,7 +350,7 @@ __device__ __forceinline__ bool io_and(bool v) {
   asm volatile(
       "{\n .reg .pred q, r;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred r, 2, %2, q;\n selp.u32 %0, 1, 0, r;\n}"
       : "=r"(r)
-      : "r"((uint32_t)v), "n"(32 * kIoWarps)
+      : "r"((uint32_t)v), "n"(kIoThreads)
       : "memory");
   return r != 0;
 }
@@ -356,15 +362,6 @@ __device__ __forceinline__ long coef_offset(long N, long m) {
   return m > 0 ? pos : pos + (2 * N - a);
 }
 __device__ __forceinline__ long order_slot(long m) { return m == 0 ? 0 : (m > 0 ? 2 * m - 1 : -2 * m); }
-// Two row segments held in registers: position t -> row.
-struct Segs {
-  int off0, len0, off1;
-};
-__device__ __forceinline__ Segs in_segs(const TcOp& op, bool fwd) {
-  return fwd ? Segs{op.in_off[0], op.in_len[0], op.in_off[1]} : Segs{op.out_off[0], op.out_len[0], op.out_off[1]};
-}
-__device__ __forceinline__ Segs out_segs(const TcOp& op, bool fwd) { return in_segs(op, !fwd); }
-__device__ __forceinline__ int seg_row(int t, const Segs& g) { return t < g.len0 ? g.off0 + t : g.off1 + (t - g.len0); }
 __device__ __forceinline__ const double* coef_base(const double* beta, int N, int am, int f, int s, int F,
                                                    int single, int msingle) {
   if (f >= F || (s == 1 && am == 0)) return nullptr;
@@ -384,23 +381,13 @@ __device__ __forceinline__ const double* value_base(const double* g, int N, int 
   return g + 2 * ((long)f * (4L * N - 1) * 2 * N + order_slot(s == 0 ? am : -am) * 2 * N);
 }
 
-
-
-
-// Byte offset of (row, piece, column) in a vector space (the group layout).
-__device__ __forceinline__ size_t grp_off(int row, int pc, int col) {
-  return (size_t)(row / kTcGrpRows) * kTcGrpBytes + pc * 2048 + (col >> 3) * 128 + (row % kTcGrpRows) * 16 +
-         (col & 7) * 2;
-}
-
-// eight consecutive values (columns 8 m8 .. 8 m8 + 7) of row `row` -> three
-// BF16 pieces, one 16-byte store per piece
-__device__ __forceinline__ void put_pieces8(unsigned char* vec, int row, int m8, float4 xa, float4 xb) {
-  float a[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+// Eight consecutive rows (one group) of one right-hand side -> three BF16
+// pieces, one 16-byte store per piece.
+__device__ __forceinline__ void put_group(unsigned char* vec, int grp, int rhs, const float (&x)[8]) {
   uint32_t h[3][4];
 #pragma unroll
   for (int jj = 0; jj < 8; jj += 2) {
-    float a0 = a[jj], a1 = a[jj + 1];
+    float a0 = x[jj], a1 = x[jj + 1];
 #pragma unroll
     for (int pc = 0; pc < 3; ++pc) {
       const __nv_bfloat162 hb = __floats2bfloat162_rn(a0, a1);
@@ -412,23 +399,12 @@ __device__ __forceinline__ void put_pieces8(unsigned char* vec, int row, int m8,
   }
 #pragma unroll
   for (int pc = 0; pc < 3; ++pc)
-    __stcg(reinterpret_cast<uint4*>(vec + grp_off(row, pc, 8 * m8)), make_uint4(h[pc][0], h[pc][1], h[pc][2], h[pc][3]));
+    __stcg(reinterpret_cast<uint4*>(vec + ((size_t)grp * 3 + pc) * 2048 + (size_t)rhs * 16),
+           make_uint4(h[pc][0], h[pc][1], h[pc][2], h[pc][3]));
 }
 
-// Shape of one op in the requested direction.
-struct OpShape {
-  int NN, KK, nT;
-  TcKGeom kg;  // the K side widened to whole row groups (nK chunks, kp_tot columns)
-};
-__device__ __forceinline__ OpShape op_shape(const TcOp& op, bool fwd) {
-  OpShape s;
-  s.NN = fwd ? op.mo : op.ni;
-  s.KK = fwd ? op.ni : op.mo;
-  s.nT = (s.NN + kTcNT - 1) / kTcNT;
-  s.kg = fwd ? tc_kgeom(op.in_off[0], op.in_len[0], op.in_off[1], op.in_len[1])
-             : tc_kgeom(op.out_off[0], op.out_len[0], op.out_off[1], op.out_len[1]);
-  if (s.KK <= 0) s.kg.nK = s.kg.ngt = s.kg.kp_tot = 0;
-  return s;
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
 struct Item {
@@ -454,13 +430,156 @@ __device__ __forceinline__ Item item_of(const TcLaunch& L, int it) {
 // descending phases for the transposed (inverse) apply.
 __device__ __forceinline__ int op_at(const Unit& u, int k, bool fwd) { return fwd ? u.op_begin + k : u.op_end - 1 - k; }
 
+// Scratch row of N position n of an accumulating output (plain segments).
+__device__ __forceinline__ int acc_pos_row(int n, const int32_t* off, const int32_t* len) {
+  return n < len[0] ? off[0] + n : off[1] + (n - len[0]);
+}
+
+// ------------------------------------------------------------------ I/O work
+// Forward gather: X_e group j holds degrees |m| + 16 j + 2 e, X_o group j the
+// odd ones |m| + 16 j + 2 e + 1 (Sec. 3.1.2): one window of 16 consecutive
+// degrees per (pair, j), read as one contiguous 256-byte run.
+__device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, int pr, int ph) {
+  const TcPlan& p = L.plan[itm.plan];
+  const int N = p.N, nx = u.nce + u.nco;
+  const TcRows tr = tc_rows(u.nce, u.nco, N);
+  const double2* src = reinterpret_cast<const double2*>(
+      coef_base(L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pr >> 1), pr & 1, L.F[itm.plan], L.single,
+                L.msingle));
+  const int nwin = (nx + 15) / 16;
+  for (int j = ph; j < nwin; j += kIoPhases) {
+    double2 v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int d = 16 * j + q;
+      v[q] = (src && d < nx) ? __ldg(src + d) : make_double2(0.0, 0.0);
+    }
+    float er[8], ei[8], orr[8], oi[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      er[e] = f64_to_f32_bits(v[2 * e].x);
+      ei[e] = f64_to_f32_bits(v[2 * e].y);
+      orr[e] = f64_to_f32_bits(v[2 * e + 1].x);
+      oi[e] = f64_to_f32_bits(v[2 * e + 1].y);
+    }
+    if (8 * j < u.nce) {
+      put_group(vec, j, 2 * pr, er);
+      put_group(vec, j, 2 * pr + 1, ei);
+    }
+    if (8 * j < u.nco) {
+      put_group(vec, tr.xo / 8 + j, 2 * pr, orr);
+      put_group(vec, tr.xo / 8 + j, 2 * pr + 1, oi);
+    }
+  }
+}
+
+// Transposed gather: the W-weighted parity fold of g (Sec. 3.1.1 with the W
+// of B = A^T W): Y_e[i] = w_{N+i} (g(theta_{N+i}) + g(theta_{N-1-i})),
+// Y_o[i] = w_{N+i} (g(theta_{N+i}) - g(theta_{N-1-i})), group j = nodes 8 j ..
+__device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, int pr, int ph) {
+  const TcPlan& p = L.plan[itm.plan];
+  const int N = p.N;
+  const TcRows tr = tc_rows(u.nce, u.nco, N);
+  const double2* src = reinterpret_cast<const double2*>(
+      value_base(L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pr >> 1), pr & 1, L.F[itm.plan], L.single,
+                 L.msingle));
+  const int nwin = (N + 7) / 8;
+  for (int j = ph; j < nwin; j += kIoPhases) {
+    double2 a[8], b[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = 8 * j + q;
+      const bool ok = src && i < N;
+      a[q] = ok ? __ldg(src + N + i) : make_double2(0.0, 0.0);
+      b[q] = ok ? __ldg(src + N - 1 - i) : make_double2(0.0, 0.0);
+    }
+    float er[8], ei[8], orr[8], oi[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = 8 * j + q;
+      const float wi = i < N ? f64_to_f32_bits(__ldg(p.w + N + i)) : 0.f;
+      const float ax = f64_to_f32_bits(a[q].x), ay = f64_to_f32_bits(a[q].y);
+      const float bx = f64_to_f32_bits(b[q].x), by = f64_to_f32_bits(b[q].y);
+      er[q] = wi * (ax + bx);
+      ei[q] = wi * (ay + by);
+      orr[q] = wi * (ax - bx);
+      oi[q] = wi * (ay - by);
+    }
+    put_group(vec, tr.ye / 8 + j, 2 * pr, er);
+    put_group(vec, tr.ye / 8 + j, 2 * pr + 1, ei);
+    put_group(vec, tr.yo / 8 + j, 2 * pr, orr);
+    put_group(vec, tr.yo / 8 + j, 2 * pr + 1, oi);
+  }
+}
+
+// Forward output: g(theta_{N+i}) = y_e[i] + y_o[i], g(theta_{N-1-i}) =
+// y_e[i] - y_o[i] (Sec. 3.1.2) from the item's accumulation rows; each thread
+// one (field, sign) pair and a contiguous range of nodes.
+__device__ void fold_forward(const TcLaunch& L, const Item& itm, const float* acc, int pr, int ph) {
+  const TcPlan& p = L.plan[itm.plan];
+  const int N = p.N;
+  double2* dst = reinterpret_cast<double2*>(const_cast<double*>(value_base(
+      L.out[itm.plan], N, itm.am, itm.grp * kTcFields + (pr >> 1), pr & 1, L.F[itm.plan], L.single, L.msingle)));
+  if (!dst) return;
+  const int yo = tc_r8(N);  // Y_o's first accumulation row
+  const int per = (N + kIoPhases - 1) / kIoPhases, i0 = ph * per, i1 = min(N, i0 + per);
+  const float* ae = acc + 2 * pr;
+  const float* ao = acc + (size_t)yo * kTcR + 2 * pr;
+  int i = i0;
+  for (; i + 4 <= i1; i += 4) {
+    float2 e[4], o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      e[q] = __ldcg(reinterpret_cast<const float2*>(ae + (size_t)(i + q) * kTcR));
+      o[q] = __ldcg(reinterpret_cast<const float2*>(ao + (size_t)(i + q) * kTcR));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __stcs(dst + N + i + q, make_double2(f32_to_f64_bits(e[q].x + o[q].x), f32_to_f64_bits(e[q].y + o[q].y)));
+      __stcs(dst + N - 1 - i - q, make_double2(f32_to_f64_bits(e[q].x - o[q].x), f32_to_f64_bits(e[q].y - o[q].y)));
+    }
+  }
+  for (; i < i1; ++i) {
+    const float2 e = __ldcg(reinterpret_cast<const float2*>(ae + (size_t)i * kTcR));
+    const float2 o = __ldcg(reinterpret_cast<const float2*>(ao + (size_t)i * kTcR));
+    __stcs(dst + N + i, make_double2(f32_to_f64_bits(e.x + o.x), f32_to_f64_bits(e.y + o.y)));
+    __stcs(dst + N - 1 - i, make_double2(f32_to_f64_bits(e.x - o.x), f32_to_f64_bits(e.y - o.y)));
+  }
+}
+
+// Transposed output: X rows back to the coefficients of degree |m| + d (X_e
+// row d / 2 for even d, X_o row (d - 1) / 2 for odd d).
+__device__ void scatter_inverse(const TcLaunch& L, const Item& itm, const Unit& u, const float* acc, int pr, int ph) {
+  const TcPlan& p = L.plan[itm.plan];
+  const int N = p.N, nx = u.nce + u.nco;
+  double2* dst = reinterpret_cast<double2*>(const_cast<double*>(coef_base(
+      L.out[itm.plan], N, itm.am, itm.grp * kTcFields + (pr >> 1), pr & 1, L.F[itm.plan], L.single, L.msingle)));
+  if (!dst) return;
+  const int xo = tc_r8(u.nce);
+  const int per = (nx + kIoPhases - 1) / kIoPhases, d0 = ph * per, d1 = min(nx, d0 + per);
+  int d = d0;
+  for (; d + 4 <= d1; d += 4) {
+    float2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int dd = d + q, row = (dd & 1) ? xo + (dd >> 1) : (dd >> 1);
+      v[q] = __ldcg(reinterpret_cast<const float2*>(acc + (size_t)row * kTcR + 2 * pr));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) __stcs(dst + d + q, make_double2(f32_to_f64_bits(v[q].x), f32_to_f64_bits(v[q].y)));
+  }
+  for (; d < d1; ++d) {
+    const int row = (d & 1) ? xo + (d >> 1) : (d >> 1);
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(acc + (size_t)row * kTcR + 2 * pr));
+    __stcs(dst + d, make_double2(f32_to_f64_bits(v.x), f32_to_f64_bits(v.y)));
+  }
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_constant__ TcLaunch L, int fwd) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  float* trbuf = reinterpret_cast<float*>(base + (size_t)kStages * kStageBytes);
-  float* iobuf = reinterpret_cast<float*>(base + (size_t)kStages * kStageBytes + kTrBytes);
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes + kTrBytes + kIoBytes);
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -493,12 +612,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = ctl->taddr;
 
-  const int nitems = L.nitems;
   const size_t slot_bytes = tc_slot_bytes(L.max_rows);
   unsigned char* slots = L.ws + (size_t)blockIdx.x * 2 * slot_bytes;  // two vector spaces, alternating by item
+  float* accs = L.acc + (size_t)blockIdx.x * 2 * L.acc_rows * kTcR;  // two accumulation slots, likewise
   const uint32_t stage0 = s32(base);
 
-  if (warp == 0) {
+  if (warp == kProdWarp) {
     // ------------------------------------------------------------ producer
     // One thread streams the stages: per (op, N tile, K chunk) the chunk's
     // operand-image piece block and its input row groups (at most one run of
@@ -508,7 +627,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
     int tiles_before = 0;  // tiles of all earlier phases (all items so far)
     bool ok = true;
     for (int iseq = 0; ok; ++iseq) {
-      // the item and its gathered inputs (the I/O warps publish both)
       int it = -1;
       if (lane == 0) it = next_item(ctl, iseq, ok);
       it = __shfl_sync(0xffffffffu, it, 0);
@@ -533,11 +651,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
           ok = __shfl_sync(0xffffffffu, ok, 0);
           cur_phase = op.phase;
         }
-        const OpShape sh = op_shape(op, fwd);
-        const TcKGeom& kg = sh.kg;
+        const TcDir d = tc_dir(op, fwd);
+        const TcKGeom& kg = d.kg;
         const uint16_t* img = p.img + (fwd ? op.img[0] : op.img[1]);
-        for (int t = 0; t < sh.nT && ok; ++t) {
-          const int Np = (min(kTcNT, sh.NN - kTcNT * t) + 15) & ~15;
+        for (int t = 0; t < d.nT && ok; ++t) {
+          const int Np = (min(kTcNT, d.NN - kTcNT * t) + 15) & ~15;
           for (int c = 0; c < kg.nK && ok; ++c) {
             if (lane == 0) {
               const int s = (int)(jp % kStages);
@@ -551,7 +669,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
                 const int ja = max(j0, min(j1, kg.ng0));
                 const uint32_t bbytes = (uint32_t)(3 * Np * Kp * 2);
                 bulk_expect(&ctl->full[s], bbytes + (uint32_t)(j1 - j0) * kTcGrpBytes);
-                bulk_copy(sB, img + (size_t)t * 384 * kg.kp_tot + (size_t)Np * (96 * c), bbytes, &ctl->full[s]);
+                bulk_copy(sB, img + (size_t)t * (3 * kTcNT) * kg.kp_tot + (size_t)Np * (3 * kTcKC * c), bbytes,
+                          &ctl->full[s]);
                 if (ja > j0)
                   bulk_copy(sA, vec + (size_t)(kg.gs0 + j0) * kTcGrpBytes, (uint32_t)(ja - j0) * kTcGrpBytes,
                             &ctl->full[s]);
@@ -586,65 +705,65 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
         const int nops = u.op_end - u.op_begin;
         TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
         for (int q = 0; q < nops && ok; ++q) {
-          {
-            const TcOp op = nxt;
-            if (q + 1 < nops) nxt = p.ops[op_at(u, q + 1, fwd)];
-            const OpShape sh = op_shape(op, fwd);
-            for (int t = 0; t < sh.nT && ok; ++t, ++tm) {
-              const int b = (int)(tm & 1);
-              const uint32_t v = (uint32_t)(tm >> 1);
-              ok = mbar_wait(ctl, &ctl->acce[b], (v & 1u) ^ 1u);
+          const TcOp op = nxt;
+          if (q + 1 < nops) nxt = p.ops[op_at(u, q + 1, fwd)];
+          const TcDir d = tc_dir(op, fwd);
+          for (int t = 0; t < d.nT && ok; ++t, ++tm) {
+            const int b = (int)(tm & 1);
+            const uint32_t v = (uint32_t)(tm >> 1);
+            ok = mbar_wait(ctl, &ctl->acce[b], (v & 1u) ^ 1u);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int Np = (min(kTcNT, d.NN - kTcNT * t) + 15) & ~15;
+            // BF16 A and B, FP32 D, both operands K-major, N = Np, M = 128
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Np >> 3) << 17) | (8u << 24);
+            const uint32_t dhi = taddr + (uint32_t)(b * kAccCols), dlo = dhi + kTcNT;
+            // descriptors of stage 0 for this tile; a stage, a K step or a piece
+            // moves the start address, i.e. adds (byte offset / 16) to the descriptor
+            const uint32_t bK = (uint32_t)(Np / 8) * 128;
+            const uint64_t a_desc0 = sdesc(stage0, kTcGrpBytes, 128);
+            const uint64_t b_desc0 = sdesc(stage0 + kStageA, bK, 128);
+            for (int c = 0; c < d.kg.nK && ok; ++c, ++jm) {
+              const int s = (int)(jm % kStages);
+              const uint32_t use = (uint32_t)(jm / kStages);
+              ok = mbar_wait(ctl, &ctl->full[s], use & 1u);
               if (!ok) break;
+              // the stage was filled by bulk copies (async proxy), which the
+              // MMAs read through the same proxy: the barrier orders them
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const int Np = (min(kTcNT, sh.NN - kTcNT * t) + 15) & ~15;
-              const uint32_t idesc =
-                  (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(Np >> 3) << 17) | (8u << 24);
-              const uint32_t dhi = taddr + (uint32_t)(b * 256), dlo = dhi + 128;
-              // descriptors of stage 0 for this tile; a stage, a K step or a piece
-              // moves the start address, i.e. adds (byte offset / 16) to the descriptor
-              const uint32_t bK = (uint32_t)(Np / 8) * 128;
-              const uint64_t a_desc0 = sdesc(stage0, kTcGrpBytes, 128);
-              const uint64_t b_desc0 = sdesc(stage0 + kStageA, bK, 128);
-              for (int c = 0; c < sh.kg.nK && ok; ++c, ++jm) {
-                const int s = (int)(jm % kStages);
-                const uint32_t use = (uint32_t)(jm / kStages);
-                ok = mbar_wait(ctl, &ctl->full[s], use & 1u);
-                if (!ok) break;
-                // the stage was filled by bulk copies (async proxy), which the
-                // MMAs read through the same proxy: the barrier orders them
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int Kp = min(kTcKC, sh.kg.kp_tot - kTcKC * c);
-                const uint64_t stg = (uint64_t)((s * kStageBytes) >> 4);
-                const uint64_t ad0 = a_desc0 + stg, bd0 = b_desc0 + stg;
-                const uint64_t bpc = (uint64_t)((Np * Kp * 2) >> 4), bks = (uint64_t)(2 * bK >> 4);
+              const int Kp = min(kTcKC, d.kg.kp_tot - kTcKC * c);
+              const uint64_t stg = (uint64_t)((s * kStageBytes) >> 4);
+              const uint64_t ad0 = a_desc0 + stg, bd0 = b_desc0 + stg;
+              const uint64_t bpc = (uint64_t)((Np * Kp * 2) >> 4), bks = (uint64_t)(2 * bK >> 4);
 #pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                  if (ks * 16 >= Kp) break;
-                  // A MN-major: core (k8, m8) of piece pa at (k8 * 3 + pa) * 2048 + m8 * 128
-                  // (K stride one row group, M stride 128); B K-major, pieces bpc apart
-                  const uint64_t ak = ad0 + (uint64_t)((ks * 2 * kTcGrpBytes) >> 4), bk = bd0 + ks * bks;
-                  const uint32_t first = (c > 0 || ks > 0) ? 1u : 0u;
-                  mma_bf16(dhi, ak, bk, idesc, first);                           // a0 b0
-                  mma_bf16(dlo, ak, bk + bpc, idesc, first);                     // a0 b1
-                  mma_bf16(dlo, ak + (2048 >> 4), bk, idesc, 1u);                // a1 b0
-                  mma_bf16(dlo, ak, bk + 2 * bpc, idesc, 1u);                    // a0 b2
-                  mma_bf16(dlo, ak + (2048 >> 4), bk + bpc, idesc, 1u);          // a1 b1
-                  mma_bf16(dlo, ak + (4096 >> 4), bk, idesc, 1u);                // a2 b0
-                }
-                mma_commit(&ctl->empty[s]);
+              for (int ks = 0; ks < 2; ++ks) {
+                if (ks * 16 >= Kp) break;
+                // A K-major: core (m8, k8) of piece pa at (k8 * 3 + pa) * 2048 + m8 * 128
+                // (K stride one row group, M stride 128); B K-major, pieces bpc apart
+                const uint64_t ak = ad0 + (uint64_t)((ks * 2 * kTcGrpBytes) >> 4), bk = bd0 + ks * bks;
+                const uint32_t first = (c > 0 || ks > 0) ? 1u : 0u;
+                mma_bf16(dhi, ak, bk, idesc, first);                          // a0 b0
+                mma_bf16(dlo, ak, bk + bpc, idesc, first);                    // a0 b1
+                mma_bf16(dlo, ak + (2048 >> 4), bk, idesc, 1u);               // a1 b0
+                mma_bf16(dlo, ak, bk + 2 * bpc, idesc, 1u);                   // a0 b2
+                mma_bf16(dlo, ak + (2048 >> 4), bk + bpc, idesc, 1u);         // a1 b1
+                mma_bf16(dlo, ak + (4096 >> 4), bk, idesc, 1u);               // a2 b0
               }
-              if (ok) mma_commit(&ctl->accf[b]);
+              mma_commit(&ctl->empty[s]);
             }
+            if (ok) mma_commit(&ctl->accf[b]);
           }
         }
       }
     }
     __syncwarp();
-  } else if (warp >= kEpiWarp0 && warp < kIoWarp0) {
-    // accumulators -> rows: warp ew owns TMEM lane quadrant ew (right-hand sides 32 ew ..)
+  } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
+    // ------------------------------------------------------------ epilogue
+    // accumulator -> rows: warp ew owns TMEM lane quadrant ew, thread = one
+    // right-hand side (32 ew + lane), 32 tile positions per TMEM load
     const int ew = warp - kEpiWarp0;
     const int e = tid - 32 * kEpiWarp0;
-    float* T = trbuf + (size_t)ew * 32 * kTrStride;
+    const int rhs = 32 * ew + lane;
     long te = 0;
     int done = 0;
     bool ok = true;
@@ -656,223 +775,128 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       const TcPlan& p = L.plan[itm.plan];
       const Unit u = p.units[itm.am];
       unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
+      float* acc = accs + (size_t)(iseq & 1) * L.acc_rows * kTcR;
+      const TcRows tr = tc_rows(u.nce, u.nco, p.N);
+      const int acc0 = fwd ? tr.ye : 0;  // accumulated rows: Y forward, X transposed
       const int nops = u.op_end - u.op_begin;
-      // accumulated rows (Y forward, X inverse) live in the item's accumulation region
-      float* acc_item = p.acc + ((size_t)itm.grp * p.nunits + itm.am) * (size_t)kTcAccRows(p.N) * kTcR;
-      const int acc0 = fwd ? u.ye : 0;
       TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
       for (int q = 0; q < nops && ok; ++q) {
-        {
-          const TcOp op = nxt;
-          if (q + 1 < nops) nxt = p.ops[op_at(u, q + 1, fwd)];
-          const OpShape sh = op_shape(op, fwd);
-          const Segs osg = out_segs(op, fwd);
-          const bool accum = (op.flags & (fwd ? OP_FWD_ACCUM : OP_BWD_ACCUM)) != 0;
-          for (int t = 0; t < sh.nT && ok; ++t, ++te) {
-            const int b = (int)(te & 1);
-            const uint32_t v = (uint32_t)(te >> 1);
-            ok = epi_and(mbar_wait(ctl, &ctl->accf[b], v & 1u));
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int Nt = min(kTcNT, sh.NN - kTcNT * t);
-            if (sh.KK > 0 || !accum) {
-              for (int c0 = 0; c0 < Nt; c0 += 32) {
-                if (sh.KK > 0) {
-                  uint32_t hv[32], lv[32];
-                  const uint32_t lanes = (uint32_t)(32 * ew) << 16;
-                  tmem_ld32(taddr + lanes + (uint32_t)(b * 256 + c0), hv);
-                  tmem_ld32(taddr + lanes + (uint32_t)(b * 256 + 128 + c0), lv);
-                  tmem_wait_ld();
+        const TcOp op = nxt;
+        if (q + 1 < nops) nxt = p.ops[op_at(u, q + 1, fwd)];
+        const TcDir d = tc_dir(op, fwd);
+        const int32_t* oo = fwd ? op.out_off : op.in_off;
+        const int32_t* ol = fwd ? op.out_len : op.in_len;
+        for (int t = 0; t < d.nT && ok; ++t, ++te) {
+          const int b = (int)(te & 1);
+          const uint32_t v = (uint32_t)(te >> 1);
+          ok = epi_and(mbar_wait(ctl, &ctl->accf[b], v & 1u));
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int Nt = min(kTcNT, d.NN - kTcNT * t);
+          for (int c0 = 0; c0 < Nt; c0 += 32) {
+            uint32_t hv[32];
+            if (d.KK > 0) {
+              uint32_t lv[32];
+              const uint32_t ta = taddr + ((uint32_t)(32 * ew) << 16) + (uint32_t)(b * kAccCols + c0);
+              tmem_ld32(ta, hv);
+              tmem_ld32(ta + kTcNT, lv);
+              tmem_wait_ld();
 #pragma unroll
-                  for (int q = 0; q < 32; ++q) T[q * kTrStride + lane] = __uint_as_float(hv[q]) + __uint_as_float(lv[q]);
-                } else {
+              for (int k = 0; k < 32; ++k) hv[k] = __float_as_uint(__uint_as_float(hv[k]) + __uint_as_float(lv[k]));
+            } else {
 #pragma unroll
-                  for (int q = 0; q < 32; ++q) T[q * kTrStride + lane] = 0.f;
-                }
-                __syncwarp();
-                const int oc = lane & 3;
-#pragma unroll
-                for (int kq = 0; kq < 4; ++kq) {
-                  const int rl = (lane >> 2) + 8 * kq, i = c0 + rl;
-                  if (i < Nt) {
-                    float x[8];
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) x[jj] = T[rl * kTrStride + 8 * oc + jj];
-                    const int r = seg_row(kTcNT * t + i, osg);
-                    const int c8 = 32 * ew + 8 * oc;
-                    if (accum) {
-                      float* dst = acc_item + (size_t)(r - acc0) * kTcR + c8;
-                      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(x[0]),
-                                   "f"(x[1]), "f"(x[2]), "f"(x[3])
-                                   : "memory");
-                      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4), "f"(x[4]),
-                                   "f"(x[5]), "f"(x[6]), "f"(x[7])
-                                   : "memory");
-                    } else {
-                      uint32_t h[3][4];
-#pragma unroll
-                      for (int jj = 0; jj < 8; jj += 2) {
-                        float a0 = x[jj], a1 = x[jj + 1];
-#pragma unroll
-                        for (int pc = 0; pc < 3; ++pc) {
-                          const __nv_bfloat162 hb = __floats2bfloat162_rn(a0, a1);
-                          const float2 hf = __bfloat1622float2(hb);
-                          a0 -= hf.x;
-                          a1 -= hf.y;
-                          h[pc][jj >> 1] = *reinterpret_cast<const uint32_t*>(&hb);
-                        }
-                      }
-#pragma unroll
-                      for (int pc = 0; pc < 3; ++pc)
-                        __stcg(reinterpret_cast<uint4*>(vec + grp_off(r, pc, c8)),
-                               make_uint4(h[pc][0], h[pc][1], h[pc][2], h[pc][3]));
-                    }
-                  }
-                }
-                __syncwarp();
-              }
+              for (int k = 0; k < 32; ++k) hv[k] = 0u;
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl->acce[b]);
-            // the rows written above are read next by bulk copies (async proxy)
-            asm volatile("fence.proxy.async.global;" ::: "memory");
-            __threadfence_block();
-            epi_bar();
-            ++done;
-            if (e == 0) *((volatile int*)&ctl->done_tiles) = done;
+            const int n0 = kTcNT * t + c0;  // N position of hv[0]
+            if (d.accum) {
+#pragma unroll
+              for (int k = 0; k < 32; ++k)
+                if (c0 + k < Nt) {
+                  const int r = acc_pos_row(n0 + k, oo, ol) - acc0;
+                  red_add(acc + (size_t)r * kTcR + rhs, __uint_as_float(hv[k]));
+                }
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj)
+                if (c0 + 8 * jj < Nt) {
+                  float x[8];
+#pragma unroll
+                  for (int k = 0; k < 8; ++k) x[k] = __uint_as_float(hv[8 * jj + k]);
+                  put_group(vec, tc_group(d.ng, n0 / 8 + jj), rhs, x);
+                }
+            }
           }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&ctl->acce[b]);
+          // rows written above are read next by bulk copies (async proxy), the
+          // accumulated rows by the I/O warps
+          if (d.accum)
+            __threadfence();
+          else
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+          __threadfence_block();
+          epi_bar();
+          ++done;
+          if (e == 0) *((volatile int*)&ctl->done_tiles) = done;
         }
       }
     }
   } else if (warp >= kIoWarp0) {
-    // I/O warps.  They take this CTA's items from the launch's work counter
-    // (decreasing cost: orders by cost, field groups inside an order), publish
-    // each in ctl->ring for the other roles, and gather item i into slot i % 2
-    // once item i - 2 (the slot's previous user) has finished all of its tiles.
-    // The outputs go to the accumulation buffer and leave through the output
-    // kernel.  Global data moves through a 32 x 128 shared tile: every load
-    // instruction reads contiguous 512-byte runs of one (field, sign) pair, each
-    // warp keeps its 8 pairs' loads in flight together, and every store writes
-    // whole 16-byte pieces of 8 consecutive columns, 8 rows of a group at a time.
-    // Column c = 4 field + 2 sign + {re, im}.
-    const int iw = warp - kIoWarp0;  // 0 .. kIoWarps - 1
-    float* T = iobuf;
+    // ------------------------------------------------------------ I/O warps
+    // They take this CTA's items from the launch's work counter (decreasing
+    // cost), publish each in ctl->ring for the other roles, gather item i
+    // into slot i % 2 once item i - 2 (the slot's previous user) has finished,
+    // zero its accumulation rows, and then write item i - 1's outputs as soon
+    // as all of its tiles are done.  Thread = (field, sign) pair pr and phase ph.
     const int e = tid - 32 * kIoWarp0;
+    const int pr = e % kPairs, ph = e / kPairs;
     int t_m2 = 0, t_m1 = 0;  // tiles of all items up to i-2, up to i-1
+    Item prev{-1, 0, 0};
     bool ok = L.stall == 0;
     for (int iseq = 0; ok; ++iseq) {
       ok = io_and(counter_wait(ctl, &ctl->done_tiles, t_m2));
       if (!ok) break;
       if (e == 0) {
         const unsigned int w = atomicAdd(L.counter, 1u);
-        ctl->ring[iseq & 3] = w < (unsigned int)nitems ? (int)w : -1;
+        ctl->ring[iseq & 3] = w < (unsigned int)L.nitems ? (int)w : -1;
       }
       io_bar();
       const int it = *((volatile int*)&ctl->ring[iseq & 3]);
-      if (it < 0) {
-        __threadfence_block();
-        if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
-        break;
+      Item itm{-1, 0, 0};
+      if (it >= 0) {
+        itm = item_of(L, it);
+        const TcPlan& p = L.plan[itm.plan];
+        const Unit u = p.units[itm.am];
+        unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
+        if (fwd)
+          gather_forward(L, itm, u, vec, pr, ph);
+        else
+          gather_inverse(L, itm, u, vec, pr, ph);
+        // the item's accumulation rows start at zero: the epilogue adds into them
+        const TcRows tr = tc_rows(u.nce, u.nco, p.N);
+        const int rows = fwd ? tr.yo - tr.ye + p.N : tr.xo + u.nco;
+        float4* a4 = reinterpret_cast<float4*>(accs + (size_t)(iseq & 1) * L.acc_rows * kTcR);
+        for (int k = e; k < rows * (kTcR / 4); k += kIoThreads) __stcg(a4 + k, make_float4(0.f, 0.f, 0.f, 0.f));
+        asm volatile("fence.proxy.async.global;" ::: "memory");  // the rows are read by bulk copies
+        __threadfence();
       }
-      const Item itm = item_of(L, it);
-      const TcPlan& p = L.plan[itm.plan];
-      const int am = itm.am, grp = itm.grp, N = p.N, F = L.F[itm.plan];
-      const double* in = L.in[itm.plan];
-      const int single = L.single, msingle = L.msingle;
-      const Unit u = p.units[am];
-      unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
-      const int nx = u.nce + u.nco;
-      if (fwd) {
-        // X rows from beta: degree k = am + d; d even -> row d/2 (X_e), d odd ->
-        // row nce + d/2 (X_o).  Tile row dl = degree d0 + dl.
-        for (int d0 = 0; d0 < nx; d0 += 32) {
-          const int d = d0 + lane;
-          double2 v[kPairsPerIo];
-#pragma unroll
-          for (int k = 0; k < kPairsPerIo; ++k) {
-            const int pr = iw + kIoWarps * k;
-            const double* bsrc = coef_base(in, N, am, grp * kTcFields + (pr >> 1), pr & 1, F, single, msingle);
-            v[k] = (bsrc && d < nx) ? __ldg(reinterpret_cast<const double2*>(bsrc) + d) : make_double2(0.0, 0.0);
-          }
-#pragma unroll
-          for (int k = 0; k < kPairsPerIo; ++k) {
-            const int pr = iw + kIoWarps * k;
-            *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * pr) =
-                make_float2(f64_to_f32_bits(v[k].x), f64_to_f32_bits(v[k].y));
-          }
-          io_bar();
-          // warp iw: 8 rows of one parity (block iw % 4) x 8 of the 16 column
-          // chunks (half iw / 4); lane = (row, chunk)
-          const int blk = iw & 3, par = blk >> 1;
-          const int j = (blk & 1) * 8 + (lane & 7);  // row of this parity within the chunk
-          const int dd = 2 * j + par;                // its tile row
-          if (d0 + dd < nx) {
-            const int row = (par ? u.nce : 0) + (d0 >> 1) + j;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              const int m8 = (iw >> 2) * 8 + q * 4 + (lane >> 3);
-              put_pieces8(vec, row, m8, *reinterpret_cast<const float4*>(T + dd * kIoStride + 8 * m8),
-                          *reinterpret_cast<const float4*>(T + dd * kIoStride + 8 * m8 + 4));
-            }
-          }
-          io_bar();
-        }
-      } else {
-        // weighted parity fold of g into Y_e, Y_o (Sec. 3.1.1 with the W of
-        // B = A^T W), 16 nodes i0 .. i0 + 15 at a time: lanes 0-15 read
-        // g(theta_{N+i}), lanes 16-31 g(theta_{N-1-i}) of the same node; tile
-        // rows 0-15 take u_e = w (a + b), rows 16-31 u_o = w (a - b).
-        const int hl = lane & 15, hi = lane >> 4;
-        for (int i0 = 0; i0 < N; i0 += 16) {
-          const int i = i0 + hl;
-          const float wi = i < N ? f64_to_f32_bits(__ldg(p.w + N + i)) : 0.f;
-          double2 v[kPairsPerIo];
-#pragma unroll
-          for (int k = 0; k < kPairsPerIo; ++k) {
-            const int pr = iw + kIoWarps * k;
-            const double* gb = value_base(in, N, am, grp * kTcFields + (pr >> 1), pr & 1, F, single, msingle);
-            v[k] = (gb && i < N) ? __ldg(reinterpret_cast<const double2*>(gb) + (hi ? N - 1 - i : N + i))
-                                 : make_double2(0.0, 0.0);
-          }
-#pragma unroll
-          for (int k = 0; k < kPairsPerIo; ++k) {
-            const int pr = iw + kIoWarps * k;
-            const float x = f64_to_f32_bits(v[k].x), y = f64_to_f32_bits(v[k].y);
-            const float ox = __shfl_xor_sync(0xffffffffu, x, 16), oy = __shfl_xor_sync(0xffffffffu, y, 16);
-            // lane < 16 holds a, its partner b; lane >= 16 holds b, its partner a
-            const float2 r = hi ? make_float2(wi * (ox - x), wi * (oy - y)) : make_float2(wi * (x + ox), wi * (y + oy));
-            *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * pr) = r;
-          }
-          io_bar();
-          // warp iw: tile rows 8 (iw % 4) .. + 7 x 8 of the 16 column chunks (half iw / 4)
-          const int tr = (iw & 3) * 8 + (lane & 7);
-          const int ii = i0 + (tr & 15);
-          if (ii < N) {
-            const int row = (tr < 16 ? u.ye : u.yo) + ii;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              const int m8 = (iw >> 2) * 8 + q * 4 + (lane >> 3);
-              put_pieces8(vec, row, m8, *reinterpret_cast<const float4*>(T + tr * kIoStride + 8 * m8),
-                          *reinterpret_cast<const float4*>(T + tr * kIoStride + 8 * m8 + 4));
-            }
-          }
-          io_bar();
-        }
-      }
-      // the item's accumulation rows start at zero: the epilogue adds into them
-      // (forward: the 2N node rows; inverse: the nx degree rows).  Zeroing them
-      // here keeps the lines in L2 for those additions.
-      {
-        float4* acc4 = reinterpret_cast<float4*>(p.acc + ((size_t)grp * p.nunits + am) * (size_t)kTcAccRows(N) * kTcR);
-        const int n4 = (fwd ? 2 * N : nx) * (kTcR / 4);
-        for (int k = e; k < n4; k += 32 * kIoWarps) __stcg(acc4 + k, make_float4(0.f, 0.f, 0.f, 0.f));
-      }
-      asm volatile("fence.proxy.async.global;" ::: "memory");  // the rows are read by bulk copies
-      __threadfence();
       io_bar();
       if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
-      const int t_cur = t_m1 + p.tiles[2 * am + (fwd ? 0 : 1)];
+      // the previous item's outputs, once all of its tiles are done
+      if (prev.plan >= 0) {
+        ok = io_and(counter_wait(ctl, &ctl->done_tiles, t_m1));
+        if (!ok) break;
+        __threadfence();
+        const float* acc = accs + (size_t)((iseq - 1) & 1) * L.acc_rows * kTcR;
+        if (fwd)
+          fold_forward(L, prev, acc, pr, ph);
+        else
+          scatter_inverse(L, prev, L.plan[prev.plan].units[prev.am], acc, pr, ph);
+      }
+      if (it < 0) break;
+      prev = itm;
+      const int t_cur = t_m1 + L.plan[itm.plan].tiles[2 * itm.am + (fwd ? 0 : 1)];
       t_m2 = t_m1;
       t_m1 = t_cur;
     }
@@ -884,106 +908,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
 }
 
-// Output side of the apply: the accumulated rows of every work item (FP32,
-// kTcR right-hand sides per row) to g (forward: the parity fold of Sec. 3.1.2,
-// g(theta_{N+i}) = y_e + y_o, g(theta_{N-1-i}) = y_e - y_o) or to beta
-// (inverse: X rows back to degrees).  A streaming kernel with many warps per
-// SM, so that this part of the I/O runs at HBM bandwidth.  One CTA step is
-// one item and 32 nodes (or degrees), transposed through shared memory so
-// that reads are whole rows and writes are 512-byte runs per (field, sign).
-constexpr int kOutThreads = 256;
-__global__ void __launch_bounds__(kOutThreads) tc_out_kernel(TcPlan p, double* __restrict__ out, int F, int single,
-                                                            int msingle, int fwd) {
-  __shared__ __align__(16) float Te[32 * kIoStride];
-  __shared__ __align__(16) float To[32 * kIoStride];
-  const int N = p.N, lane = threadIdx.x & 31, iw = threadIdx.x >> 5;
-  const int G = (F + kTcFields - 1) / kTcFields;
-  const int nitems = single ? G : p.nunits * G;
-  const int cpi = fwd ? (N + 31) / 32 : (2 * N + 31) / 32;  // chunks per item
-  const long total = (long)nitems * cpi;
-  for (long w = blockIdx.x; w < total; w += gridDim.x) {
-    const int item = (int)(w / cpi), chunk = (int)(w % cpi);
-    const int grp = item % G;
-    const int am = single ? (msingle < 0 ? -msingle : msingle) : item / G;
-    const Unit u = p.units[am];
-    const float* acc_item = p.acc + ((size_t)grp * p.nunits + am) * (size_t)kTcAccRows(N) * kTcR;
-    if (fwd) {
-      const int i0 = 32 * chunk;
-      for (int r = iw; r < 32; r += kOutThreads / 32) {
-        if (i0 + r < N) {
-          *reinterpret_cast<float4*>(Te + r * kIoStride + 4 * lane) =
-              __ldcs(reinterpret_cast<const float4*>(acc_item + (size_t)(i0 + r) * kTcR) + lane);
-          *reinterpret_cast<float4*>(To + r * kIoStride + 4 * lane) =
-              __ldcs(reinterpret_cast<const float4*>(acc_item + (size_t)(N + i0 + r) * kTcR) + lane);
-        }
-      }
-      __syncthreads();
-      const int i = i0 + lane;
-      for (int pr = iw; pr < 2 * kTcFields; pr += kOutThreads / 32) {
-        const int fl = pr >> 1, sgn = pr & 1;
-        const double* gb = value_base(out, N, am, grp * kTcFields + fl, sgn, F, single, msingle);
-        if (gb && i < N) {
-          const float2 ev = *reinterpret_cast<const float2*>(Te + lane * kIoStride + 4 * fl + 2 * sgn);
-          const float2 ov = *reinterpret_cast<const float2*>(To + lane * kIoStride + 4 * fl + 2 * sgn);
-          double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
-          __stcs(gp + N + i, make_double2(f32_to_f64_bits(ev.x + ov.x), f32_to_f64_bits(ev.y + ov.y)));
-          __stcs(gp + N - 1 - i, make_double2(f32_to_f64_bits(ev.x - ov.x), f32_to_f64_bits(ev.y - ov.y)));
-        }
-      }
-      __syncthreads();
-    } else {
-      const int nx = u.nce + u.nco, d0 = 32 * chunk;
-      if (d0 >= nx) continue;  // uniform over the CTA
-      for (int dl = iw; dl < 32; dl += kOutThreads / 32) {
-        const int d = d0 + dl;
-        if (d < nx) {
-          const int t = (d & 1) ? u.nce + (d >> 1) : (d >> 1);
-          *reinterpret_cast<float4*>(Te + dl * kIoStride + 4 * lane) =
-              __ldcs(reinterpret_cast<const float4*>(acc_item + (size_t)t * kTcR) + lane);
-        }
-      }
-      __syncthreads();
-      const int d = d0 + lane;
-      for (int pr = iw; pr < 2 * kTcFields; pr += kOutThreads / 32) {
-        const int fl = pr >> 1, sgn = pr & 1;
-        const double* bdst = coef_base(out, N, am, grp * kTcFields + fl, sgn, F, single, msingle);
-        if (bdst && d < nx) {
-          const float2 v = *reinterpret_cast<const float2*>(Te + lane * kIoStride + 4 * fl + 2 * sgn);
-          __stcs(reinterpret_cast<double2*>(const_cast<double*>(bdst)) + d,
-                 make_double2(f32_to_f64_bits(v.x), f32_to_f64_bits(v.y)));
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
 }  // namespace
 
 size_t tc_smem_bytes() { return kSmemTotal; }
 
 int tc_ctas_per_sm() { return 1; }  // the kernel holds all 512 tensor-memory columns
 
-static int sm_count() {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms;
-}
-
-static cudaError_t launch_out(const TcPlan& p, bool fwd, double* out, int F, int single, int m, int sms, cudaStream_t st) {
-  const int G = (F + kTcFields - 1) / kTcFields;
-  const long items = (long)(single ? 1 : p.nunits) * G;
-  const long chunks = items * (fwd ? (p.N + 31) / 32 : (2 * p.N + 31) / 32);
-  const int out_grid = (int)std::max(1L, std::min(chunks, (long)sms * 6));
-  tc_out_kernel<<<out_grid, kOutThreads, 0, st>>>(p, out, F, single, m, fwd ? 1 : 0);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, int F, int single, int m, int grid,
-                      cudaStream_t st, cudaEvent_t* ev) {
+                      unsigned char* ws, float* acc, unsigned int* counter, int* err, cudaStream_t st,
+                      cudaEvent_t* ev) {
   const int G = (F + kTcFields - 1) / kTcFields;
-  if (G > p.gmax) return cudaErrorInvalidValue;
   TcLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.plan[0] = p;
@@ -995,56 +929,50 @@ cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, 
   L.nitems = single ? G : p.nunits * G;
   L.single = single;
   L.msingle = m;
-  L.ws = p.ws;
+  L.ws = ws;
   L.max_rows = p.max_rows;
-  L.counter = p.counter;
-  L.err = p.err;
-  // (the kernel zeroes each item's accumulation rows itself when it gathers the item)
+  L.acc = acc;
+  L.acc_rows = tc_acc_rows(p.N);
+  L.counter = counter;
+  L.err = err;
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(L, fwd ? 1 : 0);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-  e = launch_out(p, fwd, out, F, single, m, sm_count(), st);
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
   return e;
 }
 
-cudaError_t launch_tc_stall(const TcPlan& p, int grid, cudaStream_t st) {
+cudaError_t launch_tc_stall(const TcPlan& p, unsigned char* ws, float* acc, unsigned int* counter, int* err,
+                            cudaStream_t st) {
   TcLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.plan[0] = p;
   L.F[0] = 1;
   L.nplans = 1;
   L.nitems = 1;
-  L.ws = p.ws;
+  L.ws = ws;
   L.max_rows = p.max_rows;
-  L.counter = p.counter;
-  L.err = p.err;
+  L.acc = acc;
+  L.acc_rows = tc_acc_rows(p.N);
+  L.counter = counter;
+  L.err = err;
   L.stall = 1;
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
-  alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(L, 1);
+  alt_tc_kernel<<<1, kTcThreads, kSmemTotal, st>>>(L, 1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t st, cudaEvent_t* ev) {
   if (L.nplans < 1 || L.nplans > kTcMaxPlans || !L.items) return cudaErrorInvalidValue;
-  for (int q = 0; q < L.nplans; ++q)
-    if ((L.F[q] + kTcFields - 1) / kTcFields > L.plan[q].gmax) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(L, fwd ? 1 : 0);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-  const int sms = sm_count();
-  for (int q = 0; q < L.nplans && e == cudaSuccess; ++q)
-    if (L.F[q] > 0) e = launch_out(L.plan[q], fwd, L.out[q], L.F[q], 0, 0, sms, st);
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
   return e;
 }
 

@@ -13,29 +13,71 @@ namespace sht {
 
 constexpr int kTcFields = 32;            // fields per work item
 constexpr int kTcR = 4 * kTcFields;      // 128 right-hand sides = MMA M
-constexpr int kTcNT = 128;               // N tile (rows of one block product)
+constexpr int kTcNT = 128;               // N tile (rows of one block product per MMA)
 constexpr int kTcKC = 32;                // K chunk per pipeline stage
-constexpr int kTcThreads = 512;          // producer, 2 spare, MMA, 4 epilogue and 8 I/O warps
+constexpr int kTcThreads = 512;          // producer, MMA, 2 spare, 4 epilogue and 8 I/O warps
 constexpr int kTcRowBytes = 3 * kTcR * 2;  // one scratch row: 3 BF16 pieces x 128 values
-// The scratch stores rows in groups of 8 in the tensor cores' MN-major core
+// The scratch stores rows in groups of 8 in the tensor cores' K-major core
 // matrix layout, so that a run of whole groups is the A operand of a K chunk
-// as it sits in shared memory and moves with one bulk copy:
-//   group g = row / 8, piece p, 8-value chunk m8 of the 128 right-hand sides,
-//   row-in-group e = row % 8:  byte (g * 3 + p) * 2048 + m8 * 128 + e * 16.
+// as it sits in shared memory and moves with one bulk copy, and so that one
+// thread holding eight consecutive rows of one right-hand side writes them as
+// one 16-byte store per piece:
+//   group g = row / 8, piece p, right-hand side j, row-in-group e = row % 8:
+//   byte (g * 3 + p) * 2048 + j * 16 + e * 2.
 constexpr int kTcGrpRows = 8;
 constexpr int kTcGrpBytes = kTcGrpRows * kTcRowBytes;  // 6144
 
-// Bytes of one work item's vector space (max_rows rows, whole groups, plus a
-// spare group so that a padded K chunk never reads past the slot).
+__host__ __device__ inline int tc_r8(int v) { return (v + 7) & ~7; }
+
+// Scratch rows of one order's vector space.  The logical layout of a unit is
+// X_e (nce rows), X_o (nco), Y_e (N), Y_o (N), then the intermediate segments,
+// each of which starts on a multiple of 8.  The tensor-core path moves X_o, Y_e
+// and Y_o to group boundaries too, so that every group holds rows of one
+// region only: a group of X_e is 8 even degrees, a group of Y_e 8 nodes.  The
+// intermediates keep their alignment (shifted by a multiple of 8).
+struct TcRows {
+  int xo, ye, yo;  // scratch rows of X_o, Y_e, Y_o (X_e starts at 0)
+  int shift;       // intermediate row r (logical) -> r + shift
+};
+__host__ __device__ inline TcRows tc_rows(int nce, int nco, int N) {
+  TcRows t;
+  t.xo = tc_r8(nce);
+  t.ye = tc_r8(t.xo + nco);
+  t.yo = t.ye + tc_r8(N);
+  t.shift = tc_r8(t.yo + N) - tc_r8(nce + nco + 2 * N);
+  return t;
+}
+// Scratch row of the first row of a logical segment at `off` (each segment
+// lies inside one region).
+__host__ __device__ inline int tc_seg_row(int off, int nce, int nco, int N, const TcRows& t) {
+  if (off < nce) return off;
+  if (off < nce + nco) return off - nce + t.xo;
+  if (off < nce + nco + N) return off - (nce + nco) + t.ye;
+  if (off < nce + nco + 2 * N) return off - (nce + nco + N) + t.yo;
+  return off + t.shift;
+}
+// Rows of an order's scratch vector space.
+__host__ __device__ inline int tc_nrows(int nrows, int nce, int nco, int N) {
+  const TcRows t = tc_rows(nce, nco, N);
+  return nrows + t.shift > t.yo + N ? nrows + t.shift : t.yo + N;
+}
+
+// Bytes of one work item's vector space (max_rows scratch rows, whole groups,
+// plus a spare group so that a padded K chunk never reads past the slot).
 __host__ __device__ inline size_t tc_slot_bytes(int max_rows) {
   return ((size_t)(max_rows + kTcGrpRows - 1) / kTcGrpRows + 1) * kTcGrpBytes;
 }
 
-// K side of one block product in a given direction: its input rows are the
-// two row segments (off0, len0), (off1, len1) of the vector space.  They are
-// widened to whole groups: K position 8 j + e is row 8 G(j) + e with
-// G(j) = gs0 + j for the first ng0 slots and gs1 + j - ng0 after; rows outside
-// the segments get zero columns in the operand image.  K chunks are 4 groups
+// Accumulated FP32 rows of one work item: forward, Y_e at rows 0..N-1 and
+// Y_o at r8(N)..; transposed, X_e at 0.. and X_o at r8(nce)..; kTcR values per
+// row.
+__host__ __device__ inline int tc_acc_rows(int N) { return 2 * N + 8; }
+
+// One side of a block product, widened to whole row groups: its rows are the
+// two row segments (off0, len0), (off1, len1) of the scratch vector space, and
+// position 8 j + e stands for row 8 G(j) + e with G(j) = gs0 + j for the first
+// ng0 groups and gs1 + j - ng0 after; rows outside the segments stand for
+// nothing (zero in the operand image).  On the K side, chunks are 4 groups
 // (32), the last one rounded up to a pair of groups (the MMA K step of 16).
 struct TcKGeom {
   int gs0, ng0, gs1, ng1, ngt, nK, kp_tot;
@@ -51,10 +93,11 @@ __host__ __device__ inline TcKGeom tc_kgeom(int off0, int len0, int off1, int le
   g.kp_tot = g.nK > 0 ? 32 * (g.nK - 1) + 16 * ((g.ngt - 4 * (g.nK - 1) + 1) / 2) : 0;
   return g;
 }
+// Group of the scratch behind widened position group j.
+__host__ __device__ inline int tc_group(const TcKGeom& g, int j) { return j < g.ng0 ? g.gs0 + j : g.gs1 + j - g.ng0; }
 
 // One op as the tensor-core kernel reads it: a single 64-byte record with the
-// offsets of its operand images, so that walking a unit's ops is one load per
-// op (the next one prefetched while the current one runs).
+// offsets of its operand images and its segments in scratch rows.
 struct alignas(16) TcOp {
   int64_t img[2];                    // forward / transposed image (element offsets)
   int32_t mo, ni;
@@ -64,35 +107,64 @@ struct alignas(16) TcOp {
 };
 static_assert(sizeof(TcOp) == 64, "TcOp layout");
 
+// The shape of one op in one direction (forward: out = B in; transposed:
+// in = B^T out).  The N side is the output: rows that accumulate into the
+// FP32 rows of the item (Y forward, X transposed) are N positions one to one;
+// every other output (intermediate rows, each with a single writer) is
+// widened to whole groups like the K side, so that its epilogue writes whole
+// groups.  N tiles of kTcNT positions, the last padded to 16.
+struct TcDir {
+  int NN;       // N positions
+  int nT;       // N tiles
+  int KK;       // unwidened K side
+  int accum;    // outputs accumulate in FP32
+  TcKGeom ng;   // widened output side (when !accum)
+  TcKGeom kg;   // widened input side
+};
+__host__ __device__ inline TcDir tc_dir(const TcOp& op, bool fwd) {
+  const int32_t* io = fwd ? op.in_off : op.out_off;
+  const int32_t* il = fwd ? op.in_len : op.out_len;
+  const int32_t* oo = fwd ? op.out_off : op.in_off;
+  const int32_t* ol = fwd ? op.out_len : op.in_len;
+  TcDir d;
+  d.accum = (op.flags & (fwd ? OP_FWD_ACCUM : OP_BWD_ACCUM)) != 0;
+  d.KK = fwd ? op.ni : op.mo;
+  d.kg = tc_kgeom(io[0], il[0], io[1], il[1]);
+  if (d.KK <= 0) d.kg.nK = d.kg.ngt = d.kg.kp_tot = 0;
+  d.ng = tc_kgeom(oo[0], ol[0], oo[1], ol[1]);
+  d.NN = d.accum ? (fwd ? op.mo : op.ni) : kTcGrpRows * d.ng.ngt;
+  d.nT = (d.NN + kTcNT - 1) / kTcNT;
+  return d;
+}
+
+// Elements of the split-BF16 image of one direction (3 pieces, padded); 0
+// when the op has no K side.
+__host__ __device__ inline size_t tc_image_elems(const TcDir& d) {
+  if (d.NN <= 0 || d.kg.kp_tot <= 0) return 0;
+  const size_t np_tot = (size_t)kTcNT * (d.nT - 1) + ((d.NN - kTcNT * (d.nT - 1) + 15) & ~15);
+  return 3 * np_tot * (size_t)d.kg.kp_tot;
+}
+
+// The op with its segments moved to scratch rows (unit u of order N).
+TcOp tc_op_of(const Op& op, const Unit& u, int N);
+
 struct TcPlan {
   const Unit* units;
-  const TcOp* ops;          // the program's ops, same order
-  const int32_t* tiles;     // per unit: [forward, inverse] number of N tiles of all its ops
+  const TcOp* ops;          // the program's ops, same order, in scratch rows
+  const int32_t* tiles;     // per unit: [forward, transposed] number of N tiles of all its ops
   const int32_t* order;
   const uint16_t* img;      // split-BF16 operand images of every op
   const double* w;
-  unsigned char* ws;        // per-CTA scratch: two vector spaces of tc_slot_bytes(max_rows)
-  // Accumulated rows of every work item (forward: Y_e, Y_o; inverse: X), FP32,
-  // kTcR values per row, kTcAccRows(N) rows per item; item (group g, order
-  // |m|) at (g * nunits + |m|) * kTcAccRows(N) rows.  The kernel zeroes an item's
-  // rows when it gathers the item.
-  float* acc;
-  int gmax;                 // field groups the accumulation buffer holds
-  unsigned int* counter;
-  int* err;                 // set to 1 when a bounded wait gives up
   int N;
   int nunits;
-  int max_rows;
+  int max_rows;             // scratch rows of the largest order
 };
-
-// Rows of one work item's accumulation region: the 2N outputs forward, the
-// 2N - |m| <= 2N inputs of the transposed apply.
-__host__ __device__ inline int kTcAccRows(int N) { return 2 * N; }
 
 // One launch of the tensor-core kernel: up to kTcMaxPlans plans (orders N of
 // their own), each with its own batch of fields.  The work items are
 // (plan, order |m|, field group); they share one work counter, the per-CTA
-// scratch slots (sized for the largest plan) and the error flag.
+// scratch slots and accumulation rows (sized for the largest plan) and the
+// error flag.
 constexpr int kTcMaxPlans = 8;
 struct TcLaunch {
   TcPlan plan[kTcMaxPlans];
@@ -107,6 +179,8 @@ struct TcLaunch {
   int single, msingle;            // one order msingle of plan 0 (alt_*_m)
   unsigned char* ws;              // per-CTA scratch: two slots of tc_slot_bytes(max_rows)
   int max_rows;
+  float* acc;                     // per-CTA accumulation rows: two slots of acc_rows x kTcR floats
+  int acc_rows;
   unsigned int* counter;          // zero before the launch
   int* err;
   // Self-test of the bounded waits: the I/O warps publish no item, so every
@@ -115,36 +189,35 @@ struct TcLaunch {
   int stall;
 };
 
-// Elements of the split-BF16 image of a block with NN rows and K side kg
-// (3 pieces, padded).
-size_t tc_image_elems(int NN, const TcKGeom& kg);
-
 // The split-BF16 image of one op in one direction (forward: B, transposed:
-// B^T), exactly as tc_build_images lays it out for the kernel.
-void tc_op_image(const Op& op, const double* factors, bool transposed, std::vector<uint16_t>& out);
+// B^T), exactly as tc_build_images lays it out for the kernel; `top` is the
+// op in scratch rows (tc_op_of).
+void tc_op_image(const Op& op, const TcOp& top, const double* factors, bool transposed, std::vector<uint16_t>& out);
 
-// Build the forward (NN = mo, KK = ni) and transposed (NN = ni, KK = mo)
-// images of every op from the FP64 factor store, the kernel's op records and
-// the per-unit tile counts.
+// Build the forward and transposed images of every op from the FP64 factor
+// store, the kernel's op records and the per-unit tile counts; max_rows gets
+// the scratch rows of the largest order.
 using TcImages = std::vector<uint16_t, UninitAlloc<uint16_t>>;
-void tc_build_images(const std::vector<Unit>& units, const std::vector<Op>& ops, const double* factors,
-                     TcImages& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles);
+void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op>& ops, const double* factors,
+                     TcImages& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles, int& max_rows);
 
-// One apply: run the persistent tensor-core
-// kernel (gather, block products), then the output kernel (parity fold to g,
-// or scatter to beta).  F <= kTcFields * p.gmax.
-// ev (optional, three events): recorded before the tensor-core kernel, between
-// it and the output kernel, and after the output kernel.
+// One apply of F fields (any F): the persistent tensor-core kernel gathers
+// each work item's inputs, runs its block products and writes its outputs
+// (the parity fold to g forward, the scatter to beta transposed).  ws and acc
+// hold grid CTAs' two scratch slots and two accumulation slots.  ev
+// (optional, two events): recorded before and after the kernel.
 cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, int F, int single, int m, int grid,
-                      cudaStream_t st, cudaEvent_t* ev = nullptr);
+                      unsigned char* ws, float* acc, unsigned int* counter, int* err, cudaStream_t st,
+                      cudaEvent_t* ev = nullptr);
 
-// The same for a batch of plans in one launch of the tensor-core kernel (the
-// launch's items, scratch and counter set up by the caller), followed by one
-// output kernel per plan.  L.counter must be zero on the stream.
+// The same for a batch of plans in one launch (the launch's items, scratch,
+// accumulation slots and counter set up by the caller).  L.counter must be
+// zero on the stream.
 cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t st, cudaEvent_t* ev = nullptr);
 
 // The bounded-wait self-test on plan p (see TcLaunch::stall).
-cudaError_t launch_tc_stall(const TcPlan& p, int grid, cudaStream_t st);
+cudaError_t launch_tc_stall(const TcPlan& p, unsigned char* ws, float* acc, unsigned int* counter, int* err,
+                            cudaStream_t st);
 
 size_t tc_smem_bytes();
 int tc_ctas_per_sm();

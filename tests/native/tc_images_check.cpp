@@ -43,10 +43,11 @@ int main(int argc, char** argv) {
   TcImages img;
   std::vector<TcOp> tops;
   std::vector<int32_t> tiles;
-  tc_build_images(units, ops, factors.data(), img, tops, tiles);
+  int max_rows = 0;
+  tc_build_images(N, units, ops, factors.data(), img, tops, tiles, max_rows);
   const size_t total = img.size();
   std::fill(img.begin(), img.end(), (uint16_t)0xAAAA);
-  tc_build_images(units, ops, factors.data(), img, tops, tiles);
+  tc_build_images(N, units, ops, factors.data(), img, tops, tiles, max_rows);
   if (img.size() != total || tops.size() != ops.size()) return 5;
   size_t at = 0;
   std::vector<uint16_t> want;

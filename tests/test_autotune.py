@@ -24,8 +24,9 @@ def test_candidates_include_defaults_and_are_valid():
 
 def test_work_model_invariants():
     p = sht.Plan(48, 1e-7, flags=HOST, precision=_lib.SHT_MIXED, n0=16, n_leaf=8)
-    ops = p.program(("ops",))["ops"]
-    w = autotune.work_model(ops)
+    prog = p.program(("ops", "units"))
+    ops = prog["ops"]
+    w = autotune.work_model(ops, prog["units"], 48)
     live = ops[ops["ni"] > 0]
     # every product is at least one tile and one stage
     assert w["tiles"] >= len(live) and w["stages"] >= w["tiles"]
@@ -40,8 +41,9 @@ def test_dense_plan_counts():
     # tile, so the stage count is the number of K chunks of each product
     N = 8
     p = sht.Plan(N, 1e-7, flags=HOST | _lib.SHT_FLAG_DENSE, precision=_lib.SHT_MIXED)
-    ops = p.program(("ops",))["ops"]
-    w = autotune.work_model(ops)
+    prog = p.program(("ops", "units"))
+    ops = prog["ops"]
+    w = autotune.work_model(ops, prog["units"], N)
     assert np.all(ops["mo"] <= 128)
     assert w["tiles"] == int((ops["ni"] > 0).sum())
     assert w["stages"] >= w["tiles"]
@@ -58,7 +60,8 @@ def test_rank_is_sorted_by_model():
 def test_sampled_work_model_is_exact_with_every_order():
     N, kw = 64, dict(n0=16, n_leaf=8)
     p = sht.Plan(N, 1e-7, flags=HOST, precision=_lib.SHT_MIXED, **kw)
-    full = autotune.work_model(p.program(("ops",))["ops"])
+    prog = p.program(("ops", "units"))
+    full = autotune.work_model(prog["ops"], prog["units"], N)
     w, entries = autotune.sampled_work_model(N, 1e-7, 2 * N, **kw)
     assert w == full
     assert entries == p.stats()["entries_total"]
@@ -67,7 +70,8 @@ def test_sampled_work_model_is_exact_with_every_order():
 def test_sampled_work_model_is_close_with_a_sample():
     N = 256
     p = sht.Plan(N, 1e-7, flags=HOST, precision=_lib.SHT_MIXED)
-    full = autotune.work_model(p.program(("ops",))["ops"])
+    prog = p.program(("ops", "units"))
+    full = autotune.work_model(prog["ops"], prog["units"], N)
     w, _ = autotune.sampled_work_model(N, 1e-7, 32)
     for k in full:
         assert abs(w[k] / full[k] - 1) < 0.05, (k, w[k], full[k])

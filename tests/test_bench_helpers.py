@@ -21,13 +21,19 @@ def test_workload_plan_overrides():
     assert bench.config_of(bench.workload("fp64_N1024"), 1)["plan"] == "library defaults"
 
 
-def test_headline_traffic_scales_from_its_plan_shape():
-    t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["alt_tc_kernel"]
+def test_headline_traffic_scales_from_its_plan_shape(tmp_path, monkeypatch):
+    # a capture of a smaller case of the same kernel is scaled by algorithmic bytes
+    t = {"mixed_N512_F32_tuned": 300.0, "_algorithmic_mixed_N512_F32_tuned": 200.0, "mixed_N512_F32": 7.0,
+         "_algorithmic_mixed_N512_F32": 5.0}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"alt_tc_kernel": t}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     ref = bench.TRAFFIC_REF["mixed_N1024_F64"]
     v, src = bench.traffic_for("alt_tc_kernel", "mixed_N1024_F64", 1000)
     assert ref in src and abs(v - 1000 * t[ref] / t["_algorithmic_" + ref]) < 1e-6
     v, src = bench.traffic_for("alt_tc_kernel", "mixed_N512_F32")
     assert v == t["mixed_N512_F32"]
+    assert bench.traffic_for("no_such_kernel", "mixed_N512_F32") == (None, None)
 
 
 def test_uneven_workload_names():

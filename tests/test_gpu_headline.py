@@ -97,5 +97,6 @@ def test_inverse_every_field_sampled_orders(headline):
         worst = max(worst, float(err.max()))
         assert np.all(err <= TOL_MIXED), (m, err.max(), int(err.argmax()))
         # and the oracle's inverse of its own forward values gives back beta
-        np.testing.assert_allclose(ref, beta[:, off: off + 2 * N - abs(m)], rtol=0, atol=1e-11)
+        # (FP64 sums over 2N = 2048 nodes: round-off of order 1e-11)
+        np.testing.assert_allclose(ref, beta[:, off: off + 2 * N - abs(m)], rtol=0, atol=1e-10)
     print(f"inverse: max per-(field, order) rel err {worst:.3e} over {len(ms)} orders x {F} fields")
