@@ -6,6 +6,7 @@
 - An allocation failure during plan creation (injected on the host with
   SHT_FAIL_ALLOC): SHT_ERR_OOM, with everything allocated so far released.
 """
+import gc
 import os
 
 import numpy as np
@@ -57,6 +58,9 @@ def test_selftest_needs_a_tensor_core_plan():
 @pytest.mark.parametrize("k", [1, 3, 7, 12])
 def test_injected_allocation_failure(k):
     N = 32
+    # plans of earlier tests can outlive them in reference cycles (an exception
+    # kept by pytest.raises holds its frame): free them before measuring
+    gc.collect()
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     os.environ["SHT_FAIL_ALLOC"] = str(k)
@@ -66,7 +70,10 @@ def test_injected_allocation_failure(k):
         assert e.value.status == _lib.SHT_ERR_OOM
     finally:
         del os.environ["SHT_FAIL_ALLOC"]
+    del e
+    gc.collect()
     torch.cuda.synchronize()
     assert abs(torch.cuda.mem_get_info()[0] - free0) <= 64 << 20  # nothing of the failed plan stays allocated
     p = sht.Plan(N, 1e-7, precision=_lib.SHT_MIXED, max_fields=8)
     assert forward_err(p, N) <= 1e-6
+    p.close()
