@@ -1,7 +1,7 @@
 """The per-order error measures of the GPU parity tests (CPU)."""
 import numpy as np
 
-from parity import field_err, order_err_coefficients, order_err_values
+from parity import field_err, order_err_coefficients, order_err_values, weighted_input_norms
 from paper_2004_11346_gb300 import inputs
 
 
@@ -33,3 +33,19 @@ def test_order_err_coefficients_follows_the_storage_order():
     np.testing.assert_allclose(e[0, pos], 1e-4, rtol=1e-9)
     e[0, pos] = 0
     assert np.nanmax(e) == 0.0
+
+
+def test_weighted_input_norms_bound_the_inverse():
+    # |A_m^T W g| <= |W^(1/2) g| for every order (A^T W A = I): the denominator
+    # the inverse tests use is never below the reference output
+    import oracle
+    N = 8
+    rng = np.random.default_rng(3)
+    g = rng.standard_normal((2, 4 * N - 1, 2 * N, 2))
+    x, w = oracle.gl_rule(2 * N)
+    beta = oracle.alt_inverse(N, g, x, w)
+    wn = weighted_input_norms(g, w)
+    e = order_err_coefficients(np.zeros_like(beta), beta, N, denom=wn)
+    assert e.shape == (2, 4 * N - 1) and np.all(e <= 1 + 1e-12)
+    # and the plain relative error of zero output is exactly one
+    np.testing.assert_allclose(order_err_coefficients(np.zeros_like(beta), beta, N), 1.0)
