@@ -778,6 +778,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       float* acc = accs + (size_t)(iseq & 1) * L.acc_rows * kTcR;
       const TcRows tr = tc_rows(u.nce, u.nco, p.N);
       const int acc0 = fwd ? tr.ye : 0;  // accumulated rows: Y forward, X transposed
+      const int item_tiles = p.tiles[2 * itm.am + (fwd ? 0 : 1)];
+      int tiles_in_item = 0;
       const int nops = u.op_end - u.op_begin;
       TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
       for (int q = 0; q < nops && ok; ++q) {
@@ -829,12 +831,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(&ctl->acce[b]);
-          // rows written above are read next by bulk copies (async proxy), the
-          // accumulated rows by the I/O warps
-          if (d.accum)
-            __threadfence();
-          else
-            asm volatile("fence.proxy.async.global;" ::: "memory");
+          // rows written above are read next by bulk copies (async proxy); the
+          // accumulated rows are read by the I/O warps once the item's last
+          // tile is counted, so only that tile waits for this thread's
+          // additions to be performed
+          if (!d.accum) asm volatile("fence.proxy.async.global;" ::: "memory");
+          if (++tiles_in_item == item_tiles) __threadfence();
           __threadfence_block();
           epi_bar();
           ++done;
