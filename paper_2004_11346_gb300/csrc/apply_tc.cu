@@ -215,8 +215,10 @@ constexpr int kIoWarp0 = 8;                   // warps 8-15 gather inputs and wr
 constexpr int kIoWarps = kTcThreads / 32 - kIoWarp0;
 constexpr int kIoThreads = 32 * kIoWarps;
 constexpr int kPairs = 2 * kTcFields;         // (field, sign) pairs of an item: right-hand sides 2 pr, 2 pr + 1
-constexpr int kIoPhases = kIoThreads / kPairs;
-static_assert(kIoPhases * kPairs == kIoThreads, "I/O threads split the pairs evenly");
+static_assert(kPairs % kIoWarps == 0, "I/O warps split the pairs evenly");
+static_assert(kIoThreads == 4 * kPairs, "four I/O threads per (field, sign) pair write the row groups");
+constexpr int kIoStride = 132;           // floats per I/O tile row (16-byte aligned rows)
+constexpr int kIoTile = 32 * kIoStride;  // one 32-row tile; the I/O warps use two
 constexpr int kStageA = (kTcKC / kTcGrpRows) * kTcGrpBytes;  // 4 row groups: 24 KB
 constexpr int kStageB = 3 * kTcNT * kTcKC * 2;               // 24 KB (largest N tile)
 constexpr int kStageBytes = kStageA + kStageB;
@@ -235,7 +237,7 @@ struct Ctl {
   int done_tiles;  // tiles whose epilogue is complete (all items so far)
   int ring[4];     // item index of this CTA's item iseq at ring[iseq % 4]; -1 = no more
 };
-constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + sizeof(Ctl) + 1024;
+constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + 2 * kIoTile * sizeof(float) + sizeof(Ctl) + 1024;
 static_assert(kSmemTotal <= 232448, "fits the 227 KB of shared memory one CTA may use");
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -403,8 +405,8 @@ __device__ __forceinline__ void put_group(unsigned char* vec, int grp, int rhs, 
            make_uint4(h[pc][0], h[pc][1], h[pc][2], h[pc][3]));
 }
 
-__device__ __forceinline__ void red_add(float* p, float v) {
-  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
 struct Item {
@@ -436,142 +438,184 @@ __device__ __forceinline__ int acc_pos_row(int n, const int32_t* off, const int3
 }
 
 // ------------------------------------------------------------------ I/O work
-// Forward gather: X_e group j holds degrees |m| + 16 j + 2 e, X_o group j the
-// odd ones |m| + 16 j + 2 e + 1 (Sec. 3.1.2): one window of 16 consecutive
-// degrees per (pair, j), read as one contiguous 256-byte run.
-__device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, int pr, int ph) {
+// All global traffic of the I/O warps moves through a 32-row shared tile so
+// that every warp access is a run of 32 consecutive complex values (512 bytes)
+// of one (field, sign) pair: lanes walk degrees or nodes when loading from or
+// storing to beta and g, and walk right-hand sides when writing row groups.
+// Thread e (0 .. kIoThreads - 1) is lane e % 32 of I/O warp e / 32; for the
+// row-group writes it is pair e % kPairs, quarter e / kPairs.
+
+// Forward gather: a window of 32 degrees |m| + d0 .. is two X_e groups (even
+// degrees, Sec. 3.1.2) and two X_o groups (odd degrees).
+__device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, float* T,
+                               int e) {
   const TcPlan& p = L.plan[itm.plan];
-  const int N = p.N, nx = u.nce + u.nco;
+  const int N = p.N, nx = u.nce + u.nco, iw = e >> 5, lane = e & 31;
   const TcRows tr = tc_rows(u.nce, u.nco, N);
-  const double2* src = reinterpret_cast<const double2*>(
-      coef_base(L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pr >> 1), pr & 1, L.F[itm.plan], L.single,
-                L.msingle));
-  const int nwin = (nx + 15) / 16;
-  for (int j = ph; j < nwin; j += kIoPhases) {
-    double2 v[16];
+  const int pr = e % kPairs, q = e / kPairs, par = q >> 1, half = q & 1;
+  for (int d0 = 0; d0 < nx; d0 += 32) {
+    double2 v[kPairs / kIoWarps];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int d = 16 * j + q;
-      v[q] = (src && d < nx) ? __ldg(src + d) : make_double2(0.0, 0.0);
+    for (int k = 0; k < kPairs / kIoWarps; ++k) {
+      const int pk = iw + kIoWarps * k, d = d0 + lane;
+      const double2* src = reinterpret_cast<const double2*>(coef_base(
+          L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1), pk & 1, L.F[itm.plan], L.single, L.msingle));
+      v[k] = (src && d < nx) ? __ldg(src + d) : make_double2(0.0, 0.0);
     }
-    float er[8], ei[8], orr[8], oi[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      er[e] = f64_to_f32_bits(v[2 * e].x);
-      ei[e] = f64_to_f32_bits(v[2 * e].y);
-      orr[e] = f64_to_f32_bits(v[2 * e + 1].x);
-      oi[e] = f64_to_f32_bits(v[2 * e + 1].y);
+    for (int k = 0; k < kPairs / kIoWarps; ++k) {
+      const int pk = iw + kIoWarps * k;
+      *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * pk) =
+          make_float2(f64_to_f32_bits(v[k].x), f64_to_f32_bits(v[k].y));
     }
-    if (8 * j < u.nce) {
-      put_group(vec, j, 2 * pr, er);
-      put_group(vec, j, 2 * pr + 1, ei);
+    io_bar();
+    const int j = d0 / 16 + half;  // group of X_e (par 0) or X_o (par 1)
+    if (kTcGrpRows * j < (par ? u.nco : u.nce)) {
+      float re[8], im[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float2 x = *reinterpret_cast<const float2*>(T + (16 * half + 2 * k + par) * kIoStride + 2 * pr);
+        re[k] = x.x;
+        im[k] = x.y;
+      }
+      const int G = (par ? tr.xo / kTcGrpRows : 0) + j;
+      put_group(vec, G, 2 * pr, re);
+      put_group(vec, G, 2 * pr + 1, im);
     }
-    if (8 * j < u.nco) {
-      put_group(vec, tr.xo / 8 + j, 2 * pr, orr);
-      put_group(vec, tr.xo / 8 + j, 2 * pr + 1, oi);
-    }
+    io_bar();
   }
 }
 
 // Transposed gather: the W-weighted parity fold of g (Sec. 3.1.1 with the W
 // of B = A^T W): Y_e[i] = w_{N+i} (g(theta_{N+i}) + g(theta_{N-1-i})),
-// Y_o[i] = w_{N+i} (g(theta_{N+i}) - g(theta_{N-1-i})), group j = nodes 8 j ..
-__device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, int pr, int ph) {
+// Y_o[i] = w_{N+i} (g(theta_{N+i}) - g(theta_{N-1-i})); a window of 32 nodes
+// is four groups of each.
+__device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, float* T,
+                               int e) {
   const TcPlan& p = L.plan[itm.plan];
-  const int N = p.N;
+  const int N = p.N, iw = e >> 5, lane = e & 31;
   const TcRows tr = tc_rows(u.nce, u.nco, N);
-  const double2* src = reinterpret_cast<const double2*>(
-      value_base(L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pr >> 1), pr & 1, L.F[itm.plan], L.single,
-                 L.msingle));
-  const int nwin = (N + 7) / 8;
-  for (int j = ph; j < nwin; j += kIoPhases) {
-    double2 a[8], b[8];
+  const int pr = e % kPairs, q = e / kPairs;
+  float* Ta = T;             // g(theta_{N+i})
+  float* Tb = T + kIoTile;   // g(theta_{N-1-i})
+  for (int i0 = 0; i0 < N; i0 += 32) {
+    constexpr int kHalf = kPairs / kIoWarps / 2;  // pairs per batch of loads
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int i = 8 * j + q;
-      const bool ok = src && i < N;
-      a[q] = ok ? __ldg(src + N + i) : make_double2(0.0, 0.0);
-      b[q] = ok ? __ldg(src + N - 1 - i) : make_double2(0.0, 0.0);
-    }
-    float er[8], ei[8], orr[8], oi[8];
+    for (int h = 0; h < 2; ++h) {
+      double2 a[kHalf], b[kHalf];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int i = 8 * j + q;
-      const float wi = i < N ? f64_to_f32_bits(__ldg(p.w + N + i)) : 0.f;
-      const float ax = f64_to_f32_bits(a[q].x), ay = f64_to_f32_bits(a[q].y);
-      const float bx = f64_to_f32_bits(b[q].x), by = f64_to_f32_bits(b[q].y);
-      er[q] = wi * (ax + bx);
-      ei[q] = wi * (ay + by);
-      orr[q] = wi * (ax - bx);
-      oi[q] = wi * (ay - by);
+      for (int k = 0; k < kHalf; ++k) {
+        const int pk = iw + kIoWarps * (kHalf * h + k), i = i0 + lane;
+        const double2* src = reinterpret_cast<const double2*>(value_base(
+            L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1), pk & 1, L.F[itm.plan], L.single, L.msingle));
+        const bool ok = src && i < N;
+        a[k] = ok ? __ldg(src + N + i) : make_double2(0.0, 0.0);
+        b[k] = ok ? __ldg(src + N - 1 - i) : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int k = 0; k < kHalf; ++k) {
+        const int pk = iw + kIoWarps * (kHalf * h + k);
+        *reinterpret_cast<float2*>(Ta + lane * kIoStride + 2 * pk) =
+            make_float2(f64_to_f32_bits(a[k].x), f64_to_f32_bits(a[k].y));
+        *reinterpret_cast<float2*>(Tb + lane * kIoStride + 2 * pk) =
+            make_float2(f64_to_f32_bits(b[k].x), f64_to_f32_bits(b[k].y));
+      }
     }
-    put_group(vec, tr.ye / 8 + j, 2 * pr, er);
-    put_group(vec, tr.ye / 8 + j, 2 * pr + 1, ei);
-    put_group(vec, tr.yo / 8 + j, 2 * pr, orr);
-    put_group(vec, tr.yo / 8 + j, 2 * pr + 1, oi);
+    io_bar();
+    if (i0 + kTcGrpRows * q < N) {
+      float er[8], ei[8], orr[8], oi[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int r = kTcGrpRows * q + k, i = i0 + r;
+        const float wi = i < N ? f64_to_f32_bits(__ldg(p.w + N + i)) : 0.f;
+        const float2 x = *reinterpret_cast<const float2*>(Ta + r * kIoStride + 2 * pr);
+        const float2 y = *reinterpret_cast<const float2*>(Tb + r * kIoStride + 2 * pr);
+        er[k] = wi * (x.x + y.x);
+        ei[k] = wi * (x.y + y.y);
+        orr[k] = wi * (x.x - y.x);
+        oi[k] = wi * (x.y - y.y);
+      }
+      const int j = i0 / kTcGrpRows + q;
+      put_group(vec, tr.ye / kTcGrpRows + j, 2 * pr, er);
+      put_group(vec, tr.ye / kTcGrpRows + j, 2 * pr + 1, ei);
+      put_group(vec, tr.yo / kTcGrpRows + j, 2 * pr, orr);
+      put_group(vec, tr.yo / kTcGrpRows + j, 2 * pr + 1, oi);
+    }
+    io_bar();
   }
 }
 
 // Forward output: g(theta_{N+i}) = y_e[i] + y_o[i], g(theta_{N-1-i}) =
-// y_e[i] - y_o[i] (Sec. 3.1.2) from the item's accumulation rows; each thread
-// one (field, sign) pair and a contiguous range of nodes.
-__device__ void fold_forward(const TcLaunch& L, const Item& itm, const float* acc, int pr, int ph) {
+// y_e[i] - y_o[i] (Sec. 3.1.2) from the item's accumulation rows, 32 nodes at
+// a time: whole rows into the tile, then per (field, sign) pair two runs of
+// 32 consecutive nodes of g.
+__device__ void fold_forward(const TcLaunch& L, const Item& itm, const float* acc, float* T, int e) {
   const TcPlan& p = L.plan[itm.plan];
-  const int N = p.N;
-  double2* dst = reinterpret_cast<double2*>(const_cast<double*>(value_base(
-      L.out[itm.plan], N, itm.am, itm.grp * kTcFields + (pr >> 1), pr & 1, L.F[itm.plan], L.single, L.msingle)));
-  if (!dst) return;
+  const int N = p.N, iw = e >> 5, lane = e & 31;
   const int yo = tc_r8(N);  // Y_o's first accumulation row
-  const int per = (N + kIoPhases - 1) / kIoPhases, i0 = ph * per, i1 = min(N, i0 + per);
-  const float* ae = acc + 2 * pr;
-  const float* ao = acc + (size_t)yo * kTcR + 2 * pr;
-  int i = i0;
-  for (; i + 4 <= i1; i += 4) {
-    float2 e[4], o[4];
+  float* Te = T;
+  float* To = T + kIoTile;
+  for (int i0 = 0; i0 < N; i0 += 32) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      e[q] = __ldcg(reinterpret_cast<const float2*>(ae + (size_t)(i + q) * kTcR));
-      o[q] = __ldcg(reinterpret_cast<const float2*>(ao + (size_t)(i + q) * kTcR));
+    for (int r = iw; r < 32; r += kIoWarps) {
+      const int i = i0 + r;
+      float4 ve = make_float4(0.f, 0.f, 0.f, 0.f), vo = ve;
+      if (i < N) {
+        ve = __ldcg(reinterpret_cast<const float4*>(acc + (size_t)i * kTcR) + lane);
+        vo = __ldcg(reinterpret_cast<const float4*>(acc + (size_t)(yo + i) * kTcR) + lane);
+      }
+      *reinterpret_cast<float4*>(Te + r * kIoStride + 4 * lane) = ve;
+      *reinterpret_cast<float4*>(To + r * kIoStride + 4 * lane) = vo;
     }
+    io_bar();
+    const int i = i0 + lane;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      __stcs(dst + N + i + q, make_double2(f32_to_f64_bits(e[q].x + o[q].x), f32_to_f64_bits(e[q].y + o[q].y)));
-      __stcs(dst + N - 1 - i - q, make_double2(f32_to_f64_bits(e[q].x - o[q].x), f32_to_f64_bits(e[q].y - o[q].y)));
+    for (int k = 0; k < kPairs / kIoWarps; ++k) {
+      const int pk = iw + kIoWarps * k;
+      double2* dst = reinterpret_cast<double2*>(const_cast<double*>(value_base(
+          L.out[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1), pk & 1, L.F[itm.plan], L.single, L.msingle)));
+      if (dst && i < N) {
+        const float2 ev = *reinterpret_cast<const float2*>(Te + lane * kIoStride + 2 * pk);
+        const float2 ov = *reinterpret_cast<const float2*>(To + lane * kIoStride + 2 * pk);
+        __stcs(dst + N + i, make_double2(f32_to_f64_bits(ev.x + ov.x), f32_to_f64_bits(ev.y + ov.y)));
+        __stcs(dst + N - 1 - i, make_double2(f32_to_f64_bits(ev.x - ov.x), f32_to_f64_bits(ev.y - ov.y)));
+      }
     }
-  }
-  for (; i < i1; ++i) {
-    const float2 e = __ldcg(reinterpret_cast<const float2*>(ae + (size_t)i * kTcR));
-    const float2 o = __ldcg(reinterpret_cast<const float2*>(ao + (size_t)i * kTcR));
-    __stcs(dst + N + i, make_double2(f32_to_f64_bits(e.x + o.x), f32_to_f64_bits(e.y + o.y)));
-    __stcs(dst + N - 1 - i, make_double2(f32_to_f64_bits(e.x - o.x), f32_to_f64_bits(e.y - o.y)));
+    io_bar();
   }
 }
 
 // Transposed output: X rows back to the coefficients of degree |m| + d (X_e
-// row d / 2 for even d, X_o row (d - 1) / 2 for odd d).
-__device__ void scatter_inverse(const TcLaunch& L, const Item& itm, const Unit& u, const float* acc, int pr, int ph) {
+// row d / 2 for even d, X_o row (d - 1) / 2 for odd d), 32 degrees at a time:
+// 16 X_e and 16 X_o rows into the tile, then per pair one run of 32
+// consecutive coefficients.
+__device__ void scatter_inverse(const TcLaunch& L, const Item& itm, const Unit& u, const float* acc, float* T,
+                                int e) {
   const TcPlan& p = L.plan[itm.plan];
-  const int N = p.N, nx = u.nce + u.nco;
-  double2* dst = reinterpret_cast<double2*>(const_cast<double*>(coef_base(
-      L.out[itm.plan], N, itm.am, itm.grp * kTcFields + (pr >> 1), pr & 1, L.F[itm.plan], L.single, L.msingle)));
-  if (!dst) return;
+  const int N = p.N, nx = u.nce + u.nco, iw = e >> 5, lane = e & 31;
   const int xo = tc_r8(u.nce);
-  const int per = (nx + kIoPhases - 1) / kIoPhases, d0 = ph * per, d1 = min(nx, d0 + per);
-  int d = d0;
-  for (; d + 4 <= d1; d += 4) {
-    float2 v[4];
+  for (int d0 = 0; d0 < nx; d0 += 32) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int dd = d + q, row = (dd & 1) ? xo + (dd >> 1) : (dd >> 1);
-      v[q] = __ldcg(reinterpret_cast<const float2*>(acc + (size_t)row * kTcR + 2 * pr));
+    for (int r = iw; r < 32; r += kIoWarps) {
+      const int rr = d0 / 2 + (r & 15);  // row within X_e (r < 16) or X_o
+      const bool ok = r < 16 ? rr < u.nce : rr < u.nco;
+      const float* src = acc + (size_t)(r < 16 ? rr : xo + rr) * kTcR;
+      *reinterpret_cast<float4*>(T + r * kIoStride + 4 * lane) =
+          ok ? __ldcg(reinterpret_cast<const float4*>(src) + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    io_bar();
+    const int d = d0 + lane, trow = (lane & 1) ? 16 + (lane >> 1) : (lane >> 1);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) __stcs(dst + d + q, make_double2(f32_to_f64_bits(v[q].x), f32_to_f64_bits(v[q].y)));
-  }
-  for (; d < d1; ++d) {
-    const int row = (d & 1) ? xo + (d >> 1) : (d >> 1);
-    const float2 v = __ldcg(reinterpret_cast<const float2*>(acc + (size_t)row * kTcR + 2 * pr));
-    __stcs(dst + d, make_double2(f32_to_f64_bits(v.x), f32_to_f64_bits(v.y)));
+    for (int k = 0; k < kPairs / kIoWarps; ++k) {
+      const int pk = iw + kIoWarps * k;
+      double2* dst = reinterpret_cast<double2*>(const_cast<double*>(coef_base(
+          L.out[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1), pk & 1, L.F[itm.plan], L.single, L.msingle)));
+      if (dst && d < nx) {
+        const float2 v = *reinterpret_cast<const float2*>(T + trow * kIoStride + 2 * pk);
+        __stcs(dst + d, make_double2(f32_to_f64_bits(v.x), f32_to_f64_bits(v.y)));
+      }
+    }
+    io_bar();
   }
 }
 
@@ -579,7 +623,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes);
+  float* iot = reinterpret_cast<float*>(base + (size_t)kStages * kStageBytes);  // the I/O warps' two tiles
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes + 2 * kIoTile * sizeof(float));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -811,12 +856,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
             }
             const int n0 = kTcNT * t + c0;  // N position of hv[0]
             if (d.accum) {
+              // 4 x 4 transposes within each quad of lanes (right-hand sides
+              // 4 q .. 4 q + 3): afterwards lane 4 q + k holds row 4 j + k of
+              // all four, added with one 16-byte reduction
+              const int k4 = lane & 3;
+              const bool b0 = (k4 & 1) != 0, b1 = (k4 & 2) != 0;
+              float* arow = acc + (32 * ew + (lane & ~3));
 #pragma unroll
-              for (int k = 0; k < 32; ++k)
-                if (c0 + k < Nt) {
-                  const int r = acc_pos_row(n0 + k, oo, ol) - acc0;
-                  red_add(acc + (size_t)r * kTcR + rhs, __uint_as_float(hv[k]));
+              for (int j = 0; j < 8; ++j) {
+                float x0 = __uint_as_float(hv[4 * j]), x1 = __uint_as_float(hv[4 * j + 1]);
+                float x2 = __uint_as_float(hv[4 * j + 2]), x3 = __uint_as_float(hv[4 * j + 3]);
+                float r0 = __shfl_xor_sync(0xffffffffu, b1 ? x0 : x2, 2);
+                float r1 = __shfl_xor_sync(0xffffffffu, b1 ? x1 : x3, 2);
+                if (b1) {
+                  x0 = r0;
+                  x1 = r1;
+                } else {
+                  x2 = r0;
+                  x3 = r1;
                 }
+                r0 = __shfl_xor_sync(0xffffffffu, b0 ? x0 : x1, 1);
+                r1 = __shfl_xor_sync(0xffffffffu, b0 ? x2 : x3, 1);
+                if (b0) {
+                  x0 = r0;
+                  x2 = r1;
+                } else {
+                  x1 = r0;
+                  x3 = r1;
+                }
+                if (c0 + 4 * j + k4 < Nt) {
+                  const int r = acc_pos_row(n0 + 4 * j + k4, oo, ol) - acc0;
+                  red_add4(arow + (size_t)r * kTcR, x0, x1, x2, x3);
+                }
+              }
             } else {
 #pragma unroll
               for (int jj = 0; jj < 4; ++jj)
@@ -850,9 +922,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
     // cost), publish each in ctl->ring for the other roles, gather item i
     // into slot i % 2 once item i - 2 (the slot's previous user) has finished,
     // zero its accumulation rows, and then write item i - 1's outputs as soon
-    // as all of its tiles are done.  Thread = (field, sign) pair pr and phase ph.
+    // as all of its tiles are done, all through the shared tiles iot.
     const int e = tid - 32 * kIoWarp0;
-    const int pr = e % kPairs, ph = e / kPairs;
     int t_m2 = 0, t_m1 = 0;  // tiles of all items up to i-2, up to i-1
     Item prev{-1, 0, 0};
     bool ok = L.stall == 0;
@@ -872,9 +943,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
         const Unit u = p.units[itm.am];
         unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
         if (fwd)
-          gather_forward(L, itm, u, vec, pr, ph);
+          gather_forward(L, itm, u, vec, iot, e);
         else
-          gather_inverse(L, itm, u, vec, pr, ph);
+          gather_inverse(L, itm, u, vec, iot, e);
         // the item's accumulation rows start at zero: the epilogue adds into them
         const TcRows tr = tc_rows(u.nce, u.nco, p.N);
         const int rows = fwd ? tr.yo - tr.ye + p.N : tr.xo + u.nco;
@@ -892,9 +963,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
         __threadfence();
         const float* acc = accs + (size_t)((iseq - 1) & 1) * L.acc_rows * kTcR;
         if (fwd)
-          fold_forward(L, prev, acc, pr, ph);
+          fold_forward(L, prev, acc, iot, e);
         else
-          scatter_inverse(L, prev, L.plan[prev.plan].units[prev.am], acc, pr, ph);
+          scatter_inverse(L, prev, L.plan[prev.plan].units[prev.am], acc, iot, e);
       }
       if (it < 0) break;
       prev = itm;
