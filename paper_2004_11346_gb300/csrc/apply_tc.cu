@@ -218,7 +218,7 @@ constexpr int kPairs = 2 * kTcFields;         // (field, sign) pairs of an item:
 static_assert(kPairs % kIoWarps == 0, "I/O warps split the pairs evenly");
 static_assert(kIoThreads == 4 * kPairs, "four I/O threads per (field, sign) pair write the row groups");
 constexpr int kIoStride = 132;           // floats per I/O tile row (16-byte aligned rows)
-constexpr int kIoTile = 32 * kIoStride;  // one 32-row tile; the I/O warps use two
+constexpr int kIoTile = 32 * kIoStride;  // the I/O warps' 32-row tile
 constexpr int kStageA = (kTcKC / kTcGrpRows) * kTcGrpBytes;  // 4 row groups: 24 KB
 constexpr int kStageB = 3 * kTcNT * kTcKC * 2;               // 24 KB (largest N tile)
 constexpr int kStageBytes = kStageA + kStageB;
@@ -237,7 +237,7 @@ struct Ctl {
   int done_tiles;  // tiles whose epilogue is complete (all items so far)
   int ring[4];     // item index of this CTA's item iseq at ring[iseq % 4]; -1 = no more
 };
-constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + 2 * kIoTile * sizeof(float) + sizeof(Ctl) + 1024;
+constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + kIoTile * sizeof(float) + sizeof(Ctl) + 1024;
 static_assert(kSmemTotal <= 232448, "fits the 227 KB of shared memory one CTA may use");
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -445,6 +445,10 @@ __device__ __forceinline__ int acc_pos_row(int n, const int32_t* off, const int3
 // Thread e (0 .. kIoThreads - 1) is lane e % 32 of I/O warp e / 32; for the
 // row-group writes it is pair e % kPairs, quarter e / kPairs.
 
+// Every loop below is software-pipelined: the loads of window w + 1 are
+// issued into registers before window w is taken out of the tile, so that
+// their latency overlaps the previous window's stores.
+
 // Forward gather: a window of 32 degrees |m| + d0 .. is two X_e groups (even
 // degrees, Sec. 3.1.2) and two X_o groups (odd degrees).
 __device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, float* T,
@@ -453,22 +457,30 @@ __device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u
   const int N = p.N, nx = u.nce + u.nco, iw = e >> 5, lane = e & 31;
   const TcRows tr = tc_rows(u.nce, u.nco, N);
   const int pr = e % kPairs, q = e / kPairs, par = q >> 1, half = q & 1;
+  constexpr int kP = kPairs / kIoWarps;  // pairs each lane loads per window
+  const double2* src[kP];
+#pragma unroll
+  for (int k = 0; k < kP; ++k) {
+    const int pk = iw + kIoWarps * k;
+    src[k] = reinterpret_cast<const double2*>(coef_base(L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1),
+                                                        pk & 1, L.F[itm.plan], L.single, L.msingle));
+  }
+  double2 v[kP];
+  auto load = [&](int d0) {
+#pragma unroll
+    for (int k = 0; k < kP; ++k) {
+      const int d = d0 + lane;
+      v[k] = (src[k] && d < nx) ? __ldg(src[k] + d) : make_double2(0.0, 0.0);
+    }
+  };
+  load(0);
   for (int d0 = 0; d0 < nx; d0 += 32) {
-    double2 v[kPairs / kIoWarps];
 #pragma unroll
-    for (int k = 0; k < kPairs / kIoWarps; ++k) {
-      const int pk = iw + kIoWarps * k, d = d0 + lane;
-      const double2* src = reinterpret_cast<const double2*>(coef_base(
-          L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1), pk & 1, L.F[itm.plan], L.single, L.msingle));
-      v[k] = (src && d < nx) ? __ldg(src + d) : make_double2(0.0, 0.0);
-    }
-#pragma unroll
-    for (int k = 0; k < kPairs / kIoWarps; ++k) {
-      const int pk = iw + kIoWarps * k;
-      *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * pk) =
+    for (int k = 0; k < kP; ++k)
+      *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * (iw + kIoWarps * k)) =
           make_float2(f64_to_f32_bits(v[k].x), f64_to_f32_bits(v[k].y));
-    }
     io_bar();
+    if (d0 + 32 < nx) load(d0 + 32);
     const int j = d0 / 16 + half;  // group of X_e (par 0) or X_o (par 1)
     if (kTcGrpRows * j < (par ? u.nco : u.nce)) {
       float re[8], im[8];
@@ -488,97 +500,98 @@ __device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u
 
 // Transposed gather: the W-weighted parity fold of g (Sec. 3.1.1 with the W
 // of B = A^T W): Y_e[i] = w_{N+i} (g(theta_{N+i}) + g(theta_{N-1-i})),
-// Y_o[i] = w_{N+i} (g(theta_{N+i}) - g(theta_{N-1-i})); a window of 32 nodes
-// is four groups of each.
+// Y_o[i] = w_{N+i} (g(theta_{N+i}) - g(theta_{N-1-i})).  A window is 16
+// nodes: lanes 0-15 load g(theta_{N+i}) into tile rows 0-15, lanes 16-31
+// g(theta_{N-1-i}) into rows 16-31; it makes two groups of each of Y_e, Y_o.
 __device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, float* T,
                                int e) {
   const TcPlan& p = L.plan[itm.plan];
   const int N = p.N, iw = e >> 5, lane = e & 31;
   const TcRows tr = tc_rows(u.nce, u.nco, N);
-  const int pr = e % kPairs, q = e / kPairs;
-  float* Ta = T;             // g(theta_{N+i})
-  float* Tb = T + kIoTile;   // g(theta_{N-1-i})
-  for (int i0 = 0; i0 < N; i0 += 32) {
-    constexpr int kHalf = kPairs / kIoWarps / 2;  // pairs per batch of loads
+  const int pr = e % kPairs, q = e / kPairs, grp8 = q & 1, par = q >> 1;
+  constexpr int kP = kPairs / kIoWarps;
+  const double2* src[kP];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      double2 a[kHalf], b[kHalf];
+  for (int k = 0; k < kP; ++k) {
+    const int pk = iw + kIoWarps * k;
+    src[k] = reinterpret_cast<const double2*>(value_base(L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1),
+                                                         pk & 1, L.F[itm.plan], L.single, L.msingle));
+  }
+  const int hl = lane & 15, hi = lane >> 4;
+  double2 v[kP];
+  auto load = [&](int i0) {
+    const int i = i0 + hl;
 #pragma unroll
-      for (int k = 0; k < kHalf; ++k) {
-        const int pk = iw + kIoWarps * (kHalf * h + k), i = i0 + lane;
-        const double2* src = reinterpret_cast<const double2*>(value_base(
-            L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1), pk & 1, L.F[itm.plan], L.single, L.msingle));
-        const bool ok = src && i < N;
-        a[k] = ok ? __ldg(src + N + i) : make_double2(0.0, 0.0);
-        b[k] = ok ? __ldg(src + N - 1 - i) : make_double2(0.0, 0.0);
-      }
+    for (int k = 0; k < kP; ++k)
+      v[k] = (src[k] && i < N) ? __ldg(src[k] + (hi ? N - 1 - i : N + i)) : make_double2(0.0, 0.0);
+  };
+  load(0);
+  for (int i0 = 0; i0 < N; i0 += 16) {
 #pragma unroll
-      for (int k = 0; k < kHalf; ++k) {
-        const int pk = iw + kIoWarps * (kHalf * h + k);
-        *reinterpret_cast<float2*>(Ta + lane * kIoStride + 2 * pk) =
-            make_float2(f64_to_f32_bits(a[k].x), f64_to_f32_bits(a[k].y));
-        *reinterpret_cast<float2*>(Tb + lane * kIoStride + 2 * pk) =
-            make_float2(f64_to_f32_bits(b[k].x), f64_to_f32_bits(b[k].y));
-      }
-    }
+    for (int k = 0; k < kP; ++k)
+      *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * (iw + kIoWarps * k)) =
+          make_float2(f64_to_f32_bits(v[k].x), f64_to_f32_bits(v[k].y));
     io_bar();
-    if (i0 + kTcGrpRows * q < N) {
-      float er[8], ei[8], orr[8], oi[8];
+    if (i0 + 16 < N) load(i0 + 16);
+    if (i0 + kTcGrpRows * grp8 < N) {
+      float xr[8], xi[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const int r = kTcGrpRows * q + k, i = i0 + r;
+        const int r = kTcGrpRows * grp8 + k, i = i0 + r;
         const float wi = i < N ? f64_to_f32_bits(__ldg(p.w + N + i)) : 0.f;
-        const float2 x = *reinterpret_cast<const float2*>(Ta + r * kIoStride + 2 * pr);
-        const float2 y = *reinterpret_cast<const float2*>(Tb + r * kIoStride + 2 * pr);
-        er[k] = wi * (x.x + y.x);
-        ei[k] = wi * (x.y + y.y);
-        orr[k] = wi * (x.x - y.x);
-        oi[k] = wi * (x.y - y.y);
+        const float2 a = *reinterpret_cast<const float2*>(T + r * kIoStride + 2 * pr);
+        const float2 b = *reinterpret_cast<const float2*>(T + (16 + r) * kIoStride + 2 * pr);
+        xr[k] = par ? wi * (a.x - b.x) : wi * (a.x + b.x);
+        xi[k] = par ? wi * (a.y - b.y) : wi * (a.y + b.y);
       }
-      const int j = i0 / kTcGrpRows + q;
-      put_group(vec, tr.ye / kTcGrpRows + j, 2 * pr, er);
-      put_group(vec, tr.ye / kTcGrpRows + j, 2 * pr + 1, ei);
-      put_group(vec, tr.yo / kTcGrpRows + j, 2 * pr, orr);
-      put_group(vec, tr.yo / kTcGrpRows + j, 2 * pr + 1, oi);
+      const int G = (par ? tr.yo : tr.ye) / kTcGrpRows + i0 / kTcGrpRows + grp8;
+      put_group(vec, G, 2 * pr, xr);
+      put_group(vec, G, 2 * pr + 1, xi);
     }
     io_bar();
   }
 }
 
 // Forward output: g(theta_{N+i}) = y_e[i] + y_o[i], g(theta_{N-1-i}) =
-// y_e[i] - y_o[i] (Sec. 3.1.2) from the item's accumulation rows, 32 nodes at
-// a time: whole rows into the tile, then per (field, sign) pair two runs of
-// 32 consecutive nodes of g.
+// y_e[i] - y_o[i] (Sec. 3.1.2) from the item's accumulation rows, 16 nodes at
+// a time: Y_e rows into tile rows 0-15 and Y_o rows into 16-31 (whole
+// 512-byte rows), then per (field, sign) pair lanes 0-15 write 16 consecutive
+// nodes of g(theta_{N+i}) and lanes 16-31 16 of g(theta_{N-1-i}).
 __device__ void fold_forward(const TcLaunch& L, const Item& itm, const float* acc, float* T, int e) {
   const TcPlan& p = L.plan[itm.plan];
   const int N = p.N, iw = e >> 5, lane = e & 31;
   const int yo = tc_r8(N);  // Y_o's first accumulation row
-  float* Te = T;
-  float* To = T + kIoTile;
-  for (int i0 = 0; i0 < N; i0 += 32) {
+  constexpr int kR = 32 / kIoWarps;  // tile rows each warp loads
+  float4 v[kR];
+  auto load = [&](int i0) {
 #pragma unroll
-    for (int r = iw; r < 32; r += kIoWarps) {
-      const int i = i0 + r;
-      float4 ve = make_float4(0.f, 0.f, 0.f, 0.f), vo = ve;
-      if (i < N) {
-        ve = __ldcg(reinterpret_cast<const float4*>(acc + (size_t)i * kTcR) + lane);
-        vo = __ldcg(reinterpret_cast<const float4*>(acc + (size_t)(yo + i) * kTcR) + lane);
-      }
-      *reinterpret_cast<float4*>(Te + r * kIoStride + 4 * lane) = ve;
-      *reinterpret_cast<float4*>(To + r * kIoStride + 4 * lane) = vo;
+    for (int k = 0; k < kR; ++k) {
+      const int r = iw + kIoWarps * k, i = i0 + (r & 15);
+      v[k] = i < N ? __ldcg(reinterpret_cast<const float4*>(acc + (size_t)(r < 16 ? i : yo + i) * kTcR) + lane)
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+  };
+  const int hl = lane & 15, hi = lane >> 4;
+  load(0);
+  for (int i0 = 0; i0 < N; i0 += 16) {
+#pragma unroll
+    for (int k = 0; k < kR; ++k)
+      *reinterpret_cast<float4*>(T + (iw + kIoWarps * k) * kIoStride + 4 * lane) = v[k];
     io_bar();
-    const int i = i0 + lane;
+    if (i0 + 16 < N) load(i0 + 16);
+    const int i = i0 + hl;
 #pragma unroll
     for (int k = 0; k < kPairs / kIoWarps; ++k) {
       const int pk = iw + kIoWarps * k;
       double2* dst = reinterpret_cast<double2*>(const_cast<double*>(value_base(
           L.out[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1), pk & 1, L.F[itm.plan], L.single, L.msingle)));
       if (dst && i < N) {
-        const float2 ev = *reinterpret_cast<const float2*>(Te + lane * kIoStride + 2 * pk);
-        const float2 ov = *reinterpret_cast<const float2*>(To + lane * kIoStride + 2 * pk);
-        __stcs(dst + N + i, make_double2(f32_to_f64_bits(ev.x + ov.x), f32_to_f64_bits(ev.y + ov.y)));
-        __stcs(dst + N - 1 - i, make_double2(f32_to_f64_bits(ev.x - ov.x), f32_to_f64_bits(ev.y - ov.y)));
+        const float2 ev = *reinterpret_cast<const float2*>(T + hl * kIoStride + 2 * pk);
+        const float2 ov = *reinterpret_cast<const float2*>(T + (16 + hl) * kIoStride + 2 * pk);
+        if (hi)
+          __stcs(dst + N - 1 - i, make_double2(f32_to_f64_bits(ev.x - ov.x), f32_to_f64_bits(ev.y - ov.y)));
+        else
+          __stcs(dst + N + i, make_double2(f32_to_f64_bits(ev.x + ov.x), f32_to_f64_bits(ev.y + ov.y)));
       }
     }
     io_bar();
@@ -594,16 +607,24 @@ __device__ void scatter_inverse(const TcLaunch& L, const Item& itm, const Unit& 
   const TcPlan& p = L.plan[itm.plan];
   const int N = p.N, nx = u.nce + u.nco, iw = e >> 5, lane = e & 31;
   const int xo = tc_r8(u.nce);
+  constexpr int kR = 32 / kIoWarps;
+  float4 v[kR];
+  auto load = [&](int d0) {
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
+      const int r = iw + kIoWarps * k, rr = d0 / 2 + (r & 15);  // row within X_e (r < 16) or X_o
+      const bool ok = r < 16 ? rr < u.nce : rr < u.nco;
+      v[k] = ok ? __ldcg(reinterpret_cast<const float4*>(acc + (size_t)(r < 16 ? rr : xo + rr) * kTcR) + lane)
+                : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  load(0);
   for (int d0 = 0; d0 < nx; d0 += 32) {
 #pragma unroll
-    for (int r = iw; r < 32; r += kIoWarps) {
-      const int rr = d0 / 2 + (r & 15);  // row within X_e (r < 16) or X_o
-      const bool ok = r < 16 ? rr < u.nce : rr < u.nco;
-      const float* src = acc + (size_t)(r < 16 ? rr : xo + rr) * kTcR;
-      *reinterpret_cast<float4*>(T + r * kIoStride + 4 * lane) =
-          ok ? __ldcg(reinterpret_cast<const float4*>(src) + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    for (int k = 0; k < kR; ++k)
+      *reinterpret_cast<float4*>(T + (iw + kIoWarps * k) * kIoStride + 4 * lane) = v[k];
     io_bar();
+    if (d0 + 32 < nx) load(d0 + 32);
     const int d = d0 + lane, trow = (lane & 1) ? 16 + (lane >> 1) : (lane >> 1);
 #pragma unroll
     for (int k = 0; k < kPairs / kIoWarps; ++k) {
@@ -611,8 +632,8 @@ __device__ void scatter_inverse(const TcLaunch& L, const Item& itm, const Unit& 
       double2* dst = reinterpret_cast<double2*>(const_cast<double*>(coef_base(
           L.out[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1), pk & 1, L.F[itm.plan], L.single, L.msingle)));
       if (dst && d < nx) {
-        const float2 v = *reinterpret_cast<const float2*>(T + trow * kIoStride + 2 * pk);
-        __stcs(dst + d, make_double2(f32_to_f64_bits(v.x), f32_to_f64_bits(v.y)));
+        const float2 x = *reinterpret_cast<const float2*>(T + trow * kIoStride + 2 * pk);
+        __stcs(dst + d, make_double2(f32_to_f64_bits(x.x), f32_to_f64_bits(x.y)));
       }
     }
     io_bar();
@@ -623,8 +644,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  float* iot = reinterpret_cast<float*>(base + (size_t)kStages * kStageBytes);  // the I/O warps' two tiles
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes + 2 * kIoTile * sizeof(float));
+  float* iot = reinterpret_cast<float*>(base + (size_t)kStages * kStageBytes);  // the I/O warps' tile
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes + kIoTile * sizeof(float));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
