@@ -41,9 +41,12 @@ EXTRA_WORKLOADS = {
     # the same with the headline plan's shape scaled to N=512 (n0 = N/4, leaves 4x the default)
     "mixed_N512_F32_tuned": dict(N=512, F=32, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed",
                                  plan=dict(n0=128, n_leaf=128)),
+    # the same with two field groups per order, as the 64-field headline
+    "mixed_N512_F64_tuned": dict(N=512, F=64, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed",
+                                 plan=dict(n0=128, n_leaf=128)),
 }
 # the ncu capture whose traffic a workload's roofline scales (same kernel, same plan shape, smaller case)
-TRAFFIC_REF = {"mixed_N1024_F64": "mixed_N512_F32_tuned"}
+TRAFFIC_REF = {"mixed_N1024_F64": "mixed_N512_F64_tuned"}
 FP64_PEAK_GFLOPS = 1250.0  # GB300 nominal FP64 (vector) rate
 
 
