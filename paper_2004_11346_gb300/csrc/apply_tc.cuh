@@ -68,10 +68,13 @@ __host__ __device__ inline size_t tc_slot_bytes(int max_rows) {
   return ((size_t)(max_rows + kTcGrpRows - 1) / kTcGrpRows + 1) * kTcGrpBytes;
 }
 
-// Accumulated FP32 rows of one work item: forward, Y_e at rows 0..N-1 and
-// Y_o at r8(N)..; transposed, X_e at 0.. and X_o at r8(nce)..; kTcR values per
-// row.
-__host__ __device__ inline int tc_acc_rows(int N) { return 2 * N + 8; }
+// Accumulated FP32 rows of one work item, stored per right-hand side: value
+// (rhs, row) at rhs * tc_acc_rows(N) + row, so that the rows of one
+// right-hand side are contiguous (runs of consecutive nodes or degrees of one
+// field and sign, read and written whole by the output step).  Forward: Y_e
+// at rows 0..N-1 and Y_o at r8(N)..; transposed: X_e at 0.. and X_o at
+// r8(nce)..  A multiple of 8 rows, so that every run starts 32-byte aligned.
+__host__ __device__ inline int tc_acc_rows(int N) { return tc_r8(2 * N + 8); }
 
 // One side of a block product, widened to whole row groups: its rows are the
 // two row segments (off0, len0), (off1, len1) of the scratch vector space, and

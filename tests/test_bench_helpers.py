@@ -23,7 +23,7 @@ def test_workload_plan_overrides():
 
 def test_headline_traffic_scales_from_its_plan_shape(tmp_path, monkeypatch):
     # a capture of a smaller case of the same kernel is scaled by algorithmic bytes
-    t = {"mixed_N512_F32_tuned": 300.0, "_algorithmic_mixed_N512_F32_tuned": 200.0, "mixed_N512_F32": 7.0,
+    t = {"mixed_N512_F64_tuned": 300.0, "_algorithmic_mixed_N512_F64_tuned": 200.0, "mixed_N512_F32": 7.0,
          "_algorithmic_mixed_N512_F32": 5.0}
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"alt_tc_kernel": t}))
