@@ -248,11 +248,11 @@ sht_status sht_plan_load(const char* path, sht_plan_t* out);
  * own, e.g. fields of different resolutions) to their own fields at once.  The
  * work items of all plans -- (plan, order |m|, group of 32 fields) -- form one
  * queue in decreasing order of estimated cost, which one persistent launch of
- * the tensor-core kernel works through, each item writing its own outputs.
+ * the tensor-core kernel works through; each plan's output step follows.
  *  - plans: P distinct SHT_MIXED plans (1 <= P <= 8) on the current device;
  *    fields[q] (>= 0, <= the plan's max_fields) fields go with plans[q].
- *  - The batch owns its work-item table, scratch, accumulation rows and
- *    counter; it uses each plan's ALT-value workspace, so a plan must not run
+ *  - The batch owns its work-item table, scratch and counter; it uses each
+ *    plan's accumulation rows and ALT-value workspace, so a plan must not run
  *    other calls while a batch that contains it is in flight, and must outlive
  *    the batch (destroy the batch first).
  *  - A batch with no fields at all is valid; its calls do nothing.
@@ -307,11 +307,10 @@ sht_status alt_forward_m_noalloc(sht_plan_t plan, int m, const double* beta_m, d
  * alt_* call then records CUDA events on its stream around each kernel it
  * launches; this call waits for them and returns, summed over the launches
  * since the last reset (at most the latest 256):
- *  - apply_ms: the apply kernel of each call (gather, block products and
- *    outputs: for SHT_MIXED the tensor-core kernel, whose I/O warps also write
- *    the parity fold or the scatter),
- *  - output_ms: time between the apply kernel and the end of the call (0: no
- *    path launches a separate output kernel),
+ *  - apply_ms: the block-product kernels (the tensor-core kernel with its
+ *    gather for SHT_MIXED; the whole apply for SHT_FP64 / SHT_FP32),
+ *  - output_ms: the tensor-core path's output kernel (parity fold or
+ *    scatter; 0 for the other precisions),
  *  - launches: the number of launches summed.
  * reset != 0 starts a new sum.  SHT_ERR_UNSUPPORTED without the flag. */
 sht_status sht_plan_kernel_time(sht_plan_t plan, int reset, double* apply_ms, double* output_ms, int64_t* launches);

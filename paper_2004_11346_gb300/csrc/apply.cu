@@ -335,7 +335,8 @@ struct sht_plan_s {
   TcOp* d_tcops = nullptr;
   int32_t* d_tctiles = nullptr;
   unsigned char* d_wstc = nullptr;
-  float* d_acc = nullptr;  // per CTA two accumulation slots of tc_acc_rows(N) rows
+  float* d_acc = nullptr;  // accumulated rows of every work item (tc_gmax field groups)
+  int tc_gmax = 0;
   int tc_max_rows = 0;     // scratch rows of the largest order (tensor-core layout)
   int* d_err = nullptr;
   int nslots_tc = 0;
@@ -441,6 +442,8 @@ TcPlan tc_plan_of(const sht_plan_s* p) {
   t.order = p->d_order;
   t.img = p->d_img;
   t.w = p->d_w;
+  t.acc = p->d_acc;
+  t.gmax = p->tc_gmax;
   t.N = p->prog.N;
   t.nunits = 2 * p->prog.N;
   t.max_rows = p->tc_max_rows;
@@ -460,16 +463,24 @@ sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F,
   }
   if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
   if (p->prog.opts.precision == SHT_MIXED) {
-    // one launch for any number of fields: every work item (order, group of
-    // 32 fields) gathers, applies and writes its outputs in the kernel
-    const int groups = (F + kTcFields - 1) / kTcFields;
-    const int items = (single ? 1 : 2 * p->prog.N) * groups;
-    const int grid_tc = std::min(p->nslots_tc, std::max(1, items));
-    cudaEvent_t* ev = timing_slot(p);
-    if (launch_tc(tc_plan_of(p), fwd, in, out, F, single, m, grid_tc, p->d_wstc, p->d_acc, p->d_counter, p->d_err,
-                  st, ev) != cudaSuccess)
-      return SHT_ERR_CUDA;
-    if (ev && cudaEventRecord(ev[2], st) != cudaSuccess) return SHT_ERR_CUDA;
+    const TcPlan t = tc_plan_of(p);
+    // the accumulation buffer holds tc_gmax groups of kTcFields fields: larger
+    // batches run as several launches on consecutive fields
+    const int N = p->prog.N;
+    const int64_t nb = 2L * (single ? 2 * N - (m < 0 ? -m : m) : 4L * N * N);  // doubles per field of beta
+    const int64_t ng = 2L * (single ? 2 * N : (4L * N - 1) * 2 * N);           // doubles per field of g
+    const int64_t in_stride = fwd ? nb : ng, out_stride = fwd ? ng : nb;
+    const int fb = kTcFields * p->tc_gmax;
+    for (int f0 = 0; f0 < F; f0 += fb) {
+      const int Fb = std::min(fb, F - f0);
+      if (f0 > 0 && cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
+      const int groups = (Fb + kTcFields - 1) / kTcFields;
+      const int items = (single ? 1 : 2 * N) * groups;
+      const int grid_tc = std::min(p->nslots_tc, std::max(1, items));
+      if (launch_tc(t, fwd, in + f0 * in_stride, out + f0 * out_stride, Fb, single, m, grid_tc, p->d_wstc,
+                    p->d_counter, p->d_err, st, timing_slot(p)) != cudaSuccess)
+        return SHT_ERR_CUDA;
+    }
     return SHT_OK;
   }
   if (p->prog.opts.precision == SHT_FP32) {
@@ -593,8 +604,8 @@ sht_status attach_device(sht_plan_s* p) {
     if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_wstc), std::max<size_t>(ws32, 8));
     // rows that widened K chunks read but no op writes must hold finite values
     if (e == cudaSuccess) e = cudaMemset(p->d_wstc, 0, std::max<size_t>(ws32, 8));
-    // two accumulation slots per CTA (the item being applied, the item being written out)
-    const size_t acc = (size_t)p->nslots_tc * 2 * tc_acc_rows(N) * kTcR * sizeof(float);
+    p->tc_gmax = (o.max_fields + kTcFields - 1) / kTcFields;
+    const size_t acc = (size_t)p->tc_gmax * 2 * N * tc_acc_rows(N) * kTcR * sizeof(float);
     if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_acc), acc);
     ws32 += acc;
     if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
@@ -1075,7 +1086,7 @@ sht_status sht_plan_kernel_time(sht_plan_t p, int reset, double* apply_ms, doubl
         cudaEventElapsedTime(&t1, ev[1], ev[2]) != cudaSuccess)
       return SHT_ERR_CUDA;
     a += t0;
-    (void)t1;  // every path writes its outputs inside its apply kernel: no output kernel to time
+    o += p->prog.opts.precision == SHT_MIXED ? t1 : 0.0;  // only the tensor-core path has an output kernel
   }
   *apply_ms = a;
   *output_ms = o;
@@ -1139,8 +1150,6 @@ struct sht_batch_s {
   int nitems = 0;
   unsigned char* d_ws = nullptr;
   int max_rows = 0;        // scratch rows of the largest order of all plans
-  float* d_acc = nullptr;  // per CTA two accumulation slots of tc_acc_rows(max N) rows
-  int acc_rows = 0;
   unsigned int* d_counter = nullptr;
   int* d_err = nullptr;
   int grid = 0;
@@ -1151,7 +1160,6 @@ namespace {
 void free_batch(sht_batch_s* b) {
   cudaFree(b->d_items);
   cudaFree(b->d_ws);
-  cudaFree(b->d_acc);
   cudaFree(b->d_counter);
   cudaFree(b->d_err);
 }
@@ -1181,8 +1189,6 @@ sht_status launch_batch(sht_batch_s* b, bool fwd, const double* const* in, doubl
   L.nitems = b->nitems;
   L.ws = b->d_ws;
   L.max_rows = b->max_rows;
-  L.acc = b->d_acc;
-  L.acc_rows = b->acc_rows;
   L.counter = b->d_counter;
   L.err = b->d_err;
   if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
@@ -1226,7 +1232,6 @@ sht_status sht_batch_create(int P, const sht_plan_t* plans, const int* fields, s
     b->plans[k] = plans[k];
     b->F[k] = fields[k];
     b->max_rows = std::max(b->max_rows, p->tc_max_rows);
-    b->acc_rows = std::max(b->acc_rows, tc_acc_rows(p->prog.N));
     const int G = (fields[k] + kTcFields - 1) / kTcFields;
     for (const Unit& u : p->prog.units)
       for (int g = 0; g < G; ++g) q.push_back({u.cost, make_int4(k, u.am, g, 0)});
@@ -1245,8 +1250,6 @@ sht_status sht_batch_create(int P, const sht_plan_t* plans, const int* fields, s
   if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&b->d_ws), ws);
   // rows that widened K chunks read but no op writes must hold finite values
   if (e == cudaSuccess) e = cudaMemset(b->d_ws, 0, ws);
-  if (e == cudaSuccess)
-    e = plan_malloc(reinterpret_cast<void**>(&b->d_acc), (size_t)b->grid * 2 * b->acc_rows * kTcR * sizeof(float));
   if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&b->d_counter), sizeof(unsigned int));
   if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&b->d_err), sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
@@ -1311,7 +1314,7 @@ sht_status sht_inverse_batch(sht_batch_t b, const double* const* f, double* cons
 sht_status sht_selftest_timeout(sht_plan_t p, void* stream) {
   if (!p) return SHT_ERR_ARG;
   if (p->host_only || p->prog.opts.precision != SHT_MIXED) return SHT_ERR_UNSUPPORTED;
-  return launch_tc_stall(tc_plan_of(p), p->d_wstc, p->d_acc, p->d_counter, p->d_err,
+  return launch_tc_stall(tc_plan_of(p), p->d_wstc, p->d_counter, p->d_err,
                          static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? SHT_OK
              : SHT_ERR_CUDA;

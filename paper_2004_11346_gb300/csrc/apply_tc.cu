@@ -21,10 +21,10 @@
 // them, each thread one right-hand side, and either split the results into
 // BF16 pieces for the next level (eight rows per 16-byte store) or add them
 // in FP32 into the item's accumulation rows; eight I/O warps gather the next
-// item's inputs and write the previous item's outputs (the parity fold of
-// Sec. 3.1.2 forward, the scatter to the coefficients transposed).  Ops of
-// one phase read only rows written by earlier phases: the producer starts a
-// phase after the epilogue has counted every earlier tile.
+// item's inputs.  Ops of one phase read only rows written by earlier phases:
+// the producer starts a phase after the epilogue has counted every earlier
+// tile.  A streaming output kernel then writes g (the parity fold of Sec.
+// 3.1.2) or beta (the scatter) from the accumulation rows.
 // Per 16-wide K step six MMAs accumulate a_p b_q for p + q <= 2, which keeps
 // every product to about 2^-24 relative error (FP32 quality); a0 b0 and the
 // five smaller cross products go to two separate accumulators that the
@@ -215,8 +215,10 @@ constexpr int kIoWarp0 = 8;                   // warps 8-15 gather inputs and wr
 constexpr int kIoWarps = kTcThreads / 32 - kIoWarp0;
 constexpr int kIoThreads = 32 * kIoWarps;
 constexpr int kPairs = 2 * kTcFields;         // (field, sign) pairs of an item: right-hand sides 2 pr, 2 pr + 1
-constexpr int kIoPhases = kIoThreads / kPairs;  // gather threads per (field, sign) pair
-static_assert(kIoPhases * kPairs == kIoThreads && kPairs % kIoWarps == 0, "I/O threads split the pairs evenly");
+static_assert(kPairs % kIoWarps == 0, "I/O warps split the pairs evenly");
+static_assert(kIoThreads == 4 * kPairs, "four I/O threads per (field, sign) pair write the row groups");
+constexpr int kIoStride = 132;           // floats per I/O tile row (16-byte aligned rows)
+constexpr int kIoTile = 32 * kIoStride;  // the I/O warps' 32-row tile
 constexpr int kStageA = (kTcKC / kTcGrpRows) * kTcGrpBytes;  // 4 row groups: 24 KB
 constexpr int kStageB = 3 * kTcNT * kTcKC * 2;               // 24 KB (largest N tile)
 constexpr int kStageBytes = kStageA + kStageB;
@@ -235,7 +237,7 @@ struct Ctl {
   int done_tiles;  // tiles whose epilogue is complete (all items so far)
   int ring[4];     // item index of this CTA's item iseq at ring[iseq % 4]; -1 = no more
 };
-constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + sizeof(Ctl) + 1024;
+constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + kIoTile * sizeof(float) + sizeof(Ctl) + 1024;
 static_assert(kSmemTotal <= 232448, "fits the 227 KB of shared memory one CTA may use");
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -406,29 +408,6 @@ __device__ __forceinline__ void put_group(unsigned char* vec, int grp, int rhs, 
 __device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
-__device__ __forceinline__ void red_add(float* p, float a) {
-  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(a) : "memory");
-}
-// Add values x[0..nv) to consecutive floats starting S floats after the
-// 16-byte aligned address q: whole aligned quads as one 16-byte reduction,
-// the partial quads at either end element by element.
-template <int S>
-__device__ __forceinline__ void red_run(float* q, const uint32_t (&x)[32], int nv) {
-#pragma unroll
-  for (int g = 0; g < 9; ++g) {
-    const int k0 = 4 * g - S;  // value at the quad's first position
-    if (k0 >= 0 && k0 + 3 < 32 && k0 + 3 < nv) {
-      red_add4(q + 4 * g, __uint_as_float(x[k0]), __uint_as_float(x[k0 + 1]), __uint_as_float(x[k0 + 2]),
-               __uint_as_float(x[k0 + 3]));
-    } else {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int k = k0 + t;
-        if (k >= 0 && k < 32 && k < nv) red_add(q + 4 * g + t, __uint_as_float(x[k]));
-      }
-    }
-  }
-}
 
 struct Item {
   int plan, grp, am;
@@ -459,155 +438,117 @@ __device__ __forceinline__ int acc_pos_row(int n, const int32_t* off, const int3
 }
 
 // ------------------------------------------------------------------ I/O work
-// Thread e (0 .. kIoThreads - 1) of the I/O warps.  Gathers: thread = pair
-// e % kPairs and phase e / kPairs; each reads runs of consecutive values of
-// its (field, sign) pair and writes whole row groups of its two right-hand
-// sides.  Outputs: warp e / 32 takes every kIoWarps-th pair, lanes walk 32
-// consecutive nodes or degrees, so reads of the accumulation rows and writes
-// of g or beta are 128- and 512-byte runs.  No shared memory, no barriers.
+// All global traffic of the I/O warps moves through a 32-row shared tile so
+// that every warp access is a run of 32 consecutive complex values (512 bytes)
+// of one (field, sign) pair: lanes walk degrees or nodes when loading from or
+// storing to beta and g, and walk right-hand sides when writing row groups.
+// Thread e (0 .. kIoThreads - 1) is lane e % 32 of I/O warp e / 32; for the
+// row-group writes it is pair e % kPairs, quarter e / kPairs.
 
-// Forward gather: X_e group j holds degrees |m| + 16 j + 2 e, X_o group j the
-// odd ones |m| + 16 j + 2 e + 1 (Sec. 3.1.2): one window of 16 consecutive
-// degrees per (pair, j), read as one 256-byte run.
-__device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, int e) {
+// Every loop below is software-pipelined: the loads of window w + 1 are
+// issued into registers before window w is taken out of the tile, so that
+// their latency overlaps the previous window's stores.
+
+// Forward gather: a window of 32 degrees |m| + d0 .. is two X_e groups (even
+// degrees, Sec. 3.1.2) and two X_o groups (odd degrees).
+__device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, float* T,
+                               int e) {
   const TcPlan& p = L.plan[itm.plan];
-  const int N = p.N, nx = u.nce + u.nco, pr = e % kPairs, ph = e / kPairs;
+  const int N = p.N, nx = u.nce + u.nco, iw = e >> 5, lane = e & 31;
   const TcRows tr = tc_rows(u.nce, u.nco, N);
-  const double2* src = reinterpret_cast<const double2*>(coef_base(
-      L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pr >> 1), pr & 1, L.F[itm.plan], L.single, L.msingle));
-  const int nwin = (nx + 15) / 16;
-  for (int j = ph; j < nwin; j += kIoPhases) {
-    double2 v[16];
+  const int pr = e % kPairs, q = e / kPairs, par = q >> 1, half = q & 1;
+  constexpr int kP = kPairs / kIoWarps;  // pairs each lane loads per window
+  const double2* src[kP];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int d = 16 * j + q;
-      v[q] = (src && d < nx) ? __ldg(src + d) : make_double2(0.0, 0.0);
-    }
-    float er[8], ei[8], orr[8], oi[8];
+  for (int k = 0; k < kP; ++k) {
+    const int pk = iw + kIoWarps * k;
+    src[k] = reinterpret_cast<const double2*>(coef_base(L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1),
+                                                        pk & 1, L.F[itm.plan], L.single, L.msingle));
+  }
+  double2 v[kP];
+  auto load = [&](int d0) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      er[k] = f64_to_f32_bits(v[2 * k].x);
-      ei[k] = f64_to_f32_bits(v[2 * k].y);
-      orr[k] = f64_to_f32_bits(v[2 * k + 1].x);
-      oi[k] = f64_to_f32_bits(v[2 * k + 1].y);
+    for (int k = 0; k < kP; ++k) {
+      const int d = d0 + lane;
+      v[k] = (src[k] && d < nx) ? __ldg(src[k] + d) : make_double2(0.0, 0.0);
     }
-    if (kTcGrpRows * j < u.nce) {
-      put_group(vec, j, 2 * pr, er);
-      put_group(vec, j, 2 * pr + 1, ei);
+  };
+  load(0);
+  for (int d0 = 0; d0 < nx; d0 += 32) {
+#pragma unroll
+    for (int k = 0; k < kP; ++k)
+      *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * (iw + kIoWarps * k)) =
+          make_float2(f64_to_f32_bits(v[k].x), f64_to_f32_bits(v[k].y));
+    io_bar();
+    if (d0 + 32 < nx) load(d0 + 32);
+    const int j = d0 / 16 + half;  // group of X_e (par 0) or X_o (par 1)
+    if (kTcGrpRows * j < (par ? u.nco : u.nce)) {
+      float re[8], im[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float2 x = *reinterpret_cast<const float2*>(T + (16 * half + 2 * k + par) * kIoStride + 2 * pr);
+        re[k] = x.x;
+        im[k] = x.y;
+      }
+      const int G = (par ? tr.xo / kTcGrpRows : 0) + j;
+      put_group(vec, G, 2 * pr, re);
+      put_group(vec, G, 2 * pr + 1, im);
     }
-    if (kTcGrpRows * j < u.nco) {
-      put_group(vec, tr.xo / kTcGrpRows + j, 2 * pr, orr);
-      put_group(vec, tr.xo / kTcGrpRows + j, 2 * pr + 1, oi);
-    }
+    io_bar();
   }
 }
 
 // Transposed gather: the W-weighted parity fold of g (Sec. 3.1.1 with the W
 // of B = A^T W): Y_e[i] = w_{N+i} (g(theta_{N+i}) + g(theta_{N-1-i})),
-// Y_o[i] = w_{N+i} (g(theta_{N+i}) - g(theta_{N-1-i})), group j = nodes 8 j ..
-// 8 j + 7, read as two 128-byte runs.
-__device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, int e) {
+// Y_o[i] = w_{N+i} (g(theta_{N+i}) - g(theta_{N-1-i})).  A window is 16
+// nodes: lanes 0-15 load g(theta_{N+i}) into tile rows 0-15, lanes 16-31
+// g(theta_{N-1-i}) into rows 16-31; it makes two groups of each of Y_e, Y_o.
+__device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, float* T,
+                               int e) {
   const TcPlan& p = L.plan[itm.plan];
-  const int N = p.N, pr = e % kPairs, ph = e / kPairs;
+  const int N = p.N, iw = e >> 5, lane = e & 31;
   const TcRows tr = tc_rows(u.nce, u.nco, N);
-  const double2* src = reinterpret_cast<const double2*>(value_base(
-      L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pr >> 1), pr & 1, L.F[itm.plan], L.single, L.msingle));
-  const int nwin = (N + 7) / 8;
-  for (int j = ph; j < nwin; j += kIoPhases) {
-    float er[8], ei[8], orr[8], oi[8];
+  const int pr = e % kPairs, q = e / kPairs, grp8 = q & 1, par = q >> 1;
+  constexpr int kP = kPairs / kIoWarps;
+  const double2* src[kP];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {  // two batches of four nodes keep the loads within the register budget
-      double2 a[4], b[4];
+  for (int k = 0; k < kP; ++k) {
+    const int pk = iw + kIoWarps * k;
+    src[k] = reinterpret_cast<const double2*>(value_base(L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1),
+                                                         pk & 1, L.F[itm.plan], L.single, L.msingle));
+  }
+  const int hl = lane & 15, hi = lane >> 4;
+  double2 v[kP];
+  auto load = [&](int i0) {
+    const int i = i0 + hl;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = 8 * j + 4 * h + q;
-        const bool ok = src && i < N;
-        a[q] = ok ? __ldg(src + N + i) : make_double2(0.0, 0.0);
-        b[q] = ok ? __ldg(src + N - 1 - i) : make_double2(0.0, 0.0);
-      }
+    for (int k = 0; k < kP; ++k)
+      v[k] = (src[k] && i < N) ? __ldg(src[k] + (hi ? N - 1 - i : N + i)) : make_double2(0.0, 0.0);
+  };
+  load(0);
+  for (int i0 = 0; i0 < N; i0 += 16) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = 8 * j + 4 * h + q, k = 4 * h + q;
+    for (int k = 0; k < kP; ++k)
+      *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * (iw + kIoWarps * k)) =
+          make_float2(f64_to_f32_bits(v[k].x), f64_to_f32_bits(v[k].y));
+    io_bar();
+    if (i0 + 16 < N) load(i0 + 16);
+    if (i0 + kTcGrpRows * grp8 < N) {
+      float xr[8], xi[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int r = kTcGrpRows * grp8 + k, i = i0 + r;
         const float wi = i < N ? f64_to_f32_bits(__ldg(p.w + N + i)) : 0.f;
-        const float ax = f64_to_f32_bits(a[q].x), ay = f64_to_f32_bits(a[q].y);
-        const float bx = f64_to_f32_bits(b[q].x), by = f64_to_f32_bits(b[q].y);
-        er[k] = wi * (ax + bx);
-        ei[k] = wi * (ay + by);
-        orr[k] = wi * (ax - bx);
-        oi[k] = wi * (ay - by);
+        const float2 a = *reinterpret_cast<const float2*>(T + r * kIoStride + 2 * pr);
+        const float2 b = *reinterpret_cast<const float2*>(T + (16 + r) * kIoStride + 2 * pr);
+        xr[k] = par ? wi * (a.x - b.x) : wi * (a.x + b.x);
+        xi[k] = par ? wi * (a.y - b.y) : wi * (a.y + b.y);
       }
+      const int G = (par ? tr.yo : tr.ye) / kTcGrpRows + i0 / kTcGrpRows + grp8;
+      put_group(vec, G, 2 * pr, xr);
+      put_group(vec, G, 2 * pr + 1, xi);
     }
-    put_group(vec, tr.ye / kTcGrpRows + j, 2 * pr, er);
-    put_group(vec, tr.ye / kTcGrpRows + j, 2 * pr + 1, ei);
-    put_group(vec, tr.yo / kTcGrpRows + j, 2 * pr, orr);
-    put_group(vec, tr.yo / kTcGrpRows + j, 2 * pr + 1, oi);
-  }
-}
-
-// Forward output: g(theta_{N+i}) = y_e[i] + y_o[i], g(theta_{N-1-i}) =
-// y_e[i] - y_o[i] (Sec. 3.1.2) from the item's accumulation rows (Y_e of
-// right-hand side r at rows 0..N-1 of its run, Y_o at r8(N)..).
-__device__ void fold_forward(const TcLaunch& L, const Item& itm, const float* acc, int e) {
-  const TcPlan& p = L.plan[itm.plan];
-  const int N = p.N, iw = e >> 5, lane = e & 31, yo = tc_r8(N);
-  for (int pk = iw; pk < kPairs; pk += kIoWarps) {
-    double2* dst = reinterpret_cast<double2*>(const_cast<double*>(value_base(
-        L.out[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1), pk & 1, L.F[itm.plan], L.single, L.msingle)));
-    if (!dst) continue;  // uniform over the warp
-    const float* xr = acc + (size_t)(2 * pk) * L.acc_rows;
-    const float* xi = xr + L.acc_rows;
-    for (int i0 = 0; i0 < N; i0 += 128) {
-      float v[4][4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int i = i0 + 32 * c + lane;
-        if (i < N) {
-          v[c][0] = __ldcg(xr + i);
-          v[c][1] = __ldcg(xi + i);
-          v[c][2] = __ldcg(xr + yo + i);
-          v[c][3] = __ldcg(xi + yo + i);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int i = i0 + 32 * c + lane;
-        if (i < N) {
-          __stcs(dst + N + i, make_double2(f32_to_f64_bits(v[c][0] + v[c][2]), f32_to_f64_bits(v[c][1] + v[c][3])));
-          __stcs(dst + N - 1 - i,
-                 make_double2(f32_to_f64_bits(v[c][0] - v[c][2]), f32_to_f64_bits(v[c][1] - v[c][3])));
-        }
-      }
-    }
-  }
-}
-
-// Transposed output: X rows back to the coefficients of degree |m| + d (X_e
-// row d / 2 for even d, X_o row r8(nce) + (d - 1) / 2 for odd d).
-__device__ void scatter_inverse(const TcLaunch& L, const Item& itm, const Unit& u, const float* acc, int e) {
-  const TcPlan& p = L.plan[itm.plan];
-  const int N = p.N, nx = u.nce + u.nco, iw = e >> 5, lane = e & 31, xo = tc_r8(u.nce);
-  for (int pk = iw; pk < kPairs; pk += kIoWarps) {
-    double2* dst = reinterpret_cast<double2*>(const_cast<double*>(coef_base(
-        L.out[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1), pk & 1, L.F[itm.plan], L.single, L.msingle)));
-    if (!dst) continue;  // uniform over the warp
-    const float* xr = acc + (size_t)(2 * pk) * L.acc_rows;
-    const float* xi = xr + L.acc_rows;
-    for (int d0 = 0; d0 < nx; d0 += 128) {
-      float v[4][2];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int d = d0 + 32 * c + lane, row = (d & 1) ? xo + (d >> 1) : (d >> 1);
-        if (d < nx) {
-          v[c][0] = __ldcg(xr + row);
-          v[c][1] = __ldcg(xi + row);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int d = d0 + 32 * c + lane;
-        if (d < nx) __stcs(dst + d, make_double2(f32_to_f64_bits(v[c][0]), f32_to_f64_bits(v[c][1])));
-      }
-    }
+    io_bar();
   }
 }
 
@@ -615,7 +556,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes);
+  float* iot = reinterpret_cast<float*>(base + (size_t)kStages * kStageBytes);  // the I/O warps' tile
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes + kIoTile * sizeof(float));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -650,7 +592,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
 
   const size_t slot_bytes = tc_slot_bytes(L.max_rows);
   unsigned char* slots = L.ws + (size_t)blockIdx.x * 2 * slot_bytes;  // two vector spaces, alternating by item
-  float* accs = L.acc + (size_t)blockIdx.x * 2 * L.acc_rows * kTcR;  // two accumulation slots, likewise
   const uint32_t stage0 = s32(base);
 
   if (warp == kProdWarp) {
@@ -811,11 +752,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       const TcPlan& p = L.plan[itm.plan];
       const Unit u = p.units[itm.am];
       unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
-      float* acc = accs + (size_t)(iseq & 1) * L.acc_rows * kTcR;
+      float* acc = p.acc + ((size_t)itm.grp * p.nunits + itm.am) * (size_t)tc_acc_rows(p.N) * kTcR;
       const TcRows tr = tc_rows(u.nce, u.nco, p.N);
       const int acc0 = fwd ? tr.ye : 0;  // accumulated rows: Y forward, X transposed
-      const int item_tiles = p.tiles[2 * itm.am + (fwd ? 0 : 1)];
-      int tiles_in_item = 0;
       const int nops = u.op_end - u.op_begin;
       TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
       for (int q = 0; q < nops && ok; ++q) {
@@ -847,25 +786,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
             }
             const int n0 = kTcNT * t + c0;  // N position of hv[0]
             if (d.accum) {
-              // this thread's right-hand side, 32 consecutive positions: one
-              // run of rows when they lie in one output segment (always, for
-              // the single-segment outputs the plans have), added as 16-byte
-              // reductions on aligned quads of rows
-              const int nv = min(32, Nt - c0);
-              float* arow = acc + (size_t)rhs * L.acc_rows;
-              if (n0 + 31 < ol[0] || n0 >= ol[0]) {
-                const int r0 = acc_pos_row(n0, oo, ol) - acc0;
-                float* q = arow + (r0 & ~3);
-                switch (r0 & 3) {
-                  case 0: red_run<0>(q, hv, nv); break;
-                  case 1: red_run<1>(q, hv, nv); break;
-                  case 2: red_run<2>(q, hv, nv); break;
-                  default: red_run<3>(q, hv, nv); break;
-                }
-              } else {
+              // 4 x 4 transposes within each quad of lanes (right-hand sides
+              // 4 q .. 4 q + 3): afterwards lane 4 q + k holds row 4 j + k of
+              // all four, added with one 16-byte reduction
+              const int k4 = lane & 3;
+              const bool b0 = (k4 & 1) != 0, b1 = (k4 & 2) != 0;
+              float* arow = acc + (32 * ew + (lane & ~3));
 #pragma unroll
-                for (int k = 0; k < 32; ++k)
-                  if (k < nv) red_add(arow + acc_pos_row(n0 + k, oo, ol) - acc0, __uint_as_float(hv[k]));
+              for (int j = 0; j < 8; ++j) {
+                float x0 = __uint_as_float(hv[4 * j]), x1 = __uint_as_float(hv[4 * j + 1]);
+                float x2 = __uint_as_float(hv[4 * j + 2]), x3 = __uint_as_float(hv[4 * j + 3]);
+                float r0 = __shfl_xor_sync(0xffffffffu, b1 ? x0 : x2, 2);
+                float r1 = __shfl_xor_sync(0xffffffffu, b1 ? x1 : x3, 2);
+                if (b1) {
+                  x0 = r0;
+                  x1 = r1;
+                } else {
+                  x2 = r0;
+                  x3 = r1;
+                }
+                r0 = __shfl_xor_sync(0xffffffffu, b0 ? x0 : x1, 1);
+                r1 = __shfl_xor_sync(0xffffffffu, b0 ? x2 : x3, 1);
+                if (b0) {
+                  x0 = r0;
+                  x2 = r1;
+                } else {
+                  x1 = r0;
+                  x3 = r1;
+                }
+                if (c0 + 4 * j + k4 < Nt) {
+                  const int r = acc_pos_row(n0 + 4 * j + k4, oo, ol) - acc0;
+                  red_add4(arow + (size_t)r * kTcR, x0, x1, x2, x3);
+                }
               }
             } else {
 #pragma unroll
@@ -882,11 +834,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
           __syncwarp();
           if (lane == 0) mbar_arrive(&ctl->acce[b]);
           // rows written above are read next by bulk copies (async proxy); the
-          // accumulated rows are read by the I/O warps once the item's last
-          // tile is counted, so only that tile waits for this thread's
-          // additions to be performed
+          // accumulated rows only by the output kernel
           if (!d.accum) asm volatile("fence.proxy.async.global;" ::: "memory");
-          if (++tiles_in_item == item_tiles) __threadfence();
           __threadfence_block();
           epi_bar();
           ++done;
@@ -897,13 +846,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
   } else if (warp >= kIoWarp0) {
     // ------------------------------------------------------------ I/O warps
     // They take this CTA's items from the launch's work counter (decreasing
-    // cost), publish each in ctl->ring for the other roles, gather item i
-    // into slot i % 2 once item i - 2 (the slot's previous user) has finished,
-    // zero its accumulation rows, and then write item i - 1's outputs as soon
-    // as all of its tiles are done.
+    // cost), publish each in ctl->ring for the other roles, and gather item i
+    // into slot i % 2 once item i - 2 (the slot's previous user) has finished
+    // all of its tiles, through the shared tile iot; they also zero the item's
+    // accumulation rows.
     const int e = tid - 32 * kIoWarp0;
     int t_m2 = 0, t_m1 = 0;  // tiles of all items up to i-2, up to i-1
-    Item prev{-1, 0, 0};
     bool ok = L.stall == 0;
     for (int iseq = 0; ok; ++iseq) {
       ok = io_and(counter_wait(ctl, &ctl->done_tiles, t_m2));
@@ -914,42 +862,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       }
       io_bar();
       const int it = *((volatile int*)&ctl->ring[iseq & 3]);
-      Item itm{-1, 0, 0};
-      if (it >= 0) {
-        itm = item_of(L, it);
-        const TcPlan& p = L.plan[itm.plan];
-        const Unit u = p.units[itm.am];
-        unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
-        if (fwd)
-          gather_forward(L, itm, u, vec, e);
-        else
-          gather_inverse(L, itm, u, vec, e);
-        // the item's accumulation rows start at zero: the epilogue adds into them
+      if (it < 0) {
+        __threadfence_block();
+        if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
+        break;
+      }
+      const Item itm = item_of(L, it);
+      const TcPlan& p = L.plan[itm.plan];
+      const Unit u = p.units[itm.am];
+      unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
+      if (fwd)
+        gather_forward(L, itm, u, vec, iot, e);
+      else
+        gather_inverse(L, itm, u, vec, iot, e);
+      // the item's accumulation rows start at zero: the epilogue adds into them
+      {
         const TcRows tr = tc_rows(u.nce, u.nco, p.N);
         const int rows = fwd ? tr.yo - tr.ye + p.N : tr.xo + u.nco;
-        float* a0 = accs + (size_t)(iseq & 1) * L.acc_rows * kTcR;
-        const int r4 = (rows + 3) / 4;  // float4s of each right-hand side's run
-        for (int k = e; k < r4 * kTcR; k += kIoThreads)
-          __stcg(reinterpret_cast<float4*>(a0 + (size_t)(k / r4) * L.acc_rows) + k % r4, make_float4(0.f, 0.f, 0.f, 0.f));
-        asm volatile("fence.proxy.async.global;" ::: "memory");  // the rows are read by bulk copies
-        __threadfence();
+        float4* a4 = reinterpret_cast<float4*>(p.acc + ((size_t)itm.grp * p.nunits + itm.am) *
+                                                           (size_t)tc_acc_rows(p.N) * kTcR);
+        for (int k = e; k < rows * (kTcR / 4); k += kIoThreads) __stcg(a4 + k, make_float4(0.f, 0.f, 0.f, 0.f));
       }
+      asm volatile("fence.proxy.async.global;" ::: "memory");  // the rows are read by bulk copies
+      __threadfence();
       io_bar();
       if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
-      // the previous item's outputs, once all of its tiles are done
-      if (prev.plan >= 0) {
-        ok = io_and(counter_wait(ctl, &ctl->done_tiles, t_m1));
-        if (!ok) break;
-        __threadfence();
-        const float* acc = accs + (size_t)((iseq - 1) & 1) * L.acc_rows * kTcR;
-        if (fwd)
-          fold_forward(L, prev, acc, e);
-        else
-          scatter_inverse(L, prev, L.plan[prev.plan].units[prev.am], acc, e);
-      }
-      if (it < 0) break;
-      prev = itm;
-      const int t_cur = t_m1 + L.plan[itm.plan].tiles[2 * itm.am + (fwd ? 0 : 1)];
+      const int t_cur = t_m1 + p.tiles[2 * itm.am + (fwd ? 0 : 1)];
       t_m2 = t_m1;
       t_m1 = t_cur;
     }
@@ -961,16 +899,105 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
 }
 
+// Output side of the apply: the accumulated rows of every work item (FP32,
+// kTcR right-hand sides per row) to g (forward: the parity fold of Sec. 3.1.2,
+// g(theta_{N+i}) = y_e + y_o, g(theta_{N-1-i}) = y_e - y_o) or to beta
+// (transposed: X rows back to degrees).  A streaming kernel with many warps per
+// SM, so that this part of the I/O runs at HBM bandwidth.  One CTA step is
+// one item and 32 nodes (or degrees), transposed through shared memory so
+// that reads are whole rows and writes are 512-byte runs per (field, sign).
+constexpr int kOutThreads = 256;
+__global__ void __launch_bounds__(kOutThreads) tc_out_kernel(TcPlan p, double* __restrict__ out, int F, int single,
+                                                            int msingle, int fwd) {
+  __shared__ __align__(16) float Te[32 * kIoStride];
+  __shared__ __align__(16) float To[32 * kIoStride];
+  const int N = p.N, lane = threadIdx.x & 31, iw = threadIdx.x >> 5;
+  const int G = (F + kTcFields - 1) / kTcFields;
+  const int nitems = single ? G : p.nunits * G;
+  const int cpi = fwd ? (N + 31) / 32 : (2 * N + 31) / 32;  // chunks per item
+  const long total = (long)nitems * cpi;
+  const int yo = tc_r8(N);  // Y_o's first accumulation row
+  for (long w = blockIdx.x; w < total; w += gridDim.x) {
+    const int item = (int)(w / cpi), chunk = (int)(w % cpi);
+    const int grp = item % G;
+    const int am = single ? (msingle < 0 ? -msingle : msingle) : item / G;
+    const Unit u = p.units[am];
+    const float* acc_item = p.acc + ((size_t)grp * p.nunits + am) * (size_t)tc_acc_rows(N) * kTcR;
+    if (fwd) {
+      const int i0 = 32 * chunk;
+      for (int r = iw; r < 32; r += kOutThreads / 32) {
+        if (i0 + r < N) {
+          *reinterpret_cast<float4*>(Te + r * kIoStride + 4 * lane) =
+              __ldcs(reinterpret_cast<const float4*>(acc_item + (size_t)(i0 + r) * kTcR) + lane);
+          *reinterpret_cast<float4*>(To + r * kIoStride + 4 * lane) =
+              __ldcs(reinterpret_cast<const float4*>(acc_item + (size_t)(yo + i0 + r) * kTcR) + lane);
+        }
+      }
+      __syncthreads();
+      const int i = i0 + lane;
+      for (int pr = iw; pr < kPairs; pr += kOutThreads / 32) {
+        const double* gb = value_base(out, N, am, grp * kTcFields + (pr >> 1), pr & 1, F, single, msingle);
+        if (gb && i < N) {
+          const float2 ev = *reinterpret_cast<const float2*>(Te + lane * kIoStride + 2 * pr);
+          const float2 ov = *reinterpret_cast<const float2*>(To + lane * kIoStride + 2 * pr);
+          double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
+          __stcs(gp + N + i, make_double2(f32_to_f64_bits(ev.x + ov.x), f32_to_f64_bits(ev.y + ov.y)));
+          __stcs(gp + N - 1 - i, make_double2(f32_to_f64_bits(ev.x - ov.x), f32_to_f64_bits(ev.y - ov.y)));
+        }
+      }
+      __syncthreads();
+    } else {
+      const int nx = u.nce + u.nco, d0 = 32 * chunk, xo = tc_r8(u.nce);
+      if (d0 >= nx) continue;  // uniform over the CTA
+      for (int dl = iw; dl < 32; dl += kOutThreads / 32) {
+        const int d = d0 + dl;
+        if (d < nx) {
+          const int t = (d & 1) ? xo + (d >> 1) : (d >> 1);
+          *reinterpret_cast<float4*>(Te + dl * kIoStride + 4 * lane) =
+              __ldcs(reinterpret_cast<const float4*>(acc_item + (size_t)t * kTcR) + lane);
+        }
+      }
+      __syncthreads();
+      const int d = d0 + lane;
+      for (int pr = iw; pr < kPairs; pr += kOutThreads / 32) {
+        const double* bdst = coef_base(out, N, am, grp * kTcFields + (pr >> 1), pr & 1, F, single, msingle);
+        if (bdst && d < nx) {
+          const float2 v = *reinterpret_cast<const float2*>(Te + lane * kIoStride + 2 * pr);
+          __stcs(reinterpret_cast<double2*>(const_cast<double*>(bdst)) + d,
+                 make_double2(f32_to_f64_bits(v.x), f32_to_f64_bits(v.y)));
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace
 
 size_t tc_smem_bytes() { return kSmemTotal; }
 
 int tc_ctas_per_sm() { return 1; }  // the kernel holds all 512 tensor-memory columns
 
-cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, int F, int single, int m, int grid,
-                      unsigned char* ws, float* acc, unsigned int* counter, int* err, cudaStream_t st,
-                      cudaEvent_t* ev) {
+static int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+static cudaError_t launch_out(const TcPlan& p, bool fwd, double* out, int F, int single, int m, int sms, cudaStream_t st) {
   const int G = (F + kTcFields - 1) / kTcFields;
+  const long items = (long)(single ? 1 : p.nunits) * G;
+  const long chunks = items * (fwd ? (p.N + 31) / 32 : (2 * p.N + 31) / 32);
+  const int out_grid = (int)std::max(1L, std::min(chunks, (long)sms * 6));
+  tc_out_kernel<<<out_grid, kOutThreads, 0, st>>>(p, out, F, single, m, fwd ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, int F, int single, int m, int grid,
+                      unsigned char* ws, unsigned int* counter, int* err, cudaStream_t st, cudaEvent_t* ev) {
+  const int G = (F + kTcFields - 1) / kTcFields;
+  if (G > p.gmax) return cudaErrorInvalidValue;
   TcLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.plan[0] = p;
@@ -984,8 +1011,6 @@ cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, 
   L.msingle = m;
   L.ws = ws;
   L.max_rows = p.max_rows;
-  L.acc = acc;
-  L.acc_rows = tc_acc_rows(p.N);
   L.counter = counter;
   L.err = err;
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
@@ -993,12 +1018,14 @@ cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, 
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(L, fwd ? 1 : 0);
   e = cudaGetLastError();
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+  e = launch_out(p, fwd, out, F, single, m, sm_count(), st);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
   return e;
 }
 
-cudaError_t launch_tc_stall(const TcPlan& p, unsigned char* ws, float* acc, unsigned int* counter, int* err,
-                            cudaStream_t st) {
+cudaError_t launch_tc_stall(const TcPlan& p, unsigned char* ws, unsigned int* counter, int* err, cudaStream_t st) {
   TcLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.plan[0] = p;
@@ -1007,8 +1034,6 @@ cudaError_t launch_tc_stall(const TcPlan& p, unsigned char* ws, float* acc, unsi
   L.nitems = 1;
   L.ws = ws;
   L.max_rows = p.max_rows;
-  L.acc = acc;
-  L.acc_rows = tc_acc_rows(p.N);
   L.counter = counter;
   L.err = err;
   L.stall = 1;
@@ -1020,12 +1045,19 @@ cudaError_t launch_tc_stall(const TcPlan& p, unsigned char* ws, float* acc, unsi
 
 cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t st, cudaEvent_t* ev) {
   if (L.nplans < 1 || L.nplans > kTcMaxPlans || !L.items) return cudaErrorInvalidValue;
+  for (int q = 0; q < L.nplans; ++q)
+    if ((L.F[q] + kTcFields - 1) / kTcFields > L.plan[q].gmax) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(L, fwd ? 1 : 0);
   e = cudaGetLastError();
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+  const int sms = sm_count();
+  for (int q = 0; q < L.nplans && e == cudaSuccess; ++q)
+    if (L.F[q] > 0) e = launch_out(L.plan[q], fwd, L.out[q], L.F[q], 0, 0, sms, st);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
   return e;
 }
 

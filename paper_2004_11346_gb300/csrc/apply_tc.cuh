@@ -68,13 +68,10 @@ __host__ __device__ inline size_t tc_slot_bytes(int max_rows) {
   return ((size_t)(max_rows + kTcGrpRows - 1) / kTcGrpRows + 1) * kTcGrpBytes;
 }
 
-// Accumulated FP32 rows of one work item, stored per right-hand side: value
-// (rhs, row) at rhs * tc_acc_rows(N) + row, so that the rows of one
-// right-hand side are contiguous (runs of consecutive nodes or degrees of one
-// field and sign, read and written whole by the output step).  Forward: Y_e
-// at rows 0..N-1 and Y_o at r8(N)..; transposed: X_e at 0.. and X_o at
-// r8(nce)..  A multiple of 8 rows, so that every run starts 32-byte aligned.
-__host__ __device__ inline int tc_acc_rows(int N) { return tc_r8(2 * N + 8); }
+// Accumulated FP32 rows of one work item (kTcR values per row): forward, Y_e
+// at rows 0..N-1 and Y_o at r8(N)..; transposed, X_e at 0.. and X_o at
+// r8(nce)..
+__host__ __device__ inline int tc_acc_rows(int N) { return 2 * N + 8; }
 
 // One side of a block product, widened to whole row groups: its rows are the
 // two row segments (off0, len0), (off1, len1) of the scratch vector space, and
@@ -158,6 +155,12 @@ struct TcPlan {
   const int32_t* order;
   const uint16_t* img;      // split-BF16 operand images of every op
   const double* w;
+  // Accumulated rows of every work item (forward: Y_e, Y_o; transposed: X),
+  // item (field group g, order |m|) at (g * nunits + |m|) * tc_acc_rows(N)
+  // rows.  The kernel zeroes an item's rows when it gathers the item; the
+  // output kernel reads them.
+  float* acc;
+  int gmax;                 // field groups the accumulation buffer holds
   int N;
   int nunits;
   int max_rows;             // scratch rows of the largest order
@@ -166,8 +169,7 @@ struct TcPlan {
 // One launch of the tensor-core kernel: up to kTcMaxPlans plans (orders N of
 // their own), each with its own batch of fields.  The work items are
 // (plan, order |m|, field group); they share one work counter, the per-CTA
-// scratch slots and accumulation rows (sized for the largest plan) and the
-// error flag.
+// scratch slots (sized for the largest plan) and the error flag.
 constexpr int kTcMaxPlans = 8;
 struct TcLaunch {
   TcPlan plan[kTcMaxPlans];
@@ -182,8 +184,6 @@ struct TcLaunch {
   int single, msingle;            // one order msingle of plan 0 (alt_*_m)
   unsigned char* ws;              // per-CTA scratch: two slots of tc_slot_bytes(max_rows)
   int max_rows;
-  float* acc;                     // per-CTA accumulation rows: two slots of acc_rows x kTcR floats
-  int acc_rows;
   unsigned int* counter;          // zero before the launch
   int* err;
   // Self-test of the bounded waits: the I/O warps publish no item, so every
@@ -204,23 +204,21 @@ using TcImages = std::vector<uint16_t, UninitAlloc<uint16_t>>;
 void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op>& ops, const double* factors,
                      TcImages& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles, int& max_rows);
 
-// One apply of F fields (any F): the persistent tensor-core kernel gathers
-// each work item's inputs, runs its block products and writes its outputs
-// (the parity fold to g forward, the scatter to beta transposed).  ws and acc
-// hold grid CTAs' two scratch slots and two accumulation slots.  ev
-// (optional, two events): recorded before and after the kernel.
+// One apply: the persistent tensor-core kernel (gather, block products into
+// the accumulation rows), then the output kernel (parity fold to g forward,
+// scatter to beta transposed).  F <= kTcFields * p.gmax.  ws holds grid CTAs'
+// two scratch slots.  ev (optional, three events): recorded before the
+// tensor-core kernel, between it and the output kernel, and after.
 cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, int F, int single, int m, int grid,
-                      unsigned char* ws, float* acc, unsigned int* counter, int* err, cudaStream_t st,
-                      cudaEvent_t* ev = nullptr);
+                      unsigned char* ws, unsigned int* counter, int* err, cudaStream_t st, cudaEvent_t* ev = nullptr);
 
-// The same for a batch of plans in one launch (the launch's items, scratch,
-// accumulation slots and counter set up by the caller).  L.counter must be
-// zero on the stream.
+// The same for a batch of plans in one launch of the tensor-core kernel (the
+// launch's items, scratch and counter set up by the caller), followed by one
+// output kernel per plan.  L.counter must be zero on the stream.
 cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t st, cudaEvent_t* ev = nullptr);
 
 // The bounded-wait self-test on plan p (see TcLaunch::stall).
-cudaError_t launch_tc_stall(const TcPlan& p, unsigned char* ws, float* acc, unsigned int* counter, int* err,
-                            cudaStream_t st);
+cudaError_t launch_tc_stall(const TcPlan& p, unsigned char* ws, unsigned int* counter, int* err, cudaStream_t st);
 
 size_t tc_smem_bytes();
 int tc_ctas_per_sm();

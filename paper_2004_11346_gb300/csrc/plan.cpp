@@ -551,14 +551,15 @@ static bool emit_idbf(UnitBuild& ub, const BlockCtx& b, int L, bool force) {
   return true;
 }
 
-// Dense block: one product per chunk of rows, so that a large turning-point
-// block spreads over several warps (64 rows for the SIMT kernels) or fills one
-// 128-row tensor-core tile without re-reading its inputs per 64 rows (mixed
-// precision).  Every chunk accumulates into the shared output rows (forward)
-// and input rows (transposed).
+// Dense block: for the SIMT kernels one product per chunk of 64 rows, so that
+// a large turning-point block spreads over several warps; for the tensor-core
+// path (mixed precision) the whole block as one product, whose N tiles the
+// kernel cuts itself: the transposed apply then adds each input row once per
+// block instead of once per chunk.  Every chunk accumulates into the shared
+// output rows (forward) and input rows (transposed).
 static void emit_dense(UnitBuild& ub, const BlockCtx& b) {
   const ParityMatrix& P = *b.P;
-  const int kDenseRows = b.o->precision == SHT_MIXED ? 128 : 64;
+  const int kDenseRows = b.o->precision == SHT_MIXED ? std::max(1, b.nr) : 64;
   for (int r0 = 0; r0 < b.nr; r0 += kDenseRows) {
     const int nr = std::min(kDenseRows, b.nr - r0);
     int64_t off = put_block(ub, nr, b.nc, [&](int i, int j) { return b.K(r0 + i, j); });

@@ -27,10 +27,11 @@ def test_kernel_time(prec, eps, F, tol):
     g = p.forward(b)
     back = p.inverse(g)
     t = p.kernel_time()
-    # one apply kernel per call, whatever the number of fields
-    assert t["launches"] == 2
+    # default max_fields = 1: the 40-field tensor-core call runs as two 32-field batches
+    per_call = 1 if prec == _lib.SHT_FP64 else 2
+    assert t["launches"] == 2 * per_call
     assert t["apply_ms"] > 0
-    assert t["output_ms"] == 0
+    assert (t["output_ms"] > 0) == (prec == _lib.SHT_MIXED)
     assert p.kernel_time()["launches"] == 0  # reset by the previous query
     ref = oracle.alt_forward(N, beta)
     e = np.linalg.norm((g.cpu().numpy() - ref).reshape(F, -1), axis=1) / np.linalg.norm(ref.reshape(F, -1), axis=1)
