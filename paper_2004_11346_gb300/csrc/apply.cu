@@ -334,6 +334,8 @@ struct sht_plan_s {
   uint16_t* d_img = nullptr;
   TcOp* d_tcops = nullptr;
   int32_t* d_tctiles = nullptr;
+  int32_t* d_tczr = nullptr;   // accumulation row ranges to zero per order and direction
+  int32_t* d_tczri = nullptr;
   unsigned char* d_wstc = nullptr;
   float* d_acc = nullptr;  // accumulated rows of every work item (tc_gmax field groups)
   int tc_gmax = 0;
@@ -410,6 +412,8 @@ void free_device(sht_plan_s* p) {
   cudaFree(p->d_img);
   cudaFree(p->d_tcops);
   cudaFree(p->d_tctiles);
+  cudaFree(p->d_tczr);
+  cudaFree(p->d_tczri);
   cudaFree(p->d_wstc);
   cudaFree(p->d_acc);
   cudaFree(p->d_err);
@@ -441,6 +445,8 @@ TcPlan tc_plan_of(const sht_plan_s* p) {
   t.tiles = p->d_tctiles;
   t.order = p->d_order;
   t.img = p->d_img;
+  t.zr = p->d_tczr;
+  t.zri = p->d_tczri;
   t.w = p->d_w;
   t.acc = p->d_acc;
   t.gmax = p->tc_gmax;
@@ -596,8 +602,12 @@ sht_status attach_device(sht_plan_s* p) {
     std::vector<TcOp> tops;
     std::vector<int32_t> tiles;
     tc_build_images(N, P.units, P.ops, P.factors.data(), img, tops, tiles, p->tc_max_rows);
+    std::vector<int32_t> zr, zri;
+    tc_first_writers(N, P.units, tops, zr, zri);
     e = upload(&p->d_img, img);
     if (e == cudaSuccess) e = upload(&p->d_tcops, tops);
+    if (e == cudaSuccess) e = upload(&p->d_tczr, zr);
+    if (e == cudaSuccess) e = upload(&p->d_tczri, zri);
     if (e == cudaSuccess) e = upload(&p->d_tctiles, tiles);
     p->nslots_tc = std::max(1, sms * tc_ctas_per_sm());
     ws32 = (size_t)p->nslots_tc * 2 * tc_slot_bytes(p->tc_max_rows);  // two vector spaces per CTA

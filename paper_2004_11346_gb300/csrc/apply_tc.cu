@@ -203,6 +203,56 @@ void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op
   }
 }
 
+void tc_first_writers(int N, const std::vector<Unit>& units, std::vector<TcOp>& tops, std::vector<int32_t>& zr,
+                      std::vector<int32_t>& zri) {
+  zr.clear();
+  zri.assign(2 * units.size() + 1, 0);
+  const int R = tc_acc_rows(N);
+  std::vector<char> written(R), stored(R);
+  for (size_t u = 0; u < units.size(); ++u) {
+    const Unit& un = units[u];
+    const TcRows tr = tc_rows(un.nce, un.nco, N);
+    for (int d = 0; d < 2; ++d) {
+      const bool fwd = d == 0;
+      std::fill(written.begin(), written.end(), 0);
+      std::fill(stored.begin(), stored.end(), 0);
+      const int acc0 = fwd ? tr.ye : 0;
+      const int nops = un.op_end - un.op_begin;
+      for (int q = 0; q < nops; ++q) {  // the kernel's processing order
+        TcOp& t = tops[(size_t)(fwd ? un.op_begin + q : un.op_end - 1 - q)];
+        t.flags &= ~(fwd ? kTcFwdStore : kTcBwdStore);
+        if (!(t.flags & (fwd ? OP_FWD_ACCUM : OP_BWD_ACCUM))) continue;
+        const int32_t* oo = fwd ? t.out_off : t.in_off;
+        const int32_t* ol = fwd ? t.out_len : t.in_len;
+        bool fresh = true;
+        for (int sg = 0; sg < 2; ++sg)
+          for (int r = 0; r < ol[sg]; ++r) fresh = fresh && !written[oo[sg] + r - acc0];
+        if (fresh) t.flags |= fwd ? kTcFwdStore : kTcBwdStore;
+        for (int sg = 0; sg < 2; ++sg)
+          for (int r = 0; r < ol[sg]; ++r) {
+            written[oo[sg] + r - acc0] = 1;
+            if (fresh) stored[oo[sg] + r - acc0] = 1;
+          }
+      }
+      // rows the output step reads that no store writes first: zeroed per item
+      const int ranges[2][2] = {{0, fwd ? N : un.nce}, {fwd ? tr.yo - tr.ye : tr.xo, fwd ? N : un.nco}};
+      for (const auto& rg : ranges)
+        for (int r = rg[0]; r < rg[0] + rg[1];) {
+          if (stored[r]) {
+            ++r;
+            continue;
+          }
+          int e = r;
+          while (e < rg[0] + rg[1] && !stored[e]) ++e;
+          zr.push_back(r);
+          zr.push_back(e - r);
+          r = e;
+        }
+      zri[2 * u + d + 1] = (int32_t)(zr.size() / 2);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- device side
 namespace {
 
@@ -816,7 +866,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
                 }
                 if (c0 + 4 * j + k4 < Nt) {
                   const int r = acc_pos_row(n0 + 4 * j + k4, oo, ol) - acc0;
-                  red_add4(arow + (size_t)r * kTcR, x0, x1, x2, x3);
+                  if (d.store)  // the rows' first writer
+                    __stcg(reinterpret_cast<float4*>(arow + (size_t)r * kTcR), make_float4(x0, x1, x2, x3));
+                  else
+                    red_add4(arow + (size_t)r * kTcR, x0, x1, x2, x3);
                 }
               }
             } else {
@@ -875,13 +928,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
         gather_forward(L, itm, u, vec, iot, e);
       else
         gather_inverse(L, itm, u, vec, iot, e);
-      // the item's accumulation rows start at zero: the epilogue adds into them
+      // accumulation rows that no op stores first start at zero (the
+      // epilogue adds into them; the output step reads every row)
       {
-        const TcRows tr = tc_rows(u.nce, u.nco, p.N);
-        const int rows = fwd ? tr.yo - tr.ye + p.N : tr.xo + u.nco;
         float4* a4 = reinterpret_cast<float4*>(p.acc + ((size_t)itm.grp * p.nunits + itm.am) *
                                                            (size_t)tc_acc_rows(p.N) * kTcR);
-        for (int k = e; k < rows * (kTcR / 4); k += kIoThreads) __stcg(a4 + k, make_float4(0.f, 0.f, 0.f, 0.f));
+        const int z1 = p.zri[2 * itm.am + (fwd ? 1 : 2)];
+        for (int z = p.zri[2 * itm.am + (fwd ? 0 : 1)]; z < z1; ++z) {
+          float4* a = a4 + (size_t)p.zr[2 * z] * (kTcR / 4);
+          const int n4 = p.zr[2 * z + 1] * (kTcR / 4);
+          for (int k = e; k < n4; k += kIoThreads) __stcg(a + k, make_float4(0.f, 0.f, 0.f, 0.f));
+        }
       }
       asm volatile("fence.proxy.async.global;" ::: "memory");  // the rows are read by bulk copies
       __threadfence();

@@ -97,7 +97,13 @@ __host__ __device__ inline TcKGeom tc_kgeom(int off0, int len0, int off1, int le
 __host__ __device__ inline int tc_group(const TcKGeom& g, int j) { return j < g.ng0 ? g.gs0 + j : g.gs1 + j - g.ng0; }
 
 // One op as the tensor-core kernel reads it: a single 64-byte record with the
-// offsets of its operand images and its segments in scratch rows.
+// offsets of its operand images and its segments in scratch rows.  Besides
+// the program's flags, an accumulating op is marked to store (not add) in a
+// direction when none of its output rows was written by an earlier op of the
+// order in that direction's processing order: it is their first writer, and
+// those rows need no zeroing beforehand.
+constexpr int32_t kTcFwdStore = 1 << 8;
+constexpr int32_t kTcBwdStore = 1 << 9;
 struct alignas(16) TcOp {
   int64_t img[2];                    // forward / transposed image (element offsets)
   int32_t mo, ni;
@@ -118,6 +124,7 @@ struct TcDir {
   int nT;       // N tiles
   int KK;       // unwidened K side
   int accum;    // outputs accumulate in FP32
+  int store;    // ... and this op is their first writer: plain stores
   TcKGeom ng;   // widened output side (when !accum)
   TcKGeom kg;   // widened input side
 };
@@ -128,6 +135,7 @@ __host__ __device__ inline TcDir tc_dir(const TcOp& op, bool fwd) {
   const int32_t* ol = fwd ? op.out_len : op.in_len;
   TcDir d;
   d.accum = (op.flags & (fwd ? OP_FWD_ACCUM : OP_BWD_ACCUM)) != 0;
+  d.store = d.accum && (op.flags & (fwd ? kTcFwdStore : kTcBwdStore)) != 0;
   d.KK = fwd ? op.ni : op.mo;
   d.kg = tc_kgeom(io[0], il[0], io[1], il[1]);
   if (d.KK <= 0) d.kg.nK = d.kg.ngt = d.kg.kp_tot = 0;
@@ -154,6 +162,11 @@ struct TcPlan {
   const int32_t* tiles;     // per unit: [forward, transposed] number of N tiles of all its ops
   const int32_t* order;
   const uint16_t* img;      // split-BF16 operand images of every op
+  // Accumulation rows that no storing op writes first, as (first row, rows)
+  // ranges: order u in direction d (0 forward, 1 transposed) owns ranges
+  // zr[zri[2u + d] .. zri[2u + d + 1]).  Only these are zeroed per item.
+  const int32_t* zr;
+  const int32_t* zri;
   const double* w;
   // Accumulated rows of every work item (forward: Y_e, Y_o; transposed: X),
   // item (field group g, order |m|) at (g * nunits + |m|) * tc_acc_rows(N)
@@ -198,11 +211,16 @@ struct TcLaunch {
 void tc_op_image(const Op& op, const TcOp& top, const double* factors, bool transposed, std::vector<uint16_t>& out);
 
 // Build the forward and transposed images of every op from the FP64 factor
-// store, the kernel's op records and the per-unit tile counts; max_rows gets
-// the scratch rows of the largest order.
+// store, the kernel's op records (with the store marks) and the per-unit tile
+// counts; max_rows gets the scratch rows of the largest order.
 using TcImages = std::vector<uint16_t, UninitAlloc<uint16_t>>;
 void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op>& ops, const double* factors,
                      TcImages& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles, int& max_rows);
+
+// The store marks of the ops (in tops) and the zero ranges (zr, zri as in
+// TcPlan) of every order, from the op records in scratch rows.
+void tc_first_writers(int N, const std::vector<Unit>& units, std::vector<TcOp>& tops, std::vector<int32_t>& zr,
+                      std::vector<int32_t>& zri);
 
 // One apply: the persistent tensor-core kernel (gather, block products into
 // the accumulation rows), then the output kernel (parity fold to g forward,

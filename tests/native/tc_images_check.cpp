@@ -72,6 +72,52 @@ int main(int argc, char** argv) {
   if (at > total || (total > 8 && at != total)) return 9;
   for (size_t i = at; i < total; ++i)
     if (img[i] != 0) return 10;
+  // first-writer marks and zero ranges: per order and direction, replay the
+  // ops in processing order; a storing op may touch no row written before,
+  // and every row the output step reads is first written by a storing op or
+  // lies in one zero range -- exactly one of the two
+  std::vector<int32_t> zr, zri;
+  tc_first_writers(N, units, tops, zr, zri);
+  if (zri.size() != 2 * units.size() + 1 || zri[0] != 0) return 11;
+  for (size_t u = 0; u < units.size(); ++u) {
+    const Unit& un = units[u];
+    const TcRows tr = tc_rows(un.nce, un.nco, N);
+    for (int d = 0; d < 2; ++d) {
+      const bool fwd = d == 0;
+      const int acc0 = fwd ? tr.ye : 0;
+      std::vector<int> state(tc_acc_rows(N), 0);  // 0 untouched, 1 stored first, 2 added first
+      for (int q = 0; q < un.op_end - un.op_begin; ++q) {
+        const TcOp& t = tops[(size_t)(fwd ? un.op_begin + q : un.op_end - 1 - q)];
+        if (!(t.flags & (fwd ? OP_FWD_ACCUM : OP_BWD_ACCUM))) {
+          if (t.flags & (fwd ? kTcFwdStore : kTcBwdStore)) return 12;
+          continue;
+        }
+        const bool st = (t.flags & (fwd ? kTcFwdStore : kTcBwdStore)) != 0;
+        const int32_t* oo = fwd ? t.out_off : t.in_off;
+        const int32_t* ol = fwd ? t.out_len : t.in_len;
+        for (int sg = 0; sg < 2; ++sg)
+          for (int r = 0; r < ol[sg]; ++r) {
+            const int a = oo[sg] + r - acc0;
+            if (a < 0 || a >= tc_acc_rows(N)) return 13;
+            if (st && state[a] != 0) return 14;
+            if (state[a] == 0) state[a] = st ? 1 : 2;
+          }
+      }
+      std::vector<int> zeroed(tc_acc_rows(N), 0);
+      for (int z = zri[2 * u + d]; z < zri[2 * u + d + 1]; ++z)
+        for (int r = zr[2 * z]; r < zr[2 * z] + zr[2 * z + 1]; ++r) {
+          if (r < 0 || r >= tc_acc_rows(N)) return 15;
+          ++zeroed[r];
+        }
+      const int rg[2][2] = {{0, fwd ? N : un.nce}, {fwd ? tr.yo - tr.ye : tr.xo, fwd ? N : un.nco}};
+      for (const auto& g : rg)
+        for (int r = g[0]; r < g[0] + g[1]; ++r)
+          if ((state[r] == 1) + zeroed[r] != 1) {
+            std::printf("order %zu dir %d row %d: state %d zeroed %d\n", u, d, r, state[r], zeroed[r]);
+            return 16;
+          }
+    }
+  }
   std::printf("ok %zu\n", at);
   sht_plan_destroy(p);
   return 0;
