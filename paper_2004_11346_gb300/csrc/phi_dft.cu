@@ -6,14 +6,23 @@
 // with M = 4N-1 samples phi_j = 2 pi (j + 1/2) / M.  Writing
 // e^{i m phi_j} = e^{i pi m / M} e^{2 pi i m j / M}, synthesis is a length-M
 // DFT of c[m mod M] = g(m) e^{i pi m / M}, and analysis is the conjugate
-// transform followed by the conjugate shift.  One CTA transforms one
-// (node, field) row in shared memory with a self-sorting mixed-radix
-// (Stockham) FFT over the factors of M; every pass reads its twiddles from a
-// host-built table e^{+2 pi i t / (Ns R)}, t < Ns R.  The shift factors
-// e^{i pi m / M} come from a table too.  Arithmetic type T is double or float;
-// inputs and outputs are FP64 complex.
+// transform followed by the conjugate shift.
+//
+// One CTA transforms NT consecutive (node, field) rows in shared memory, one
+// buffer of M values per row: an in-place mixed-radix decimation-in-time FFT
+// over the factors R_0 .. R_{P-1} of M.  The load places input n at its
+// digit-reversed position (n = s_{P-1} + R_{P-1} (s_{P-2} + ...) goes to
+// sum_p s_p L_p with L_p = R_0 ... R_{p-1}); pass p then combines blocks of
+// length L_p into blocks of length L_p R_p, each butterfly reading and writing
+// the same R_p positions, and the result ends in natural order.  Every pass
+// reads its twiddles from a host-built table e^{+2 pi i t / (L_p R_p)}; the
+// shift factors e^{i pi m / M} come from a table too.  Arithmetic type T is
+// double or float; inputs and outputs are FP64 complex.  With NT = 2 the two
+// rows are adjacent nodes, so that the strided accesses along the orders of g
+// move whole 32-byte sectors.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -29,11 +38,9 @@ struct C2 {
 
 namespace {
 
-// threads per CTA: FP32 rows fit three CTAs per SM; an FP64 row's two buffers
-// take most of shared memory, so its single CTA carries more warps
 template <class T>
 struct PhiThreads {
-  static constexpr int value = sizeof(T) == 8 ? 512 : 256;
+  static constexpr int value = 256;
 };
 
 __device__ __forceinline__ long order_slot(long m) { return m == 0 ? 0 : (m > 0 ? 2 * m - 1 : -2 * m); }
@@ -53,47 +60,49 @@ __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
   return C2<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 
-// One Stockham pass of radix R: y[idxD + k Ns] = sum_r x[j + r n/R] w^{r (j%Ns + k Ns)}
-// with w = e^{s 2 pi i / (Ns R)} (s = +1 synthesis, -1 analysis via conjugation).
-// Generic form (any R): every output re-reads its R inputs; used only for
-// radices without a specialised butterfly (prime factors of M above 13).
-template <class T>
-__device__ void stockham_pass(const C2<T>* __restrict__ x, C2<T>* __restrict__ y, int n, int R, int Ns,
-                              const C2<T>* __restrict__ tw, bool conj) {
-  const int nb = n / R, NsR = Ns * R;
-  for (int o = threadIdx.x; o < n; o += blockDim.x) {
-    const int j = o % nb, k = o / nb;  // butterfly j, output k of it
-    const int q = j % Ns + k * Ns;     // in [0, Ns R)
-    const int idxD = (j / Ns) * NsR + (j % Ns);
+// One DIT pass of radix R over NT rows of M values each, out of place: output
+// position b Ns R + q Ns + j (b < M / (Ns R), q < R, j < Ns) is
+// X_q = sum_s x_s w^{s j} e^{+-2 pi i s q / R} over the inputs x_s at
+// b Ns R + s Ns + j, with w = e^{+-2 pi i / (Ns R)}; w^{s j} e^{2 pi i s q / R}
+// is the table entry tw[s (j + q Ns) mod Ns R].  Every output re-reads its R
+// inputs: used only for radices without a specialised butterfly (prime
+// factors of M above 13), which is why such plans keep a second buffer.
+template <class T, int NT>
+__device__ void dit_pass_oop(const C2<T>* __restrict__ xin, C2<T>* __restrict__ yout, int M, int R, int Ns,
+                             const C2<T>* __restrict__ tw, bool conj) {
+  const int NsR = Ns * R;
+  const T sg = conj ? T(-1) : T(1);
+  for (int o = threadIdx.x; o < NT * M; o += blockDim.x) {
+    const int row = o / M, pos = o % M;
+    const C2<T>* x = xin + (size_t)row * M;
+    const int rem = pos % NsR, q = rem / Ns, j = rem % Ns;
+    const int base = pos - rem + j;
+    const int step = j + q * Ns;  // < Ns R
     T ax = 0, ay = 0;
-    int t = 0;  // (r q) mod Ns R
-    for (int r = 0; r < R; ++r) {
-      const C2<T> v = x[j + r * nb];
+    int t = 0;
+    for (int s = 0; s < R; ++s) {
+      const C2<T> v = x[base + s * Ns];
       C2<T> w = tw[t];
-      if (conj) w.y = -w.y;
+      w.y *= sg;
       ax += v.x * w.x - v.y * w.y;
       ay += v.x * w.y + v.y * w.x;
-      t += q;
+      t += step;
       if (t >= NsR) t -= NsR;
     }
-    y[idxD + k * Ns] = C2<T>{ax, ay};
+    yout[(size_t)row * M + pos] = C2<T>{ax, ay};
   }
 }
 
-// The same pass for a fixed small odd radix.  The phase factor splits as
-// w^{r (jn + k Ns)} = w^{r jn} * omega^{r k} (jn = j mod Ns, omega =
-// e^{s 2 pi i / R} = w^{Ns}): each thread takes whole butterflies, loads the
-// R inputs once and applies the R-1 twiddles w^{r jn} (r jn < Ns R, a table
-// entry).  The R-point DFT that remains pairs outputs k and R-k: with
-// P_r = v_r + v_{R-r}, Q_r = v_r - v_{R-r} (r = 1..h, h = (R-1)/2),
-//   y_k, y_{R-k} = v_0 + sum_r P_r cos(2 pi r k / R) +- i sum_r Q_r s sin(2 pi r k / R),
+// The same pass for a fixed small odd radix.  The R-point DFT after the
+// twiddles pairs outputs q and R-q: with P_r = v_r + v_{R-r},
+// Q_r = v_r - v_{R-r} (r = 1..h, h = (R-1)/2),
+//   y_q, y_{R-q} = v_0 + sum_r P_r cos(2 pi r q / R) +- i sum_r Q_r s sin(2 pi r q / R),
 // about a quarter of the multiplications of the direct R x R product.
-template <class T, int R>
-__device__ void stockham_pass_r(const C2<T>* __restrict__ x, C2<T>* __restrict__ y, int n, int Ns,
-                                const C2<T>* __restrict__ tw, bool conj) {
+template <class T, int R, int NT>
+__device__ void dit_pass_r(C2<T>* __restrict__ buf, int M, int Ns, const C2<T>* __restrict__ tw, bool conj) {
   static_assert(R % 2 == 1, "odd radix");
   constexpr int h = (R - 1) / 2;
-  const int nb = n / R;
+  const int nb = M / R;
   const T sg = conj ? T(-1) : T(1);
   T cs[h + 1], sn[h + 1];  // cos and s*sin of 2 pi t / R, t = 0..h
 #pragma unroll
@@ -102,16 +111,16 @@ __device__ void stockham_pass_r(const C2<T>* __restrict__ x, C2<T>* __restrict__
     cs[t] = w.x;
     sn[t] = sg * w.y;
   }
-  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-    const int jn = j % Ns;
-    const int idxD = (j - jn) * R + jn;  // (j / Ns) * Ns R + jn
+  for (int o = threadIdx.x; o < NT * nb; o += blockDim.x) {
+    const int row = o / nb, bf = o % nb;
+    C2<T>* x = buf + (size_t)row * M;
+    const int j = bf % Ns, base = (bf / Ns) * Ns * R + j;
     C2<T> v[R];
-    v[0] = x[j];
 #pragma unroll
-    for (int r = 1; r < R; ++r) v[r] = x[j + r * nb];
+    for (int r = 0; r < R; ++r) v[r] = x[base + r * Ns];
 #pragma unroll
     for (int r = 1; r < R; ++r) {
-      C2<T> w = tw[r * jn];
+      C2<T> w = tw[r * j];
       w.y *= sg;
       v[r] = cmul(v[r], w);
     }
@@ -124,13 +133,13 @@ __device__ void stockham_pass_r(const C2<T>* __restrict__ x, C2<T>* __restrict__
       sx += P[r].x;
       sy += P[r].y;
     }
-    y[idxD] = C2<T>{sx, sy};
+    x[base] = C2<T>{sx, sy};
 #pragma unroll
-    for (int k = 1; k <= h; ++k) {
+    for (int q = 1; q <= h; ++q) {
       T ax = v[0].x, ay = v[0].y, bx = 0, by = 0;
 #pragma unroll
       for (int r = 1; r <= h; ++r) {
-        const int t = (r * k) % R;  // compile-time after unrolling
+        const int t = (r * q) % R;  // compile-time after unrolling
         const T c = t <= h ? cs[t] : cs[R - t];
         const T sv = t <= h ? sn[t] : -sn[R - t];
         ax += P[r].x * c;
@@ -138,79 +147,110 @@ __device__ void stockham_pass_r(const C2<T>* __restrict__ x, C2<T>* __restrict__
         bx += Q[r].x * sv;
         by += Q[r].y * sv;
       }
-      y[idxD + k * Ns] = C2<T>{ax - by, ay + bx};
-      y[idxD + (R - k) * Ns] = C2<T>{ax + by, ay - bx};
+      x[base + q * Ns] = C2<T>{ax - by, ay + bx};
+      x[base + (R - q) * Ns] = C2<T>{ax + by, ay - bx};
     }
   }
 }
 
-template <class T>
-__device__ __forceinline__ void run_pass(const C2<T>* x, C2<T>* y, int n, int R, int Ns, const C2<T>* tw,
-                                         bool conj) {
-  switch (R) {
-    case 3: stockham_pass_r<T, 3>(x, y, n, Ns, tw, conj); break;
-    case 5: stockham_pass_r<T, 5>(x, y, n, Ns, tw, conj); break;
-    case 7: stockham_pass_r<T, 7>(x, y, n, Ns, tw, conj); break;
-    case 11: stockham_pass_r<T, 11>(x, y, n, Ns, tw, conj); break;
-    case 13: stockham_pass_r<T, 13>(x, y, n, Ns, tw, conj); break;
-    default: stockham_pass<T>(x, y, n, R, Ns, tw, conj); break;
+// Radix 2 and 4 (even factors of M never occur: M = 4N - 1 is odd; kept for
+// completeness of the factorisation).
+template <class T, int NT>
+__device__ void dit_pass_2(C2<T>* __restrict__ buf, int M, int Ns, const C2<T>* __restrict__ tw, bool conj) {
+  const int nb = M / 2;
+  const T sg = conj ? T(-1) : T(1);
+  for (int o = threadIdx.x; o < NT * nb; o += blockDim.x) {
+    const int row = o / nb, bf = o % nb;
+    C2<T>* x = buf + (size_t)row * M;
+    const int j = bf % Ns, base = (bf / Ns) * Ns * 2 + j;
+    C2<T> w = tw[j];
+    w.y *= sg;
+    const C2<T> a = x[base], b = cmul(x[base + Ns], w);
+    x[base] = C2<T>{a.x + b.x, a.y + b.y};
+    x[base + Ns] = C2<T>{a.x - b.x, a.y - b.y};
   }
 }
 
-template <class T>
+__host__ __device__ __forceinline__ bool in_place_radix(int R) {
+  return R == 2 || R == 3 || R == 5 || R == 7 || R == 11 || R == 13;
+}
+
+// Pass on the current buffer; an out-of-place pass writes the other one and
+// the two swap.
+template <class T, int NT>
+__device__ __forceinline__ void run_pass(C2<T>*& cur, C2<T>*& oth, int M, int R, int Ns, const C2<T>* tw,
+                                         bool conj) {
+  switch (R) {
+    case 2: dit_pass_2<T, NT>(cur, M, Ns, tw, conj); break;
+    case 3: dit_pass_r<T, 3, NT>(cur, M, Ns, tw, conj); break;
+    case 5: dit_pass_r<T, 5, NT>(cur, M, Ns, tw, conj); break;
+    case 7: dit_pass_r<T, 7, NT>(cur, M, Ns, tw, conj); break;
+    case 11: dit_pass_r<T, 11, NT>(cur, M, Ns, tw, conj); break;
+    case 13: dit_pass_r<T, 13, NT>(cur, M, Ns, tw, conj); break;
+    default: {
+      dit_pass_oop<T, NT>(cur, oth, M, R, Ns, tw, conj);
+      C2<T>* t = cur;
+      cur = oth;
+      oth = t;
+    }
+  }
+}
+
+template <class T, int NT>
 __global__ void __launch_bounds__(PhiThreads<T>::value) phi_kernel(PhiPlanDev<T> p, const double* __restrict__ in,
                                                        double* __restrict__ out, int F, int analysis) {
   extern __shared__ unsigned char smem_raw[];
   C2<T>* buf0 = reinterpret_cast<C2<T>*>(smem_raw);
-  C2<T>* buf1 = buf0 + p.M;
+  C2<T>* buf1 = buf0 + (size_t)NT * p.M;  // used by out-of-place passes only
   const int N = p.N, K = 2 * N, M = p.M;
   const long nval = (long)M * K;  // per-field size of g and of f (complex)
-  const int rows = K * F;
-  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int f = row / K, l = row % K;
-    // load
+  const int groups = K * F / NT;  // NT divides K (even)
+  for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
+    const int row0 = grp * NT, f = row0 / K, l0 = row0 % K;
+    // load into digit-reversed positions
     if (!analysis) {
-      // c[m mod M] = g(m, l) e^{i pi m / M}; unrolled so that several strided loads are in flight
-#pragma unroll 8
-      for (int mm = threadIdx.x; mm < M; mm += blockDim.x) {
+      // c[m mod M] = g(m, l) e^{i pi m / M}; the NT nodes of one order are adjacent
+#pragma unroll 4
+      for (int idx = threadIdx.x; idx < NT * M; idx += blockDim.x) {
+        const int mm = idx / NT, r = idx % NT;
         const int m = mm - (K - 1);  // -(K-1) .. K-1
-        const double2 v = __ldg(reinterpret_cast<const double2*>(in) + f * nval + order_slot(m) * K + l);
-        const C2<T> s = p.shift[mm];
+        const double2 v = __ldg(reinterpret_cast<const double2*>(in) + f * nval + order_slot(m) * K + l0 + r);
         const C2<T> a{from_f64<T>(v.x), from_f64<T>(v.y)};
-        buf0[(m % M + M) % M] = cmul(a, s);
+        buf0[(size_t)r * M + __ldg(p.perm + (m % M + M) % M)] = cmul(a, p.shift[mm]);
       }
     } else {
-#pragma unroll 8
-      for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        const double2 v = __ldg(reinterpret_cast<const double2*>(in) + f * nval + (long)l * M + j);
-        buf0[j] = C2<T>{from_f64<T>(v.x), from_f64<T>(v.y)};
+#pragma unroll 4
+      for (int idx = threadIdx.x; idx < NT * M; idx += blockDim.x) {
+        const int r = idx / M, j = idx % M;
+        const double2 v = __ldg(reinterpret_cast<const double2*>(in) + f * nval + (long)(l0 + r) * M + j);
+        buf0[(size_t)r * M + __ldg(p.perm + j)] = C2<T>{from_f64<T>(v.x), from_f64<T>(v.y)};
       }
     }
     __syncthreads();
-    C2<T>* src = buf0;
-    C2<T>* dst = buf1;
+    C2<T>* cur = buf0;
+    C2<T>* oth = buf1;
     for (int ps = 0; ps < p.npass; ++ps) {
-      run_pass<T>(src, dst, M, p.radix[ps], p.ns[ps], p.tw + p.tw_off[ps], analysis != 0);
+      run_pass<T, NT>(cur, oth, M, p.radix[ps], p.ns[ps], p.tw + p.tw_off[ps], analysis != 0);
       __syncthreads();
-      C2<T>* t = src;
-      src = dst;
-      dst = t;
     }
-    // store
+    // store (natural order)
     if (!analysis) {
-      for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        const C2<T> v = src[j];
-        reinterpret_cast<double2*>(out)[f * nval + (long)l * M + j] = make_double2(to_f64(v.x), to_f64(v.y));
+      for (int idx = threadIdx.x; idx < NT * M; idx += blockDim.x) {
+        const int r = idx / M, j = idx % M;
+        const C2<T> v = cur[idx];
+        reinterpret_cast<double2*>(out)[f * nval + (long)(l0 + r) * M + j] = make_double2(to_f64(v.x), to_f64(v.y));
       }
     } else {
       // g(m, l) = (1/M) e^{-i pi m / M} C[m mod M]
-      for (int mm = threadIdx.x; mm < M; mm += blockDim.x) {
+      const T inv = T(1) / (T)M;
+      for (int idx = threadIdx.x; idx < NT * M; idx += blockDim.x) {
+        const int mm = idx / NT, r = idx % NT;
         const int m = mm - (K - 1);
-        C2<T> s = p.shift[mm];
-        s.y = -s.y;
-        const C2<T> v = cmul(src[(m % M + M) % M], s);
-        const T inv = T(1) / (T)M;
-        reinterpret_cast<double2*>(out)[f * nval + order_slot(m) * K + l] = make_double2(to_f64(v.x * inv), to_f64(v.y * inv));
+        C2<T> sh = p.shift[mm];
+        sh.y = -sh.y;
+        const C2<T> v = cmul(cur[(size_t)r * M + (m % M + M) % M], sh);
+        reinterpret_cast<double2*>(out)[f * nval + order_slot(m) * K + l0 + r] =
+            make_double2(to_f64(v.x * inv), to_f64(v.y * inv));
       }
     }
     __syncthreads();
@@ -223,7 +263,7 @@ __global__ void __launch_bounds__(PhiThreads<T>::value) phi_kernel(PhiPlanDev<T>
 static std::vector<int> factor_radices(int M) {
   std::vector<int> r;
   int n = M;
-  for (int p : {4, 2, 3, 5, 7, 11, 13}) {
+  for (int p : {2, 3, 5, 7, 11, 13}) {
     while (n % p == 0) {
       r.push_back(p);
       n /= p;
@@ -244,12 +284,14 @@ bool PhiTables<T>::build(int N) {
   std::vector<int> rad = factor_radices(M);
   if ((int)rad.size() > kMaxPasses) return false;
   npass = (int)rad.size();
+  two_buf = false;
   std::vector<C2<T>> tw_h;
   int Ns = 1;
   for (int ps = 0; ps < npass; ++ps) {
     radix[ps] = rad[ps];
     ns[ps] = Ns;
     tw_off[ps] = (int)tw_h.size();
+    two_buf = two_buf || !in_place_radix(rad[ps]);
     const int L = Ns * rad[ps];
     for (int t = 0; t < L; ++t) {
       // e^{+2 pi i t / L}, argument reduced exactly (t < L)
@@ -258,6 +300,19 @@ bool PhiTables<T>::build(int N) {
     }
     Ns *= rad[ps];
   }
+  // digit-reversed position of input n: with n = s_{P-1} + R_{P-1} (s_{P-2} + ...),
+  // position sum_p s_p L_p, L_p = R_0 ... R_{p-1}
+  std::vector<int> L(npass + 1, 1);
+  for (int ps = 0; ps < npass; ++ps) L[ps + 1] = L[ps] * rad[ps];
+  std::vector<int> perm(M);
+  for (int n0 = 0; n0 < M; ++n0) {
+    int n = n0, pos = 0;
+    for (int ps = npass - 1; ps >= 0; --ps) {
+      pos += (n % rad[ps]) * L[ps];
+      n /= rad[ps];
+    }
+    perm[n0] = pos;
+  }
   std::vector<C2<T>> sh(M);
   for (int mm = 0; mm < M; ++mm) {
     const long m = mm - (2L * N - 1);
@@ -265,12 +320,17 @@ bool PhiTables<T>::build(int N) {
     const long double a = 3.141592653589793238462643383279502884L * (long double)r / (long double)M;
     sh[mm] = C2<T>{(T)std::cos(a), (T)std::sin(a)};
   }
+  // two adjacent rows per CTA while three such CTAs still fit an SM
+  nt = (sizeof(T) == 4 && 2 * (two_buf ? 2 : 1) * sizeof(C2<T>) * (size_t)M <= 76 * 1024) ? 2 : 1;
   n_tw = (int)tw_h.size();
   if (cudaMalloc(&d_tw, sizeof(C2<T>) * tw_h.size()) != cudaSuccess) return false;
   if (cudaMalloc(&d_shift, sizeof(C2<T>) * sh.size()) != cudaSuccess) return false;
+  if (cudaMalloc(&d_perm, sizeof(int) * perm.size()) != cudaSuccess) return false;
   if (cudaMemcpy(d_tw, tw_h.data(), sizeof(C2<T>) * tw_h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return false;
   if (cudaMemcpy(d_shift, sh.data(), sizeof(C2<T>) * sh.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return false;
+  if (cudaMemcpy(d_perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return false;
   this->N = N;
   return true;
@@ -280,8 +340,10 @@ template <class T>
 void PhiTables<T>::release() {
   cudaFree(d_tw);
   cudaFree(d_shift);
+  cudaFree(d_perm);
   d_tw = nullptr;
   d_shift = nullptr;
+  d_perm = nullptr;
 }
 
 template <class T>
@@ -298,16 +360,26 @@ cudaError_t PhiTables<T>::launch(const double* in, double* out, int F, bool anal
   }
   d.tw = static_cast<const C2<T>*>(d_tw);
   d.shift = static_cast<const C2<T>*>(d_shift);
-  const size_t smem = 2 * sizeof(C2<T>) * (size_t)M;
-  cudaError_t e = cudaFuncSetAttribute(phi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  phi_kernel<T><<<grid, PhiThreads<T>::value, smem, st>>>(d, in, out, F, analysis ? 1 : 0);
+  d.perm = static_cast<const int*>(d_perm);
+  const size_t smem = smem_bytes();
+  const int groups = std::max(1, 2 * N * F / nt);
+  grid = std::max(1, std::min(grid, groups));
+  cudaError_t e;
+  if (nt == 2) {
+    e = cudaFuncSetAttribute(phi_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    phi_kernel<T, 2><<<grid, PhiThreads<T>::value, smem, st>>>(d, in, out, F, analysis ? 1 : 0);
+  } else {
+    e = cudaFuncSetAttribute(phi_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    phi_kernel<T, 1><<<grid, PhiThreads<T>::value, smem, st>>>(d, in, out, F, analysis ? 1 : 0);
+  }
   return cudaGetLastError();
 }
 
 template <class T>
 size_t PhiTables<T>::smem_bytes() const {
-  return 2 * sizeof(C2<T>) * (size_t)M;
+  return (size_t)nt * (two_buf ? 2 : 1) * sizeof(C2<T>) * (size_t)M;
 }
 
 template struct PhiTables<double>;
