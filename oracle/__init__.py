@@ -59,13 +59,16 @@ def _load():
         lib.oracle_alt_inverse_m.argtypes = [i, i, d, d, d, d]
         lib.oracle_phi_synthesis.argtypes = [i, d, d, i]
         lib.oracle_phi_analysis.argtypes = [i, d, d, i]
+        lib.oracle_phi_synthesis_nodes.argtypes = [i, i, d, d, i]
+        lib.oracle_phi_analysis_nodes.argtypes = [i, i, d, d, i]
         lib.oracle_coef_offset.argtypes = [ctypes.c_long, ctypes.c_long]
         lib.oracle_coef_offset.restype = ctypes.c_long
         lib.oracle_order_slot.argtypes = [ctypes.c_long]
         lib.oracle_order_slot.restype = ctypes.c_long
         for name in ["oracle_gl_rule", "oracle_alf_table", "oracle_alt_forward",
                      "oracle_alt_inverse", "oracle_alt_forward_m", "oracle_alt_inverse_m",
-                     "oracle_phi_synthesis", "oracle_phi_analysis", "oracle_num_threads"]:
+                     "oracle_phi_synthesis", "oracle_phi_analysis", "oracle_phi_synthesis_nodes",
+                     "oracle_phi_analysis_nodes", "oracle_num_threads"]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -197,6 +200,28 @@ def phi_analysis(N: int, f: np.ndarray) -> np.ndarray:
     F = f.shape[0]
     g = np.empty((F, 4 * N - 1, 2 * N, 2))
     _check(_load().oracle_phi_analysis(N, _p(f), _p(g), F), "phi_analysis")
+    return g
+
+
+def phi_synthesis_nodes(N: int, g_nodes: np.ndarray) -> np.ndarray:
+    """phi_synthesis at a subset of nodes: g_nodes (F,4N-1,nl,2), the chosen node
+    columns of g (orders in the storage sequence) -> their grid rows (F,nl,4N-1,2)."""
+    g_nodes = np.ascontiguousarray(g_nodes, dtype=np.float64)
+    F, M, nl = g_nodes.shape[0], g_nodes.shape[1], g_nodes.shape[2]
+    assert M == 4 * N - 1 and g_nodes.shape[3] == 2
+    f = np.empty((F, nl, M, 2))
+    _check(_load().oracle_phi_synthesis_nodes(N, nl, _p(g_nodes), _p(f), F), "phi_synthesis_nodes")
+    return f
+
+
+def phi_analysis_nodes(N: int, f_rows: np.ndarray) -> np.ndarray:
+    """phi_analysis at a subset of nodes: grid rows f_rows (F,nl,4N-1,2) -> the
+    nodes' ALT values (F,4N-1,nl,2)."""
+    f_rows = np.ascontiguousarray(f_rows, dtype=np.float64)
+    F, nl, M = f_rows.shape[0], f_rows.shape[1], f_rows.shape[2]
+    assert M == 4 * N - 1 and f_rows.shape[3] == 2
+    g = np.empty((F, M, nl, 2))
+    _check(_load().oracle_phi_analysis_nodes(N, nl, _p(f_rows), _p(g), F), "phi_analysis_nodes")
     return g
 
 

@@ -362,6 +362,56 @@ int oracle_phi_analysis(int N, const double* f, double* g, int F) {
   return 0;
 }
 
+/* The same two sums at a chosen set of nl nodes only (large N, where the   */
+/* full grid is out of reach): g holds the nodes' values of every order,    */
+/* (F x M x nl) in the order sequence above, f their grid rows (F x nl x M). */
+int oracle_phi_synthesis_nodes(int N, int nl, const double* g, double* f, int F) {
+  if (N < 1 || nl < 0 || F < 0) return 1;
+  const long K = 2L * N, M = 4L * N - 1, L = nl;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (long l = 0; l < L; ++l) {
+    for (long j = 0; j < M; ++j) {
+      for (int fi = 0; fi < F; ++fi) {
+        double re = 0.0, im = 0.0;
+        for (long m = -(K - 1); m <= K - 1; ++m) {
+          double c, s;
+          phase(m, j, M, &c, &s);
+          const double* gv = g + 2 * ((fi * M + order_slot(m)) * L + l);
+          re += gv[0] * c - gv[1] * s;
+          im += gv[0] * s + gv[1] * c;
+        }
+        f[2 * ((fi * L + l) * M + j)] = re;
+        f[2 * ((fi * L + l) * M + j) + 1] = im;
+      }
+    }
+  }
+  return 0;
+}
+
+int oracle_phi_analysis_nodes(int N, int nl, const double* f, double* g, int F) {
+  if (N < 1 || nl < 0 || F < 0) return 1;
+  const long K = 2L * N, M = 4L * N - 1, L = nl;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (long l = 0; l < L; ++l) {
+    for (long m = -(K - 1); m <= K - 1; ++m) {
+      for (int fi = 0; fi < F; ++fi) {
+        double re = 0.0, im = 0.0;
+        for (long j = 0; j < M; ++j) {
+          double c, s;
+          phase(m, j, M, &c, &s);
+          const double* fv = f + 2 * ((fi * L + l) * M + j);
+          re += fv[0] * c + fv[1] * s;
+          im += fv[1] * c - fv[0] * s;
+        }
+        double* gv = g + 2 * ((fi * M + order_slot(m)) * L + l);
+        gv[0] = re / (double)M;
+        gv[1] = im / (double)M;
+      }
+    }
+  }
+  return 0;
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -277,6 +277,30 @@ def test_phi_round_trip():
     np.testing.assert_allclose(oracle.phi_analysis(N, oracle.phi_synthesis(N, g)), g, atol=1e-13)
 
 
+def _phi_analysis_fft(N, f):
+    """(1/M) sum_j f e^{-i m phi_j} = e^{-i pi m / M} FFT(f)[m mod M] / M."""
+    M = 4 * N - 1
+    F = np.fft.fft(f[..., 0] + 1j * f[..., 1], axis=-1) / M  # (F, rows, M)
+    g = np.zeros((f.shape[0], M, f.shape[1]), dtype=complex)
+    for mm in range(-(2 * N - 1), 2 * N):
+        g[:, oracle.order_slot(mm), :] = F[:, :, mm % M] * np.exp(-1j * np.pi * mm / M)
+    return np.stack([g.real, g.imag], axis=-1)
+
+
+def test_phi_nodes_match_fft():
+    # the node-subset sums against numpy's FFT at chosen nodes, both directions
+    N = 7
+    rng = np.random.default_rng(8)
+    g = rng.standard_normal((2, 4 * N - 1, 2 * N, 2))
+    nodes = [0, 3, 13]
+    f = oracle.phi_synthesis_nodes(N, g[:, :, nodes])
+    np.testing.assert_allclose(f, _phi_synthesis_fft(N, g)[:, nodes], atol=1e-12)
+    frows = rng.standard_normal((2, 3, 4 * N - 1, 2))
+    np.testing.assert_allclose(oracle.phi_analysis_nodes(N, frows), _phi_analysis_fft(N, frows), atol=1e-13)
+    # and a subset of the full sums is the node-subset sum (same arithmetic)
+    np.testing.assert_array_equal(f, oracle.phi_synthesis(N, g)[:, nodes])
+
+
 def test_sht_round_trip():
     N = 8
     beta = inputs.coefficients(N, 1, seed=0, real_m0=True)
