@@ -94,6 +94,12 @@ typedef struct {
                                    transform, kept as a baseline)                */
 #define SHT_FLAG_TIMING 8       /* record CUDA events around every apply kernel
                                    launch (see sht_plan_kernel_time)             */
+#define SHT_FLAG_PHI_ONLY 16    /* build only the nodes and the phi-direction
+                                   transform (sht_phi_*, sht_plan_nodes): no ALT
+                                   program, so any N up to 16384 is cheap; ALT
+                                   and full SHT calls, batches and save return
+                                   SHT_ERR_UNSUPPORTED.  Not with
+                                   SHT_FLAG_HOST_ONLY (SHT_ERR_ARG)            */
 
 /* Plan statistics (Sec. 5 experiments: block counts, ranks, timings). */
 typedef struct {
@@ -186,8 +192,11 @@ sht_status alt_inverse_m(sht_plan_t plan, int m, const double* g_m, double* beta
  *   analysis  g(m, theta_l) = (1/M) sum_j f(theta_l, phi_j) e^{-i m phi_j},
  * phi_j = 2 pi (j + 1/2) / M, M = 4N-1 (exact inverse of each other).  g as
  * for alt_forward (F x (4N-1) x 2N complex), f theta-major (F x 2N x (4N-1)).
- * Arithmetic in FP64 for FP64 plans, else FP32.  SHT_ERR_UNSUPPORTED when one
- * length-M transform does not fit in shared memory (FP64: N <= 3584). */
+ * Arithmetic in FP64 for FP64 plans, else FP32.  Each length-M row is
+ * transformed in the shared memory of one CTA, or spread over a cluster of up
+ * to 8 CTAs when it is longer; SHT_ERR_UNSUPPORTED when it does not fit 8 CTAs
+ * (FP64: M up to about 116,000 values, half that when M has a prime factor
+ * above 13, e.g. N = 16384: M = 65535 = 3 5 17 257 is refused in FP64). */
 sht_status sht_phi_synthesis(sht_plan_t plan, const double* g, double* f, int F, void* stream);
 sht_status sht_phi_analysis(sht_plan_t plan, const double* f, double* g, int F, void* stream);
 
@@ -332,6 +341,14 @@ sht_status sht_plan_set_timing(sht_plan_t plan, int enable);
  * after it, sht_sync must return SHT_ERR_TIMEOUT.  SHT_MIXED plans only
  * (SHT_ERR_UNSUPPORTED otherwise).  Takes a second or more of GPU time. */
 sht_status sht_selftest_timeout(sht_plan_t plan, void* stream);
+
+/* Self-test of the binary64 <-> binary32 conversions that the FP32 and
+ * tensor-core paths apply to every input and output value (integer
+ * arithmetic, round to nearest even, subnormals, infinities and NaN per IEEE
+ * 754; the paper has no counterpart): f32[i] = (float)f64[i] and
+ * back[i] = (double)f32[i], i < n.  Device pointers, caller-owned;
+ * SHT_ERR_ARG for n < 0 or a NULL pointer with n > 0. */
+sht_status sht_selftest_convert(const double* f64, float* f32, double* back, int64_t n, void* stream);
 
 /* Wait for the plan's work on `stream` and return any latched device error. */
 sht_status sht_sync(sht_plan_t plan, void* stream);

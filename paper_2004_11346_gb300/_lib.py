@@ -23,6 +23,7 @@ SHT_FLAG_FORCE_FACTOR = 1
 SHT_FLAG_HOST_ONLY = 2
 SHT_FLAG_DENSE = 4
 SHT_FLAG_TIMING = 8
+SHT_FLAG_PHI_ONLY = 16
 (SHT_EXPORT_UNITS, SHT_EXPORT_OPS, SHT_EXPORT_PHASES, SHT_EXPORT_FACTORS, SHT_EXPORT_ORDER, SHT_EXPORT_OPTS,
  SHT_EXPORT_UNIT_BLOCKS) = range(7)
 
@@ -121,6 +122,7 @@ EXPORTED = [
     "sht_inverse", "sht_plan_save", "sht_plan_load", "sht_plan_kernel_time", "sht_batch_create",
     "sht_batch_destroy", "alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch",
     "sht_batch_sync", "sht_selftest_timeout", "sht_plan_op_image", "sht_order_stats", "sht_plan_set_timing",
+    "sht_selftest_convert",
 ]
 
 
@@ -156,6 +158,7 @@ def load(build: bool = True):
     lib.sht_batch_destroy.argtypes = [vp]
     lib.sht_batch_sync.argtypes = [vp, vp]
     lib.sht_selftest_timeout.argtypes = [vp, vp]
+    lib.sht_selftest_convert.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
     lib.sht_plan_op_image.argtypes = [vp, ctypes.c_int64, i, vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.sht_order_stats.argtypes = [i, d, ctypes.POINTER(sht_opts), i, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(sht_order_info)]
@@ -320,6 +323,10 @@ def sht_batch_sync(batch: int, stream: int = 0):
 
 def sht_selftest_timeout(plan: int, stream: int = 0):
     check(load().sht_selftest_timeout(plan, stream), "sht_selftest_timeout")
+
+
+def sht_selftest_convert(f64: int, f32: int, back: int, n: int, stream: int = 0):
+    check(load().sht_selftest_convert(f64, f32, back, n, stream), "sht_selftest_convert")
 
 
 def sht_plan_op_image(plan: int, op: int, transposed: bool):

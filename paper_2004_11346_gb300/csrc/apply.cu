@@ -24,6 +24,7 @@
 
 #include "apply_f32.cuh"
 #include "apply_tc.cuh"
+#include "f64_bits.cuh"
 #include "phi_dft.cuh"
 #include "plan.hpp"
 
@@ -320,6 +321,7 @@ struct sht_plan_s {
   unsigned int* d_counter = nullptr;
   sht_status latched = SHT_OK;
   bool host_only = false;
+  bool phi_only = false;  // SHT_FLAG_PHI_ONLY: nodes and phi tables, no ALT program
   // FP32 many-field path (precision SHT_FP32 / SHT_MIXED)
   float* d_fac32 = nullptr;
   float* d_ws32 = nullptr;
@@ -458,7 +460,7 @@ TcPlan tc_plan_of(const sht_plan_s* p) {
 
 sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F, int single, int m,
                   cudaStream_t st) {
-  if (p->host_only) return SHT_ERR_UNSUPPORTED;
+  if (p->host_only || p->phi_only) return SHT_ERR_UNSUPPORTED;
   // complex values are moved as 16-byte pairs
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return SHT_ERR_ARG;
   if ((int64_t)F * 2 * p->prog.N > (int64_t)1 << 30) return SHT_ERR_ARG;
@@ -527,15 +529,23 @@ sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F,
   return SHT_OK;
 }
 
+// The conversion helpers over an array (sht_selftest_convert).
+__global__ void convert_selftest_kernel(const double* __restrict__ f64, float* __restrict__ f32,
+                                        double* __restrict__ back, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = f64_to_f32_bits(f64[i]);
+    f32[i] = v;
+    back[i] = f32_to_f64_bits(v);
+  }
+}
+
 sht_status launch_phi(sht_plan_s* p, const double* in, double* out, int F, bool analysis, cudaStream_t st) {
   if (p->host_only) return SHT_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return SHT_ERR_ARG;
   if ((int64_t)F * 2 * p->prog.N > (int64_t)1 << 30) return SHT_ERR_ARG;
   if (p->phi_grid < 1) return SHT_ERR_UNSUPPORTED;
-  const int rows = 2 * p->prog.N * F;
-  const int grid = std::max(1, std::min(p->phi_grid, rows));
-  cudaError_t e = p->prog.opts.precision == SHT_FP64 ? p->phi64.launch(in, out, F, analysis, grid, st)
-                                                     : p->phi32.launch(in, out, F, analysis, grid, st);
+  cudaError_t e = p->prog.opts.precision == SHT_FP64 ? p->phi64.launch(in, out, F, analysis, st)
+                                                     : p->phi32.launch(in, out, F, analysis, st);
   return e == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
 }
 
@@ -635,11 +645,9 @@ sht_status attach_device(sht_plan_s* p) {
   if (e == cudaSuccess) {
     const bool ok = o.precision == SHT_FP64 ? p->phi64.build(N) : p->phi32.build(N);
     if (!ok) e = cudaErrorMemoryAllocation;
-    const size_t smem = o.precision == SHT_FP64 ? p->phi64.smem_bytes() : p->phi32.smem_bytes();
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
-    const int per_sm = smem > 0 && (size_t)optin >= smem ? std::max(1, (int)((size_t)optin / smem)) : 0;
-    p->phi_grid = sms * std::min(per_sm, 4);  // 0: transform length too long for shared memory
+    // co-resident clusters of the transform's launch shape; 0: one row does
+    // not fit the shared memory of a cluster
+    p->phi_grid = o.precision == SHT_FP64 ? p->phi64.max_clusters : p->phi32.max_clusters;
   }
   if (e == cudaSuccess) {
     gws = (size_t)o.max_fields * (4 * (size_t)N - 1) * 2 * N * 2 * sizeof(double);
@@ -679,6 +687,21 @@ bool resolve_opts(int N, double eps, const sht_opts* opts, sht_opts& o) {
          o.trim_delta >= 0.0 && o.max_fields >= 1;
 }
 
+// Device side of a phi-only plan: the phi-direction tables alone.
+sht_status attach_phi(sht_plan_s* p) {
+  const int N = p->prog.N;
+  cudaGetDevice(&p->device);
+  const bool fp64 = p->prog.opts.precision == SHT_FP64;
+  const bool ok = fp64 ? p->phi64.build(N) : p->phi32.build(N);
+  cudaError_t e = ok ? cudaDeviceSynchronize() : cudaErrorMemoryAllocation;
+  if (e != cudaSuccess) {
+    free_device(p);
+    return e == cudaErrorMemoryAllocation ? SHT_ERR_OOM : SHT_ERR_CUDA;
+  }
+  p->phi_grid = fp64 ? p->phi64.max_clusters : p->phi32.max_clusters;
+  return SHT_OK;
+}
+
 }  // namespace
 
 sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* out) {
@@ -687,10 +710,32 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
   sht_opts o;
   if (!resolve_opts(N, eps, opts, o)) return SHT_ERR_ARG;
   const bool host_only = (o.flags & SHT_FLAG_HOST_ONLY) != 0;
+  const bool phi_only = (o.flags & SHT_FLAG_PHI_ONLY) != 0;
+  if (host_only && phi_only) return SHT_ERR_ARG;  // nothing to build
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)) return SHT_ERR_CUDA;
   sht_plan_s* p = new (std::nothrow) sht_plan_s();
   if (!p) return SHT_ERR_OOM;
+  if (phi_only) {
+    p->phi_only = true;
+    p->prog.N = N;
+    p->prog.opts = o;
+    p->prog.info.N = N;
+    p->prog.info.eps = o.eps;
+    sht_status s = SHT_OK;
+    try {
+      gauss_legendre(2 * N, p->prog.x, p->prog.w);
+    } catch (const std::bad_alloc&) {
+      s = SHT_ERR_OOM;
+    }
+    if (s == SHT_OK) s = attach_phi(p);
+    if (s != SHT_OK) {
+      delete p;
+      return s;
+    }
+    *out = p;
+    return SHT_OK;
+  }
   std::string err;
   sht_status s;
   try {
@@ -899,6 +944,7 @@ extern "C" {
 
 sht_status sht_plan_save(sht_plan_t p, const char* path) {
   if (!p || !path) return SHT_ERR_ARG;
+  if (p->phi_only) return SHT_ERR_UNSUPPORTED;  // no program to save
   std::FILE* f = std::fopen(path, "wb");
   if (!f) return SHT_ERR_IO;
   const HostProgram& P = p->prog;
@@ -1218,7 +1264,8 @@ sht_status sht_batch_create(int P, const sht_plan_t* plans, const int* fields, s
     if (!plans[q] || fields[q] < 0) return SHT_ERR_ARG;
     for (int r = 0; r < q; ++r)
       if (plans[r] == plans[q]) return SHT_ERR_ARG;  // each plan's accumulation rows serve one batch slot
-    if (plans[q]->host_only || plans[q]->prog.opts.precision != SHT_MIXED) return SHT_ERR_UNSUPPORTED;
+    if (plans[q]->host_only || plans[q]->phi_only || plans[q]->prog.opts.precision != SHT_MIXED)
+      return SHT_ERR_UNSUPPORTED;
     if (fields[q] > plans[q]->prog.opts.max_fields) return SHT_ERR_ARG;
     if ((int64_t)fields[q] * 2 * plans[q]->prog.N > (int64_t)1 << 30) return SHT_ERR_ARG;
   }
@@ -1323,11 +1370,19 @@ sht_status sht_inverse_batch(sht_batch_t b, const double* const* f, double* cons
 
 sht_status sht_selftest_timeout(sht_plan_t p, void* stream) {
   if (!p) return SHT_ERR_ARG;
-  if (p->host_only || p->prog.opts.precision != SHT_MIXED) return SHT_ERR_UNSUPPORTED;
+  if (p->host_only || p->phi_only || p->prog.opts.precision != SHT_MIXED) return SHT_ERR_UNSUPPORTED;
   return launch_tc_stall(tc_plan_of(p), p->d_wstc, p->d_counter, p->d_err,
                          static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? SHT_OK
              : SHT_ERR_CUDA;
+}
+
+sht_status sht_selftest_convert(const double* f64, float* f32, double* back, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!f64 || !f32 || !back))) return SHT_ERR_ARG;
+  if (n == 0) return SHT_OK;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  convert_selftest_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(f64, f32, back, n);
+  return cudaGetLastError() == cudaSuccess ? SHT_OK : SHT_ERR_CUDA;
 }
 
 sht_status sht_batch_sync(sht_batch_t b, void* stream) {

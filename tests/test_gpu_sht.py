@@ -81,6 +81,69 @@ def test_sht_N64_fp64_workload():
 
 
 @pytest.mark.slow
+def _rows_err(got, ref):
+    """Relative l2 error of every (field, row) of arrays shaped (F, rows, ..., 2)."""
+    d = np.linalg.norm((got - ref).reshape(got.shape[0], got.shape[1], -1), axis=2)
+    return d / np.linalg.norm(ref.reshape(ref.shape[0], ref.shape[1], -1), axis=2)
+
+
+# Rows longer than one CTA's shared memory are spread over a cluster of CTAs:
+# M = 15015 = 3 5 7 11 13 (FP64, 240 KB), M = 16383 = 3 43 127 (FP64 with
+# the generic pass and its second buffer: the order of the largest config),
+# M = 29403 = 3^5 11^2 (FP32, 235 KB).  Phi-only plans: no ALT program.
+@pytest.mark.parametrize("N,prec", [(3754, _lib.SHT_FP64), (4096, _lib.SHT_FP64), (7351, _lib.SHT_FP32)])
+def test_phi_rows_split_over_a_cluster(N, prec):
+    p = sht.Plan(N, 1e-12 if prec == _lib.SHT_FP64 else 1e-7, precision=prec, flags=_lib.SHT_FLAG_PHI_ONLY)
+    M, K = 4 * N - 1, 2 * N
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(N)
+    g = torch.randn((1, M, K, 2), dtype=torch.float64, device="cuda", generator=gen)
+    nodes = [0, 1, N, K - 1]
+    f = p.phi_synthesis(g)
+    ref = oracle.phi_synthesis_nodes(N, g[:, :, nodes].cpu().numpy())
+    err = _rows_err(f[:, nodes].cpu().numpy(), ref)
+    assert np.all(err <= TOL[prec]), err
+    # analysis of the synthesis gives back every order at every node
+    g2 = p.phi_analysis(f)
+    assert float((g2 - g).norm() / g.norm()) <= TOL[prec]
+    del f, g2
+    fin = torch.randn((1, K, M, 2), dtype=torch.float64, device="cuda", generator=gen)
+    ga = p.phi_analysis(fin)
+    refa = oracle.phi_analysis_nodes(N, fin[:, nodes].cpu().numpy())
+    erra = _rows_err(np.moveaxis(ga[:, :, nodes].cpu().numpy(), 2, 1), np.moveaxis(refa, 2, 1))
+    assert np.all(erra <= TOL[prec]), erra
+    del g, fin, ga
+    torch.cuda.empty_cache()
+
+
+def test_phi_only_plan_refuses_the_alt():
+    N = 8
+    p = sht.Plan(N, 1e-12, flags=_lib.SHT_FLAG_PHI_ONLY)
+    x, w = p.nodes()
+    xo, wo = oracle.gl_rule(2 * N)
+    np.testing.assert_allclose(x, xo, atol=1e-14)
+    np.testing.assert_allclose(w, wo, atol=1e-14)
+    beta = dev(inputs.coefficients(N, 1, seed=0))
+    for call in (lambda: p.forward(beta), lambda: p.sht_forward(beta)):
+        with pytest.raises(_lib.ShtError) as e:
+            call()
+        assert e.value.status == _lib.SHT_ERR_UNSUPPORTED
+    # and the phi transform itself runs
+    g = np.random.default_rng(1).standard_normal((2, 4 * N - 1, 2 * N, 2))
+    f = p.phi_synthesis(dev(g)).cpu().numpy()
+    assert np.all(rel_err(f, oracle.phi_synthesis(N, g)) <= 1e-10)
+
+
+def test_phi_row_too_long_is_refused():
+    # N = 16384 in FP64: M = 65535 = 3 5 17 257 needs the second buffer, 2 MB
+    # per row, more than 8 CTAs hold; the call is refused before any launch
+    p = sht.Plan(16384, 1e-12, flags=_lib.SHT_FLAG_PHI_ONLY)
+    buf = torch.zeros(16, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.ShtError) as e:
+        _lib.sht_phi_synthesis(p.handle, buf.data_ptr(), buf.data_ptr(), 1, torch.cuda.current_stream().cuda_stream)
+    assert e.value.status == _lib.SHT_ERR_UNSUPPORTED
+
+
 def test_phi_N256():
     N = 256
     p = sht.Plan(N, 1e-12)
