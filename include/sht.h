@@ -94,10 +94,15 @@ typedef struct {
                                    transform, kept as a baseline)                */
 #define SHT_FLAG_TIMING 8       /* record CUDA events around every apply kernel
                                    launch (see sht_plan_kernel_time)             */
-#define SHT_FLAG_PHI_ONLY 16    /* build only the nodes and the phi-direction
-                                   transform (sht_phi_*, sht_plan_nodes): no ALT
-                                   program, so any N up to 16384 is cheap; ALT
-                                   and full SHT calls, batches and save return
+#define SHT_FLAG_DIRECT 16      /* no partition and no factorisation, nothing
+                                   stored: alt_forward / alt_inverse (and the
+                                   full SHT) apply the dense ALT in FP64 with the
+                                   Legendre recurrence run on the fly for every
+                                   call (O(N^3) work, any N up to 16384 whose
+                                   per-CTA scratch fits, about 16 N^2 bytes per
+                                   SM); the phi transform as for other plans.
+                                   Single-order calls, batches, the no-allocation
+                                   entry point and save return
                                    SHT_ERR_UNSUPPORTED.  Not with
                                    SHT_FLAG_HOST_ONLY (SHT_ERR_ARG)            */
 

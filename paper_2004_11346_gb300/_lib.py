@@ -23,7 +23,7 @@ SHT_FLAG_FORCE_FACTOR = 1
 SHT_FLAG_HOST_ONLY = 2
 SHT_FLAG_DENSE = 4
 SHT_FLAG_TIMING = 8
-SHT_FLAG_PHI_ONLY = 16
+SHT_FLAG_DIRECT = 16
 (SHT_EXPORT_UNITS, SHT_EXPORT_OPS, SHT_EXPORT_PHASES, SHT_EXPORT_FACTORS, SHT_EXPORT_ORDER, SHT_EXPORT_OPTS,
  SHT_EXPORT_UNIT_BLOCKS) = range(7)
 

@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libsht.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 HOST_SRC = ["plan.cpp"]
-CUDA_SRC = ["apply.cu", "apply_f32.cu", "apply_tc.cu", "phi_dft.cu"]
+CUDA_SRC = ["apply.cu", "apply_f32.cu", "apply_tc.cu", "phi_dft.cu", "alt_direct.cu"]
 
 
 def cuda_home() -> str:

@@ -22,6 +22,7 @@
 #include <new>
 #include <string>
 
+#include "alt_direct.cuh"
 #include "apply_f32.cuh"
 #include "apply_tc.cuh"
 #include "f64_bits.cuh"
@@ -321,7 +322,8 @@ struct sht_plan_s {
   unsigned int* d_counter = nullptr;
   sht_status latched = SHT_OK;
   bool host_only = false;
-  bool phi_only = false;  // SHT_FLAG_PHI_ONLY: nodes and phi tables, no ALT program
+  bool direct = false;  // SHT_FLAG_DIRECT: no ALT program; dense ALT by the recurrence on the fly
+  DirectPlan dplan;
   // FP32 many-field path (precision SHT_FP32 / SHT_MIXED)
   float* d_fac32 = nullptr;
   float* d_ws32 = nullptr;
@@ -421,6 +423,7 @@ void free_device(sht_plan_s* p) {
   cudaFree(p->d_err);
   p->phi64.release();
   p->phi32.release();
+  p->dplan.release();
 }
 
 DevPlan dev_plan(const sht_plan_s* p) {
@@ -460,7 +463,7 @@ TcPlan tc_plan_of(const sht_plan_s* p) {
 
 sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F, int single, int m,
                   cudaStream_t st) {
-  if (p->host_only || p->phi_only) return SHT_ERR_UNSUPPORTED;
+  if (p->host_only) return SHT_ERR_UNSUPPORTED;
   // complex values are moved as 16-byte pairs
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return SHT_ERR_ARG;
   if ((int64_t)F * 2 * p->prog.N > (int64_t)1 << 30) return SHT_ERR_ARG;
@@ -468,6 +471,23 @@ sht_status launch(sht_plan_s* p, bool fwd, const double* in, double* out, int F,
     sht_status s = p->latched;
     p->latched = SHT_OK;
     return s;
+  }
+  if (p->direct) {
+    // the dense recurrence on the fly, all orders, max_fields fields per launch
+    if (single) return SHT_ERR_UNSUPPORTED;
+    const int N = p->prog.N;
+    const int64_t nb = 2L * 4L * N * N, ng = 2L * (4L * N - 1) * 2 * N;  // doubles per field
+    const int64_t in_stride = fwd ? nb : ng, out_stride = fwd ? ng : nb;
+    cudaEvent_t* ev = timing_slot(p);
+    if (ev && cudaEventRecord(ev[0], st) != cudaSuccess) return SHT_ERR_CUDA;
+    for (int f0 = 0; f0 < F; f0 += p->dplan.F_max) {
+      const int Fb = std::min(p->dplan.F_max, F - f0);
+      if (p->dplan.launch(fwd, in + f0 * in_stride, out + f0 * out_stride, Fb, st) != cudaSuccess)
+        return SHT_ERR_CUDA;
+    }
+    if (ev && (cudaEventRecord(ev[1], st) != cudaSuccess || cudaEventRecord(ev[2], st) != cudaSuccess))
+      return SHT_ERR_CUDA;
+    return SHT_OK;
   }
   if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess) return SHT_ERR_CUDA;
   if (p->prog.opts.precision == SHT_MIXED) {
@@ -687,13 +707,31 @@ bool resolve_opts(int N, double eps, const sht_opts* opts, sht_opts& o) {
          o.trim_delta >= 0.0 && o.max_fields >= 1;
 }
 
-// Device side of a phi-only plan: the phi-direction tables alone.
-sht_status attach_phi(sht_plan_s* p) {
+// Device side of a direct plan: the phi-direction tables and the dense
+// on-the-fly ALT (nodes, weights and per-CTA scratch for max_fields fields).
+sht_status attach_direct(sht_plan_s* p) {
+  alloc_hook_reset();
   const int N = p->prog.N;
+  const sht_opts& o = p->prog.opts;
   cudaGetDevice(&p->device);
-  const bool fp64 = p->prog.opts.precision == SHT_FP64;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  const bool fp64 = o.precision == SHT_FP64;
   const bool ok = fp64 ? p->phi64.build(N) : p->phi32.build(N);
-  cudaError_t e = ok ? cudaDeviceSynchronize() : cudaErrorMemoryAllocation;
+  cudaError_t e = ok ? cudaSuccess : cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) e = p->dplan.build(N, o.max_fields, p->prog.x.data(), p->prog.w.data(), std::max(1, sms));
+  if (e == cudaSuccess) {
+    const size_t gws = (size_t)o.max_fields * (4 * (size_t)N - 1) * 2 * N * 2 * sizeof(double);
+    e = plan_malloc(reinterpret_cast<void**>(&p->d_gws), gws);
+    p->prog.info.workspace_bytes =
+        (int64_t)(gws + (size_t)p->dplan.grid * p->dplan.per_cta * sizeof(double));
+  }
+  if (e == cudaSuccess && (o.flags & SHT_FLAG_TIMING)) {
+    p->tev.assign(3 * kTimingSlots, nullptr);
+    for (cudaEvent_t& ev : p->tev)
+      if (e == cudaSuccess) e = cudaEventCreate(&ev);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_device(p);
     return e == cudaErrorMemoryAllocation ? SHT_ERR_OOM : SHT_ERR_CUDA;
@@ -710,14 +748,14 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
   sht_opts o;
   if (!resolve_opts(N, eps, opts, o)) return SHT_ERR_ARG;
   const bool host_only = (o.flags & SHT_FLAG_HOST_ONLY) != 0;
-  const bool phi_only = (o.flags & SHT_FLAG_PHI_ONLY) != 0;
-  if (host_only && phi_only) return SHT_ERR_ARG;  // nothing to build
+  const bool direct = (o.flags & SHT_FLAG_DIRECT) != 0;
+  if (host_only && direct) return SHT_ERR_ARG;  // nothing to build
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)) return SHT_ERR_CUDA;
   sht_plan_s* p = new (std::nothrow) sht_plan_s();
   if (!p) return SHT_ERR_OOM;
-  if (phi_only) {
-    p->phi_only = true;
+  if (direct) {
+    p->direct = true;
     p->prog.N = N;
     p->prog.opts = o;
     p->prog.info.N = N;
@@ -728,7 +766,7 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
     } catch (const std::bad_alloc&) {
       s = SHT_ERR_OOM;
     }
-    if (s == SHT_OK) s = attach_phi(p);
+    if (s == SHT_OK) s = attach_direct(p);
     if (s != SHT_OK) {
       delete p;
       return s;
@@ -944,7 +982,7 @@ extern "C" {
 
 sht_status sht_plan_save(sht_plan_t p, const char* path) {
   if (!p || !path) return SHT_ERR_ARG;
-  if (p->phi_only) return SHT_ERR_UNSUPPORTED;  // no program to save
+  if (p->direct) return SHT_ERR_UNSUPPORTED;  // no program to save
   std::FILE* f = std::fopen(path, "wb");
   if (!f) return SHT_ERR_IO;
   const HostProgram& P = p->prog;
@@ -1264,7 +1302,7 @@ sht_status sht_batch_create(int P, const sht_plan_t* plans, const int* fields, s
     if (!plans[q] || fields[q] < 0) return SHT_ERR_ARG;
     for (int r = 0; r < q; ++r)
       if (plans[r] == plans[q]) return SHT_ERR_ARG;  // each plan's accumulation rows serve one batch slot
-    if (plans[q]->host_only || plans[q]->phi_only || plans[q]->prog.opts.precision != SHT_MIXED)
+    if (plans[q]->host_only || plans[q]->direct || plans[q]->prog.opts.precision != SHT_MIXED)
       return SHT_ERR_UNSUPPORTED;
     if (fields[q] > plans[q]->prog.opts.max_fields) return SHT_ERR_ARG;
     if ((int64_t)fields[q] * 2 * plans[q]->prog.N > (int64_t)1 << 30) return SHT_ERR_ARG;
@@ -1370,7 +1408,7 @@ sht_status sht_inverse_batch(sht_batch_t b, const double* const* f, double* cons
 
 sht_status sht_selftest_timeout(sht_plan_t p, void* stream) {
   if (!p) return SHT_ERR_ARG;
-  if (p->host_only || p->phi_only || p->prog.opts.precision != SHT_MIXED) return SHT_ERR_UNSUPPORTED;
+  if (p->host_only || p->direct || p->prog.opts.precision != SHT_MIXED) return SHT_ERR_UNSUPPORTED;
   return launch_tc_stall(tc_plan_of(p), p->d_wstc, p->d_counter, p->d_err,
                          static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? SHT_OK

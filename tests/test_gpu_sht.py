@@ -93,7 +93,7 @@ def _rows_err(got, ref):
 # M = 29403 = 3^5 11^2 (FP32, 235 KB).  Phi-only plans: no ALT program.
 @pytest.mark.parametrize("N,prec", [(3754, _lib.SHT_FP64), (4096, _lib.SHT_FP64), (7351, _lib.SHT_FP32)])
 def test_phi_rows_split_over_a_cluster(N, prec):
-    p = sht.Plan(N, 1e-12 if prec == _lib.SHT_FP64 else 1e-7, precision=prec, flags=_lib.SHT_FLAG_PHI_ONLY)
+    p = sht.Plan(N, 1e-12 if prec == _lib.SHT_FP64 else 1e-7, precision=prec, flags=_lib.SHT_FLAG_DIRECT)
     M, K = 4 * N - 1, 2 * N
     gen = torch.Generator(device="cuda")
     gen.manual_seed(N)
@@ -116,28 +116,26 @@ def test_phi_rows_split_over_a_cluster(N, prec):
     torch.cuda.empty_cache()
 
 
-def test_phi_only_plan_refuses_the_alt():
+def test_direct_plan_nodes_and_refusals():
     N = 8
-    p = sht.Plan(N, 1e-12, flags=_lib.SHT_FLAG_PHI_ONLY)
+    p = sht.Plan(N, 1e-12, flags=_lib.SHT_FLAG_DIRECT)
     x, w = p.nodes()
     xo, wo = oracle.gl_rule(2 * N)
     np.testing.assert_allclose(x, xo, atol=1e-14)
     np.testing.assert_allclose(w, wo, atol=1e-14)
-    beta = dev(inputs.coefficients(N, 1, seed=0))
-    for call in (lambda: p.forward(beta), lambda: p.sht_forward(beta)):
+    beta_m = dev(np.zeros((1, 2 * N - 3, 2)))
+    for call in (lambda: p.forward_m(3, beta_m), lambda: p.save("/dev/null")):
         with pytest.raises(_lib.ShtError) as e:
             call()
         assert e.value.status == _lib.SHT_ERR_UNSUPPORTED
-    # and the phi transform itself runs
-    g = np.random.default_rng(1).standard_normal((2, 4 * N - 1, 2 * N, 2))
-    f = p.phi_synthesis(dev(g)).cpu().numpy()
-    assert np.all(rel_err(f, oracle.phi_synthesis(N, g)) <= 1e-10)
+    with pytest.raises(_lib.ShtError):
+        sht.Plan(N, 1e-12, flags=_lib.SHT_FLAG_DIRECT | _lib.SHT_FLAG_HOST_ONLY)
 
 
 def test_phi_row_too_long_is_refused():
     # N = 16384 in FP64: M = 65535 = 3 5 17 257 needs the second buffer, 2 MB
     # per row, more than 8 CTAs hold; the call is refused before any launch
-    p = sht.Plan(16384, 1e-12, flags=_lib.SHT_FLAG_PHI_ONLY)
+    p = sht.Plan(16384, 1e-12, flags=_lib.SHT_FLAG_DIRECT)
     buf = torch.zeros(16, dtype=torch.float64, device="cuda")
     with pytest.raises(_lib.ShtError) as e:
         _lib.sht_phi_synthesis(p.handle, buf.data_ptr(), buf.data_ptr(), 1, torch.cuda.current_stream().cuda_stream)
