@@ -526,6 +526,20 @@ def compare(torch, sht, _lib, w, plan, beta, g, args, stream):
     out["dense_fp64"] = {"fields_per_s": 1e3 / ms, "forward_ms": f, "inverse_ms": i,
                          "entries": pd.stats()["entries_total"], "t_mat_s": pd.stats()["t_factor_s"]}
     del pd
+    # the dense FP64 transform with the recurrence on the fly (nothing stored),
+    # on 16 fields: its GEMM tiles take 64 right-hand sides, 4 per field
+    F16 = min(16, beta.shape[0])
+    b16 = beta[:F16].contiguous()
+    g16 = torch.empty((F16, 4 * N - 1, 2 * N, 2), dtype=torch.float64, device="cuda")
+    r16 = torch.empty_like(b16)
+    pdd = sht.Plan(N, 1e-12, precision=_lib.SHT_FP64, flags=_lib.SHT_FLAG_DIRECT, max_fields=F16)
+    ms, f, i = time_steps(torch, pdd, b16, g16, r16, 1, 1, stream)
+    out["dense_direct_fp64"] = {"fields_per_s": F16 * 1e3 / ms, "forward_ms": f, "inverse_ms": i, "fields": F16,
+                                "round_trip_rel_err": float((r16 - b16).norm() / b16.norm()),
+                                "tflops": 2 * 2 * 2 * N ** 3 * 4 * F16 / ms / 1e9,
+                                "what": "SHT_FLAG_DIRECT plan: Legendre recurrence on the fly, FP64, nothing stored"}
+    del pdd, b16, g16, r16
+    torch.cuda.empty_cache()
     # the paper's speedup ratios (its last experiment), FP64 on both sides: the
     # dense transform's time over the IDBF apply's, and building the dense
     # matrices over factoring them

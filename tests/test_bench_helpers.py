@@ -69,14 +69,27 @@ def test_compare_reports_the_paper_ratios(monkeypatch):
     """compare()'s bookkeeping with stand-ins for the GPU parts: the IDBF and
     dense plans' times and build times give the paper's two speedup ratios."""
     class FakeTensor:
+        shape = (16,)
+
         def __getitem__(self, k):
+            return self
+
+        def __sub__(self, o):
             return self
 
         def contiguous(self):
             return self
 
+        def norm(self):
+            return 1.0
+
     class FakeTorch:
         float64 = "f64"
+
+        class cuda:
+            @staticmethod
+            def empty_cache():
+                pass
 
         @staticmethod
         def empty(*a, **k):
@@ -87,7 +100,7 @@ def test_compare_reports_the_paper_ratios(monkeypatch):
             return FakeTensor()
 
     class FakePlan:
-        def __init__(self, N, eps, precision=None, flags=0):
+        def __init__(self, N, eps, precision=None, flags=0, max_fields=1):
             self.dense = bool(flags & 4)
 
         def stats(self):
@@ -96,11 +109,13 @@ def test_compare_reports_the_paper_ratios(monkeypatch):
     class FakeSht:
         Plan = FakePlan
 
-    lib = type("L", (), {"SHT_FP64": 0, "SHT_FLAG_DENSE": 4})
-    times = iter([(10.0, 4.0, 6.0), (40.0, 15.0, 25.0)])  # FP64 IDBF, then dense
+    lib = type("L", (), {"SHT_FP64": 0, "SHT_FLAG_DENSE": 4, "SHT_FLAG_DIRECT": 16})
+    # FP64 IDBF, dense stored, dense on the fly (16 fields)
+    times = iter([(10.0, 4.0, 6.0), (40.0, 15.0, 25.0), (2000.0, 900.0, 1100.0)])
     monkeypatch.setattr(bench, "time_steps", lambda *a: next(times))
     monkeypatch.setattr(bench, "sht_timings", lambda *a, **k: {})
     args = type("A", (), {"steps": 4})
     out = bench.compare(FakeTorch, FakeSht, lib, {"N": 8, "precision": "fp64"}, None, FakeTensor(), None, args, None)
     assert out["fp64_idbf"]["t_fac_s"] == 2.0 and out["dense_fp64"]["t_mat_s"] == 6.0
     assert out["paper_ratios"] == {"t_dir_over_t_app": 4.0, "t_mat_over_t_fac": 3.0}
+    assert out["dense_direct_fp64"]["fields_per_s"] == 8.0 and out["dense_direct_fp64"]["fields"] == 16
