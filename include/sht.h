@@ -347,6 +347,16 @@ sht_status sht_plan_set_timing(sht_plan_t plan, int enable);
  * (SHT_ERR_UNSUPPORTED otherwise).  Takes a second or more of GPU time. */
 sht_status sht_selftest_timeout(sht_plan_t plan, void* stream);
 
+/* The order in which the apply's persistent CTAs take the orders |m| from
+ * the work queue (the m-to-CTA schedule; the paper has no counterpart, one
+ * order is one independent ALT, Eq. sht_fft): order[q] = |m| of the q-th
+ * unit, a permutation of 0 .. 2N-1 (each field group of a unit follows it).
+ * Plans start with the orders by decreasing modelled cost; any permutation
+ * gives the same results.  Host array, copied; the plan is synchronised
+ * first, so no call on it may be in flight.  SHT_ERR_ARG unless n = 2N and
+ * order is a permutation; SHT_ERR_UNSUPPORTED for direct plans. */
+sht_status sht_plan_set_order(sht_plan_t plan, const int32_t* order, int n);
+
 /* Self-test of the binary64 <-> binary32 conversions that the FP32 and
  * tensor-core paths apply to every input and output value (integer
  * arithmetic, round to nearest even, subnormals, infinities and NaN per IEEE

@@ -85,6 +85,14 @@ class Plan:
     def stats(self) -> dict:
         return _lib.sht_plan_stats(self.handle)
 
+    def order(self) -> np.ndarray:
+        """The unit queue order of the apply (|m| of each unit in the order taken)."""
+        return self.program(("order",))["order"].copy()
+
+    def set_order(self, order):
+        """Set the unit queue order (sht_plan_set_order): any permutation of 0 .. 2N-1."""
+        _lib.sht_plan_set_order(self.handle, order)
+
     def nodes(self):
         x = np.empty(2 * self.N)
         w = np.empty(2 * self.N)

@@ -122,7 +122,7 @@ EXPORTED = [
     "sht_inverse", "sht_plan_save", "sht_plan_load", "sht_plan_kernel_time", "sht_batch_create",
     "sht_batch_destroy", "alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch",
     "sht_batch_sync", "sht_selftest_timeout", "sht_plan_op_image", "sht_order_stats", "sht_plan_set_timing",
-    "sht_selftest_convert",
+    "sht_selftest_convert", "sht_plan_set_order",
 ]
 
 
@@ -159,6 +159,7 @@ def load(build: bool = True):
     lib.sht_batch_sync.argtypes = [vp, vp]
     lib.sht_selftest_timeout.argtypes = [vp, vp]
     lib.sht_selftest_convert.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
+    lib.sht_plan_set_order.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i]
     lib.sht_plan_op_image.argtypes = [vp, ctypes.c_int64, i, vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.sht_order_stats.argtypes = [i, d, ctypes.POINTER(sht_opts), i, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(sht_order_info)]
@@ -323,6 +324,14 @@ def sht_batch_sync(batch: int, stream: int = 0):
 
 def sht_selftest_timeout(plan: int, stream: int = 0):
     check(load().sht_selftest_timeout(plan, stream), "sht_selftest_timeout")
+
+
+def sht_plan_set_order(plan: int, order):
+    """Set the plan's unit queue order (a permutation of 0 .. 2N-1)."""
+    import numpy as np
+    a = np.ascontiguousarray(order, dtype=np.int32)
+    check(load().sht_plan_set_order(plan, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(a.size)),
+          "sht_plan_set_order")
 
 
 def sht_selftest_convert(f64: int, f32: int, back: int, n: int, stream: int = 0):

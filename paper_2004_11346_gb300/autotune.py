@@ -11,8 +11,9 @@ products.
 
 autotune() ranks candidate (n0, n_leaf) pairs by that work model on host-only
 plans (no GPU needed), then builds the best few on the device, times a forward
-and an inverse apply of the requested batch with CUDA events, and returns the
-fastest.  The model's counts mirror how the kernel cuts the work: segments
+and an inverse apply of the requested batch with CUDA events, and keeps the
+fastest; on it, it then times the queue orders of the persistent kernel (the
+m-to-CTA schedule, schedule()) and keeps the fastest of those too.  The model's counts mirror how the kernel cuts the work: segments
 moved to the kernel's scratch rows (X_o, Y_e and Y_o start on whole groups),
 K sides widened to whole 8-row groups, chunks of 4 groups (the last rounded
 to an even number), the outputs of products that write intermediate rows
@@ -156,13 +157,68 @@ def rank(N: int, eps: float, cands=None, sample: int | None = None, **plan_kw):
     return rows
 
 
+SCHEDULES = ("lpt", "pairs", "ascending")
+
+
+def schedule(units, kind: str) -> np.ndarray:
+    """A queue order of the units (the m-to-CTA schedule) from a plan's unit
+    records: "lpt", decreasing modelled cost (the order plans start with);
+    "pairs", the costliest and the cheapest remaining units alternately, so
+    that the CTAs in flight mix large and small working sets; "ascending",
+    |m| = 0, 1, ... (an order's work falls with |m|)."""
+    cost = np.asarray(units["cost"], dtype=np.float64)
+    am = np.asarray(units["am"], dtype=np.int32)
+    lpt = am[np.argsort(-cost, kind="stable")]
+    if kind == "lpt":
+        return lpt
+    if kind == "pairs":
+        out = np.empty_like(lpt)
+        out[0::2] = lpt[: (len(lpt) + 1) // 2]
+        out[1::2] = lpt[::-1][: len(lpt) // 2]
+        return out
+    if kind == "ascending":
+        return np.sort(am)
+    raise ValueError(kind)
+
+
+def _time_round_trip(torch, p, beta, gv, back, steps):
+    p.forward(beta, out=gv)
+    p.inverse(gv, out=back)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        p.forward(beta, out=gv)
+        p.inverse(gv, out=back)
+    e1.record()
+    torch.cuda.synchronize()
+    p.sync()
+    return e0.elapsed_time(e1) / steps
+
+
+def tune_schedule(p, beta, gv, back, steps: int = 3):
+    """Time every schedule of SCHEDULES on plan p (forward + inverse of the
+    given batch), leave the fastest set on the plan and return one row per
+    schedule."""
+    import torch
+    units = p.program(("units",))["units"]
+    rows = []
+    for kind in SCHEDULES:
+        p.set_order(schedule(units, kind))
+        rows.append({"schedule": kind, "measured_ms": _time_round_trip(torch, p, beta, gv, back, steps)})
+    best = min(rows, key=lambda r: r["measured_ms"])
+    p.set_order(schedule(units, best["schedule"]))
+    return rows
+
+
 def autotune(N: int, eps: float, fields: int, top: int = 3, steps: int = 3, cands=None, seed: int = 0,
-             sample: int | None = None):
+             sample: int | None = None, schedules: bool = True):
     """Rank the candidates by the work model (from sampled orders when
     `sample` is given), time the best `top` of them on the current CUDA
     device (forward + inverse ALT of `fields` random fields, CUDA events,
-    after a warm-up) and return (best Plan, table of all rows).  The returned
-    plan is built on the device with the winning parameters."""
+    after a warm-up), then, on the fastest, time the queue orders of
+    SCHEDULES, and return (best Plan, table of all rows).  The returned plan
+    is built on the device with the winning parameters and schedule."""
     import torch
     from . import Plan
     rows = rank(N, eps, cands, sample=sample, max_fields=fields)
@@ -173,24 +229,16 @@ def autotune(N: int, eps: float, fields: int, top: int = 3, steps: int = 3, cand
     best, best_ms = None, float("inf")
     for r in rows[:top]:
         p = Plan(N, eps, precision=_lib.SHT_MIXED, n0=r["n0"], n_leaf=r["n_leaf"], max_fields=fields)
-        p.forward(beta, out=gv)
-        p.inverse(gv, out=back)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(steps):
-            p.forward(beta, out=gv)
-            p.inverse(gv, out=back)
-        e1.record()
-        torch.cuda.synchronize()
-        p.sync()
-        r["measured_ms"] = e0.elapsed_time(e1) / steps
+        r["measured_ms"] = _time_round_trip(torch, p, beta, gv, back, steps)
         if r["measured_ms"] < best_ms:
             if best is not None:
                 best.close()
             best, best_ms = p, r["measured_ms"]
         else:
             p.close()
+    if schedules:
+        for s in tune_schedule(best, beta, gv, back, steps):
+            rows.append({"n0": int(best.opts.n0), "n_leaf": int(best.opts.n_leaf), **s})
     return best, rows
 
 
@@ -219,8 +267,10 @@ def main(argv=None):
     plan, rows = autotune(a.N, a.eps, a.fields, top=a.top, steps=a.steps, cands=cands, sample=a.sample)
     for r in rows:
         print(json.dumps(r), flush=True)
-    print(json.dumps({"best": {"n0": int(plan.opts.n0), "n_leaf": int(plan.opts.n_leaf)}, "N": a.N, "eps": a.eps,
-                      "fields": a.fields}), flush=True)
+    sched = [r for r in rows if "schedule" in r]
+    best_sched = min(sched, key=lambda r: r["measured_ms"])["schedule"] if sched else "lpt"
+    print(json.dumps({"best": {"n0": int(plan.opts.n0), "n_leaf": int(plan.opts.n_leaf), "schedule": best_sched},
+                      "N": a.N, "eps": a.eps, "fields": a.fields}), flush=True)
 
 
 if __name__ == "__main__":

@@ -1415,6 +1415,23 @@ sht_status sht_selftest_timeout(sht_plan_t p, void* stream) {
              : SHT_ERR_CUDA;
 }
 
+sht_status sht_plan_set_order(sht_plan_t p, const int32_t* order, int n) {
+  if (!p || !order || n != 2 * p->prog.N) return SHT_ERR_ARG;
+  if (p->direct) return SHT_ERR_UNSUPPORTED;
+  std::vector<char> seen((size_t)n, 0);
+  for (int q = 0; q < n; ++q) {
+    if (order[q] < 0 || order[q] >= n || seen[(size_t)order[q]]) return SHT_ERR_ARG;
+    seen[(size_t)order[q]] = 1;
+  }
+  if (!p->host_only) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return SHT_ERR_CUDA;
+    if (cudaMemcpy(p->d_order, order, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
+      return SHT_ERR_CUDA;
+  }
+  std::copy(order, order + n, p->prog.order.begin());
+  return SHT_OK;
+}
+
 sht_status sht_selftest_convert(const double* f64, float* f32, double* back, int64_t n, void* stream) {
   if (n < 0 || (n > 0 && (!f64 || !f32 || !back))) return SHT_ERR_ARG;
   if (n == 0) return SHT_OK;

@@ -85,3 +85,35 @@ def test_rank_from_samples(capsys):
     autotune.main(["--N", "64", "--eps", "1e-7", "--cands", "16:8,32:16", "--sample", "16", "--rank-only"])
     out = [json.loads(l) for l in capsys.readouterr().out.strip().splitlines()]
     assert len(out) == 2 and out[0]["model_us"] <= out[1]["model_us"]
+
+
+def test_schedules_are_permutations_and_set_on_the_plan():
+    N = 24
+    p = sht.Plan(N, 1e-7, flags=HOST, precision=_lib.SHT_MIXED, n0=12, n_leaf=6)
+    units = p.program(("units",))["units"]
+    cost = {int(u["am"]): float(u["cost"]) for u in units}
+    for kind in autotune.SCHEDULES:
+        o = autotune.schedule(units, kind)
+        assert sorted(o.tolist()) == list(range(2 * N))
+        p.set_order(o)
+        assert np.array_equal(p.order(), o)
+    lpt = autotune.schedule(units, "lpt")
+    assert all(cost[int(a)] >= cost[int(b)] for a, b in zip(lpt[:-1], lpt[1:]))
+    # the plan starts in LPT order
+    q = sht.Plan(N, 1e-7, flags=HOST, precision=_lib.SHT_MIXED, n0=12, n_leaf=6)
+    assert np.array_equal(q.order(), lpt)
+    pairs = autotune.schedule(units, "pairs")
+    assert pairs[0] == lpt[0] and pairs[1] == lpt[-1] and pairs[2] == lpt[1]
+    assert np.array_equal(autotune.schedule(units, "ascending"), np.arange(2 * N))
+
+
+def test_set_order_refuses_what_is_not_a_permutation():
+    import pytest
+    N = 8
+    p = sht.Plan(N, 1e-7, flags=HOST, precision=_lib.SHT_MIXED)
+    before = p.order()
+    for bad in ([0] * (2 * N), list(range(2 * N - 1)), list(range(1, 2 * N + 1)), [-1] + list(range(1, 2 * N))):
+        with pytest.raises(_lib.ShtError) as e:
+            p.set_order(bad)
+        assert e.value.status == _lib.SHT_ERR_ARG
+    assert np.array_equal(p.order(), before)

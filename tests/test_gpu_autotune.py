@@ -19,13 +19,50 @@ def _cuda():
 def test_autotune_returns_fastest_measured_plan():
     N, F = 48, 8
     plan, rows = autotune.autotune(N, 1e-7, F, top=2, steps=2, cands=[(12, 6), (24, 6), (24, 12)])
-    timed = [r for r in rows if "measured_ms" in r]
+    timed = [r for r in rows if "measured_ms" in r and "schedule" not in r]
     assert len(timed) == 2
     best = min(timed, key=lambda r: r["measured_ms"])
     assert (plan.opts.n0, plan.opts.n_leaf) == (best["n0"], best["n_leaf"])
+    # then every schedule was timed on the winner, and the fastest is set
+    sched = [r for r in rows if "schedule" in r]
+    assert [r["schedule"] for r in sched] == list(autotune.SCHEDULES)
+    fastest = min(sched, key=lambda r: r["measured_ms"])["schedule"]
+    units = plan.program(("units",))["units"]
+    assert np.array_equal(plan.order(), autotune.schedule(units, fastest))
     beta = inputs.coefficients(N, F, seed=2)
     g = plan.forward(torch.from_numpy(beta).cuda())
     torch.cuda.synchronize()
     ref = oracle.alt_forward(N, beta)
     err = np.linalg.norm((g.cpu().numpy() - ref).reshape(F, -1), axis=1) / np.linalg.norm(ref.reshape(F, -1), axis=1)
     assert np.all(err <= 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_queue_order_does_not_change_results(prec):
+    """Every (order, field group) item is computed by one CTA, so the queue
+    order changes nothing but timing: bit-identical outputs on the tensor-core
+    path (each accumulation row is added to by one thread in a fixed
+    sequence); on the FP64 path the products of one phase that accumulate into
+    the same rows do so with atomic adds from different warps, whose order
+    follows the warp timing, so there the outputs agree to rounding."""
+    import paper_2004_11346_gb300 as sht
+    from paper_2004_11346_gb300 import _lib
+    N, F = 40, 3
+    p = sht.Plan(N, 1e-7 if prec == "mixed" else 1e-12,
+                 precision=_lib.SHT_MIXED if prec == "mixed" else _lib.SHT_FP64, n0=10, n_leaf=5)
+    beta = torch.from_numpy(inputs.coefficients(N, F, seed=3)).cuda()
+    units = p.program(("units",))["units"]
+    outs = []
+    for kind in autotune.SCHEDULES:
+        p.set_order(autotune.schedule(units, kind))
+        g = p.forward(beta)
+        b = p.inverse(g)
+        torch.cuda.synchronize()
+        p.sync()
+        outs.append((g.cpu(), b.cpu()))
+    for g, b in outs[1:]:
+        if prec == "mixed":
+            assert torch.equal(g, outs[0][0]) and torch.equal(b, outs[0][1])
+        else:
+            assert float((g - outs[0][0]).norm() / outs[0][0].norm()) <= 1e-14
+            assert float((b - outs[0][1]).norm() / outs[0][1].norm()) <= 1e-14
