@@ -342,6 +342,7 @@ struct sht_plan_s {
   int32_t* d_tczri = nullptr;
   unsigned char* d_wstc = nullptr;
   float* d_acc = nullptr;  // accumulated rows of every work item (tc_gmax field groups)
+  unsigned char* d_pre = nullptr;  // transposed inputs gathered ahead (tc_gmax field groups)
   int tc_gmax = 0;
   int tc_max_rows = 0;     // scratch rows of the largest order (tensor-core layout)
   int* d_err = nullptr;
@@ -420,6 +421,7 @@ void free_device(sht_plan_s* p) {
   cudaFree(p->d_tczri);
   cudaFree(p->d_wstc);
   cudaFree(p->d_acc);
+  cudaFree(p->d_pre);
   cudaFree(p->d_err);
   p->phi64.release();
   p->phi32.release();
@@ -454,6 +456,7 @@ TcPlan tc_plan_of(const sht_plan_s* p) {
   t.zri = p->d_tczri;
   t.w = p->d_w;
   t.acc = p->d_acc;
+  t.pre = p->d_pre;
   t.gmax = p->tc_gmax;
   t.N = p->prog.N;
   t.nunits = 2 * p->prog.N;
@@ -647,6 +650,9 @@ sht_status attach_device(sht_plan_s* p) {
     p->tc_gmax = (o.max_fields + kTcFields - 1) / kTcFields;
     const size_t acc = (size_t)p->tc_gmax * 2 * N * tc_acc_rows(N) * kTcR * sizeof(float);
     if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_acc), acc);
+    const size_t pre = (size_t)p->tc_gmax * 2 * N * tc_pre_groups(N) * kTcGrpBytes;
+    if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_pre), pre);
+    ws32 += pre;
     ws32 += acc;
     if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
@@ -1273,6 +1279,7 @@ sht_status launch_batch(sht_batch_s* b, bool fwd, const double* const* in, doubl
       return s;
     }
     L.plan[q] = tc_plan_of(p);
+    L.plan[q].pre = nullptr;  // a batch's I/O warps gather the transposed inputs themselves
     L.in[q] = in[q];
     L.out[q] = out[q];
     L.F[q] = b->F[q];

@@ -553,8 +553,9 @@ __device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u
 // Y_o[i] = w_{N+i} (g(theta_{N+i}) - g(theta_{N-1-i})).  A window is 16
 // nodes: lanes 0-15 load g(theta_{N+i}) into tile rows 0-15, lanes 16-31
 // g(theta_{N-1-i}) into rows 16-31; it makes two groups of each of Y_e, Y_o.
+// Groups are written at their scratch-row group index minus gbase.
 __device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u, unsigned char* vec, float* T,
-                               int e) {
+                               int e, int gbase) {
   const TcPlan& p = L.plan[itm.plan];
   const int N = p.N, iw = e >> 5, lane = e & 31;
   const TcRows tr = tc_rows(u.nce, u.nco, N);
@@ -594,11 +595,26 @@ __device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u
         xr[k] = par ? wi * (a.x - b.x) : wi * (a.x + b.x);
         xi[k] = par ? wi * (a.y - b.y) : wi * (a.y + b.y);
       }
-      const int G = (par ? tr.yo : tr.ye) / kTcGrpRows + i0 / kTcGrpRows + grp8;
+      const int G = (par ? tr.yo : tr.ye) / kTcGrpRows + i0 / kTcGrpRows + grp8 - gbase;
       put_group(vec, G, 2 * pr, xr);
       put_group(vec, G, 2 * pr + 1, xi);
     }
     io_bar();
+  }
+}
+
+// The transposed call's inputs ahead of the apply, one item per CTA
+// iteration: the same gather as the I/O warps', into the item's block of
+// plan 0's pre-gathered buffer, by many CTAs per SM.
+__global__ void __launch_bounds__(kIoThreads) tc_in_kernel(const __grid_constant__ TcLaunch L) {
+  __shared__ __align__(16) float T[kIoTile];
+  const TcPlan& p = L.plan[0];
+  const int nyg = tc_pre_groups(p.N);
+  for (int it = blockIdx.x; it < L.nitems; it += gridDim.x) {
+    const Item itm = item_of(L, it);
+    const Unit u = p.units[itm.am];
+    unsigned char* dst = p.pre + ((size_t)itm.grp * p.nunits + itm.am) * nyg * kTcGrpBytes;
+    gather_inverse(L, itm, u, dst, T, threadIdx.x, tc_rows(u.nce, u.nco, p.N).ye / kTcGrpRows);
   }
 }
 
@@ -663,6 +679,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       const TcPlan& p = L.plan[itm.plan];
       const Unit u = p.units[itm.am];
       const unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
+      // transposed inputs gathered ahead: the groups of Y_e, Y_o come from
+      // the item's block of the pre-gathered buffer
+      const int gye = tc_rows(u.nce, u.nco, p.N).ye / kTcGrpRows, nyg = tc_pre_groups(p.N);
+      const unsigned char* pre =
+          (!fwd && p.pre) ? p.pre + ((size_t)itm.grp * p.nunits + itm.am) * nyg * kTcGrpBytes : nullptr;
+      auto grp_src = [&](int g) -> const unsigned char* {
+        return (pre && g >= gye && g < gye + nyg) ? pre + (size_t)(g - gye) * kTcGrpBytes
+                                                  : vec + (size_t)g * kTcGrpBytes;
+      };
       const int nops = u.op_end - u.op_begin;
       TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
       int cur_phase = -1, tiles_here = 0;
@@ -699,12 +724,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
                 bulk_copy(sB, img + (size_t)t * (3 * kTcNT) * kg.kp_tot + (size_t)Np * (3 * kTcKC * c), bbytes,
                           &ctl->full[s]);
                 if (ja > j0)
-                  bulk_copy(sA, vec + (size_t)(kg.gs0 + j0) * kTcGrpBytes, (uint32_t)(ja - j0) * kTcGrpBytes,
-                            &ctl->full[s]);
+                  bulk_copy(sA, grp_src(kg.gs0 + j0), (uint32_t)(ja - j0) * kTcGrpBytes, &ctl->full[s]);
                 if (j1 > ja)
-                  bulk_copy(sA + (uint32_t)(ja - j0) * kTcGrpBytes,
-                            vec + (size_t)(kg.gs1 + ja - kg.ng0) * kTcGrpBytes, (uint32_t)(j1 - ja) * kTcGrpBytes,
-                            &ctl->full[s]);
+                  bulk_copy(sA + (uint32_t)(ja - j0) * kTcGrpBytes, grp_src(kg.gs1 + ja - kg.ng0),
+                            (uint32_t)(j1 - ja) * kTcGrpBytes, &ctl->full[s]);
               }
             }
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -926,8 +949,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
       if (fwd)
         gather_forward(L, itm, u, vec, iot, e);
-      else
-        gather_inverse(L, itm, u, vec, iot, e);
+      else if (!p.pre)
+        gather_inverse(L, itm, u, vec, iot, e, 0);
       // accumulation rows that no op stores first start at zero (the
       // epilogue adds into them; the output step reads every row)
       {
@@ -1073,6 +1096,11 @@ cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, 
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+  if (!fwd && p.pre) {
+    tc_in_kernel<<<std::max(1, std::min(L.nitems, 8 * sm_count())), kIoThreads, 0, st>>>(L);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(L, fwd ? 1 : 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
