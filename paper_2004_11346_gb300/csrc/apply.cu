@@ -343,6 +343,8 @@ struct sht_plan_s {
   unsigned char* d_wstc = nullptr;
   float* d_acc = nullptr;  // accumulated rows of every work item (tc_gmax field groups)
   unsigned char* d_pre = nullptr;  // transposed inputs gathered ahead (tc_gmax field groups)
+  int32_t* d_tcford = nullptr;     // the tensor-core kernel's op processing order, forward
+  int32_t* d_tctord = nullptr;     // and transposed
   int tc_gmax = 0;
   int tc_max_rows = 0;     // scratch rows of the largest order (tensor-core layout)
   int* d_err = nullptr;
@@ -422,6 +424,8 @@ void free_device(sht_plan_s* p) {
   cudaFree(p->d_wstc);
   cudaFree(p->d_acc);
   cudaFree(p->d_pre);
+  cudaFree(p->d_tcford);
+  cudaFree(p->d_tctord);
   cudaFree(p->d_err);
   p->phi64.release();
   p->phi32.release();
@@ -457,6 +461,8 @@ TcPlan tc_plan_of(const sht_plan_s* p) {
   t.w = p->d_w;
   t.acc = p->d_acc;
   t.pre = p->d_pre;
+  t.ford = p->d_tcford;
+  t.tord = p->d_tctord;
   t.gmax = p->tc_gmax;
   t.N = p->prog.N;
   t.nunits = 2 * p->prog.N;
@@ -636,11 +642,15 @@ sht_status attach_device(sht_plan_s* p) {
     std::vector<int32_t> tiles;
     tc_build_images(N, P.units, P.ops, P.factors.data(), img, tops, tiles, p->tc_max_rows);
     std::vector<int32_t> zr, zri;
-    tc_first_writers(N, P.units, tops, zr, zri);
+    std::vector<int32_t> ford, tord;
+    tc_proc_order(P.units, tops, ford, tord);
+    tc_first_writers(N, P.units, tops, ford, tord, zr, zri);
     e = upload(&p->d_img, img);
     if (e == cudaSuccess) e = upload(&p->d_tcops, tops);
     if (e == cudaSuccess) e = upload(&p->d_tczr, zr);
     if (e == cudaSuccess) e = upload(&p->d_tczri, zri);
+    if (e == cudaSuccess) e = upload(&p->d_tcford, ford);
+    if (e == cudaSuccess) e = upload(&p->d_tctord, tord);
     if (e == cudaSuccess) e = upload(&p->d_tctiles, tiles);
     p->nslots_tc = std::max(1, sms * tc_ctas_per_sm());
     ws32 = (size_t)p->nslots_tc * 2 * tc_slot_bytes(p->tc_max_rows);  // two vector spaces per CTA

@@ -203,8 +203,33 @@ void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op
   }
 }
 
-void tc_first_writers(int N, const std::vector<Unit>& units, std::vector<TcOp>& tops, std::vector<int32_t>& zr,
-                      std::vector<int32_t>& zri) {
+void tc_proc_order(const std::vector<Unit>& units, const std::vector<TcOp>& tops, std::vector<int32_t>& ford,
+                   std::vector<int32_t>& tord) {
+  ford.resize(tops.size());
+  tord.resize(tops.size());
+  for (const Unit& un : units) {
+    const int b = un.op_begin, e = un.op_end;
+    for (int d = 0; d < 2; ++d) {
+      const bool fwd = d == 0;
+      std::vector<int32_t>& o = fwd ? ford : tord;
+      for (int i = b; i < e; ++i) o[(size_t)i] = i;
+      auto key = [&](int32_t i) {
+        const TcOp& t = tops[(size_t)i];
+        const int32_t* off = fwd ? t.in_off : t.out_off;
+        const int32_t* len = fwd ? t.in_len : t.out_len;
+        return len[0] > 0 ? off[0] : off[1];
+      };
+      std::stable_sort(o.begin() + b, o.begin() + e, [&](int32_t x, int32_t y) {
+        const int px = tops[(size_t)x].phase, py = tops[(size_t)y].phase;
+        if (px != py) return fwd ? px < py : px > py;
+        return key(x) < key(y);
+      });
+    }
+  }
+}
+
+void tc_first_writers(int N, const std::vector<Unit>& units, std::vector<TcOp>& tops, const std::vector<int32_t>& ford,
+                      const std::vector<int32_t>& tord, std::vector<int32_t>& zr, std::vector<int32_t>& zri) {
   zr.clear();
   zri.assign(2 * units.size() + 1, 0);
   const int R = tc_acc_rows(N);
@@ -219,7 +244,7 @@ void tc_first_writers(int N, const std::vector<Unit>& units, std::vector<TcOp>& 
       const int acc0 = fwd ? tr.ye : 0;
       const int nops = un.op_end - un.op_begin;
       for (int q = 0; q < nops; ++q) {  // the kernel's processing order
-        TcOp& t = tops[(size_t)(fwd ? un.op_begin + q : un.op_end - 1 - q)];
+        TcOp& t = tops[(size_t)(fwd ? ford : tord)[(size_t)(un.op_begin + q)]];
         t.flags &= ~(fwd ? kTcFwdStore : kTcBwdStore);
         if (!(t.flags & (fwd ? OP_FWD_ACCUM : OP_BWD_ACCUM))) continue;
         const int32_t* oo = fwd ? t.out_off : t.in_off;
@@ -478,9 +503,11 @@ __device__ __forceinline__ Item item_of(const TcLaunch& L, int it) {
   return r;
 }
 
-// The k-th op of a unit in processing order: ascending phases forward,
-// descending phases for the transposed (inverse) apply.
-__device__ __forceinline__ int op_at(const Unit& u, int k, bool fwd) { return fwd ? u.op_begin + k : u.op_end - 1 - k; }
+// The k-th op of a unit in processing order (tc_proc_order): ascending
+// phases forward, descending phases for the transposed (inverse) apply.
+__device__ __forceinline__ int op_at(const TcPlan& p, const Unit& u, int k, bool fwd) {
+  return __ldg((fwd ? p.ford : p.tord) + u.op_begin + k);
+}
 
 // Scratch row of N position n of an accumulating output (plain segments).
 __device__ __forceinline__ int acc_pos_row(int n, const int32_t* off, const int32_t* len) {
@@ -689,11 +716,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
                                                   : vec + (size_t)g * kTcGrpBytes;
       };
       const int nops = u.op_end - u.op_begin;
-      TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
+      TcOp nxt = nops > 0 ? p.ops[op_at(p, u, 0, fwd)] : TcOp{};
       int cur_phase = -1, tiles_here = 0;
       for (int q = 0; q < nops && ok; ++q) {
         const TcOp op = nxt;
-        if (q + 1 < nops) nxt = p.ops[op_at(u, q + 1, fwd)];
+        if (q + 1 < nops) nxt = p.ops[op_at(p, u, q + 1, fwd)];
         if (op.phase != cur_phase) {
           // a phase reads rows that earlier phases of this item wrote: wait for
           // their tiles (the item's first phase reads only gathered rows)
@@ -753,10 +780,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
         const TcPlan& p = L.plan[itm.plan];
         const Unit u = p.units[itm.am];
         const int nops = u.op_end - u.op_begin;
-        TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
+        TcOp nxt = nops > 0 ? p.ops[op_at(p, u, 0, fwd)] : TcOp{};
         for (int q = 0; q < nops && ok; ++q) {
           const TcOp op = nxt;
-          if (q + 1 < nops) nxt = p.ops[op_at(u, q + 1, fwd)];
+          if (q + 1 < nops) nxt = p.ops[op_at(p, u, q + 1, fwd)];
           const TcDir d = tc_dir(op, fwd);
           for (int t = 0; t < d.nT && ok; ++t, ++tm) {
             const int b = (int)(tm & 1);
@@ -829,10 +856,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       const TcRows tr = tc_rows(u.nce, u.nco, p.N);
       const int acc0 = fwd ? tr.ye : 0;  // accumulated rows: Y forward, X transposed
       const int nops = u.op_end - u.op_begin;
-      TcOp nxt = nops > 0 ? p.ops[op_at(u, 0, fwd)] : TcOp{};
+      TcOp nxt = nops > 0 ? p.ops[op_at(p, u, 0, fwd)] : TcOp{};
       for (int q = 0; q < nops && ok; ++q) {
         const TcOp op = nxt;
-        if (q + 1 < nops) nxt = p.ops[op_at(u, q + 1, fwd)];
+        if (q + 1 < nops) nxt = p.ops[op_at(p, u, q + 1, fwd)];
         const TcDir d = tc_dir(op, fwd);
         const int32_t* oo = fwd ? op.out_off : op.in_off;
         const int32_t* ol = fwd ? op.out_len : op.in_len;

@@ -164,6 +164,10 @@ struct TcPlan {
   const TcOp* ops;          // the program's ops, same order, in scratch rows
   const int32_t* tiles;     // per unit: [forward, transposed] number of N tiles of all its ops
   const int32_t* order;
+  // The kernel's processing order of each unit's ops, per direction: op
+  // indices for positions op_begin .. op_end - 1 (tc_proc_order)
+  const int32_t* ford;
+  const int32_t* tord;
   const uint16_t* img;      // split-BF16 operand images of every op
   // Accumulation rows that no storing op writes first, as (first row, rows)
   // ranges: order u in direction d (0 forward, 1 transposed) owns ranges
@@ -227,7 +231,17 @@ void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op
 
 // The store marks of the ops (in tops) and the zero ranges (zr, zri as in
 // TcPlan) of every order, from the op records in scratch rows.
-void tc_first_writers(int N, const std::vector<Unit>& units, std::vector<TcOp>& tops, std::vector<int32_t>& zr,
+// The processing order of every unit's ops in each direction: forward,
+// ascending phases; transposed, descending phases; within a phase the ops
+// sorted by the first scratch row of the side they read (forward: the input
+// rows, transposed: the output rows), so that products reading the same rows
+// (the blocks of one column or row strip) run one after another and find them
+// in L2.  ford / tord hold global op indices at the units' op positions.
+void tc_proc_order(const std::vector<Unit>& units, const std::vector<TcOp>& tops, std::vector<int32_t>& ford,
+                   std::vector<int32_t>& tord);
+// First writers, in the processing order of ford / tord.
+void tc_first_writers(int N, const std::vector<Unit>& units, std::vector<TcOp>& tops, const std::vector<int32_t>& ford,
+                      const std::vector<int32_t>& tord, std::vector<int32_t>& zr,
                       std::vector<int32_t>& zri);
 
 // One apply: the persistent tensor-core kernel (gather, block products into

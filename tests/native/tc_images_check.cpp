@@ -76,8 +76,33 @@ int main(int argc, char** argv) {
   // ops in processing order; a storing op may touch no row written before,
   // and every row the output step reads is first written by a storing op or
   // lies in one zero range -- exactly one of the two
+  // processing orders: per unit and direction a permutation of its ops, the
+  // phases ascending (forward) or descending (transposed), and within a phase
+  // the first row of the side read non-decreasing
+  std::vector<int32_t> ford, tord;
+  tc_proc_order(units, tops, ford, tord);
+  if (ford.size() != tops.size() || tord.size() != tops.size()) return 20;
+  for (const Unit& un : units)
+    for (int d = 0; d < 2; ++d) {
+      const std::vector<int32_t>& o = d == 0 ? ford : tord;
+      std::vector<char> seen((size_t)(un.op_end - un.op_begin), 0);
+      for (int i = un.op_begin; i < un.op_end; ++i) {
+        const int32_t k = o[(size_t)i];
+        if (k < un.op_begin || k >= un.op_end || seen[(size_t)(k - un.op_begin)]) return 21;
+        seen[(size_t)(k - un.op_begin)] = 1;
+        if (i > un.op_begin) {
+          const TcOp &a = tops[(size_t)o[(size_t)i - 1]], &b = tops[(size_t)k];
+          if (d == 0 ? a.phase > b.phase : a.phase < b.phase) return 22;
+          const int32_t* ao = d == 0 ? a.in_off : a.out_off;
+          const int32_t* al = d == 0 ? a.in_len : a.out_len;
+          const int32_t* bo = d == 0 ? b.in_off : b.out_off;
+          const int32_t* bl = d == 0 ? b.in_len : b.out_len;
+          if (a.phase == b.phase && (al[0] > 0 ? ao[0] : ao[1]) > (bl[0] > 0 ? bo[0] : bo[1])) return 23;
+        }
+      }
+    }
   std::vector<int32_t> zr, zri;
-  tc_first_writers(N, units, tops, zr, zri);
+  tc_first_writers(N, units, tops, ford, tord, zr, zri);
   if (zri.size() != 2 * units.size() + 1 || zri[0] != 0) return 11;
   for (size_t u = 0; u < units.size(); ++u) {
     const Unit& un = units[u];
@@ -87,7 +112,7 @@ int main(int argc, char** argv) {
       const int acc0 = fwd ? tr.ye : 0;
       std::vector<int> state(tc_acc_rows(N), 0);  // 0 untouched, 1 stored first, 2 added first
       for (int q = 0; q < un.op_end - un.op_begin; ++q) {
-        const TcOp& t = tops[(size_t)(fwd ? un.op_begin + q : un.op_end - 1 - q)];
+        const TcOp& t = tops[(size_t)(fwd ? ford : tord)[(size_t)(un.op_begin + q)]];
         if (!(t.flags & (fwd ? OP_FWD_ACCUM : OP_BWD_ACCUM))) {
           if (t.flags & (fwd ? kTcFwdStore : kTcBwdStore)) return 12;
           continue;
