@@ -44,6 +44,10 @@ EXTRA_WORKLOADS = {
     # the same with two field groups per order, as the 64-field headline
     "mixed_N512_F64_tuned": dict(N=512, F=64, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed",
                                  plan=dict(n0=128, n_leaf=128)),
+    # single components (--only): the FP32 phi transform of 8 fields at the
+    # headline's N (1.07 GB per array), the on-the-fly dense FP64 ALT
+    "mixed_N1024_F8": dict(N=1024, F=8, seed=0, decay=0.0, real_m0=False, eps=1e-7, precision="mixed"),
+    "fp64_N512_F16": dict(N=512, F=16, seed=0, decay=0.0, real_m0=False, eps=1e-12, precision="fp64"),
 }
 # the ncu capture whose traffic a workload's roofline scales (same kernel, same plan shape, smaller case)
 TRAFFIC_REF = {"mixed_N1024_F64": "mixed_N512_F64_tuned"}
@@ -393,7 +397,9 @@ def run_ours(args):
     rt_err = float((back - beta).norm() / beta.norm())
 
     K = args.steps
-    kernels_per_call = 2 if w["precision"] == "mixed" else 1  # tensor-core kernel + output kernel
+    # mixed: forward = tensor-core kernel + output kernel, inverse = the
+    # pre-gather kernel + those two; other precisions one kernel per call
+    kernels_per_step = 5 if w["precision"] == "mixed" else 2
     # headline: K replays of the step captured in a CUDA graph, the library's
     # event instrumentation paused; value from the median replay
     plan.set_timing(False)
@@ -403,7 +409,7 @@ def run_ours(args):
     time.sleep(0.3)
     ms, ms_mean = time_graph(torch, plan, beta, g, back, K, max(3, args.warmup), stream)
     clk = clocks.stop()
-    launches = K * 2 * kernels_per_call  # forward + inverse per step
+    launches = K * kernels_per_step
     plan.set_timing(True)
     # separate pass: forward / inverse split and the dominant kernel alone
     # (library CUDA events around each kernel, on the launching stream)
@@ -414,6 +420,13 @@ def run_ours(args):
     kf = plan.kernel_time(reset=True)
     main_ms = kf["apply_ms"] / max(1, kf["launches"])
     out_ms = kf["output_ms"] / max(1, kf["launches"])
+    for _ in range(K):
+        plan.inverse(g, out=back)
+    ki = plan.kernel_time(reset=True)
+    inv_split = {"apply_ms": ki["apply_ms"] / max(1, ki["launches"]),
+                 "output_ms": ki["output_ms"] / max(1, ki["launches"]),
+                 "what": "inverse call: pre-gather + tensor-core kernel (apply), then the output kernel"
+                 if w["precision"] == "mixed" else "inverse call"}
     barrier()
     plan.sync()
     ms, ms_mean, fwd_ms, inv_ms = max_over_ranks([ms, ms_mean, fwd_ms, inv_ms])
@@ -436,7 +449,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "bf16x3 split, f32 accumulate"}[w["precision"]],
         "data": "synthetic", "config": config_of(w, world),
-        "forward_ms": fwd_ms, "inverse_ms": inv_ms,
+        "forward_ms": fwd_ms, "inverse_ms": inv_ms, "inverse_kernels": inv_split,
         "forward_fields_per_s": world * F / (fwd_ms * 1e-3), "inverse_fields_per_s": world * F / (inv_ms * 1e-3),
         "round_trip_rel_err": rt_err,
         "roofline": roof,
@@ -793,6 +806,52 @@ def run_uneven(args):
         print(json.dumps(line), flush=True)
 
 
+def run_only(args):
+    """One component on the workload's N and F, for profiling captures and
+    component timings (not the benchmark line): "phi", the phi-direction
+    synthesis then analysis of F random grids in the plan precision's
+    arithmetic; "direct", the forward then inverse ALT of the on-the-fly dense
+    FP64 transform.  Prints one JSON line."""
+    import torch
+    import paper_2004_11346_gb300 as sht
+    from paper_2004_11346_gb300 import _lib
+    w = workload(args.workload)
+    N, F = w["N"], w["F"]
+    prec = _lib.SHT_FP64 if args.only == "direct" or w["precision"] == "fp64" else _lib.SHT_MIXED
+    plan = sht.Plan(N, w["eps"], precision=prec, flags=_lib.SHT_FLAG_DIRECT, max_fields=F)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w["seed"])
+    if args.only == "phi":
+        a = torch.randn((F, 4 * N - 1, 2 * N, 2), dtype=torch.float64, device="cuda", generator=gen)
+        b = torch.empty((F, 2 * N, 4 * N - 1, 2), dtype=torch.float64, device="cuda")
+        back = torch.empty_like(a)
+
+        def step():
+            plan.phi_synthesis(a, out=b)
+            plan.phi_analysis(b, out=back)
+    else:
+        a = torch.from_numpy(rank_fields(N, F, w, 0)).cuda()
+        b = torch.empty((F, 4 * N - 1, 2 * N, 2), dtype=torch.float64, device="cuda")
+        back = torch.empty_like(a)
+
+        def step():
+            plan.forward(a, out=b)
+            plan.inverse(b, out=back)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    print(json.dumps({"component": args.only, "workload": args.workload, "N": N, "fields": F, "ms_per_step": ms,
+                      "fields_per_s": F / (ms * 1e-3), "round_trip_rel_err": float((back - a).norm() / a.norm())}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -805,8 +864,12 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 IDBF and dense comparators")
     ap.add_argument("--n0", type=int, default=None, help="override the workload's partition stop size n0")
     ap.add_argument("--n-leaf", type=int, default=None, help="override the workload's IDBF leaf size")
+    ap.add_argument("--only", choices=["phi", "direct"], default=None,
+                    help="time one component on the workload's N and fields instead of the benchmark step")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.only:
+        run_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload.startswith(UNEVEN_PREFIX):
         run_uneven(args)
