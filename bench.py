@@ -293,11 +293,14 @@ def time_graph(torch, plan, beta, g, back, K, W, stream):
     return float(np.median(per)), ev[0].elapsed_time(ev[K]) / K
 
 
-def run_e2e(torch, plan, beta_h, g, K, W, barrier, chunk=32):
+def run_e2e(torch, plan, beta_h, g, K, W, barrier, chunk=None):
     """ms per step of host -> device -> forward + inverse ALT -> host for the
-    whole batch, pipelined over chunks of `chunk` fields on three streams."""
+    whole batch, pipelined over chunks of `chunk` fields (default 32, one
+    field group of the tensor-core kernel) on three streams with two device
+    buffers per side, so that one chunk's copy in, the previous chunk's
+    transform and the one before's copy out can run at the same time."""
     F = beta_h.shape[0]
-    C = min(chunk, F)
+    C = min(chunk or 32, F)
     starts = list(range(0, F, C))
     beta_pin = torch.from_numpy(beta_h).pin_memory()
     out_pin = torch.empty(beta_pin.shape, dtype=torch.float64).pin_memory()
@@ -437,7 +440,8 @@ def run_ours(args):
     # on three streams (copy in, transform, copy out) so that the copies of one
     # chunk overlap the transforms of its neighbours; the transforms themselves
     # stay in order on one stream (calls on one plan must not overlap).
-    e2e_ms, io_bytes, e2e_chunks = run_e2e(torch, plan, beta_h, g, K, max(1, args.warmup), barrier)
+    e2e_ms, io_bytes, e2e_chunks = run_e2e(torch, plan, beta_h, g, K, max(1, args.warmup), barrier,
+                                           chunk=args.e2e_chunk)
     e2e_ms = max_over_ranks([e2e_ms])[0]
 
     flops, entries = program_flops(plan, F)
@@ -864,6 +868,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 IDBF and dense comparators")
     ap.add_argument("--n0", type=int, default=None, help="override the workload's partition stop size n0")
     ap.add_argument("--n-leaf", type=int, default=None, help="override the workload's IDBF leaf size")
+    ap.add_argument("--e2e-chunk", type=int, default=None,
+                    help="fields per host-copy chunk of the end-to-end loop (default 32)")
     ap.add_argument("--only", choices=["phi", "direct"], default=None,
                     help="time one component on the workload's N and fields instead of the benchmark step")
     args = ap.parse_args()
