@@ -600,6 +600,10 @@ def sht_timings(torch, w, plan, beta_in, g, K, stream, p64=None):
     g64 = gc.to(torch.complex64)
     fft64_ms = timed(lambda: (torch.fft.ifft(g64, dim=1), torch.fft.fft(g64, dim=1)))
     del g64
+    # like against like: the library calls' own contract (FP64 g in the order
+    # storage sequence -> FP64 theta-major f and back, half-sample shift
+    # included) done with torch operations around complex64 cuFFT
+    lib_ms, lib_err = torch_phi_same_contract(torch, N, g, f, timed)
     phi_bytes = 2 * 2 * g.numel() * 8  # each direction reads and writes F x (4N-1) x 2N complex FP64
     out = {"phi_round_trip_ms": phi_ms, "phi_round_trip_rel_err": phi_err,
            "phi_GBps": phi_bytes / (phi_ms * 1e-3) / 1e9,
@@ -607,7 +611,9 @@ def sht_timings(torch, w, plan, beta_in, g, K, stream, p64=None):
            "sht_round_trip_ms": sht_ms, "sht_fields_per_s": F / (sht_ms * 1e-3),
            "sht_round_trip_rel_err": sht_err,
            "phi_arith": "f64" if w["precision"] == "fp64" else "f32",
-           "cufft_c64_round_trip_ms": fft64_ms, "cufft_c128_round_trip_ms": fft128_ms}
+           "cufft_c64_round_trip_ms": fft64_ms, "cufft_c128_round_trip_ms": fft128_ms,
+           "torch_cufft_c64_same_contract_round_trip_ms": lib_ms,
+           "torch_cufft_c64_same_contract_vs_ours_rel_diff": lib_err}
     if p64 is not None and w["precision"] != "fp64":
         # the FP64 plan's own phi transform on the same batch, against complex128 cuFFT
         phi64_ms = timed(lambda: (p64.phi_synthesis(g, out=f), p64.phi_analysis(f, out=g2)))
@@ -615,6 +621,47 @@ def sht_timings(torch, w, plan, beta_in, g, K, stream, p64=None):
         out["phi_fp64_round_trip_ms"] = phi64_ms
         out["phi_fp64_round_trip_rel_err"] = float((g2 - g).norm() / g.norm())
     return out
+
+
+def torch_phi_same_contract(torch, N, g, f_ours, timed):
+    """The phi round trip with the library's layouts and half-sample shift,
+    written with torch operations around complex64 cuFFT (reorder the orders
+    to DFT positions, shift, transpose, inverse FFT, FP64 out; and back):
+    returns (ms per round trip, relative difference of its synthesis from
+    ours)."""
+    import math
+    M, K = 4 * N - 1, 2 * N
+    dev = g.device
+    ms = torch.arange(-(K - 1), K, device=dev)
+    slot = torch.where(ms == 0, torch.zeros_like(ms), torch.where(ms > 0, 2 * ms - 1, -2 * ms))
+    pos = torch.remainder(ms, M)
+    by_pos = torch.argsort(pos)                 # natural-order index of the order at DFT position j
+    slot_at_pos = slot[by_pos]
+    ang = math.pi * ms.to(torch.float64) / M
+    shift = torch.polar(torch.ones_like(ang), ang).to(torch.complex64)
+    shift_at_pos = shift[by_pos]
+    pos_at_slot = torch.empty_like(pos)
+    pos_at_slot[slot] = pos                     # DFT position of the order in storage slot s
+    cshift_at_slot = torch.empty_like(shift)
+    cshift_at_slot[slot] = shift.conj() / M
+    out = {}
+
+    def syn():
+        x = torch.view_as_complex(g).to(torch.complex64).index_select(1, slot_at_pos) * shift_at_pos[None, :, None]
+        y = torch.fft.ifft(x.transpose(1, 2).contiguous(), dim=2, norm="forward")
+        out["f"] = torch.view_as_real(y.to(torch.complex128))
+
+    def ana():
+        y = torch.fft.fft(torch.view_as_complex(out["f"]).to(torch.complex64), dim=2)
+        z = y.index_select(2, pos_at_slot) * cshift_at_slot[None, None, :]
+        out["g"] = torch.view_as_real(z.transpose(1, 2).contiguous().to(torch.complex128))
+
+    ms_rt = timed(lambda: (syn(), ana()))
+    syn()
+    err = float((out["f"] - f_ours).norm() / f_ours.norm())
+    out.clear()
+    torch.cuda.empty_cache()
+    return ms_rt, err
 
 
 def measured_peaks():
