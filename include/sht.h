@@ -94,6 +94,14 @@ typedef struct {
                                    transform, kept as a baseline)                */
 #define SHT_FLAG_TIMING 8       /* record CUDA events around every apply kernel
                                    launch (see sht_plan_kernel_time)             */
+#define SHT_FLAG_GPU_LEGENDRE 32 /* the plan builder takes each order's Legendre
+                                   matrices (Sec. 3.1.2) from the device
+                                   recurrence of sht_legendre instead of its
+                                   host recurrence; the rest of the
+                                   precomputation stays on the host.  Values
+                                   agree to rounding, so plans can differ from
+                                   host-built ones in the last bits.  Not with
+                                   SHT_FLAG_HOST_ONLY (SHT_ERR_ARG)            */
 #define SHT_FLAG_DIRECT 16      /* no partition and no factorisation, nothing
                                    stored: alt_forward / alt_inverse (and the
                                    full SHT) apply the dense ALT in FP64 with the
@@ -347,6 +355,17 @@ sht_status sht_plan_set_timing(sht_plan_t plan, int enable);
  * after it, sht_sync must return SHT_ERR_TIMEOUT.  SHT_MIXED plans only
  * (SHT_ERR_UNSUPPORTED otherwise).  Takes a second or more of GPU time. */
 sht_status sht_selftest_timeout(sht_plan_t plan, void* stream);
+
+/* Pbar_k^{|m|}(x_{N+i}) for one order on the device (Sec. 1, the normalised
+ * associated Legendre functions without Condon-Shortley phase; the recurrence
+ * of Sec. 3's matrices): out[t * N + i] = Pbar_{am+t}^{am}(x_{N+i}) for
+ * t < 2N - am, i < N, at the plan's N positive Gauss-Legendre nodes
+ * (ascending).  Three-term recurrence in FP64 from Pbar_am^am, carried with a
+ * separate binary exponent below the FP64 range; values below 2^-760 are
+ * written as 0.  out: caller-owned device array of (2N - am) N doubles.
+ * Asynchronous on the stream.  SHT_ERR_ARG for a bad am or NULL out;
+ * SHT_ERR_UNSUPPORTED for host-only plans. */
+sht_status sht_legendre(sht_plan_t plan, int am, double* out, void* stream);
 
 /* The order in which the apply's persistent CTAs take the orders |m| from
  * the work queue (the m-to-CTA schedule; the paper has no counterpart, one

@@ -89,6 +89,14 @@ class Plan:
         """The unit queue order of the apply (|m| of each unit in the order taken)."""
         return self.program(("order",))["order"].copy()
 
+    def legendre(self, am: int):
+        """Pbar_{am+t}^{am} at the N positive nodes from the device recurrence
+        (sht_legendre): a CUDA float64 tensor (2N - am, N)."""
+        import torch
+        out = torch.empty((2 * self.N - am, self.N), dtype=torch.float64, device="cuda")
+        _lib.sht_legendre(self.handle, am, out.data_ptr(), self._stream())
+        return out
+
     def set_order(self, order):
         """Set the unit queue order (sht_plan_set_order): any permutation of 0 .. 2N-1."""
         _lib.sht_plan_set_order(self.handle, order)

@@ -24,6 +24,7 @@ SHT_FLAG_HOST_ONLY = 2
 SHT_FLAG_DENSE = 4
 SHT_FLAG_TIMING = 8
 SHT_FLAG_DIRECT = 16
+SHT_FLAG_GPU_LEGENDRE = 32
 (SHT_EXPORT_UNITS, SHT_EXPORT_OPS, SHT_EXPORT_PHASES, SHT_EXPORT_FACTORS, SHT_EXPORT_ORDER, SHT_EXPORT_OPTS,
  SHT_EXPORT_UNIT_BLOCKS) = range(7)
 
@@ -122,7 +123,7 @@ EXPORTED = [
     "sht_inverse", "sht_plan_save", "sht_plan_load", "sht_plan_kernel_time", "sht_batch_create",
     "sht_batch_destroy", "alt_forward_batch", "alt_inverse_batch", "sht_forward_batch", "sht_inverse_batch",
     "sht_batch_sync", "sht_selftest_timeout", "sht_plan_op_image", "sht_order_stats", "sht_plan_set_timing",
-    "sht_selftest_convert", "sht_plan_set_order",
+    "sht_selftest_convert", "sht_plan_set_order", "sht_legendre",
 ]
 
 
@@ -160,6 +161,7 @@ def load(build: bool = True):
     lib.sht_selftest_timeout.argtypes = [vp, vp]
     lib.sht_selftest_convert.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
     lib.sht_plan_set_order.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i]
+    lib.sht_legendre.argtypes = [vp, i, vp, vp]
     lib.sht_plan_op_image.argtypes = [vp, ctypes.c_int64, i, vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.sht_order_stats.argtypes = [i, d, ctypes.POINTER(sht_opts), i, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(sht_order_info)]
@@ -324,6 +326,10 @@ def sht_batch_sync(batch: int, stream: int = 0):
 
 def sht_selftest_timeout(plan: int, stream: int = 0):
     check(load().sht_selftest_timeout(plan, stream), "sht_selftest_timeout")
+
+
+def sht_legendre(plan: int, am: int, out: int, stream: int = 0):
+    check(load().sht_legendre(plan, am, out, stream), "sht_legendre")
 
 
 def sht_plan_set_order(plan: int, order):

@@ -86,47 +86,71 @@ __device__ void pow_ext(double s, int a, double& mant, int& e) {
   }
 }
 
-// Steps 1 and 2 for order a: coefficients, then Pbar_{a+t}^a(x_{N+i}) into
-// P[t * N + i], t < K = 2N - a.
-__device__ void direct_legendre(const DirectArgs& g, int a, double* coef, double* P) {
-  const int N = g.N, K = 2 * N - a;
-  // coef[2t] = sqrt((4k^2 - 1) / (k^2 - a^2)), coef[2t + 1] =
-  // sqrt((2k + 1)(k - 1 - a)(k - 1 + a) / ((2k - 3)(k^2 - a^2))), k = a + t, t >= 1
-  for (int t = 1 + threadIdx.x; t < K; t += blockDim.x) {
+// The recurrence coefficients of order a for degrees a + t, t in [t0, K),
+// stepping by `stride` from t0: coef[2t] = sqrt((4k^2 - 1) / (k^2 - a^2)),
+// coef[2t + 1] = sqrt((2k + 1)(k - 1 - a)(k - 1 + a) / ((2k - 3)(k^2 - a^2))),
+// k = a + t, t >= 1 (0 for t = 1, where Pbar_{a-1}^a does not exist).
+__device__ __forceinline__ void legendre_coefs(int a, int K, int t0, int stride, double* coef) {
+  for (int t = t0; t < K; t += stride) {
+    if (t < 1) continue;
     const double k = (double)(a + t), aa = (double)a;
     const double d = k * k - aa * aa;
     coef[2 * t] = sqrt((4.0 * k * k - 1.0) / d);
     coef[2 * t + 1] = t >= 2 ? sqrt((2.0 * k + 1.0) * (k - 1.0 - aa) * (k - 1.0 + aa) / ((2.0 * k - 3.0) * d)) : 0.0;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const double x = g.x[i];
-    double cur;
-    int e;
-    pow_ext(g.s[i], a, cur, e);
-    cur *= g.cm[a];
-    double prev = 0.0;
-    bool plain = e >= kDPlainExp;
-    if (plain) cur = ldexp(cur, e);
-    for (int t = 0; t < K; ++t) {
-      P[(size_t)t * N + i] = plain ? cur : 0.0;
-      if (t + 1 < K) {
-        const double nx = coef[2 * (t + 1)] * x * cur - coef[2 * (t + 1) + 1] * prev;
-        prev = cur;
-        cur = nx;
-        if (!plain && fabs(cur) > 0x1p200) {
-          cur = ldexp(cur, -kDScaleBits);
-          prev = ldexp(prev, -kDScaleBits);
-          e += kDScaleBits;
-          if (e >= kDPlainExp) {
-            cur = ldexp(cur, e);
-            prev = ldexp(prev, e);
-            plain = true;
-          }
+}
+
+// Pbar_{a+t}^a(x) for t < K into P[t * ld], one node: from
+// Pbar_a^a = c_a s^a (s = sqrt(1 - x^2)), carried as mantissa and binary
+// exponent while below the FP64 range, plain doubles from exponent -960 on;
+// values still below that are stored as 0 (they are below 2^-760).
+__device__ __forceinline__ void legendre_node(double x, double s, double ca, int a, int K, const double* coef,
+                                              double* P, size_t ld) {
+  double cur;
+  int e;
+  pow_ext(s, a, cur, e);
+  cur *= ca;
+  double prev = 0.0;
+  bool plain = e >= kDPlainExp;
+  if (plain) cur = ldexp(cur, e);
+  for (int t = 0; t < K; ++t) {
+    P[(size_t)t * ld] = plain ? cur : 0.0;
+    if (t + 1 < K) {
+      const double nx = coef[2 * (t + 1)] * x * cur - coef[2 * (t + 1) + 1] * prev;
+      prev = cur;
+      cur = nx;
+      if (!plain && fabs(cur) > 0x1p200) {
+        cur = ldexp(cur, -kDScaleBits);
+        prev = ldexp(prev, -kDScaleBits);
+        e += kDScaleBits;
+        if (e >= kDPlainExp) {
+          cur = ldexp(cur, e);
+          prev = ldexp(prev, e);
+          plain = true;
         }
       }
     }
   }
+}
+
+// Steps 1 and 2 for order a: coefficients, then Pbar_{a+t}^a(x_{N+i}) into
+// P[t * N + i], t < K = 2N - a.
+__device__ void direct_legendre(const DirectArgs& g, int a, double* coef, double* P) {
+  const int N = g.N, K = 2 * N - a;
+  legendre_coefs(a, K, threadIdx.x, blockDim.x, coef);
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) legendre_node(g.x[i], g.s[i], g.cm[a], a, K, coef, P + i, N);
+}
+
+// The same table for one order as a grid of its own: coefficients first (one
+// kernel), then one thread per node.
+__global__ void legendre_coef_kernel(int a, int K, double* coef) {
+  legendre_coefs(a, K, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, coef);
+}
+__global__ void legendre_table_kernel(int N, int a, const double* __restrict__ x, const double* __restrict__ s,
+                                      const double* __restrict__ cm, const double* __restrict__ coef, double* P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) legendre_node(x[i], s[i], cm[a], a, 2 * N - a, coef, P + i, N);
 }
 
 // Step 3, forward: B[t * R + j] = the degree-(a + t) coefficient of right-hand
@@ -316,6 +340,41 @@ static std::vector<double> sectoral_constants(int n) {
     c[a] = (double)v;
   }
   return c;
+}
+
+cudaError_t LegendreDev::build(int N_, const double* x) {
+  N = N_;
+  std::vector<double> xp(N), sp(N);
+  for (int i = 0; i < N; ++i) {
+    const long double xi = x[N + i];
+    xp[i] = x[N + i];
+    sp[i] = (double)std::sqrt((1.0L - xi) * (1.0L + xi));
+  }
+  const std::vector<double> cm = sectoral_constants(2 * N);
+  cudaError_t e = cudaSuccess;
+  auto up = [&](double** d, const std::vector<double>& h) {
+    if (e == cudaSuccess) e = cudaMalloc(d, h.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(*d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+  };
+  up(&d_x, xp);
+  up(&d_s, sp);
+  up(&d_cm, cm);
+  return e;
+}
+
+void LegendreDev::release() {
+  cudaFree(d_x);
+  cudaFree(d_s);
+  cudaFree(d_cm);
+  d_x = d_s = d_cm = nullptr;
+}
+
+cudaError_t LegendreDev::table(int am, double* out, double* coef, cudaStream_t st) const {
+  if (am < 0 || am >= 2 * N || !d_x) return cudaErrorInvalidValue;
+  const int K = 2 * N - am;
+  legendre_coef_kernel<<<std::max(1, (K + 255) / 256), 256, 0, st>>>(am, K, coef);
+  legendre_table_kernel<<<std::max(1, (N + 127) / 128), 128, 0, st>>>(N, am, d_x, d_s, d_cm, coef, out);
+  return cudaGetLastError();
 }
 
 cudaError_t DirectPlan::build(int N_, int F_, const double* x, const double* w, int sms) {

@@ -8,6 +8,21 @@
 
 namespace sht {
 
+// Pbar_k^{|m|} at the N positive nodes on the device (the recurrence of the
+// on-the-fly transform, on its own): nodes, sqrt(1 - x^2) and the sectoral
+// constants of a plan.
+struct LegendreDev {
+  int N = 0;
+  double* d_x = nullptr;
+  double* d_s = nullptr;
+  double* d_cm = nullptr;
+  cudaError_t build(int N, const double* x);  // x: the 2N-point rule, ascending
+  void release();
+  // out[t * N + i] = Pbar_{am+t}^{am}(x_{N+i}), t < 2N - am, i < N; coef: 2(2N)
+  // doubles of scratch.  Asynchronous on st.
+  cudaError_t table(int am, double* out, double* coef, cudaStream_t st) const;
+};
+
 struct DirectPlan {
   int N = 0, F_max = 0, R_max = 0, grid = 0;
   size_t per_cta = 0;               // scratch doubles per CTA

@@ -13,16 +13,19 @@
 // The inverse runs the transposed products in reverse phase order after the
 // W-weighted fold (Sec. 3.1.1, B = A^T W) and scatters X back into beta.
 #include <cuda_runtime.h>
+#include <omp.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 
 #include "alt_direct.cuh"
+#include "dense.hpp"
 #include "apply_f32.cuh"
 #include "apply_tc.cuh"
 #include "f64_bits.cuh"
@@ -324,6 +327,8 @@ struct sht_plan_s {
   bool host_only = false;
   bool direct = false;  // SHT_FLAG_DIRECT: no ALT program; dense ALT by the recurrence on the fly
   DirectPlan dplan;
+  LegendreDev leg;               // Pbar on the device (sht_legendre)
+  double* d_legcoef = nullptr;   // its recurrence coefficients, 4N doubles
   // FP32 many-field path (precision SHT_FP32 / SHT_MIXED)
   float* d_fac32 = nullptr;
   float* d_ws32 = nullptr;
@@ -430,6 +435,16 @@ void free_device(sht_plan_s* p) {
   p->phi64.release();
   p->phi32.release();
   p->dplan.release();
+  p->leg.release();
+  cudaFree(p->d_legcoef);
+  p->d_legcoef = nullptr;
+}
+
+// The device's Legendre table for this plan (kept when the builder made it).
+cudaError_t attach_legendre(sht_plan_s* p) {
+  cudaError_t e = p->leg.d_x ? cudaSuccess : p->leg.build(p->prog.N, p->prog.x.data());
+  if (e == cudaSuccess && !p->d_legcoef) e = cudaMalloc(&p->d_legcoef, 4 * (size_t)p->prog.N * sizeof(double));
+  return e;
 }
 
 DevPlan dev_plan(const sht_plan_s* p) {
@@ -681,6 +696,7 @@ sht_status attach_device(sht_plan_s* p) {
   if (e == cudaSuccess) {
     const bool ok = o.precision == SHT_FP64 ? p->phi64.build(N) : p->phi32.build(N);
     if (!ok) e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = attach_legendre(p);
     // co-resident clusters of the transform's launch shape; 0: one row does
     // not fit the shared memory of a cluster
     p->phi_grid = o.precision == SHT_FP64 ? p->phi64.max_clusters : p->phi32.max_clusters;
@@ -736,6 +752,7 @@ sht_status attach_direct(sht_plan_s* p) {
   const bool ok = fp64 ? p->phi64.build(N) : p->phi32.build(N);
   cudaError_t e = ok ? cudaSuccess : cudaErrorMemoryAllocation;
   if (e == cudaSuccess) e = p->dplan.build(N, o.max_fields, p->prog.x.data(), p->prog.w.data(), std::max(1, sms));
+  if (e == cudaSuccess) e = attach_legendre(p);
   if (e == cudaSuccess) {
     const size_t gws = (size_t)o.max_fields * (4 * (size_t)N - 1) * 2 * N * 2 * sizeof(double);
     e = plan_malloc(reinterpret_cast<void**>(&p->d_gws), gws);
@@ -756,6 +773,57 @@ sht_status attach_direct(sht_plan_s* p) {
   return SHT_OK;
 }
 
+// The plan builder's Legendre matrices from the device (SHT_FLAG_GPU_LEGENDRE):
+// each host thread has its own stream, device table and pinned host copy;
+// the table of one order is computed, copied back and split by parity.
+class DeviceLegendreSource final : public LegendreSource {
+ public:
+  DeviceLegendreSource(const LegendreDev& leg, int N) : leg_(leg), N_(N), slots_((size_t)omp_get_max_threads()) {}
+  ~DeviceLegendreSource() override {
+    for (Slot& s : slots_) {
+      if (s.st) cudaStreamDestroy(s.st);
+      cudaFree(s.d_out);
+      cudaFree(s.d_coef);
+      cudaFreeHost(s.h_out);
+    }
+  }
+  bool parity_matrices(int N, int am, const double* /*xp*/, Mat& E, Mat& O) override {
+    const int tid = omp_get_thread_num();
+    if (N != N_ || tid < 0 || tid >= (int)slots_.size()) return false;
+    Slot& s = slots_[(size_t)tid];
+    const size_t full = 2 * (size_t)N * N;
+    if (!s.st) {
+      if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaMalloc(&s.d_out, full * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&s.d_coef, 4 * (size_t)N * sizeof(double)) != cudaSuccess ||
+          cudaMallocHost(&s.h_out, full * sizeof(double)) != cudaSuccess)
+        return false;
+    }
+    const int K = 2 * N - am;
+    if (leg_.table(am, s.d_out, s.d_coef, s.st) != cudaSuccess) return false;
+    if (cudaMemcpyAsync(s.h_out, s.d_out, (size_t)K * N * sizeof(double), cudaMemcpyDeviceToHost, s.st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s.st) != cudaSuccess)
+      return false;
+    E = Mat(N, (K + 1) / 2);
+    O = Mat(N, K / 2);
+    for (int t = 0; t < K; ++t)
+      std::memcpy((t & 1) ? O.col(t >> 1) : E.col(t >> 1), s.h_out + (size_t)t * N, sizeof(double) * (size_t)N);
+    return true;
+  }
+
+ private:
+  struct Slot {
+    cudaStream_t st = nullptr;
+    double* d_out = nullptr;
+    double* d_coef = nullptr;
+    double* h_out = nullptr;
+  };
+  const LegendreDev& leg_;
+  int N_;
+  std::vector<Slot> slots_;
+};
+
 }  // namespace
 
 sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* out) {
@@ -766,6 +834,7 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
   const bool host_only = (o.flags & SHT_FLAG_HOST_ONLY) != 0;
   const bool direct = (o.flags & SHT_FLAG_DIRECT) != 0;
   if (host_only && direct) return SHT_ERR_ARG;  // nothing to build
+  if (host_only && (o.flags & SHT_FLAG_GPU_LEGENDRE)) return SHT_ERR_ARG;  // the builder would need a device
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)) return SHT_ERR_CUDA;
   sht_plan_s* p = new (std::nothrow) sht_plan_s();
@@ -793,11 +862,25 @@ sht_status sht_plan_create(int N, double eps, const sht_opts* opts, sht_plan_t* 
   std::string err;
   sht_status s;
   try {
-    s = build_program(N, o, p->prog, err);
+    if (o.flags & SHT_FLAG_GPU_LEGENDRE) {
+      // the builder's Legendre matrices from the device; the table stays with the plan
+      std::vector<double> x, w;
+      gauss_legendre(2 * N, x, w);
+      if (p->leg.build(N, x.data()) != cudaSuccess) {
+        p->leg.release();
+        delete p;
+        return SHT_ERR_CUDA;
+      }
+      DeviceLegendreSource src(p->leg, N);
+      s = build_program(N, o, p->prog, err, &src);
+    } else {
+      s = build_program(N, o, p->prog, err);
+    }
   } catch (const std::bad_alloc&) {
     s = SHT_ERR_OOM;
   }
   if (s != SHT_OK) {
+    p->leg.release();
     delete p;
     return s;
   }
@@ -1430,6 +1513,13 @@ sht_status sht_selftest_timeout(sht_plan_t p, void* stream) {
                          static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? SHT_OK
              : SHT_ERR_CUDA;
+}
+
+sht_status sht_legendre(sht_plan_t p, int am, double* out, void* stream) {
+  if (!p || !out || am < 0 || am >= 2 * p->prog.N) return SHT_ERR_ARG;
+  if (p->host_only || !p->leg.d_x || !p->d_legcoef) return SHT_ERR_UNSUPPORTED;
+  return p->leg.table(am, out, p->d_legcoef, static_cast<cudaStream_t>(stream)) == cudaSuccess ? SHT_OK
+                                                                                                 : SHT_ERR_CUDA;
 }
 
 sht_status sht_plan_set_order(sht_plan_t p, const int32_t* order, int n) {

@@ -723,10 +723,17 @@ static void build_parity(UnitBuild& ub, const ParityMatrix& P, const sht_opts& o
 }
 
 static void build_unit(int N, int am, const sht_opts& o, const double* xp, UnitBuild& ub, Unit& u,
-                       double* t_mat = nullptr) {
+                       double* t_mat = nullptr, LegendreSource* src = nullptr) {
   Mat E, O;
   const auto t0 = std::chrono::steady_clock::now();
-  legendre_parity_matrices(N, am, xp, E, O);
+  if (src) {
+    if (!src->parity_matrices(N, am, xp, E, O)) {
+      ub.err = "device Legendre evaluation failed";
+      return;
+    }
+  } else {
+    legendre_parity_matrices(N, am, xp, E, O);
+  }
   if (t_mat) *t_mat = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   const int nce = E.c, nco = O.c;
   u = Unit{};
@@ -759,7 +766,7 @@ static void build_unit(int N, int am, const sht_opts& o, const double* xp, UnitB
   u.cost = (float)ub.cost;
 }
 
-sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::string& err) {
+sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::string& err, LegendreSource* src) {
   auto t0 = std::chrono::steady_clock::now();
   P = HostProgram{};
   P.N = N;
@@ -775,7 +782,12 @@ sht_status build_program(int N, const sht_opts& opts, HostProgram& P, std::strin
 #endif
   // heavy orders (small |m|) first
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int am = 0; am < K; ++am) build_unit(N, am, opts, xp, ub[am], units[am]);
+  for (int am = 0; am < K; ++am) build_unit(N, am, opts, xp, ub[am], units[am], nullptr, src);
+  for (int am = 0; am < K; ++am)
+    if (ub[am].err == "device Legendre evaluation failed") {
+      err = ub[am].err + " at order " + std::to_string(am);
+      return SHT_ERR_CUDA;
+    }
   const auto t_units = std::chrono::steady_clock::now();
 
   // concatenate into the global program: offsets first, then every unit's

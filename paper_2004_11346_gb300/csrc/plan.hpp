@@ -24,8 +24,23 @@ struct HostProgram {
   sht_plan_info info{};
 };
 
-// Build the apply program (Sec. 3.2-3.3).  Returns SHT_OK or an error code.
-sht_status build_program(int N, const sht_opts& opts, HostProgram& out, std::string& err);
+struct Mat;
+
+// A source of the Legendre parity matrices of one order (Sec. 3.1.2) other
+// than the builder's own host recurrence (e.g. the device).  Called from
+// several host threads at once.  E(i, j) = Pbar_{am+2j}^{am}(xp_i) and
+// O(i, j) = Pbar_{am+1+2j}^{am}(xp_i) at the N positive nodes xp (ascending),
+// sized N x ceil((2N-am)/2) and N x floor((2N-am)/2); false on failure.
+struct LegendreSource {
+  virtual ~LegendreSource() = default;
+  virtual bool parity_matrices(int N, int am, const double* xp, Mat& E, Mat& O) = 0;
+};
+
+// Build the apply program (Sec. 3.2-3.3), the Legendre matrices from `src`
+// when given.  Returns SHT_OK or an error code (SHT_ERR_CUDA when the source
+// fails).
+sht_status build_program(int N, const sht_opts& opts, HostProgram& out, std::string& err,
+                         LegendreSource* src = nullptr);
 
 // One order built on its own, as in the per-order experiments of Sec. 5: the
 // unit's ops (op_begin = 0) with its block statistics, and the time spent on

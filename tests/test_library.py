@@ -55,6 +55,10 @@ def test_argument_errors_need_no_device():
     assert lib.alt_forward(None, None, None, 1, None) == 1
     o = sht.opts(16, 1e-12, n_leaf=0)
     assert lib.sht_plan_create(16, 1e-12, ctypes.byref(o), ctypes.byref(h)) == 1
+    # host-only plans cannot take the device's Legendre matrices nor be direct
+    for fl in (_lib.SHT_FLAG_GPU_LEGENDRE, _lib.SHT_FLAG_DIRECT):
+        o = sht.opts(16, 1e-12, flags=HOST | fl)
+        assert lib.sht_plan_create(16, 1e-12, ctypes.byref(o), ctypes.byref(h)) == 1
 
 
 def test_host_only_plan_refuses_device_calls():
