@@ -884,6 +884,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
 #pragma unroll
               for (int k = 0; k < 32; ++k) hv[k] = 0u;
             }
+            if (c0 + 32 >= Nt) {
+              // the tile's last columns are in registers: the accumulator pair
+              // is free for the MMAs of tile te + 2 while these are stored
+              asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&ctl->acce[b]);
+            }
             const int n0 = kTcNT * t + c0;  // N position of hv[0]
             if (d.accum) {
               // 4 x 4 transposes within each quad of lanes (right-hand sides
@@ -933,9 +940,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
                 }
             }
           }
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&ctl->acce[b]);
           // rows written above are read next by bulk copies (async proxy); the
           // accumulated rows only by the output kernel
           if (!d.accum) asm volatile("fence.proxy.async.global;" ::: "memory");
