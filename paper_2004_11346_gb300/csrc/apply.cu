@@ -1372,7 +1372,6 @@ sht_status launch_batch(sht_batch_s* b, bool fwd, const double* const* in, doubl
       return s;
     }
     L.plan[q] = tc_plan_of(p);
-    L.plan[q].pre = nullptr;  // a batch's I/O warps gather the transposed inputs themselves
     L.in[q] = in[q];
     L.out[q] = out[q];
     L.F[q] = b->F[q];

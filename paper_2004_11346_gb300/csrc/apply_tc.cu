@@ -1166,6 +1166,23 @@ cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t 
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+  if (!fwd) {
+    // each plan's transposed inputs gathered ahead, one launch per plan
+    for (int q = 0; q < L.nplans; ++q) {
+      if (L.F[q] <= 0 || !L.plan[q].pre) continue;
+      TcLaunch Lq;
+      std::memset(&Lq, 0, sizeof(Lq));
+      Lq.plan[0] = L.plan[q];
+      Lq.in[0] = L.in[q];
+      Lq.out[0] = L.out[q];
+      Lq.F[0] = L.F[q];
+      Lq.nplans = 1;
+      Lq.nitems = L.plan[q].nunits * ((L.F[q] + kTcFields - 1) / kTcFields);
+      tc_in_kernel<<<std::max(1, std::min(Lq.nitems, 8 * sm_count())), kIoThreads, 0, st>>>(Lq);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
   alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(L, fwd ? 1 : 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
