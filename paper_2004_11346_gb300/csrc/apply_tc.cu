@@ -20,11 +20,15 @@
 // products into two alternating TMEM accumulator pairs; four epilogue warps drain
 // them, each thread one right-hand side, and either split the results into
 // BF16 pieces for the next level (eight rows per 16-byte store) or add them
-// in FP32 into the item's accumulation rows; eight I/O warps gather the next
-// item's inputs.  Ops of one phase read only rows written by earlier phases:
-// the producer starts a phase after the epilogue has counted every earlier
-// tile.  A streaming output kernel then writes g (the parity fold of Sec.
-// 3.1.2) or beta (the scatter) from the accumulation rows.
+// in FP32 into the item's accumulation rows; eight I/O warps take the items,
+// zero their accumulation rows and, forward, gather the next item's inputs
+// (beta into X rows).  The transposed call's inputs (the W-weighted parity
+// fold of g into Y rows) are gathered ahead of it by a streaming kernel,
+// tc_in_kernel, that the producer's bulk copies then read.  Ops of one phase
+// read only rows written by earlier phases: the producer starts a phase after
+// the epilogue has counted every earlier tile.  A streaming output kernel then
+// writes g (the parity fold of Sec. 3.1.2) or beta (the scatter) from the
+// accumulation rows.
 // Per 16-wide K step six MMAs accumulate a_p b_q for p + q <= 2, which keeps
 // every product to about 2^-24 relative error (FP32 quality); a0 b0 and the
 // five smaller cross products go to two separate accumulators that the

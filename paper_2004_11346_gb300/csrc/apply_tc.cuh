@@ -183,7 +183,7 @@ struct TcPlan {
   // Transposed inputs gathered ahead by tc_in_kernel: the W-weighted parity
   // fold of g as the Y_e, Y_o row groups of every item, item (g, |m|) at
   // (g * nunits + |m|) * tc_pre_groups(N) groups; null: the kernel's I/O warps
-  // gather them (batches)
+  // gather them
   unsigned char* pre;
   int gmax;                 // field groups the accumulation buffer holds
   int N;
