@@ -329,9 +329,9 @@ sht_status alt_forward_m_noalloc(sht_plan_t plan, int m, const double* beta_m, d
  * alt_* call then records CUDA events on its stream around each kernel it
  * launches; this call waits for them and returns, summed over the launches
  * since the last reset (at most the latest 256):
- *  - apply_ms: the block-product kernels (for SHT_MIXED the tensor-core
- *    kernel with its gather, and for the inverse the pre-gather kernel
- *    before it; the whole apply for SHT_FP64 / SHT_FP32 and direct plans),
+ *  - apply_ms: the block-product kernels (for SHT_MIXED the pre-gather
+ *    kernel of the inputs and the tensor-core kernel after it; the whole
+ *    apply for SHT_FP64 / SHT_FP32 and direct plans),
  *  - output_ms: the tensor-core path's output kernel (parity fold or
  *    scatter; 0 for the other precisions),
  *  - launches: the number of launches summed.

@@ -20,11 +20,12 @@
 // products into two alternating TMEM accumulator pairs; four epilogue warps drain
 // them, each thread one right-hand side, and either split the results into
 // BF16 pieces for the next level (eight rows per 16-byte store) or add them
-// in FP32 into the item's accumulation rows; eight I/O warps take the items,
-// zero their accumulation rows and, forward, gather the next item's inputs
-// (beta into X rows).  The transposed call's inputs (the W-weighted parity
-// fold of g into Y rows) are gathered ahead of it by a streaming kernel,
-// tc_in_kernel, that the producer's bulk copies then read.  Ops of one phase
+// in FP32 into the item's accumulation rows; eight I/O warps take the items
+// and zero their accumulation rows.  The inputs (forward: beta into X rows;
+// transposed: the W-weighted parity fold of g into Y rows) are gathered ahead
+// of the launch by a streaming kernel, tc_in_kernel, whose per-item row groups
+// the producer's bulk copies read (without that buffer the I/O warps gather
+// them into the CTA's scratch).  Ops of one phase
 // read only rows written by earlier phases: the producer starts a phase after
 // the epilogue has counted every earlier tile.  A streaming output kernel then
 // writes g (the parity fold of Sec. 3.1.2) or beta (the scatter) from the
@@ -634,18 +635,22 @@ __device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u
   }
 }
 
-// The transposed call's inputs ahead of the apply, one item per CTA
-// iteration: the same gather as the I/O warps', into the item's block of
-// plan 0's pre-gathered buffer, by many CTAs per SM.
-__global__ void __launch_bounds__(kIoThreads) tc_in_kernel(const __grid_constant__ TcLaunch L) {
+// The call's inputs ahead of the apply, one item per CTA iteration: the same
+// gathers as the I/O warps', into the item's block of plan 0's pre-gathered
+// buffer (forward: X_e, X_o from group 0; transposed: Y_e, Y_o), by many CTAs
+// per SM.
+__global__ void __launch_bounds__(kIoThreads) tc_in_kernel(const __grid_constant__ TcLaunch L, int fwd) {
   __shared__ __align__(16) float T[kIoTile];
   const TcPlan& p = L.plan[0];
-  const int nyg = tc_pre_groups(p.N);
+  const int npg = tc_pre_groups(p.N);
   for (int it = blockIdx.x; it < L.nitems; it += gridDim.x) {
     const Item itm = item_of(L, it);
     const Unit u = p.units[itm.am];
-    unsigned char* dst = p.pre + ((size_t)itm.grp * p.nunits + itm.am) * nyg * kTcGrpBytes;
-    gather_inverse(L, itm, u, dst, T, threadIdx.x, tc_rows(u.nce, u.nco, p.N).ye / kTcGrpRows);
+    unsigned char* dst = p.pre + ((size_t)itm.grp * p.nunits + itm.am) * npg * kTcGrpBytes;
+    if (fwd)
+      gather_forward(L, itm, u, dst, T, threadIdx.x);
+    else
+      gather_inverse(L, itm, u, dst, T, threadIdx.x, tc_rows(u.nce, u.nco, p.N).ye / kTcGrpRows);
   }
 }
 
@@ -712,11 +717,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       const unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
       // transposed inputs gathered ahead: the groups of Y_e, Y_o come from
       // the item's block of the pre-gathered buffer
-      const int gye = tc_rows(u.nce, u.nco, p.N).ye / kTcGrpRows, nyg = tc_pre_groups(p.N);
+      // inputs gathered ahead: forward, the X_e, X_o groups (from group 0);
+      // transposed, the Y_e, Y_o groups (from group ye / 8), each from the
+      // item's block of the pre-gathered buffer
+      const TcRows trp = tc_rows(u.nce, u.nco, p.N);
+      const int pg0 = fwd ? 0 : trp.ye / kTcGrpRows;
+      const int png = fwd ? (trp.xo + tc_r8(u.nco)) / kTcGrpRows : tc_pre_groups(p.N);
       const unsigned char* pre =
-          (!fwd && p.pre) ? p.pre + ((size_t)itm.grp * p.nunits + itm.am) * nyg * kTcGrpBytes : nullptr;
+          p.pre ? p.pre + ((size_t)itm.grp * p.nunits + itm.am) * tc_pre_groups(p.N) * kTcGrpBytes : nullptr;
       auto grp_src = [&](int g) -> const unsigned char* {
-        return (pre && g >= gye && g < gye + nyg) ? pre + (size_t)(g - gye) * kTcGrpBytes
+        return (pre && g >= pg0 && g < pg0 + png) ? pre + (size_t)(g - pg0) * kTcGrpBytes
                                                   : vec + (size_t)g * kTcGrpBytes;
       };
       const int nops = u.op_end - u.op_begin;
@@ -982,10 +992,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       const TcPlan& p = L.plan[itm.plan];
       const Unit u = p.units[itm.am];
       unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
-      if (fwd)
-        gather_forward(L, itm, u, vec, iot, e);
-      else if (!p.pre)
-        gather_inverse(L, itm, u, vec, iot, e, 0);
+      if (!p.pre) {
+        if (fwd)
+          gather_forward(L, itm, u, vec, iot, e);
+        else
+          gather_inverse(L, itm, u, vec, iot, e, 0);
+      }
       // accumulation rows that no op stores first start at zero (the
       // epilogue adds into them; the output step reads every row)
       {
@@ -1131,8 +1143,8 @@ cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, 
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-  if (!fwd && p.pre) {
-    tc_in_kernel<<<std::max(1, std::min(L.nitems, 8 * sm_count())), kIoThreads, 0, st>>>(L);
+  if (p.pre) {
+    tc_in_kernel<<<std::max(1, std::min(L.nitems, 8 * sm_count())), kIoThreads, 0, st>>>(L, fwd ? 1 : 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1170,8 +1182,8 @@ cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t 
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-  if (!fwd) {
-    // each plan's transposed inputs gathered ahead, one launch per plan
+  {
+    // each plan's inputs gathered ahead, one launch per plan
     for (int q = 0; q < L.nplans; ++q) {
       if (L.F[q] <= 0 || !L.plan[q].pre) continue;
       TcLaunch Lq;
@@ -1182,7 +1194,7 @@ cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t 
       Lq.F[0] = L.F[q];
       Lq.nplans = 1;
       Lq.nitems = L.plan[q].nunits * ((L.F[q] + kTcFields - 1) / kTcFields);
-      tc_in_kernel<<<std::max(1, std::min(Lq.nitems, 8 * sm_count())), kIoThreads, 0, st>>>(Lq);
+      tc_in_kernel<<<std::max(1, std::min(Lq.nitems, 8 * sm_count())), kIoThreads, 0, st>>>(Lq, fwd ? 1 : 0);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }

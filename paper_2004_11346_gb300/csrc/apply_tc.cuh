@@ -72,8 +72,9 @@ __host__ __device__ inline size_t tc_slot_bytes(int max_rows) {
 // at rows 0..N-1 and Y_o at r8(N)..; transposed, X_e at 0.. and X_o at
 // r8(nce)..
 __host__ __device__ inline int tc_acc_rows(int N) { return 2 * N + 8; }
-// Row groups of one item's transposed inputs Y_e, Y_o (rows ye .. yo + N,
-// yo = ye + r8(N)) as tc_in_kernel writes them.
+// Row groups of one item's pre-gathered inputs: at most 2 r8(N) rows, both
+// for the forward's X_e, X_o (nce, nco <= N) and the transposed Y_e, Y_o
+// (rows ye .. yo + N, yo = ye + r8(N)).
 __host__ __device__ inline int tc_pre_groups(int N) { return 2 * tc_r8(N) / kTcGrpRows; }
 
 // One side of a block product, widened to whole row groups: its rows are the
@@ -180,9 +181,10 @@ struct TcPlan {
   // rows.  The kernel zeroes an item's rows when it gathers the item; the
   // output kernel reads them.
   float* acc;
-  // Transposed inputs gathered ahead by tc_in_kernel: the W-weighted parity
-  // fold of g as the Y_e, Y_o row groups of every item, item (g, |m|) at
-  // (g * nunits + |m|) * tc_pre_groups(N) groups; null: the kernel's I/O warps
+  // Inputs gathered ahead by tc_in_kernel, the row groups of every item at
+  // (g * nunits + |m|) * tc_pre_groups(N) groups: forward, X_e and X_o as
+  // they sit from scratch group 0; transposed, the W-weighted parity fold of g
+  // as Y_e, Y_o from scratch group ye / 8.  Null: the kernel's I/O warps
   // gather them
   unsigned char* pre;
   int gmax;                 // field groups the accumulation buffer holds
