@@ -289,16 +289,20 @@ namespace {
 constexpr int kStages = 4;
 constexpr int kProdWarp = 0;                  // one thread stages operands
 constexpr int kMmaWarp = 1;                   // one thread issues the MMAs; the warp owns TMEM
-constexpr int kEpiWarp0 = 4;                  // warps 4-7: TMEM lane quadrants 0-3
-constexpr int kEpiWarps = 4;
-constexpr int kIoWarp0 = 8;                   // warps 8-15 gather inputs and write outputs
-constexpr int kIoWarps = kTcThreads / 32 - kIoWarp0;
-constexpr int kIoThreads = 32 * kIoWarps;
+constexpr int kEpiWarp0 = 4;                  // warps 4-11: two teams of four, TMEM lane quadrant warp % 4
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kIoWarp0 = 12;                  // warps 12-15 take the items and zero their rows
+constexpr int kIoThreads = kTcThreads - 32 * kIoWarp0;
+// The input gathers (tc_in_kernel's CTAs): 8 warps
+constexpr int kGatherWarps = 8;
+constexpr int kGatherThreads = 32 * kGatherWarps;
 constexpr int kPairs = 2 * kTcFields;         // (field, sign) pairs of an item: right-hand sides 2 pr, 2 pr + 1
-static_assert(kPairs % kIoWarps == 0, "I/O warps split the pairs evenly");
-static_assert(kIoThreads == 4 * kPairs, "four I/O threads per (field, sign) pair write the row groups");
+static_assert(kPairs % kGatherWarps == 0, "the gather's warps split the pairs evenly");
+static_assert(kGatherThreads == 4 * kPairs, "four gather threads per (field, sign) pair write the row groups");
+static_assert(kEpiWarp0 % 4 == 0 && kEpiWarps == 8, "each epilogue team covers the four TMEM lane quadrants");
 constexpr int kIoStride = 132;           // floats per I/O tile row (16-byte aligned rows)
-constexpr int kIoTile = 32 * kIoStride;  // the I/O warps' 32-row tile
+constexpr int kIoTile = 32 * kIoStride;  // the gather's 32-row tile
 constexpr int kStageA = (kTcKC / kTcGrpRows) * kTcGrpBytes;  // 4 row groups: 24 KB
 constexpr int kStageB = 3 * kTcNT * kTcKC * 2;               // 24 KB (largest N tile)
 constexpr int kStageBytes = kStageA + kStageB;
@@ -317,7 +321,7 @@ struct Ctl {
   int done_tiles;  // tiles whose epilogue is complete (all items so far)
   int ring[4];     // item index of this CTA's item iseq at ring[iseq % 4]; -1 = no more
 };
-constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + kIoTile * sizeof(float) + sizeof(Ctl) + 1024;
+constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + sizeof(Ctl) + 1024;
 static_assert(kSmemTotal <= 232448, "fits the 227 KB of shared memory one CTA may use");
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -414,16 +418,17 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
       "l"(src), "r"(bytes), "r"(s32(bar))
       : "memory");
 }
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 __device__ __forceinline__ void io_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kIoThreads) : "memory"); }
+__device__ __forceinline__ void gather_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kGatherThreads) : "memory"); }
 // The named barriers with an AND over the group: every warp of the group takes
 // the same decision after a bounded wait, so none is left at a barrier alone.
 __device__ __forceinline__ bool epi_and(bool v) {
   uint32_t r;
   asm volatile(
-      "{\n .reg .pred q, r;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred r, 1, 128, q;\n selp.u32 %0, 1, 0, r;\n}"
+      "{\n .reg .pred q, r;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred r, 1, %2, q;\n selp.u32 %0, 1, 0, r;\n}"
       : "=r"(r)
-      : "r"((uint32_t)v)
+      : "r"((uint32_t)v), "n"(kEpiThreads)
       : "memory");
   return r != 0;
 }
@@ -524,7 +529,7 @@ __device__ __forceinline__ int acc_pos_row(int n, const int32_t* off, const int3
 // that every warp access is a run of 32 consecutive complex values (512 bytes)
 // of one (field, sign) pair: lanes walk degrees or nodes when loading from or
 // storing to beta and g, and walk right-hand sides when writing row groups.
-// Thread e (0 .. kIoThreads - 1) is lane e % 32 of I/O warp e / 32; for the
+// Thread e (0 .. kGatherThreads - 1) is lane e % 32 of gather warp e / 32; for the
 // row-group writes it is pair e % kPairs, quarter e / kPairs.
 
 // Every loop below is software-pipelined: the loads of window w + 1 are
@@ -539,11 +544,11 @@ __device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u
   const int N = p.N, nx = u.nce + u.nco, iw = e >> 5, lane = e & 31;
   const TcRows tr = tc_rows(u.nce, u.nco, N);
   const int pr = e % kPairs, q = e / kPairs, par = q >> 1, half = q & 1;
-  constexpr int kP = kPairs / kIoWarps;  // pairs each lane loads per window
+  constexpr int kP = kPairs / kGatherWarps;  // pairs each lane loads per window
   const double2* src[kP];
 #pragma unroll
   for (int k = 0; k < kP; ++k) {
-    const int pk = iw + kIoWarps * k;
+    const int pk = iw + kGatherWarps * k;
     src[k] = reinterpret_cast<const double2*>(coef_base(L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1),
                                                         pk & 1, L.F[itm.plan], L.single, L.msingle));
   }
@@ -559,9 +564,9 @@ __device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u
   for (int d0 = 0; d0 < nx; d0 += 32) {
 #pragma unroll
     for (int k = 0; k < kP; ++k)
-      *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * (iw + kIoWarps * k)) =
+      *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * (iw + kGatherWarps * k)) =
           make_float2(f64_to_f32_bits(v[k].x), f64_to_f32_bits(v[k].y));
-    io_bar();
+    gather_bar();
     if (d0 + 32 < nx) load(d0 + 32);
     const int j = d0 / 16 + half;  // group of X_e (par 0) or X_o (par 1)
     if (kTcGrpRows * j < (par ? u.nco : u.nce)) {
@@ -576,7 +581,7 @@ __device__ void gather_forward(const TcLaunch& L, const Item& itm, const Unit& u
       put_group(vec, G, 2 * pr, re);
       put_group(vec, G, 2 * pr + 1, im);
     }
-    io_bar();
+    gather_bar();
   }
 }
 
@@ -592,11 +597,11 @@ __device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u
   const int N = p.N, iw = e >> 5, lane = e & 31;
   const TcRows tr = tc_rows(u.nce, u.nco, N);
   const int pr = e % kPairs, q = e / kPairs, grp8 = q & 1, par = q >> 1;
-  constexpr int kP = kPairs / kIoWarps;
+  constexpr int kP = kPairs / kGatherWarps;
   const double2* src[kP];
 #pragma unroll
   for (int k = 0; k < kP; ++k) {
-    const int pk = iw + kIoWarps * k;
+    const int pk = iw + kGatherWarps * k;
     src[k] = reinterpret_cast<const double2*>(value_base(L.in[itm.plan], N, itm.am, itm.grp * kTcFields + (pk >> 1),
                                                          pk & 1, L.F[itm.plan], L.single, L.msingle));
   }
@@ -612,9 +617,9 @@ __device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u
   for (int i0 = 0; i0 < N; i0 += 16) {
 #pragma unroll
     for (int k = 0; k < kP; ++k)
-      *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * (iw + kIoWarps * k)) =
+      *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * (iw + kGatherWarps * k)) =
           make_float2(f64_to_f32_bits(v[k].x), f64_to_f32_bits(v[k].y));
-    io_bar();
+    gather_bar();
     if (i0 + 16 < N) load(i0 + 16);
     if (i0 + kTcGrpRows * grp8 < N) {
       float xr[8], xi[8];
@@ -631,7 +636,7 @@ __device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u
       put_group(vec, G, 2 * pr, xr);
       put_group(vec, G, 2 * pr + 1, xi);
     }
-    io_bar();
+    gather_bar();
   }
 }
 
@@ -639,7 +644,7 @@ __device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u
 // gathers as the I/O warps', into the item's block of plan 0's pre-gathered
 // buffer (forward: X_e, X_o from group 0; transposed: Y_e, Y_o), by many CTAs
 // per SM.
-__global__ void __launch_bounds__(kIoThreads) tc_in_kernel(const __grid_constant__ TcLaunch L, int fwd) {
+__global__ void __launch_bounds__(kGatherThreads) tc_in_kernel(const __grid_constant__ TcLaunch L, int fwd) {
   __shared__ __align__(16) float T[kIoTile];
   const TcPlan& p = L.plan[0];
   const int npg = tc_pre_groups(p.N);
@@ -658,8 +663,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  float* iot = reinterpret_cast<float*>(base + (size_t)kStages * kStageBytes);  // the I/O warps' tile
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes + kIoTile * sizeof(float));
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)kStages * kStageBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -850,9 +854,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
     __syncwarp();
   } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
     // ------------------------------------------------------------ epilogue
-    // accumulator -> rows: warp ew owns TMEM lane quadrant ew, thread = one
-    // right-hand side (32 ew + lane), 32 tile positions per TMEM load
-    const int ew = warp - kEpiWarp0;
+    // accumulator -> rows: two teams of four warps; warp w owns TMEM lane
+    // quadrant ew = w % 4, thread = one right-hand side (32 ew + lane); team
+    // t takes the 32-position chunks t, t + 2, ... of every tile
+    const int ew = warp % 4, team = (warp - kEpiWarp0) / 4;
     const int e = tid - 32 * kEpiWarp0;
     const int rhs = 32 * ew + lane;
     long te = 0;
@@ -884,7 +889,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const int Nt = min(kTcNT, d.NN - kTcNT * t);
-          for (int c0 = 0; c0 < Nt; c0 += 32) {
+          if (32 * team >= Nt) {
+            // no chunk of this tile for this team: its share of the accumulator is free
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->acce[b]);
+          }
+          for (int c0 = 32 * team; c0 < Nt; c0 += 64) {
             uint32_t hv[32];
             if (d.KK > 0) {
               uint32_t lv[32];
@@ -898,9 +909,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
 #pragma unroll
               for (int k = 0; k < 32; ++k) hv[k] = 0u;
             }
-            if (c0 + 32 >= Nt) {
-              // the tile's last columns are in registers: the accumulator pair
-              // is free for the MMAs of tile te + 2 while these are stored
+            if (c0 + 64 >= Nt) {
+              // the team's last columns of the tile are in registers: its share
+              // of the accumulator pair is free for the MMAs of tile te + 2
               asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
               __syncwarp();
               if (lane == 0) mbar_arrive(&ctl->acce[b]);
@@ -965,12 +976,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       }
     }
   } else if (warp >= kIoWarp0) {
-    // ------------------------------------------------------------ I/O warps
+    // ------------------------------------------------------------ item warps
     // They take this CTA's items from the launch's work counter (decreasing
-    // cost), publish each in ctl->ring for the other roles, and gather item i
-    // into slot i % 2 once item i - 2 (the slot's previous user) has finished
-    // all of its tiles, through the shared tile iot; they also zero the item's
-    // accumulation rows.
+    // cost) once item i - 2 has finished all of its tiles (the ring holds four
+    // and slot i % 2 of the intermediate rows is item i - 2's), zero the item's
+    // accumulation rows that no op stores first, and publish it in ctl->ring
+    // for the other roles; its inputs were gathered ahead by tc_in_kernel.
     const int e = tid - 32 * kIoWarp0;
     int t_m2 = 0, t_m1 = 0;  // tiles of all items up to i-2, up to i-1
     bool ok = L.stall == 0;
@@ -990,14 +1001,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       }
       const Item itm = item_of(L, it);
       const TcPlan& p = L.plan[itm.plan];
-      const Unit u = p.units[itm.am];
-      unsigned char* vec = slots + (size_t)(iseq & 1) * slot_bytes;
-      if (!p.pre) {
-        if (fwd)
-          gather_forward(L, itm, u, vec, iot, e);
-        else
-          gather_inverse(L, itm, u, vec, iot, e, 0);
-      }
       // accumulation rows that no op stores first start at zero (the
       // epilogue adds into them; the output step reads every row)
       {
@@ -1010,7 +1013,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
           for (int k = e; k < n4; k += kIoThreads) __stcg(a + k, make_float4(0.f, 0.f, 0.f, 0.f));
         }
       }
-      asm volatile("fence.proxy.async.global;" ::: "memory");  // the rows are read by bulk copies
       __threadfence();
       io_bar();
       if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
@@ -1143,8 +1145,9 @@ cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, 
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-  if (p.pre) {
-    tc_in_kernel<<<std::max(1, std::min(L.nitems, 8 * sm_count())), kIoThreads, 0, st>>>(L, fwd ? 1 : 0);
+  if (!p.pre) return cudaErrorInvalidValue;  // the inputs are always gathered ahead
+  {
+    tc_in_kernel<<<std::max(1, std::min(L.nitems, 8 * sm_count())), kGatherThreads, 0, st>>>(L, fwd ? 1 : 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1185,7 +1188,8 @@ cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t 
   {
     // each plan's inputs gathered ahead, one launch per plan
     for (int q = 0; q < L.nplans; ++q) {
-      if (L.F[q] <= 0 || !L.plan[q].pre) continue;
+      if (L.F[q] <= 0) continue;
+      if (!L.plan[q].pre) return cudaErrorInvalidValue;
       TcLaunch Lq;
       std::memset(&Lq, 0, sizeof(Lq));
       Lq.plan[0] = L.plan[q];
@@ -1194,7 +1198,7 @@ cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t 
       Lq.F[0] = L.F[q];
       Lq.nplans = 1;
       Lq.nitems = L.plan[q].nunits * ((L.F[q] + kTcFields - 1) / kTcFields);
-      tc_in_kernel<<<std::max(1, std::min(Lq.nitems, 8 * sm_count())), kIoThreads, 0, st>>>(Lq, fwd ? 1 : 0);
+      tc_in_kernel<<<std::max(1, std::min(Lq.nitems, 8 * sm_count())), kGatherThreads, 0, st>>>(Lq, fwd ? 1 : 0);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
