@@ -332,8 +332,9 @@ sht_status alt_forward_m_noalloc(sht_plan_t plan, int m, const double* beta_m, d
  *  - apply_ms: the block-product kernels (for SHT_MIXED the pre-gather
  *    kernel of the inputs and the tensor-core kernel after it; the whole
  *    apply for SHT_FP64 / SHT_FP32 and direct plans),
- *  - output_ms: the tensor-core path's output kernel (parity fold or
- *    scatter; 0 for the other precisions),
+ *  - output_ms: the tensor-core path's output kernel (the forward's parity
+ *    fold; 0 for the inverse, whose scatter to beta the tensor-core kernel
+ *    does as each work item finishes, and for the other precisions),
  *  - launches: the number of launches summed.
  * reset != 0 starts a new sum.  SHT_ERR_UNSUPPORTED without the flag. */
 sht_status sht_plan_kernel_time(sht_plan_t plan, int reset, double* apply_ms, double* output_ms, int64_t* launches);

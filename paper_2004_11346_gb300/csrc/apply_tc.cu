@@ -292,8 +292,8 @@ constexpr int kMmaWarp = 1;                   // one thread issues the MMAs; the
 constexpr int kEpiWarp0 = 4;                  // warps 4-11: two teams of four, TMEM lane quadrant warp % 4
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kIoWarp0 = 12;                  // warps 12-15 take the items and zero their rows
-constexpr int kIoThreads = kTcThreads - 32 * kIoWarp0;
+constexpr int kIoWarp0 = 12;                  // warps 2-3 and 12-15: the items, their zeroed rows and outputs
+constexpr int kIoThreads = kTcThreads - 32 * kIoWarp0 + 64;
 // The input gathers (tc_in_kernel's CTAs): 8 warps
 constexpr int kGatherWarps = 8;
 constexpr int kGatherThreads = 32 * kGatherWarps;
@@ -659,6 +659,65 @@ __global__ void __launch_bounds__(kGatherThreads) tc_in_kernel(const __grid_cons
   }
 }
 
+// Output side of one finished item, by the persistent kernel's item warps
+// while the tensor cores work on later items: the item's accumulated rows
+// (FP32, kTcR right-hand sides per row) to g (forward: the parity fold of
+// Sec. 3.1.2, g(theta_{N+i}) = y_e + y_o, g(theta_{N-1-i}) = y_e - y_o) or to
+// beta (transposed: X rows back to degrees, even degrees from X_e, odd from
+// X_o).  A warp's unit is 16 rows and 8 fields: lanes 2k, 2k + 1 read one 32-byte
+// sector of row k (the (+m, -m) values of two fields each), so every load
+// takes whole sectors, and every store instruction writes two 256-byte runs
+// (16 consecutive nodes or degrees of two fields).  The rows were written by
+// this CTA's epilogue and are read past L1.
+__device__ void item_out(const TcLaunch& L, const Item& itm, bool fwd, int e, int nthreads) {
+  const TcPlan& p = L.plan[itm.plan];
+  const Unit u = p.units[itm.am];
+  const int N = p.N, lane = e & 31, k = lane >> 1, h = lane & 1;
+  double* out = L.out[itm.plan];
+  const int F = L.F[itm.plan];
+  const float* acc = p.acc + ((size_t)itm.grp * p.nunits + itm.am) * (size_t)tc_acc_rows(N) * kTcR;
+  const int nrow = fwd ? N : u.nce + u.nco;
+  const int yo = tc_r8(N), xo = tc_r8(u.nce);
+  const int units = ((nrow + 15) >> 4) * (kTcFields / 8);
+  for (int q = e >> 5; q < units; q += nthreads >> 5) {
+    const int r = 16 * (q / (kTcFields / 8)) + k;  // node i (forward) or degree offset d (transposed)
+    const int fb = 8 * (q % (kTcFields / 8));      // first field of the unit within the group
+    if (r >= nrow) continue;
+    const int row = fwd ? r : ((r & 1) ? xo + (r >> 1) : (r >> 1));
+    const float4* src = reinterpret_cast<const float4*>(acc + (size_t)row * kTcR + 4 * fb) + h;
+    float4 a[4], b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = __ldcg(src + 2 * j);
+    if (fwd) {
+      const float4* so = reinterpret_cast<const float4*>(acc + (size_t)(yo + r) * kTcR + 4 * fb) + h;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = __ldcg(so + 2 * j);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int f = itm.grp * kTcFields + fb + 2 * j + h;  // this lane's field; float4 = (+m re, im, -m re, im)
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const float xr = s ? a[j].z : a[j].x, xi = s ? a[j].w : a[j].y;
+        if (fwd) {
+          const double* gb = value_base(out, N, itm.am, f, s, F, L.single, L.msingle);
+          if (gb) {
+            const float yr = s ? b[j].z : b[j].x, yi = s ? b[j].w : b[j].y;
+            double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
+            __stcs(gp + N + r, make_double2(f32_to_f64_bits(xr + yr), f32_to_f64_bits(xi + yi)));
+            __stcs(gp + N - 1 - r, make_double2(f32_to_f64_bits(xr - yr), f32_to_f64_bits(xi - yi)));
+          }
+        } else {
+          const double* bdst = coef_base(out, N, itm.am, f, s, F, L.single, L.msingle);
+          if (bdst)
+            __stcs(reinterpret_cast<double2*>(const_cast<double*>(bdst)) + r,
+                   make_double2(f32_to_f64_bits(xr), f32_to_f64_bits(xi)));
+        }
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_constant__ TcLaunch L, int fwd) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
@@ -966,24 +1025,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
             }
           }
           // rows written above are read next by bulk copies (async proxy); the
-          // accumulated rows only by the output kernel
+          // accumulated rows, after the item's last tile, by the item warps'
+          // output step, which reads them from L2: there every epilogue
+          // thread's stores and reductions are made visible at GPU scope
           if (!d.accum) asm volatile("fence.proxy.async.global;" ::: "memory");
-          __threadfence_block();
+          if (L.fuse_out && q + 1 == nops && t + 1 == d.nT)
+            __threadfence();
+          else
+            __threadfence_block();
           epi_bar();
           ++done;
           if (e == 0) *((volatile int*)&ctl->done_tiles) = done;
         }
       }
     }
-  } else if (warp >= kIoWarp0) {
+  } else if (warp >= kIoWarp0 || warp == 2 || warp == 3) {
     // ------------------------------------------------------------ item warps
     // They take this CTA's items from the launch's work counter (decreasing
     // cost) once item i - 2 has finished all of its tiles (the ring holds four
     // and slot i % 2 of the intermediate rows is item i - 2's), zero the item's
     // accumulation rows that no op stores first, and publish it in ctl->ring
     // for the other roles; its inputs were gathered ahead by tc_in_kernel.
-    const int e = tid - 32 * kIoWarp0;
+    // Then they write item i - 2's outputs from its finished rows, while the
+    // tensor cores work on items i - 1 and i.
+    const int e = warp < 4 ? tid - 64 : tid - 32 * kIoWarp0 + 64;
     int t_m2 = 0, t_m1 = 0;  // tiles of all items up to i-2, up to i-1
+    int it_m2 = -1, it_m1 = -1;  // items i-2, i-1 (-1: none)
     bool ok = L.stall == 0;
     for (int iseq = 0; ok; ++iseq) {
       ok = io_and(counter_wait(ctl, &ctl->done_tiles, t_m2));
@@ -997,6 +1064,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       if (it < 0) {
         __threadfence_block();
         if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
+        // the last two items: outputs once their tiles are done
+        if (L.fuse_out) {
+          if (it_m2 >= 0) item_out(L, item_of(L, it_m2), fwd, e, kIoThreads);
+          if (it_m1 >= 0 && io_and(counter_wait(ctl, &ctl->done_tiles, t_m1)))
+            item_out(L, item_of(L, it_m1), fwd, e, kIoThreads);
+        }
         break;
       }
       const Item itm = item_of(L, it);
@@ -1016,9 +1089,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       __threadfence();
       io_bar();
       if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
+      if (L.fuse_out && it_m2 >= 0) item_out(L, item_of(L, it_m2), fwd, e, kIoThreads);
       const int t_cur = t_m1 + p.tiles[2 * itm.am + (fwd ? 0 : 1)];
       t_m2 = t_m1;
       t_m1 = t_cur;
+      it_m2 = it_m1;
+      it_m1 = it;
     }
   }
   if (*((volatile int*)&ctl->abort) && tid == 0) atomicExch(L.err, 1);
@@ -1142,6 +1218,7 @@ cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, 
   L.max_rows = p.max_rows;
   L.counter = counter;
   L.err = err;
+  L.fuse_out = fwd ? 0 : 1;
   cudaError_t e = cudaFuncSetAttribute(alt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTotal);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
@@ -1155,7 +1232,7 @@ cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, 
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-  e = launch_out(p, fwd, out, F, single, m, sm_count(), st);
+  if (!L.fuse_out) e = launch_out(p, fwd, out, F, single, m, sm_count(), st);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
   return e;
 }
@@ -1203,12 +1280,14 @@ cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t 
       if (e != cudaSuccess) return e;
     }
   }
-  alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(L, fwd ? 1 : 0);
+  TcLaunch Lk = L;
+  Lk.fuse_out = fwd ? 0 : 1;
+  alt_tc_kernel<<<grid, kTcThreads, kSmemTotal, st>>>(Lk, fwd ? 1 : 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
   const int sms = sm_count();
-  for (int q = 0; q < L.nplans && e == cudaSuccess; ++q)
+  for (int q = 0; q < L.nplans && e == cudaSuccess && !Lk.fuse_out; ++q)
     if (L.F[q] > 0) e = launch_out(L.plan[q], fwd, L.out[q], L.F[q], 0, 0, sms, st);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
   return e;

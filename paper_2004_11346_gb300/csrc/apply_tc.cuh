@@ -213,6 +213,9 @@ struct TcLaunch {
   int max_rows;
   unsigned int* counter;          // zero before the launch
   int* err;
+  // The item warps write each finished item's outputs (the output kernel then
+  // does not run); otherwise the output kernel runs after the launch.
+  int fuse_out;
   // Self-test of the bounded waits: the I/O warps publish no item, so every
   // other role's wait for its first item runs out and the launch reports a
   // timeout through err.
@@ -246,17 +249,21 @@ void tc_first_writers(int N, const std::vector<Unit>& units, std::vector<TcOp>& 
                       const std::vector<int32_t>& tord, std::vector<int32_t>& zr,
                       std::vector<int32_t>& zri);
 
-// One apply: the persistent tensor-core kernel (gather, block products into
-// the accumulation rows), then the output kernel (parity fold to g forward,
-// scatter to beta transposed).  F <= kTcFields * p.gmax.  ws holds grid CTAs'
-// two scratch slots.  ev (optional, three events): recorded before the
-// tensor-core kernel, between it and the output kernel, and after.
+// One apply: the pre-gather of the inputs, then the persistent tensor-core
+// kernel (block products into the accumulation rows), and the output step:
+// forward, the parity fold to g by the output kernel after the launch;
+// transposed, the scatter to beta by the tensor-core kernel's item warps as
+// each item finishes.  F <= kTcFields * p.gmax.  ws holds grid CTAs' two
+// scratch slots.  ev (optional, three events): recorded before the pre-gather,
+// after the tensor-core kernel and after the output kernel (an empty interval
+// when the output step ran inside the tensor-core kernel).
 cudaError_t launch_tc(const TcPlan& p, bool fwd, const double* in, double* out, int F, int single, int m, int grid,
                       unsigned char* ws, unsigned int* counter, int* err, cudaStream_t st, cudaEvent_t* ev = nullptr);
 
 // The same for a batch of plans in one launch of the tensor-core kernel (the
-// launch's items, scratch and counter set up by the caller), followed by one
-// output kernel per plan.  L.counter must be zero on the stream.
+// launch's items, scratch and counter set up by the caller), after one
+// pre-gather launch per plan; forward, one output kernel per plan after it.
+// L.counter must be zero on the stream.
 cudaError_t launch_tc_batch(const TcLaunch& L, bool fwd, int grid, cudaStream_t st, cudaEvent_t* ev = nullptr);
 
 // The bounded-wait self-test on plan p (see TcLaunch::stall).
