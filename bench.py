@@ -430,7 +430,7 @@ def run_ours(args):
     ki = plan.kernel_time(reset=True)
     inv_split = {"apply_ms": ki["apply_ms"] / max(1, ki["launches"]),
                  "output_ms": ki["output_ms"] / max(1, ki["launches"]),
-                 "what": "inverse call: pre-gather + tensor-core kernel, whose item warps write the outputs "
+                 "what": "inverse call: pre-gather + tensor-core kernel, whose output warps write the outputs "
                          "(apply; the output interval is empty)"
                  if w["precision"] == "mixed" else "inverse call"}
     barrier()

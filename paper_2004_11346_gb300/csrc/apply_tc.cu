@@ -292,8 +292,11 @@ constexpr int kMmaWarp = 1;                   // one thread issues the MMAs; the
 constexpr int kEpiWarp0 = 4;                  // warps 4-11: two teams of four, TMEM lane quadrant warp % 4
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kIoWarp0 = 12;                  // warps 2-3 and 12-15: the items, their zeroed rows and outputs
-constexpr int kIoThreads = kTcThreads - 32 * kIoWarp0 + 64;
+constexpr int kIoWarp0 = 2;                   // warps 2-3 take the items and zero their rows
+constexpr int kIoThreads = 64;
+constexpr int kOutWarp0 = 12;                 // warps 12-15 write finished items' outputs
+constexpr int kOutTeam = kTcThreads - 32 * kOutWarp0;
+constexpr int kRing = 16;                     // published items a CTA keeps for its roles
 // The input gathers (tc_in_kernel's CTAs): 8 warps
 constexpr int kGatherWarps = 8;
 constexpr int kGatherThreads = 32 * kGatherWarps;
@@ -319,7 +322,8 @@ struct Ctl {
   int abort;
   int gathered;    // items whose gather is complete (or found the queue empty)
   int done_tiles;  // tiles whose epilogue is complete (all items so far)
-  int ring[4];     // item index of this CTA's item iseq at ring[iseq % 4]; -1 = no more
+  int out_next;    // items whose index the output warps have taken from the ring
+  int ring[kRing];  // item index of this CTA's item iseq at ring[iseq % kRing]; -1 = no more
 };
 constexpr size_t kSmemTotal = (size_t)kStages * kStageBytes + sizeof(Ctl) + 1024;
 static_assert(kSmemTotal <= 232448, "fits the 227 KB of shared memory one CTA may use");
@@ -406,7 +410,7 @@ __device__ __forceinline__ bool counter_wait(Ctl* ctl, int* ctr, int target) {
 // are gathered; -1 when the work counter ran out.
 __device__ __forceinline__ int next_item(Ctl* ctl, int iseq, bool& ok) {
   ok = counter_wait(ctl, &ctl->gathered, iseq + 1);
-  return ok ? *((volatile int*)&ctl->ring[iseq & 3]) : -1;
+  return ok ? *((volatile int*)&ctl->ring[iseq % kRing]) : -1;
 }
 
 __device__ __forceinline__ void bulk_expect(uint64_t* bar, uint32_t bytes) {
@@ -420,6 +424,7 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
 }
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 __device__ __forceinline__ void io_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kIoThreads) : "memory"); }
+__device__ __forceinline__ void out_bar() { asm volatile("bar.sync 3, %0;" ::"n"(kOutTeam) : "memory"); }
 __device__ __forceinline__ void gather_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kGatherThreads) : "memory"); }
 // The named barriers with an AND over the group: every warp of the group takes
 // the same decision after a bounded wait, so none is left at a barrier alone.
@@ -438,6 +443,15 @@ __device__ __forceinline__ bool io_and(bool v) {
       "{\n .reg .pred q, r;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred r, 2, %2, q;\n selp.u32 %0, 1, 0, r;\n}"
       : "=r"(r)
       : "r"((uint32_t)v), "n"(kIoThreads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ bool out_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred q, r;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred r, 3, %2, q;\n selp.u32 %0, 1, 0, r;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kOutTeam)
       : "memory");
   return r != 0;
 }
@@ -736,6 +750,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
     ctl->abort = 0;
     ctl->gathered = 0;
     ctl->done_tiles = 0;
+    ctl->out_next = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // Stage memory starts at zero: the MMA of a padded last K step reads one row
@@ -1039,37 +1054,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
         }
       }
     }
-  } else if (warp >= kIoWarp0 || warp == 2 || warp == 3) {
+  } else if (warp >= kIoWarp0 && warp < kIoWarp0 + kIoThreads / 32) {
     // ------------------------------------------------------------ item warps
     // They take this CTA's items from the launch's work counter (decreasing
-    // cost) once item i - 2 has finished all of its tiles (the ring holds four
-    // and slot i % 2 of the intermediate rows is item i - 2's), zero the item's
-    // accumulation rows that no op stores first, and publish it in ctl->ring
-    // for the other roles; its inputs were gathered ahead by tc_in_kernel.
-    // Then they write item i - 2's outputs from its finished rows, while the
-    // tensor cores work on items i - 1 and i.
-    const int e = warp < 4 ? tid - 64 : tid - 32 * kIoWarp0 + 64;
+    // cost) once item i - 2 has finished all of its tiles (slot i % 2 of the
+    // intermediate rows is item i - 2's) and, when the kernel writes the
+    // outputs, the output warps have taken item i - kRing from the ring; zero
+    // the item's accumulation rows that no op stores first, and publish it in
+    // ctl->ring for the other roles.  Its inputs were gathered ahead by
+    // tc_in_kernel.
+    const int e = tid - 32 * kIoWarp0;
     int t_m2 = 0, t_m1 = 0;  // tiles of all items up to i-2, up to i-1
-    int it_m2 = -1, it_m1 = -1;  // items i-2, i-1 (-1: none)
     bool ok = L.stall == 0;
     for (int iseq = 0; ok; ++iseq) {
-      ok = io_and(counter_wait(ctl, &ctl->done_tiles, t_m2));
+      ok = counter_wait(ctl, &ctl->done_tiles, t_m2);
+      if (ok && L.fuse_out) ok = counter_wait(ctl, &ctl->out_next, iseq - kRing + 1);
+      ok = io_and(ok);
       if (!ok) break;
       if (e == 0) {
         const unsigned int w = atomicAdd(L.counter, 1u);
-        ctl->ring[iseq & 3] = w < (unsigned int)L.nitems ? (int)w : -1;
+        ctl->ring[iseq % kRing] = w < (unsigned int)L.nitems ? (int)w : -1;
       }
       io_bar();
-      const int it = *((volatile int*)&ctl->ring[iseq & 3]);
+      const int it = *((volatile int*)&ctl->ring[iseq % kRing]);
       if (it < 0) {
         __threadfence_block();
         if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
-        // the last two items: outputs once their tiles are done
-        if (L.fuse_out) {
-          if (it_m2 >= 0) item_out(L, item_of(L, it_m2), fwd, e, kIoThreads);
-          if (it_m1 >= 0 && io_and(counter_wait(ctl, &ctl->done_tiles, t_m1)))
-            item_out(L, item_of(L, it_m1), fwd, e, kIoThreads);
-        }
         break;
       }
       const Item itm = item_of(L, it);
@@ -1089,12 +1099,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       __threadfence();
       io_bar();
       if (e == 0) *((volatile int*)&ctl->gathered) = iseq + 1;
-      if (L.fuse_out && it_m2 >= 0) item_out(L, item_of(L, it_m2), fwd, e, kIoThreads);
       const int t_cur = t_m1 + p.tiles[2 * itm.am + (fwd ? 0 : 1)];
       t_m2 = t_m1;
       t_m1 = t_cur;
-      it_m2 = it_m1;
-      it_m1 = it;
+    }
+  } else if (warp >= kOutWarp0 && L.fuse_out) {
+    // ------------------------------------------------------------ output warps
+    // Each published item in turn, once its last tile is done: its outputs
+    // from its finished rows (item_out), while the tensor cores work on the
+    // items after it.  They run behind the other roles by as many items as
+    // the outputs take, up to kRing - 1.
+    const int e = tid - 32 * kOutWarp0;
+    int t_acc = 0;  // tiles of all items up to this one
+    bool ok = true;
+    for (int j = 0; ok; ++j) {
+      ok = out_and(counter_wait(ctl, &ctl->gathered, j + 1));
+      if (!ok) break;
+      const int it = *((volatile int*)&ctl->ring[j % kRing]);
+      out_bar();
+      if (e == 0) *((volatile int*)&ctl->out_next) = j + 1;
+      if (it < 0) break;
+      const Item itm = item_of(L, it);
+      t_acc += L.plan[itm.plan].tiles[2 * itm.am + (fwd ? 0 : 1)];
+      ok = out_and(counter_wait(ctl, &ctl->done_tiles, t_acc));
+      if (!ok) break;
+      item_out(L, itm, fwd, e, kOutTeam);
     }
   }
   if (*((volatile int*)&ctl->abort) && tid == 0) atomicExch(L.err, 1);
