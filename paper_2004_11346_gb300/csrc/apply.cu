@@ -348,6 +348,7 @@ struct sht_plan_s {
   unsigned char* d_wstc = nullptr;
   float* d_acc = nullptr;  // accumulated rows of every work item (tc_gmax field groups)
   unsigned char* d_pre = nullptr;  // transposed inputs gathered ahead (tc_gmax field groups)
+  float* d_w32 = nullptr;          // the weights of the positive nodes, rounded to FP32
   int32_t* d_tcford = nullptr;     // the tensor-core kernel's op processing order, forward
   int32_t* d_tctord = nullptr;     // and transposed
   int tc_gmax = 0;
@@ -429,6 +430,7 @@ void free_device(sht_plan_s* p) {
   cudaFree(p->d_wstc);
   cudaFree(p->d_acc);
   cudaFree(p->d_pre);
+  cudaFree(p->d_w32);
   cudaFree(p->d_tcford);
   cudaFree(p->d_tctord);
   cudaFree(p->d_err);
@@ -473,7 +475,7 @@ TcPlan tc_plan_of(const sht_plan_s* p) {
   t.img = p->d_img;
   t.zr = p->d_tczr;
   t.zri = p->d_tczri;
-  t.w = p->d_w;
+  t.w32 = p->d_w32;
   t.acc = p->d_acc;
   t.pre = p->d_pre;
   t.ford = p->d_tcford;
@@ -661,6 +663,12 @@ sht_status attach_device(sht_plan_s* p) {
     tc_proc_order(P.units, tops, ford, tord);
     tc_first_writers(N, P.units, tops, ford, tord, zr, zri);
     e = upload(&p->d_img, img);
+    {
+      // round to nearest, as the kernels' FP64 -> FP32 conversions do
+      std::vector<float> w32((size_t)N);
+      for (int i = 0; i < N; ++i) w32[(size_t)i] = (float)P.w[(size_t)(N + i)];
+      if (e == cudaSuccess) e = upload(&p->d_w32, w32);
+    }
     if (e == cudaSuccess) e = upload(&p->d_tcops, tops);
     if (e == cudaSuccess) e = upload(&p->d_tczr, zr);
     if (e == cudaSuccess) e = upload(&p->d_tczri, zri);

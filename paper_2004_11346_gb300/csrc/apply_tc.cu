@@ -640,7 +640,7 @@ __device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int r = kTcGrpRows * grp8 + k, i = i0 + r;
-        const float wi = i < N ? f64_to_f32_bits(__ldg(p.w + N + i)) : 0.f;
+        const float wi = i < N ? __ldg(p.w32 + i) : 0.f;
         const float2 a = *reinterpret_cast<const float2*>(T + r * kIoStride + 2 * pr);
         const float2 b = *reinterpret_cast<const float2*>(T + (16 + r) * kIoStride + 2 * pr);
         xr[k] = par ? wi * (a.x - b.x) : wi * (a.x + b.x);
@@ -673,7 +673,7 @@ __global__ void __launch_bounds__(kGatherThreads) tc_in_kernel(const __grid_cons
   }
 }
 
-// Output side of one finished item, by the persistent kernel's item warps
+// Output side of one finished item, by the persistent kernel's output warps
 // while the tensor cores work on later items: the item's accumulated rows
 // (FP32, kTcR right-hand sides per row) to g (forward: the parity fold of
 // Sec. 3.1.2, g(theta_{N+i}) = y_e + y_o, g(theta_{N-1-i}) = y_e - y_o) or to
@@ -682,54 +682,72 @@ __global__ void __launch_bounds__(kGatherThreads) tc_in_kernel(const __grid_cons
 // sector of row k (the (+m, -m) values of two fields each), so every load
 // takes whole sectors, and every store instruction writes two 256-byte runs
 // (16 consecutive nodes or degrees of two fields).  The rows were written by
-// this CTA's epilogue and are read past L1.
-__device__ void item_out(const TcLaunch& L, const Item& itm, bool fwd, int e, int nthreads) {
+// this CTA's epilogue and are read past L1.  The loads of U units are issued
+// before any of their stores, so that each warp keeps U units in flight.
+template <bool FWD, int U>
+__device__ void item_out_t(const TcLaunch& L, const Item& itm, int e, int nthreads) {
   const TcPlan& p = L.plan[itm.plan];
   const Unit u = p.units[itm.am];
-  const int N = p.N, lane = e & 31, k = lane >> 1, h = lane & 1;
+  const int N = p.N, lane = e & 31, k = lane >> 1, h = lane & 1, nw = nthreads >> 5;
   double* out = L.out[itm.plan];
   const int F = L.F[itm.plan];
   const float* acc = p.acc + ((size_t)itm.grp * p.nunits + itm.am) * (size_t)tc_acc_rows(N) * kTcR;
-  const int nrow = fwd ? N : u.nce + u.nco;
+  const int nrow = FWD ? N : u.nce + u.nco;
   const int yo = tc_r8(N), xo = tc_r8(u.nce);
-  const int units = ((nrow + 15) >> 4) * (kTcFields / 8);
-  for (int q = e >> 5; q < units; q += nthreads >> 5) {
-    const int r = 16 * (q / (kTcFields / 8)) + k;  // node i (forward) or degree offset d (transposed)
-    const int fb = 8 * (q % (kTcFields / 8));      // first field of the unit within the group
-    if (r >= nrow) continue;
-    const int row = fwd ? r : ((r & 1) ? xo + (r >> 1) : (r >> 1));
-    const float4* src = reinterpret_cast<const float4*>(acc + (size_t)row * kTcR + 4 * fb) + h;
-    float4 a[4], b[4];
+  constexpr int kUF = kTcFields / 8;  // units per 16 rows
+  const int units = ((nrow + 15) >> 4) * kUF;
+  for (int q0 = e >> 5; q0 < units; q0 += U * nw) {
+    float4 a[U][4], b[FWD ? U : 1][4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) a[j] = __ldcg(src + 2 * j);
-    if (fwd) {
-      const float4* so = reinterpret_cast<const float4*>(acc + (size_t)(yo + r) * kTcR + 4 * fb) + h;
+    for (int v = 0; v < U; ++v) {
+      const int q = q0 + v * nw, r = 16 * (q / kUF) + k, fb = 8 * (q % kUF);
+      if (q < units && r < nrow) {
+        const int row = FWD ? r : ((r & 1) ? xo + (r >> 1) : (r >> 1));
+        const float4* src = reinterpret_cast<const float4*>(acc + (size_t)row * kTcR + 4 * fb) + h;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = __ldcg(so + 2 * j);
+        for (int j = 0; j < 4; ++j) a[v][j] = __ldcg(src + 2 * j);
+        if (FWD) {
+          const float4* so = reinterpret_cast<const float4*>(acc + (size_t)(yo + r) * kTcR + 4 * fb) + h;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[FWD ? v : 0][j] = __ldcg(so + 2 * j);
+        }
+      }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int f = itm.grp * kTcFields + fb + 2 * j + h;  // this lane's field; float4 = (+m re, im, -m re, im)
+    for (int v = 0; v < U; ++v) {
+      const int q = q0 + v * nw, r = 16 * (q / kUF) + k, fb = 8 * (q % kUF);
+      if (q >= units || r >= nrow) continue;
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const float xr = s ? a[j].z : a[j].x, xi = s ? a[j].w : a[j].y;
-        if (fwd) {
-          const double* gb = value_base(out, N, itm.am, f, s, F, L.single, L.msingle);
-          if (gb) {
-            const float yr = s ? b[j].z : b[j].x, yi = s ? b[j].w : b[j].y;
-            double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
-            __stcs(gp + N + r, make_double2(f32_to_f64_bits(xr + yr), f32_to_f64_bits(xi + yi)));
-            __stcs(gp + N - 1 - r, make_double2(f32_to_f64_bits(xr - yr), f32_to_f64_bits(xi - yi)));
+      for (int j = 0; j < 4; ++j) {
+        const int f = itm.grp * kTcFields + fb + 2 * j + h;  // this lane's field; float4 = (+m re, im, -m re, im)
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const float xr = s ? a[v][j].z : a[v][j].x, xi = s ? a[v][j].w : a[v][j].y;
+          if (FWD) {
+            const double* gb = value_base(out, N, itm.am, f, s, F, L.single, L.msingle);
+            if (gb) {
+              const float4 y = b[FWD ? v : 0][j];
+              const float yr = s ? y.z : y.x, yi = s ? y.w : y.y;
+              double2* gp = reinterpret_cast<double2*>(const_cast<double*>(gb));
+              __stcs(gp + N + r, make_double2(f32_to_f64_bits(xr + yr), f32_to_f64_bits(xi + yi)));
+              __stcs(gp + N - 1 - r, make_double2(f32_to_f64_bits(xr - yr), f32_to_f64_bits(xi - yi)));
+            }
+          } else {
+            const double* bdst = coef_base(out, N, itm.am, f, s, F, L.single, L.msingle);
+            if (bdst)
+              __stcs(reinterpret_cast<double2*>(const_cast<double*>(bdst)) + r,
+                     make_double2(f32_to_f64_bits(xr), f32_to_f64_bits(xi)));
           }
-        } else {
-          const double* bdst = coef_base(out, N, itm.am, f, s, F, L.single, L.msingle);
-          if (bdst)
-            __stcs(reinterpret_cast<double2*>(const_cast<double*>(bdst)) + r,
-                   make_double2(f32_to_f64_bits(xr), f32_to_f64_bits(xi)));
         }
       }
     }
   }
+}
+__device__ __forceinline__ void item_out(const TcLaunch& L, const Item& itm, bool fwd, int e, int nthreads) {
+  if (fwd)
+    item_out_t<true, 1>(L, itm, e, nthreads);
+  else
+    item_out_t<false, 4>(L, itm, e, nthreads);
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_constant__ TcLaunch L, int fwd) {

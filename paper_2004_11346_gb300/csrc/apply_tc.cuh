@@ -175,7 +175,7 @@ struct TcPlan {
   // zr[zri[2u + d] .. zri[2u + d + 1]).  Only these are zeroed per item.
   const int32_t* zr;
   const int32_t* zri;
-  const double* w;
+  const float* w32;          // w_{N+i} rounded to FP32, i < N
   // Accumulated rows of every work item (forward: Y_e, Y_o; transposed: X),
   // item (field group g, order |m|) at (g * nunits + |m|) * tc_acc_rows(N)
   // rows.  The kernel zeroes an item's rows when it gathers the item; the
