@@ -345,6 +345,7 @@ struct sht_plan_s {
   int32_t* d_tctiles = nullptr;
   int32_t* d_tczr = nullptr;   // accumulation row ranges to zero per order and direction
   int32_t* d_tczri = nullptr;
+  int32_t* d_tclive = nullptr;  // per order: node rows that some op reaches (tc_live_rows)
   unsigned char* d_wstc = nullptr;
   float* d_acc = nullptr;  // accumulated rows of every work item (tc_gmax field groups)
   unsigned char* d_pre = nullptr;  // transposed inputs gathered ahead (tc_gmax field groups)
@@ -427,6 +428,7 @@ void free_device(sht_plan_s* p) {
   cudaFree(p->d_tctiles);
   cudaFree(p->d_tczr);
   cudaFree(p->d_tczri);
+  cudaFree(p->d_tclive);
   cudaFree(p->d_wstc);
   cudaFree(p->d_acc);
   cudaFree(p->d_pre);
@@ -475,6 +477,7 @@ TcPlan tc_plan_of(const sht_plan_s* p) {
   t.img = p->d_img;
   t.zr = p->d_tczr;
   t.zri = p->d_tczri;
+  t.live = p->d_tclive;
   t.w32 = p->d_w32;
   t.acc = p->d_acc;
   t.pre = p->d_pre;
@@ -661,7 +664,9 @@ sht_status attach_device(sht_plan_s* p) {
     std::vector<int32_t> zr, zri;
     std::vector<int32_t> ford, tord;
     tc_proc_order(P.units, tops, ford, tord);
-    tc_first_writers(N, P.units, tops, ford, tord, zr, zri);
+    std::vector<int32_t> live;
+    tc_live_rows(N, P.units, tops, live);
+    tc_first_writers(N, P.units, tops, ford, tord, live, zr, zri);
     e = upload(&p->d_img, img);
     {
       // round to nearest, as the kernels' FP64 -> FP32 conversions do
@@ -672,6 +677,7 @@ sht_status attach_device(sht_plan_s* p) {
     if (e == cudaSuccess) e = upload(&p->d_tcops, tops);
     if (e == cudaSuccess) e = upload(&p->d_tczr, zr);
     if (e == cudaSuccess) e = upload(&p->d_tczri, zri);
+    if (e == cudaSuccess) e = upload(&p->d_tclive, live);
     if (e == cudaSuccess) e = upload(&p->d_tcford, ford);
     if (e == cudaSuccess) e = upload(&p->d_tctord, tord);
     if (e == cudaSuccess) e = upload(&p->d_tctiles, tiles);

@@ -233,8 +233,30 @@ void tc_proc_order(const std::vector<Unit>& units, const std::vector<TcOp>& tops
   }
 }
 
+void tc_live_rows(int N, const std::vector<Unit>& units, const std::vector<TcOp>& tops, std::vector<int32_t>& live) {
+  live.assign(units.size(), 0);
+  for (size_t u = 0; u < units.size(); ++u) {
+    const Unit& un = units[u];
+    const TcRows tr = tc_rows(un.nce, un.nco, N);
+    int lv = 0;
+    for (int q = un.op_begin; q < un.op_end; ++q) {
+      const TcOp& t = tops[(size_t)q];
+      for (int sg = 0; sg < 2; ++sg) {
+        if (t.out_len[sg] <= 0) continue;
+        const int off = t.out_off[sg], end = off + t.out_len[sg];
+        if (off >= tr.ye && off < tr.yo)
+          lv = std::max(lv, tc_r8(end - tr.ye));
+        else if (off >= tr.yo && off < tr.yo + tc_r8(N))
+          lv = std::max(lv, tc_r8(end - tr.yo));
+      }
+    }
+    live[u] = std::min(lv, tc_r8(N));
+  }
+}
+
 void tc_first_writers(int N, const std::vector<Unit>& units, std::vector<TcOp>& tops, const std::vector<int32_t>& ford,
-                      const std::vector<int32_t>& tord, std::vector<int32_t>& zr, std::vector<int32_t>& zri) {
+                      const std::vector<int32_t>& tord, const std::vector<int32_t>& live, std::vector<int32_t>& zr,
+                      std::vector<int32_t>& zri) {
   zr.clear();
   zri.assign(2 * units.size() + 1, 0);
   const int R = tc_acc_rows(N);
@@ -265,7 +287,9 @@ void tc_first_writers(int N, const std::vector<Unit>& units, std::vector<TcOp>& 
           }
       }
       // rows the output step reads that no store writes first: zeroed per item
-      const int ranges[2][2] = {{0, fwd ? N : un.nce}, {fwd ? tr.yo - tr.ye : tr.xo, fwd ? N : un.nco}};
+      // (forward, only the live node rows: the output step reads no others)
+      const int nl = std::min(N, live[u]);
+      const int ranges[2][2] = {{0, fwd ? nl : un.nce}, {fwd ? tr.yo - tr.ye : tr.xo, fwd ? nl : un.nco}};
       for (const auto& rg : ranges)
         for (int r = rg[0]; r < rg[0] + rg[1];) {
           if (stored[r]) {
@@ -620,27 +644,29 @@ __device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u
                                                          pk & 1, L.F[itm.plan], L.single, L.msingle));
   }
   const int hl = lane & 15, hi = lane >> 4;
+  // node rows that some op reads (whole groups); the rest are never read
+  const int lv = __ldg(p.live + itm.am), nl = min(N, lv);
   double2 v[kP];
   auto load = [&](int i0) {
     const int i = i0 + hl;
 #pragma unroll
     for (int k = 0; k < kP; ++k)
-      v[k] = (src[k] && i < N) ? __ldg(src[k] + (hi ? N - 1 - i : N + i)) : make_double2(0.0, 0.0);
+      v[k] = (src[k] && i < nl) ? __ldg(src[k] + (hi ? N - 1 - i : N + i)) : make_double2(0.0, 0.0);
   };
   load(0);
-  for (int i0 = 0; i0 < N; i0 += 16) {
+  for (int i0 = 0; i0 < lv; i0 += 16) {
 #pragma unroll
     for (int k = 0; k < kP; ++k)
       *reinterpret_cast<float2*>(T + lane * kIoStride + 2 * (iw + kGatherWarps * k)) =
           make_float2(f64_to_f32_bits(v[k].x), f64_to_f32_bits(v[k].y));
     gather_bar();
-    if (i0 + 16 < N) load(i0 + 16);
-    if (i0 + kTcGrpRows * grp8 < N) {
+    if (i0 + 16 < lv) load(i0 + 16);
+    if (i0 + kTcGrpRows * grp8 < lv) {
       float xr[8], xi[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int r = kTcGrpRows * grp8 + k, i = i0 + r;
-        const float wi = i < N ? __ldg(p.w32 + i) : 0.f;
+        const float wi = i < nl ? __ldg(p.w32 + i) : 0.f;
         const float2 a = *reinterpret_cast<const float2*>(T + r * kIoStride + 2 * pr);
         const float2 b = *reinterpret_cast<const float2*>(T + (16 + r) * kIoStride + 2 * pr);
         xr[k] = par ? wi * (a.x - b.x) : wi * (a.x + b.x);
@@ -694,6 +720,7 @@ __device__ void item_out_t(const TcLaunch& L, const Item& itm, int e, int nthrea
   const float* acc = p.acc + ((size_t)itm.grp * p.nunits + itm.am) * (size_t)tc_acc_rows(N) * kTcR;
   const int nrow = FWD ? N : u.nce + u.nco;
   const int yo = tc_r8(N), xo = tc_r8(u.nce);
+  const int nlive = FWD ? __ldg(p.live + itm.am) : nrow;  // rows past it are zero (never written)
   constexpr int kUF = kTcFields / 8;  // units per 16 rows
   const int units = ((nrow + 15) >> 4) * kUF;
   for (int q0 = e >> 5; q0 < units; q0 += U * nw) {
@@ -701,7 +728,7 @@ __device__ void item_out_t(const TcLaunch& L, const Item& itm, int e, int nthrea
 #pragma unroll
     for (int v = 0; v < U; ++v) {
       const int q = q0 + v * nw, r = 16 * (q / kUF) + k, fb = 8 * (q % kUF);
-      if (q < units && r < nrow) {
+      if (q < units && r < nrow && r < nlive) {
         const int row = FWD ? r : ((r & 1) ? xo + (r >> 1) : (r >> 1));
         const float4* src = reinterpret_cast<const float4*>(acc + (size_t)row * kTcR + 4 * fb) + h;
 #pragma unroll
@@ -710,6 +737,12 @@ __device__ void item_out_t(const TcLaunch& L, const Item& itm, int e, int nthrea
           const float4* so = reinterpret_cast<const float4*>(acc + (size_t)(yo + r) * kTcR + 4 * fb) + h;
 #pragma unroll
           for (int j = 0; j < 4; ++j) b[FWD ? v : 0][j] = __ldcg(so + 2 * j);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          a[v][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (FWD) b[FWD ? v : 0][j] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
     }
@@ -1177,12 +1210,16 @@ __global__ void __launch_bounds__(kOutThreads) tc_out_kernel(TcPlan p, double* _
     const float* acc_item = p.acc + ((size_t)grp * p.nunits + am) * (size_t)tc_acc_rows(N) * kTcR;
     if (fwd) {
       const int i0 = 32 * chunk;
+      const int nl = __ldg(p.live + am);  // node rows past it are zero (never written)
       for (int r = iw; r < 32; r += kOutThreads / 32) {
-        if (i0 + r < N) {
+        if (i0 + r < N && i0 + r < nl) {
           *reinterpret_cast<float4*>(Te + r * kIoStride + 4 * lane) =
               __ldcs(reinterpret_cast<const float4*>(acc_item + (size_t)(i0 + r) * kTcR) + lane);
           *reinterpret_cast<float4*>(To + r * kIoStride + 4 * lane) =
               __ldcs(reinterpret_cast<const float4*>(acc_item + (size_t)(yo + i0 + r) * kTcR) + lane);
+        } else if (i0 + r < N) {
+          *reinterpret_cast<float4*>(Te + r * kIoStride + 4 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
+          *reinterpret_cast<float4*>(To + r * kIoStride + 4 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
       __syncthreads();

@@ -175,6 +175,10 @@ struct TcPlan {
   // zr[zri[2u + d] .. zri[2u + d + 1]).  Only these are zeroed per item.
   const int32_t* zr;
   const int32_t* zri;
+  // Per unit: the node rows i < live of Y_e and Y_o that some op writes
+  // forward (reads transposed), a multiple of 8 (tc_live_rows); the others
+  // hold zero forward and are not gathered transposed
+  const int32_t* live;
   const float* w32;          // w_{N+i} rounded to FP32, i < N
   // Accumulated rows of every work item (forward: Y_e, Y_o; transposed: X),
   // item (field group g, order |m|) at (g * nunits + |m|) * tc_acc_rows(N)
@@ -244,9 +248,15 @@ void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op
 // in L2.  ford / tord hold global op indices at the units' op positions.
 void tc_proc_order(const std::vector<Unit>& units, const std::vector<TcOp>& tops, std::vector<int32_t>& ford,
                    std::vector<int32_t>& tord);
-// First writers, in the processing order of ford / tord.
+// Node rows that some op of each unit reaches: the Y_e and Y_o rows written
+// forward (read transposed), counted from the first positive node and
+// rounded up to whole groups.  The nodes past them, near the poles beyond
+// every degree's turning point (Sec. 3.2), have g = 0 and are never read.
+void tc_live_rows(int N, const std::vector<Unit>& units, const std::vector<TcOp>& tops, std::vector<int32_t>& live);
+// First writers, in the processing order of ford / tord; the zeroed ranges
+// leave out the node rows past live (the output step takes them as zero).
 void tc_first_writers(int N, const std::vector<Unit>& units, std::vector<TcOp>& tops, const std::vector<int32_t>& ford,
-                      const std::vector<int32_t>& tord, std::vector<int32_t>& zr,
+                      const std::vector<int32_t>& tord, const std::vector<int32_t>& live, std::vector<int32_t>& zr,
                       std::vector<int32_t>& zri);
 
 // One apply: the pre-gather of the inputs, then the persistent tensor-core

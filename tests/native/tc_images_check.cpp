@@ -101,8 +101,38 @@ int main(int argc, char** argv) {
         }
       }
     }
+  // live node rows: whole groups, within the Y regions, covering every Y row
+  // written forward and every Y group read transposed, and tight (a write in
+  // the last live group)
+  std::vector<int32_t> live;
+  tc_live_rows(N, units, tops, live);
+  if (live.size() != units.size()) return 24;
+  for (size_t u = 0; u < units.size(); ++u) {
+    const Unit& un = units[u];
+    const TcRows tr = tc_rows(un.nce, un.nco, N);
+    const int lv = live[u];
+    if (lv < 0 || lv % 8 != 0 || lv > tc_r8(N)) return 25;
+    int top = 0;
+    for (int q = un.op_begin; q < un.op_end; ++q) {
+      const TcOp& t = tops[(size_t)q];
+      for (int sg = 0; sg < 2; ++sg)
+        for (int r = t.out_off[sg]; r < t.out_off[sg] + t.out_len[sg]; ++r) {
+          const int i = r >= tr.yo ? r - tr.yo : r - tr.ye;  // node row in Y_e or Y_o
+          if (r < tr.ye || r >= tr.yo + N) continue;
+          if (i >= lv) return 26;
+          top = std::max(top, i + 1);
+        }
+      const TcDir dt = tc_dir(t, false);
+      for (int j = 0; j < dt.kg.ngt; ++j) {
+        const int r0 = kTcGrpRows * tc_group(dt.kg, j);
+        if (r0 < tr.ye || r0 >= tr.yo + N) continue;
+        if ((r0 >= tr.yo ? r0 - tr.yo : r0 - tr.ye) >= lv) return 27;
+      }
+    }
+    if (tc_r8(top) != lv) return 28;
+  }
   std::vector<int32_t> zr, zri;
-  tc_first_writers(N, units, tops, ford, tord, zr, zri);
+  tc_first_writers(N, units, tops, ford, tord, live, zr, zri);
   if (zri.size() != 2 * units.size() + 1 || zri[0] != 0) return 11;
   for (size_t u = 0; u < units.size(); ++u) {
     const Unit& un = units[u];
@@ -134,13 +164,18 @@ int main(int argc, char** argv) {
           if (r < 0 || r >= tc_acc_rows(N)) return 15;
           ++zeroed[r];
         }
+      // rows the output step reads (forward, the live node rows: the others
+      // are neither written nor zeroed) are stored first or zeroed, once
+      const int nl = std::min(N, (int)live[u]);
       const int rg[2][2] = {{0, fwd ? N : un.nce}, {fwd ? tr.yo - tr.ye : tr.xo, fwd ? N : un.nco}};
       for (const auto& g : rg)
-        for (int r = g[0]; r < g[0] + g[1]; ++r)
-          if ((state[r] == 1) + zeroed[r] != 1) {
+        for (int r = g[0]; r < g[0] + g[1]; ++r) {
+          const bool read = !fwd || r - g[0] < nl;
+          if (read ? (state[r] == 1) + zeroed[r] != 1 : state[r] != 0 || zeroed[r] != 0) {
             std::printf("order %zu dir %d row %d: state %d zeroed %d\n", u, d, r, state[r], zeroed[r]);
             return 16;
           }
+        }
     }
   }
   std::printf("ok %zu\n", at);
