@@ -221,11 +221,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# The tensor-core kernel's tile (compile-time in csrc/apply_tc.cuh and apply_tc.cu): 128 right-hand
+# sides (MMA M) x 128 block rows (MMA N) per accumulator pair, K chunks of 32 per pipeline stage
+TC_TILE = {"M_rhs": 128, "N": 128, "K_chunk": 32, "stages": 4}
+
+
 def config_of(w, world):
-    return {"workload": w["name"], "N": w["N"], "fields_per_rank": w["F"], "global_batch": w["F"] * world,
-            "eps": w["eps"], "precision": w["precision"], "orders": 4 * w["N"] - 1,
-            "step": "forward ALT + inverse ALT", "parallelism": f"replicas{world}",
-            "l2": "inputs and factor store larger than L2", "plan": w.get("plan", "library defaults")}
+    cfg = {"workload": w["name"], "N": w["N"], "fields_per_rank": w["F"], "global_batch": w["F"] * world,
+           "eps": w["eps"], "precision": w["precision"], "orders": 4 * w["N"] - 1,
+           "step": "forward ALT + inverse ALT", "parallelism": f"replicas{world}",
+           "l2": "inputs and factor store larger than L2", "plan": w.get("plan", "library defaults")}
+    if w["precision"] == "mixed":
+        cfg["tile"] = TC_TILE
+    return cfg
 
 
 # ---------------------------------------------------------------- our arm

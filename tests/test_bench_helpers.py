@@ -21,6 +21,23 @@ def test_workload_plan_overrides():
     assert bench.config_of(bench.workload("fp64_N1024"), 1)["plan"] == "library defaults"
 
 
+def test_recorded_tile_matches_the_kernel_source():
+    # the bench line's config.tile restates compile-time constants of the
+    # tensor-core kernel; read them back from the sources
+    import re
+    csrc = os.path.join(ROOT, "paper_2004_11346_gb300", "csrc")
+    src = open(os.path.join(csrc, "apply_tc.cuh")).read() + open(os.path.join(csrc, "apply_tc.cu")).read()
+
+    def const(name):
+        return int(re.search(r"constexpr int %s = (\d+);" % name, src).group(1))
+
+    fields = const("kTcFields")
+    assert bench.TC_TILE == {"M_rhs": 4 * fields, "N": const("kTcNT"), "K_chunk": const("kTcKC"),
+                             "stages": const("kStages")}
+    assert bench.config_of(bench.workload("mixed_N1024_F64"), 1)["tile"] == bench.TC_TILE
+    assert "tile" not in bench.config_of(bench.workload("fp64_N1024"), 1)
+
+
 def test_headline_traffic_scales_from_its_plan_shape(tmp_path, monkeypatch):
     # a capture of a smaller case of the same kernel is scaled by algorithmic bytes
     t = {"mixed_N512_F64_tuned": 300.0, "_algorithmic_mixed_N512_F64_tuned": 200.0, "mixed_N512_F32": 7.0,
