@@ -359,15 +359,21 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
+// One MMA and one commit, issued by a single lane elected from the converged
+// MMA warp: every lane computes the same operands, so they stay warp-uniform
+// (issuing from a lane-0 branch instead took the forward call from 7.54 to
+// 7.77 ms).
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s32(bar))
-               : "memory");
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}" ::"r"(s32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
@@ -913,66 +919,70 @@ __global__ void __launch_bounds__(kTcThreads, 1) alt_tc_kernel(const __grid_cons
       for (long j = max(0L, jp - kStages); j < jp; ++j) mbar_drain(&ctl->full[j % kStages], (uint32_t)(j / kStages) & 1u);
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      long jm = 0, tm = 0;
-      bool ok = true;
-      for (int iseq = 0; ok; ++iseq) {
-        const int it = next_item(ctl, iseq, ok);
-        if (!ok || it < 0) break;
-        const Item itm = item_of(L, it);
-        const TcPlan& p = L.plan[itm.plan];
-        const Unit u = p.units[itm.am];
-        const int nops = u.op_end - u.op_begin;
-        TcOp nxt = nops > 0 ? p.ops[op_at(p, u, 0, fwd)] : TcOp{};
-        for (int q = 0; q < nops && ok; ++q) {
-          const TcOp op = nxt;
-          if (q + 1 < nops) nxt = p.ops[op_at(p, u, q + 1, fwd)];
-          const TcDir d = tc_dir(op, fwd);
-          for (int t = 0; t < d.nT && ok; ++t, ++tm) {
-            const int b = (int)(tm & 1);
-            const uint32_t v = (uint32_t)(tm >> 1);
-            ok = mbar_wait(ctl, &ctl->acce[b], (v & 1u) ^ 1u);
+    // The whole warp runs the loop with warp-uniform values (broadcast from
+    // lane 0), and one elected lane issues each MMA and commit.
+    long jm = 0, tm = 0;
+    bool ok = true;
+    for (int iseq = 0; ok; ++iseq) {
+      int it = next_item(ctl, iseq, ok);
+      ok = __all_sync(0xffffffffu, ok);
+      it = __shfl_sync(0xffffffffu, it, 0);
+      if (!ok || it < 0) break;
+      const Item itm = item_of(L, it);
+      const TcPlan& p = L.plan[itm.plan];
+      const Unit u = p.units[itm.am];
+      const int nops = __shfl_sync(0xffffffffu, u.op_end - u.op_begin, 0);
+      TcOp nxt = nops > 0 ? p.ops[op_at(p, u, 0, fwd)] : TcOp{};
+      for (int q = 0; q < nops && ok; ++q) {
+        const TcOp op = nxt;
+        if (q + 1 < nops) nxt = p.ops[op_at(p, u, q + 1, fwd)];
+        const TcDir d = tc_dir(op, fwd);
+        const int nT = __shfl_sync(0xffffffffu, d.nT, 0), NN = __shfl_sync(0xffffffffu, d.NN, 0);
+        const int nK = __shfl_sync(0xffffffffu, d.kg.nK, 0), kp_tot = __shfl_sync(0xffffffffu, d.kg.kp_tot, 0);
+        for (int t = 0; t < nT && ok; ++t, ++tm) {
+          const int b = (int)(tm & 1);
+          const uint32_t v = (uint32_t)(tm >> 1);
+          ok = __all_sync(0xffffffffu, mbar_wait(ctl, &ctl->acce[b], (v & 1u) ^ 1u));
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int Np = (min(kTcNT, NN - kTcNT * t) + 15) & ~15;
+          // BF16 A and B, FP32 D, both operands K-major, N = Np, M = 128
+          const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Np >> 3) << 17) | (8u << 24);
+          const uint32_t dhi = taddr + (uint32_t)(b * kAccCols), dlo = dhi + kTcNT;
+          // descriptors of stage 0 for this tile; a stage, a K step or a piece
+          // moves the start address, i.e. adds (byte offset / 16) to the descriptor
+          const uint32_t bK = (uint32_t)(Np / 8) * 128;
+          const uint64_t a_desc0 = sdesc(stage0, kTcGrpBytes, 128);
+          const uint64_t b_desc0 = sdesc(stage0 + kStageA, bK, 128);
+          for (int c = 0; c < nK && ok; ++c, ++jm) {
+            const int s = (int)(jm % kStages);
+            const uint32_t use = (uint32_t)(jm / kStages);
+            ok = __all_sync(0xffffffffu, mbar_wait(ctl, &ctl->full[s], use & 1u));
             if (!ok) break;
+            // the stage was filled by bulk copies (async proxy), which the
+            // MMAs read through the same proxy: the barrier orders them
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int Np = (min(kTcNT, d.NN - kTcNT * t) + 15) & ~15;
-            // BF16 A and B, FP32 D, both operands K-major, N = Np, M = 128
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Np >> 3) << 17) | (8u << 24);
-            const uint32_t dhi = taddr + (uint32_t)(b * kAccCols), dlo = dhi + kTcNT;
-            // descriptors of stage 0 for this tile; a stage, a K step or a piece
-            // moves the start address, i.e. adds (byte offset / 16) to the descriptor
-            const uint32_t bK = (uint32_t)(Np / 8) * 128;
-            const uint64_t a_desc0 = sdesc(stage0, kTcGrpBytes, 128);
-            const uint64_t b_desc0 = sdesc(stage0 + kStageA, bK, 128);
-            for (int c = 0; c < d.kg.nK && ok; ++c, ++jm) {
-              const int s = (int)(jm % kStages);
-              const uint32_t use = (uint32_t)(jm / kStages);
-              ok = mbar_wait(ctl, &ctl->full[s], use & 1u);
-              if (!ok) break;
-              // the stage was filled by bulk copies (async proxy), which the
-              // MMAs read through the same proxy: the barrier orders them
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const int Kp = min(kTcKC, d.kg.kp_tot - kTcKC * c);
-              const uint64_t stg = (uint64_t)((s * kStageBytes) >> 4);
-              const uint64_t ad0 = a_desc0 + stg, bd0 = b_desc0 + stg;
-              const uint64_t bpc = (uint64_t)((Np * Kp * 2) >> 4), bks = (uint64_t)(2 * bK >> 4);
+            const int Kp = min(kTcKC, kp_tot - kTcKC * c);
+            const uint64_t stg = (uint64_t)((s * kStageBytes) >> 4);
+            const uint64_t ad0 = a_desc0 + stg, bd0 = b_desc0 + stg;
+            const uint64_t bpc = (uint64_t)((Np * Kp * 2) >> 4), bks = (uint64_t)(2 * bK >> 4);
 #pragma unroll
-              for (int ks = 0; ks < 2; ++ks) {
-                if (ks * 16 >= Kp) break;
-                // A K-major: core (m8, k8) of piece pa at (k8 * 3 + pa) * 2048 + m8 * 128
-                // (K stride one row group, M stride 128); B K-major, pieces bpc apart
-                const uint64_t ak = ad0 + (uint64_t)((ks * 2 * kTcGrpBytes) >> 4), bk = bd0 + ks * bks;
-                const uint32_t first = (c > 0 || ks > 0) ? 1u : 0u;
-                mma_bf16(dhi, ak, bk, idesc, first);                          // a0 b0
-                mma_bf16(dlo, ak, bk + bpc, idesc, first);                    // a0 b1
-                mma_bf16(dlo, ak + (2048 >> 4), bk, idesc, 1u);               // a1 b0
-                mma_bf16(dlo, ak, bk + 2 * bpc, idesc, 1u);                   // a0 b2
-                mma_bf16(dlo, ak + (2048 >> 4), bk + bpc, idesc, 1u);         // a1 b1
-                mma_bf16(dlo, ak + (4096 >> 4), bk, idesc, 1u);               // a2 b0
-              }
-              mma_commit(&ctl->empty[s]);
+            for (int ks = 0; ks < 2; ++ks) {
+              if (ks * 16 >= Kp) break;
+              // A K-major: core (m8, k8) of piece pa at (k8 * 3 + pa) * 2048 + m8 * 128
+              // (K stride one row group, M stride 128); B K-major, pieces bpc apart
+              const uint64_t ak = ad0 + (uint64_t)((ks * 2 * kTcGrpBytes) >> 4), bk = bd0 + ks * bks;
+              const uint32_t first = (c > 0 || ks > 0) ? 1u : 0u;
+              mma_bf16(dhi, ak, bk, idesc, first);                          // a0 b0
+              mma_bf16(dlo, ak, bk + bpc, idesc, first);                    // a0 b1
+              mma_bf16(dlo, ak + (2048 >> 4), bk, idesc, 1u);               // a1 b0
+              mma_bf16(dlo, ak, bk + 2 * bpc, idesc, 1u);                   // a0 b2
+              mma_bf16(dlo, ak + (2048 >> 4), bk + bpc, idesc, 1u);         // a1 b1
+              mma_bf16(dlo, ak + (4096 >> 4), bk, idesc, 1u);               // a2 b0
             }
-            if (ok) mma_commit(&ctl->accf[b]);
+            mma_commit(&ctl->empty[s]);
           }
+          if (ok) mma_commit(&ctl->accf[b]);
         }
       }
     }
