@@ -351,7 +351,7 @@ sht_status sht_plan_set_timing(sht_plan_t plan, int enable);
  * wait inside the tensor-core kernel is bounded (about a second); when one
  * runs out the kernel stops all its roles, releases its tensor memory, and
  * flags the plan, so that the next sht_sync returns SHT_ERR_TIMEOUT and the
- * plan stays usable.  This call launches that kernel with its I/O warps
+ * plan stays usable.  This call launches that kernel with its item warps
  * publishing no work item, so that the other roles' first waits run out:
  * after it, sht_sync must return SHT_ERR_TIMEOUT.  SHT_MIXED plans only
  * (SHT_ERR_UNSUPPORTED otherwise).  Takes a second or more of GPU time. */

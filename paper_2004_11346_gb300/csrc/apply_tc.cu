@@ -16,20 +16,20 @@
 //   D         = 128 x N FP32 accumulators in tensor memory.
 // The CTA is warp-specialised and persistent (one per SM): one producer
 // thread streams (op, tile, 32-wide K chunk) operand stages into a 4-deep
-// shared memory ring with bulk copies; an MMA thread issues the tensor-core
-// products into two alternating TMEM accumulator pairs; four epilogue warps drain
-// them, each thread one right-hand side, and either split the results into
-// BF16 pieces for the next level (eight rows per 16-byte store) or add them
-// in FP32 into the item's accumulation rows; eight I/O warps take the items
-// and zero their accumulation rows.  The inputs (forward: beta into X rows;
-// transposed: the W-weighted parity fold of g into Y rows) are gathered ahead
-// of the launch by a streaming kernel, tc_in_kernel, whose per-item row groups
-// the producer's bulk copies read (without that buffer the I/O warps gather
-// them into the CTA's scratch).  Ops of one phase
-// read only rows written by earlier phases: the producer starts a phase after
-// the epilogue has counted every earlier tile.  A streaming output kernel then
-// writes g (the parity fold of Sec. 3.1.2) or beta (the scatter) from the
-// accumulation rows.
+// shared memory ring with bulk copies; the MMA warp issues the tensor-core
+// products (one elected lane) into two alternating TMEM accumulator pairs;
+// two teams of four epilogue warps drain them, each thread one right-hand
+// side, and either split the results into BF16 pieces for the next level
+// (eight rows per 16-byte store) or add them in FP32 into the item's
+// accumulation rows; two item warps take the items and zero their
+// accumulation rows.  The inputs (forward: beta into X rows; transposed: the
+// W-weighted parity fold of g into Y rows) are gathered ahead of the launch by
+// a streaming kernel, tc_in_kernel, whose per-item row groups the producer's
+// bulk copies read.  Ops of one phase read only rows written by earlier
+// phases: the producer starts a phase after the epilogue has counted every
+// earlier tile.  Forward, a streaming output kernel then writes g (the parity
+// fold of Sec. 3.1.2) from the accumulation rows; transposed, four output
+// warps scatter each finished item's rows to beta inside this kernel.
 // Per 16-wide K step six MMAs accumulate a_p b_q for p + q <= 2, which keeps
 // every product to about 2^-24 relative error (FP32 quality); a0 b0 and the
 // five smaller cross products go to two separate accumulators that the
@@ -436,8 +436,8 @@ __device__ __forceinline__ bool counter_wait(Ctl* ctl, int* ctr, int target) {
   return false;
 }
 
-// This CTA's item number iseq as the I/O warps published it, once its inputs
-// are gathered; -1 when the work counter ran out.
+// This CTA's item number iseq as the item warps published it, once its rows
+// are zeroed; -1 when the work counter ran out.
 __device__ __forceinline__ int next_item(Ctl* ctl, int iseq, bool& ok) {
   ok = counter_wait(ctl, &ctl->gathered, iseq + 1);
   return ok ? *((volatile int*)&ctl->ring[iseq % kRing]) : -1;
@@ -568,8 +568,8 @@ __device__ __forceinline__ int acc_pos_row(int n, const int32_t* off, const int3
   return n < len[0] ? off[0] + n : off[1] + (n - len[0]);
 }
 
-// ------------------------------------------------------------------ I/O work
-// All global traffic of the I/O warps moves through a 32-row shared tile so
+// ------------------------------------------------------------------ input gathers
+// All global traffic of the pre-gather moves through a 32-row shared tile so
 // that every warp access is a run of 32 consecutive complex values (512 bytes)
 // of one (field, sign) pair: lanes walk degrees or nodes when loading from or
 // storing to beta and g, and walk right-hand sides when writing row groups.
@@ -686,8 +686,8 @@ __device__ void gather_inverse(const TcLaunch& L, const Item& itm, const Unit& u
   }
 }
 
-// The call's inputs ahead of the apply, one item per CTA iteration: the same
-// gathers as the I/O warps', into the item's block of plan 0's pre-gathered
+// The call's inputs ahead of the apply, one item per CTA iteration: the
+// gathers above, into the item's block of plan 0's pre-gathered
 // buffer (forward: X_e, X_o from group 0; transposed: Y_e, Y_o), by many CTAs
 // per SM.
 __global__ void __launch_bounds__(kGatherThreads) tc_in_kernel(const __grid_constant__ TcLaunch L, int fwd) {

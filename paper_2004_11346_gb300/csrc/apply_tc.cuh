@@ -15,7 +15,7 @@ constexpr int kTcFields = 32;            // fields per work item
 constexpr int kTcR = 4 * kTcFields;      // 128 right-hand sides = MMA M
 constexpr int kTcNT = 128;               // N tile (rows of one block product per MMA)
 constexpr int kTcKC = 32;                // K chunk per pipeline stage
-constexpr int kTcThreads = 512;          // producer, MMA, 2 spare, 4 epilogue and 8 I/O warps
+constexpr int kTcThreads = 512;          // producer, MMA, 2 item, 8 epilogue and 4 output warps
 constexpr int kTcRowBytes = 3 * kTcR * 2;  // one scratch row: 3 BF16 pieces x 128 values
 // The scratch stores rows in groups of 8 in the tensor cores' K-major core
 // matrix layout, so that a run of whole groups is the A operand of a K chunk
@@ -182,14 +182,14 @@ struct TcPlan {
   const float* w32;          // w_{N+i} rounded to FP32, i < N
   // Accumulated rows of every work item (forward: Y_e, Y_o; transposed: X),
   // item (field group g, order |m|) at (g * nunits + |m|) * tc_acc_rows(N)
-  // rows.  The kernel zeroes an item's rows when it gathers the item; the
-  // output kernel reads them.
+  // rows.  The kernel's item warps zero an item's rows (those no op stores
+  // first) when they take the item; the output step reads them.
   float* acc;
   // Inputs gathered ahead by tc_in_kernel, the row groups of every item at
   // (g * nunits + |m|) * tc_pre_groups(N) groups: forward, X_e and X_o as
   // they sit from scratch group 0; transposed, the W-weighted parity fold of g
-  // as Y_e, Y_o from scratch group ye / 8.  Null: the kernel's I/O warps
-  // gather them
+  // as Y_e, Y_o from scratch group ye / 8.  Required: the kernel gathers
+  // no inputs itself
   unsigned char* pre;
   int gmax;                 // field groups the accumulation buffer holds
   int N;
@@ -217,10 +217,10 @@ struct TcLaunch {
   int max_rows;
   unsigned int* counter;          // zero before the launch
   int* err;
-  // The item warps write each finished item's outputs (the output kernel then
-  // does not run); otherwise the output kernel runs after the launch.
+  // The output warps write each finished item's outputs (the output kernel
+  // then does not run); otherwise the output kernel runs after the launch.
   int fuse_out;
-  // Self-test of the bounded waits: the I/O warps publish no item, so every
+  // Self-test of the bounded waits: the item warps publish no item, so every
   // other role's wait for its first item runs out and the launch reports a
   // timeout through err.
   int stall;
