@@ -107,6 +107,7 @@ int main(int argc, char** argv) {
   std::vector<int32_t> live;
   tc_live_rows(N, units, tops, live);
   if (live.size() != units.size()) return 24;
+  int dead_units = 0;  // orders with node rows no block reaches
   for (size_t u = 0; u < units.size(); ++u) {
     const Unit& un = units[u];
     const TcRows tr = tc_rows(un.nce, un.nco, N);
@@ -130,6 +131,7 @@ int main(int argc, char** argv) {
       }
     }
     if (tc_r8(top) != lv) return 28;
+    if (lv < N) ++dead_units;
   }
   std::vector<int32_t> zr, zri;
   tc_first_writers(N, units, tops, ford, tord, live, zr, zri);
@@ -178,7 +180,7 @@ int main(int argc, char** argv) {
         }
     }
   }
-  std::printf("ok %zu\n", at);
+  std::printf("ok %zu %d\n", at, dead_units);
   sht_plan_destroy(p);
   return 0;
 }
