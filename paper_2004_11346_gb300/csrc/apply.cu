@@ -382,6 +382,11 @@ void alloc_hook_reset() {
   g_alloc_seen = 0;
 }
 
+// Tensor-core image sets up to this size are packed whole on the host before
+// one copy; larger ones in windows of about kImageWindow bytes.
+constexpr size_t kImagesWhole = (size_t)32 << 30;
+constexpr size_t kImageWindow = (size_t)1 << 30;
+
 cudaError_t plan_malloc(void** ptr, size_t bytes) {
   if (g_alloc_fail_at > 0 && ++g_alloc_seen == g_alloc_fail_at) {
     *ptr = nullptr;
@@ -657,17 +662,34 @@ sht_status attach_device(sht_plan_s* p) {
   }
   size_t ws32 = 0;
   if (e == cudaSuccess && o.precision == SHT_MIXED) {
-    TcImages img;
     std::vector<TcOp> tops;
     std::vector<int32_t> tiles;
-    tc_build_images(N, P.units, P.ops, P.factors.data(), img, tops, tiles, p->tc_max_rows);
+    const size_t img_elems = tc_image_layout(N, P.units, P.ops, tops, tiles, p->tc_max_rows);
+    const size_t img_alloc = std::max<size_t>(img_elems, 8);
     std::vector<int32_t> zr, zri;
     std::vector<int32_t> ford, tord;
     tc_proc_order(P.units, tops, ford, tord);
     std::vector<int32_t> live;
     tc_live_rows(N, P.units, tops, live);
     tc_first_writers(N, P.units, tops, ford, tord, live, zr, zri);
-    e = upload(&p->d_img, img);
+    if (img_alloc * sizeof(uint16_t) <= kImagesWhole) {
+      // packed whole on the host, one copy
+      TcImages img(img_alloc);
+      std::fill(img.begin() + img_elems, img.end(), (uint16_t)0);
+      tc_pack_ops(P.ops, tops, P.factors.data(), 0, P.ops.size(), img.data(), 0);
+      e = upload(&p->d_img, img);
+    } else {
+      // a store larger than that (N around 2048 and up) is packed in windows
+      // of consecutive ops, each copied to its place, so that the host holds
+      // one window beside the FP64 factor store instead of the whole image set
+      e = plan_malloc(reinterpret_cast<void**>(&p->d_img), img_alloc * sizeof(uint16_t));
+      if (e == cudaSuccess)
+        tc_pack_windows(P.ops, tops, P.factors.data(), img_elems, kImageWindow / sizeof(uint16_t),
+                        [&](size_t first, const uint16_t* data, size_t n) {
+                          e = cudaMemcpy(p->d_img + first, data, n * sizeof(uint16_t), cudaMemcpyHostToDevice);
+                          return e == cudaSuccess;
+                        });
+    }
     {
       // round to nearest, as the kernels' FP64 -> FP32 conversions do
       std::vector<float> w32((size_t)N);
@@ -695,7 +717,7 @@ sht_status attach_device(sht_plan_s* p) {
     ws32 += acc;
     if (e == cudaSuccess) e = plan_malloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
-    p->prog.info.factor_bytes = (int64_t)(img.size() * sizeof(uint16_t));
+    p->prog.info.factor_bytes = (int64_t)(img_alloc * sizeof(uint16_t));
   }
   if (e == cudaSuccess && o.precision == SHT_FP32) {
     std::vector<float, UninitAlloc<float>> f32(P.factors.size());

@@ -45,6 +45,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <functional>
 
 #include "apply_tc.cuh"
 #include "f64_bits.cuh"
@@ -175,8 +176,8 @@ void tc_op_image(const Op& op, const TcOp& top, const double* factors, bool tran
   pack_dir(op, top, factors, transposed, out.data());
 }
 
-void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op>& ops, const double* factors,
-                     TcImages& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles, int& max_rows) {
+size_t tc_image_layout(int N, const std::vector<Unit>& units, const std::vector<Op>& ops, std::vector<TcOp>& tops,
+                       std::vector<int32_t>& tiles, int& max_rows) {
   const size_t n = ops.size();
   tops.assign(n, TcOp{});
   tiles.assign(2 * units.size(), 0);
@@ -197,15 +198,44 @@ void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op
       tiles[2 * u + 1] += db.nT;
     }
   }
+  return tot;
+}
+
+void tc_pack_ops(const std::vector<Op>& ops, const std::vector<TcOp>& tops, const double* factors, size_t i0,
+                 size_t i1, uint16_t* dst, size_t base) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long i = (long)i0; i < (long)i1; ++i) {
+    pack_dir(ops[(size_t)i], tops[(size_t)i], factors, false, dst + ((size_t)tops[(size_t)i].img[0] - base));
+    pack_dir(ops[(size_t)i], tops[(size_t)i], factors, true, dst + ((size_t)tops[(size_t)i].img[1] - base));
+  }
+}
+
+void tc_pack_windows(const std::vector<Op>& ops, const std::vector<TcOp>& tops, const double* factors, size_t tot,
+                     size_t window, const std::function<bool(size_t, const uint16_t*, size_t)>& sink) {
+  const size_t n = ops.size();
+  // the images of op i occupy [tops[i].img[0], end(i)), op after op
+  auto end_of = [&](size_t i) { return i + 1 < n ? (size_t)tops[i + 1].img[0] : tot; };
+  TcImages buf;
+  for (size_t i0 = 0; i0 < n;) {
+    const size_t begin = (size_t)tops[i0].img[0];
+    size_t i1 = i0 + 1;
+    while (i1 < n && end_of(i1) - begin <= window) ++i1;
+    const size_t span = end_of(i1 - 1) - begin;
+    if (buf.size() < span) buf.resize(span);
+    tc_pack_ops(ops, tops, factors, i0, i1, buf.data(), begin);
+    if (!sink(begin, buf.data(), span)) return;
+    i0 = i1;
+  }
+}
+
+void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op>& ops, const double* factors,
+                     TcImages& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles, int& max_rows) {
+  const size_t tot = tc_image_layout(N, units, ops, tops, tiles, max_rows);
   // pack_dir writes every element of an op's two images (padding included),
   // so only the minimum-size tail of an empty store needs zeroing here
   img.resize(std::max<size_t>(tot, 8));
   std::fill(img.begin() + tot, img.end(), (uint16_t)0);
-#pragma omp parallel for schedule(dynamic, 64)
-  for (long i = 0; i < (long)n; ++i) {
-    pack_dir(ops[(size_t)i], tops[(size_t)i], factors, false, img.data() + tops[(size_t)i].img[0]);
-    pack_dir(ops[(size_t)i], tops[(size_t)i], factors, true, img.data() + tops[(size_t)i].img[1]);
-  }
+  tc_pack_ops(ops, tops, factors, 0, ops.size(), img.data(), 0);
 }
 
 void tc_proc_order(const std::vector<Unit>& units, const std::vector<TcOp>& tops, std::vector<int32_t>& ford,

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include "program.hpp"
@@ -237,6 +238,18 @@ void tc_op_image(const Op& op, const TcOp& top, const double* factors, bool tran
 using TcImages = std::vector<uint16_t, UninitAlloc<uint16_t>>;
 void tc_build_images(int N, const std::vector<Unit>& units, const std::vector<Op>& ops, const double* factors,
                      TcImages& img, std::vector<TcOp>& tops, std::vector<int32_t>& tiles, int& max_rows);
+// The same in parts, so that a large store need not sit on the host whole:
+// the layout (op records, tile counts, total elements), then the images of
+// ops [i0, i1) packed at dst[offset - base], and a driver that packs windows
+// of consecutive ops spanning at most `window` elements (more for one op that
+// is larger) into a reusable buffer and hands each to `sink` as (first
+// element, data, elements); a false return from `sink` stops it.
+size_t tc_image_layout(int N, const std::vector<Unit>& units, const std::vector<Op>& ops, std::vector<TcOp>& tops,
+                       std::vector<int32_t>& tiles, int& max_rows);
+void tc_pack_ops(const std::vector<Op>& ops, const std::vector<TcOp>& tops, const double* factors, size_t i0,
+                 size_t i1, uint16_t* dst, size_t base);
+void tc_pack_windows(const std::vector<Op>& ops, const std::vector<TcOp>& tops, const double* factors, size_t tot,
+                     size_t window, const std::function<bool(size_t, const uint16_t*, size_t)>& sink);
 
 // The store marks of the ops (in tops) and the zero ranges (zr, zri as in
 // TcPlan) of every order, from the op records in scratch rows.

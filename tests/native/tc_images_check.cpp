@@ -72,6 +72,26 @@ int main(int argc, char** argv) {
   if (at > total || (total > 8 && at != total)) return 9;
   for (size_t i = at; i < total; ++i)
     if (img[i] != 0) return 10;
+  // packed in windows (the path of large stores): windows in order, end to
+  // end, covering the images, and together equal to the whole store; small
+  // windows, so that some ops are larger than one
+  for (size_t window : {(size_t)2048, (size_t)65536}) {
+    std::vector<TcOp> tops2;
+    std::vector<int32_t> tiles2;
+    int max_rows2 = 0;
+    const size_t tot2 = tc_image_layout(N, units, ops, tops2, tiles2, max_rows2);
+    if (tot2 != at || tiles2 != tiles || max_rows2 != max_rows) return 29;
+    size_t next = 0, nwin = 0;
+    bool same = true;
+    tc_pack_windows(ops, tops2, factors.data(), tot2, window, [&](size_t first, const uint16_t* data, size_t n) {
+      if (first != next) same = false;
+      for (size_t i = 0; i < n && same; ++i) same = data[i] == img[first + i];
+      next = first + n;
+      ++nwin;
+      return same;
+    });
+    if (!same || next != tot2 || (tot2 > window && nwin < 2)) return 30;
+  }
   // first-writer marks and zero ranges: per order and direction, replay the
   // ops in processing order; a storing op may touch no row written before,
   // and every row the output step reads is first written by a storing op or
